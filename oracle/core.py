@@ -1,0 +1,282 @@
+"""ctypes wrapper of the oracle's C core (``oracle/oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Numbering (shared convention, not shared code): vertex (i, j, k) of the
+(n+1)^3 grid has index ``i + (n+1)*(j + (n+1)*k)``; the interior vertex
+(i, j, k), 1 <= i, j, k <= n-1, is unknown number
+``(i-1) + (n-1)*((j-1) + (n-1)*(k-1))``.  Boundary vertices carry the
+homogeneous Dirichlet value 0 and are not unknowns (Sec. 2: V_h = S_h^1 cap H_0^1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+import scipy.sparse as sp
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+T_SINE, T_BOX, T_BUMPS, T_SINE_PLUS_ONE, T_SINE_SCALED = 0, 1, 2, 3, 4
+_KINDS = {"sine": T_SINE, "box": T_BOX, "bumps": T_BUMPS,
+          "sine_plus_one": T_SINE_PLUS_ONE, "sine_scaled": T_SINE_SCALED}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C core with gcc (no FMA contraction: same results on x86 and Arm)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Target(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nb", C.c_int), ("c", C.POINTER(C.c_double)),
+                ("w", C.POINTER(C.c_double)), ("a", C.POINTER(C.c_double)),
+                ("lo", C.c_double), ("hi", C.c_double), ("scale", C.c_double)]
+
+
+class _Sys(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.POINTER(C.c_int64)),
+                ("col", C.POINTER(C.c_int32)), ("K", C.POINTER(C.c_double)),
+                ("M", C.POINTER(C.c_double)), ("f", C.POINTER(C.c_double))]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.POINTER
+            lib.ora_uniform_xyz.argtypes = [C.c_int, P(C.c_double)]
+            lib.ora_kuhn_tets.argtypes = [C.c_int, P(C.c_int32)]
+            lib.ora_element.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double)]
+            lib.ora_element.restype = C.c_double
+            lib.ora_qrule.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
+            lib.ora_qrule.restype = C.c_int
+            lib.ora_assemble.argtypes = [C.c_int64, P(C.c_double), C.c_int64, P(C.c_int32),
+                                         P(C.c_int32), C.c_int64, P(_Target), C.c_int, P(_Sys)]
+            lib.ora_assemble.restype = C.c_int
+            lib.ora_sys_free.argtypes = [P(_Sys)]
+            lib.ora_tet_dets.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double)]
+            lib.ora_apply.argtypes = [P(_Sys), C.c_double, P(C.c_double), P(C.c_double)]
+            lib.ora_jacobi_pcg.argtypes = [P(_Sys), C.c_double, P(C.c_double), P(C.c_double),
+                                           C.c_double, C.c_int, P(C.c_double)]
+            lib.ora_jacobi_pcg.restype = C.c_int
+            lib.ora_cholesky.argtypes = [C.c_int, P(C.c_double)]
+            lib.ora_cholesky.restype = C.c_int
+            lib.ora_cholesky_solve.argtypes = [C.c_int, P(C.c_double), P(C.c_double),
+                                               P(C.c_double)]
+            lib.ora_errors.argtypes = [C.c_int64, P(C.c_double), C.c_int64, P(C.c_int32),
+                                       P(C.c_double), P(_Target), C.c_int, P(C.c_double),
+                                       P(C.c_double)]
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+# ---------------------------------------------------------------- mesh
+
+def uniform_xyz(n: int) -> np.ndarray:
+    xyz = np.empty(((n + 1) ** 3, 3), dtype=np.float64)
+    _load().ora_uniform_xyz(n, _dp(xyz))
+    return xyz
+
+
+def kuhn_tets(n: int) -> np.ndarray:
+    tets = np.empty((6 * n ** 3, 4), dtype=np.int32)
+    _load().ora_kuhn_tets(n, _ip(tets))
+    return tets
+
+
+def interior_dof_map(n: int) -> np.ndarray:
+    """vertex -> unknown index (or -1 on the boundary)."""
+    i = np.arange(n + 1)
+    K, J, I = np.meshgrid(i, i, i, indexing="ij")
+    inside = (I > 0) & (I < n) & (J > 0) & (J < n) & (K > 0) & (K < n)
+    d = (I - 1) + (n - 1) * ((J - 1) + (n - 1) * (K - 1))
+    return np.where(inside, d, -1).astype(np.int32).reshape(-1)
+
+
+def element(X: np.ndarray):
+    """(det J, K_e, M_e) of one tet with vertex coordinates X (4x3)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Ke = np.empty((4, 4)); Me = np.empty((4, 4))
+    det = _load().ora_element(_dp(X), _dp(Ke), _dp(Me))
+    return det, Ke, Me
+
+
+def qrule(level: int):
+    npts = 4 * 8 ** level
+    bary = np.empty((npts, 4)); wt = np.empty(npts)
+    _load().ora_qrule(level, _dp(bary), _dp(wt))
+    return bary, wt
+
+
+def tet_dets(tets: np.ndarray, xyz: np.ndarray) -> np.ndarray:
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    out = np.empty(len(tets))
+    _load().ora_tet_dets(len(tets), _ip(tets), _dp(xyz), _dp(out))
+    return out
+
+
+# ---------------------------------------------------------------- targets
+
+def _target_struct(target: dict):
+    kind = _KINDS[target["kind"]]
+    keep = []
+    t = _Target()
+    t.kind = kind
+    t.nb = 0
+    t.lo = float(target.get("lo", 0.25))
+    t.hi = float(target.get("hi", 0.75))
+    t.scale = float(target.get("scale", 1.0))
+    if kind == T_BUMPS:
+        c = np.ascontiguousarray(target["centers"], dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(target["widths"], dtype=np.float64).reshape(-1)
+        a = np.ascontiguousarray(target["amps"], dtype=np.float64).reshape(-1)
+        keep += [c, w, a]
+        t.nb = len(w)
+        t.c, t.w, t.a = _dp(c), _dp(w), _dp(a)
+    return t, keep
+
+
+# ---------------------------------------------------------------- assembly
+
+class System:
+    """Assembled K, M (scipy CSR, sorted columns) and load f on the unknowns."""
+
+    def __init__(self, K, M, f, dof, n, xyz, tets):
+        self.K, self.M, self.f, self.dof, self.n = K, M, f, dof, n
+        self.xyz, self.tets = xyz, tets
+
+    def A(self, rho: float):
+        """A = rho K + M (Sec. 2, eq. (linsys)); same pattern as K and M."""
+        return sp.csr_matrix((rho * self.K.data + self.M.data, self.K.indices, self.K.indptr),
+                             shape=self.K.shape)
+
+    def full_vector(self, u: np.ndarray) -> np.ndarray:
+        """Extend an unknown vector by the Dirichlet zeros to all vertices."""
+        U = np.zeros(len(self.dof))
+        m = self.dof >= 0
+        U[m] = u[self.dof[m]]
+        return U
+
+
+def assemble(n: int, target: dict, xyz: np.ndarray | None = None, qlevel: int = 0,
+             full: bool = False) -> System:
+    """Assemble the P1 system on the Kuhn mesh of the unit cube with n cells per side.
+
+    ``xyz`` overrides the vertex coordinates (e.g. a jittered mesh); ``full``
+    keeps every vertex as an unknown (no Dirichlet elimination; used by the
+    invariant checks)."""
+    lib = _load()
+    if xyz is None:
+        xyz = uniform_xyz(n)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = kuhn_tets(n)
+    nv = (n + 1) ** 3
+    dof = np.arange(nv, dtype=np.int32) if full else interior_dof_map(n)
+    ndof = int((dof >= 0).sum())
+    t, keep = _target_struct(target)
+    s = _Sys()
+    rc = lib.ora_assemble(nv, _dp(xyz), len(tets), _ip(tets), _ip(dof), ndof, C.byref(t),
+                          qlevel, C.byref(s))
+    if rc == -1:
+        raise MemoryError("oracle assembly: allocation failed")
+    try:
+        if rc == -2:
+            raise ValueError("oracle assembly: degenerate tetrahedron")
+        nnz = s.nnz
+        rowptr = np.ctypeslib.as_array(s.rowptr, (ndof + 1,)).copy()
+        col = np.ctypeslib.as_array(s.col, (nnz,)).copy() if nnz else np.zeros(0, np.int32)
+        Kv = np.ctypeslib.as_array(s.K, (nnz,)).copy() if nnz else np.zeros(0)
+        Mv = np.ctypeslib.as_array(s.M, (nnz,)).copy() if nnz else np.zeros(0)
+        f = np.ctypeslib.as_array(s.f, (ndof,)).copy() if ndof else np.zeros(0)
+    finally:
+        lib.ora_sys_free(C.byref(s))
+    K = sp.csr_matrix((Kv, col, rowptr), shape=(ndof, ndof))
+    M = sp.csr_matrix((Mv, col.copy(), rowptr.copy()), shape=(ndof, ndof))
+    K.has_sorted_indices = True
+    M.has_sorted_indices = True
+    return System(K, M, f, dof, n, xyz, tets)
+
+
+def _sys_struct(system: System):
+    K = system.K
+    rowptr = np.ascontiguousarray(K.indptr, dtype=np.int64)
+    col = np.ascontiguousarray(K.indices, dtype=np.int32)
+    Kv = np.ascontiguousarray(K.data, dtype=np.float64)
+    Mv = np.ascontiguousarray(system.M.data, dtype=np.float64)
+    s = _Sys()
+    s.nrows = K.shape[0]
+    s.nnz = len(col)
+    s.rowptr = rowptr.ctypes.data_as(C.POINTER(C.c_int64))
+    s.col = _ip(col)
+    s.K, s.M = _dp(Kv), _dp(Mv)
+    return s, (rowptr, col, Kv, Mv)
+
+
+def apply(system: System, rho: float, x: np.ndarray) -> np.ndarray:
+    """y = (rho K + M) x, row by row in column order."""
+    s, keep = _sys_struct(system)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    _load().ora_apply(C.byref(s), rho, _dp(x), _dp(y))
+    return y
+
+
+def jacobi_pcg(system: System, rho: float, b: np.ndarray, tol: float = 1e-13,
+               maxit: int = 100000, x0: np.ndarray | None = None):
+    """Diagonally preconditioned CG in FP64; returns (x, iterations, ||b-Ax||/||b||)."""
+    s, keep = _sys_struct(system)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    rr = C.c_double(0.0)
+    it = _load().ora_jacobi_pcg(C.byref(s), rho, _dp(b), _dp(x), tol, maxit, C.byref(rr))
+    if it < 0:
+        raise FloatingPointError("oracle PCG breakdown after %d iterations" % (-it - 1))
+    return x, it, rr.value
+
+
+def cholesky_solve(A_dense: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Own dense Cholesky factorisation and triangular solves."""
+    L = np.ascontiguousarray(A_dense, dtype=np.float64).copy()
+    n = L.shape[0]
+    rc = _load().ora_cholesky(n, _dp(L))
+    if rc != 0:
+        raise np.linalg.LinAlgError("non-positive pivot %d" % rc)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty(n)
+    _load().ora_cholesky_solve(n, _dp(L), _dp(b), _dp(x))
+    return x
+
+
+def errors(system: System, u: np.ndarray, exact: dict, qlevel: int = 1):
+    """(||exact - u_h||_L2^2, ||grad(exact - u_h)||_L2^2) by quadrature."""
+    U = system.full_vector(u)
+    t, keep = _target_struct(exact)
+    l2 = C.c_double(0.0); h1 = C.c_double(0.0)
+    tets = np.ascontiguousarray(system.tets, dtype=np.int32)
+    _load().ora_errors(len(U), _dp(system.xyz), len(tets), _ip(tets), _dp(U), C.byref(t),
+                       qlevel, C.byref(l2), C.byref(h1))
+    return l2.value, h1.value

@@ -1,0 +1,190 @@
+"""Pins of the oracle's smoothed-aggregation hierarchy, smoother, V-cycle and PCG.
+
+The hierarchy's rules are checked against brute force (greedy MIS-2, dense
+products), the defining formulas in dense arithmetic, the closed form of the
+Chebyshev error polynomial, and the exact discrete solution.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fem_workloads as W
+from oracle import amg, core
+
+
+def _greedy_mis2(adj, prio, isolated):
+    """Scan nodes by decreasing priority; take a node if no taken node is within distance 2."""
+    n = len(adj)
+    taken = np.zeros(n, dtype=bool)
+    for i in sorted(range(n), key=lambda t: -int(prio[t])):
+        if isolated[i]:
+            continue
+        ball = set(adj[i])
+        for j in adj[i]:
+            ball |= set(adj[j])
+        ball.discard(i)
+        if not any(taken[j] for j in ball):
+            taken[i] = True
+    return taken
+
+
+def _random_graph(n, p, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.random((n, n)) < p
+    M = np.triu(M, 1)
+    M = M | M.T
+    return sp.csr_matrix(M.astype(float))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mis2_equals_greedy_by_priority(seed):
+    S = _random_graph(60, 0.06, seed)
+    S.sort_indices()
+    adj = [list(S.indices[S.indptr[i]:S.indptr[i + 1]]) for i in range(60)]
+    isolated = np.diff(S.indptr) == 0
+    prio = amg.priority(60, seed)
+    state = amg.mis2(S, prio, isolated)
+    assert np.array_equal(state == amg.IN, _greedy_mis2(adj, prio, isolated))
+
+
+def test_priorities_are_unique_and_hash_is_murmur_finaliser():
+    # fmix32 reference values computed by hand from its definition
+    h = amg.fmix32(np.array([0, 1, 0xFFFFFFFF], dtype=np.uint32))
+    assert int(h[0]) == 0
+    assert int(h[1]) == 0x514E28B7
+    assert int(h[2]) == 0x81F16F39
+    p = amg.priority(1000, 3)
+    assert len(np.unique(p)) == 1000
+    assert np.array_equal(p & np.uint64(0x7FFFFFFF), np.arange(1000, dtype=np.uint64))
+
+
+def _hier_problem(n=12, rho=1.0 / 144):
+    s = core.assemble(n, W.sine_target())
+    return s, s.A(rho)
+
+
+def test_aggregates_are_valid():
+    s, A = _hier_problem()
+    agg, nagg, smask = amg.aggregate(A, 0.05, 0)
+    r = amg.rows_of(A)
+    strong = sp.csr_matrix((np.ones(int(smask.sum())), (r[smask], A.indices[smask])),
+                           shape=A.shape)
+    deg = np.diff(strong.indptr)
+    assert np.all((agg >= 0) == (deg > 0))
+    assert set(np.unique(agg[agg >= 0])) == set(range(nagg))
+    # each aggregate is connected in the strong graph
+    for a in range(nagg):
+        nodes = np.flatnonzero(agg == a)
+        sub = strong[nodes][:, nodes]
+        ncomp, _ = sp.csgraph.connected_components(sub, directed=False)
+        assert ncomp == 1
+    # roots (one per aggregate) are pairwise at strong-graph distance >= 3
+    S2 = (strong + strong @ strong).tocsr()
+    state = amg.mis2(strong, amg.priority(A.shape[0], 0), deg == 0)
+    roots = np.flatnonzero(state == amg.IN)
+    assert len(roots) == nagg
+    sub = S2[roots][:, roots].tolil()
+    sub.setdiag(0)
+    assert sp.csr_matrix(sub).count_nonzero() == 0
+
+
+def test_spgemm_matches_dense_and_keeps_structural_zeros():
+    rng = np.random.default_rng(0)
+    A = sp.random(40, 30, density=0.15, random_state=1, format="csr")
+    B = sp.random(30, 20, density=0.2, random_state=2, format="csr")
+    C = amg.spgemm(A, B)
+    np.testing.assert_allclose(C.toarray(), A.toarray() @ B.toarray(), rtol=1e-14, atol=1e-15)
+    # cancellation: [1 1] @ [[1],[-1]] = 0 is kept as a stored entry
+    Z = amg.spgemm(sp.csr_matrix([[1.0, 1.0]]), sp.csr_matrix([[1.0], [-1.0]]))
+    assert Z.nnz == 1 and Z.data[0] == 0.0
+    del rng
+
+
+def test_prolongator_and_galerkin_operator_formulas():
+    s, A = _hier_problem()
+    agg, nagg, smask = amg.aggregate(A, 0.05, 0)
+    P, omega = amg.smoothed_prolongator(A, smask, agg, nagg)
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    Pt = np.zeros((n, nagg))
+    Pt[np.arange(n)[agg >= 0], agg[agg >= 0]] = 1.0
+    strongD = np.zeros_like(Ad)
+    r = amg.rows_of(A)
+    strongD[r[smask], A.indices[smask]] = 1.0
+    F = np.where(strongD > 0, Ad, 0.0) + np.diag(np.diag(Ad))
+    lam = np.max(np.abs(F).sum(axis=1) / np.diag(Ad))
+    assert omega == pytest.approx(4.0 / (3.0 * lam), rel=1e-15)
+    Pd = Pt - omega * (F / np.diag(Ad)[:, None]) @ Pt
+    np.testing.assert_allclose(P.toarray(), Pd, rtol=1e-13, atol=1e-15)
+    # coarse operator
+    H = amg.build_hierarchy(A, dict(coarse_max=50))
+    Ac = H[1].A.toarray()
+    Pd = H[0].P.toarray()
+    np.testing.assert_allclose(Ac, Pd.T @ Ad @ Pd, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    assert np.abs(Ac - Ac.T).max() <= 1e-14 * np.abs(Ac).max()
+    assert np.linalg.eigvalsh(Ac).min() > 0
+
+
+def test_chebyshev_error_polynomial_closed_form():
+    # D = I, A = diag(lam): after k steps from x0 = 0 for A x = A 1, the error is
+    # -T_k((theta - lam)/delta) / T_k(theta/delta) (Chebyshev acceleration)
+    lam = np.linspace(0.05, 2.0, 25)
+    A = sp.diags(lam).tocsr()
+    b = lam.copy()
+    lmax, ratio = 2.0, 6.0
+    a_, b_ = lmax / ratio, lmax
+    theta, delta = (a_ + b_) / 2, (b_ - a_) / 2
+    for k in [1, 2, 3, 4]:
+        x = amg.chebyshev(A, np.ones(25), b, None, lmax, ratio, k)
+        Tk = np.polynomial.chebyshev.Chebyshev.basis(k)
+        expect = 1.0 - Tk((theta - lam) / delta) / Tk(theta / delta)
+        np.testing.assert_allclose(x, expect, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("smoother", ["chebyshev", "l1"])
+def test_vcycle_is_symmetric_positive_definite(smoother):
+    s, A = _hier_problem(10, 1.0)
+    opts = dict(smoother=smoother, coarse_max=40)
+    H = amg.build_hierarchy(A, opts)
+    assert len(H) >= 3
+    N = A.shape[0]
+    x, y = W.random_vector(N, 1), W.random_vector(N, 2)
+    Vx, Vy = amg.vcycle(H, x, opts), amg.vcycle(H, y, opts)
+    assert abs(Vx @ y - x @ Vy) <= 1e-12 * np.linalg.norm(Vx) * np.linalg.norm(y)
+    assert x @ Vx > 0 and y @ Vy > 0
+    # linear in its argument
+    np.testing.assert_allclose(amg.vcycle(H, 2 * x - y, opts), 2 * Vx - Vy, rtol=1e-11,
+                               atol=1e-13 * np.abs(Vx).max())
+
+
+@pytest.mark.parametrize("rho", [1.0, 1.0 / 256, 1e-6])
+def test_amg_pcg_reaches_exact_discrete_solution(rho):
+    n = 16
+    s = core.assemble(n, W.sine_target())
+    A = s.A(rho)
+    H = amg.build_hierarchy(A)
+    x, it, rr, hist = amg.pcg(A, s.f, lambda r: amg.vcycle(H, r), tol=1e-13, maxit=200)
+    x_ref = spl_solve(A, s.f)
+    assert rr <= 1e-12
+    assert np.linalg.norm(x - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+    assert it <= 30
+    # flexible CG with the same (fixed) preconditioner converges as well
+    xf, itf, rrf, _ = amg.pcg(A, s.f, lambda r: amg.vcycle(H, r), tol=1e-13, maxit=200,
+                              flexible=True)
+    assert np.linalg.norm(xf - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+
+
+def spl_solve(A, b):
+    import scipy.sparse.linalg as spl
+    return spl.spsolve(A.tocsc(), b)
+
+
+def test_pencil_hierarchy_matches_direct_galerkin():
+    # with P fixed, P^T (rho K + M) P = rho P^T K P + P^T M P
+    n, rho = 10, 1.0 / 100
+    s = core.assemble(n, W.sine_target())
+    A = s.A(rho)
+    H = amg.build_hierarchy(A, dict(coarse_max=30), K=s.K, M=s.M)
+    for L in H[1:]:
+        np.testing.assert_allclose(L.A.toarray(), (rho * L.K + L.M).toarray(), rtol=1e-12,
+                                   atol=1e-13 * abs(L.A).max())
