@@ -1,0 +1,263 @@
+/*
+ * femamg.h -- C ABI of the GB300 solver for the P1 finite element system
+ *
+ *     (rho K + M) u = f,   K_ij = int grad phi_j . grad phi_i,  M_ij = int phi_j phi_i,
+ *                          f_i  = int ubar phi_i
+ *
+ * of the reduced optimality system -rho Lap(u) + u = ubar in the unit cube, u = 0 on
+ * its boundary (Langer, Steinbach, Yang, "Robust discretization and solvers for elliptic
+ * optimal control problems with energy regularization", arXiv 2102.03515: Sec. 1 eq.
+ * (sigular), Sec. 2 eq. (linsys)).  The system is solved by conjugate gradients
+ * preconditioned by one algebraic-multigrid V-cycle with one pre- and one post-smoothing
+ * step (Sec. 3.1 eq. (amgpre); Sec. 4), stopped on a relative residual (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a fem_status and never aborts the process.  On failure,
+ *    fem_last_error() returns a message for the calling thread.
+ *  - "stream" is a cudaStream_t (pass the caller's current stream, or NULL for the
+ *    legacy default stream).  Work is stream-ordered; a call returns once the results
+ *    it reports on the host are available.
+ *  - Pointers named *_dev are device pointers owned by the caller, contiguous, FP64,
+ *    in unknown order; pointers named *_host are host pointers borrowed for the duration
+ *    of the call.  Handles (fem_system, amg_hier, pcg_batch) are owned by the library
+ *    and released by the matching *_destroy call.
+ *  - Unknowns: the interior vertices (i,j,k), 1 <= i,j,k <= n-1, of the (n+1)^3 vertex
+ *    grid, numbered (i-1) + (n-1)*((j-1) + (n-1)*(k-1)); boundary vertices carry the
+ *    homogeneous Dirichlet value and are not unknowns (V_h = S_h^1 cap H_0^1, Sec. 2).
+ *  - Matrices are kept in "CSR4": CSR whose rows are padded to a multiple of 4 entries
+ *    with (column -1, value 0) so that every row starts on a 16-byte boundary.
+ */
+#ifndef FEMAMG_H
+#define FEMAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FEM_OK = 0,
+  FEM_EINVAL = 1,        /* invalid argument (null handle, bad size, bad option)        */
+  FEM_ENOMEM = 2,        /* device or host allocation failed, or over the memory budget */
+  FEM_ECUDA = 3,         /* a CUDA runtime call failed                                  */
+  FEM_ENOCONV = 4,       /* max_iter reached; the best iterate is still written          */
+  FEM_EBREAKDOWN = 5,    /* <p, A p> <= 0 or a NaN appeared in a CG scalar             */
+  FEM_ECANCELLED = 6,    /* the caller's cancel flag was raised                         */
+  FEM_EDEVCHECK = 7,     /* a device-side consistency check failed (see message)        */
+  FEM_EUNSUPPORTED = 8   /* input outside what this build handles (see message)         */
+} fem_status;
+
+/* ------------------------------------------------------------------ mesh + target */
+
+/* Kuhn mesh of the unit cube: n^3 cubes, each split into the 6 tetrahedra along the
+ * monotone lattice paths from its corner (i,j,k) to (i+1,j+1,k+1) (the paper's
+ * admissible simplicial decomposition, Sec. 2; the Kuhn type is this library's choice).
+ * xyz_host, if not NULL, gives all (n+1)^3 vertex coordinates (x,y,z interleaved,
+ * vertex (i,j,k) at index i + (n+1)*(j + (n+1)*k)), e.g. a jittered grid; NULL means the
+ * uniform grid h*(i,j,k), h = 1/n.  Requires 2 <= n <= 1290. */
+typedef struct {
+  int32_t n;
+  const double* xyz_host;
+} fem_kuhn_desc;
+
+/* Targets of Sec. 4: FEM_TARGET_SINE (4.1), FEM_TARGET_BOX = 1 on (lo,hi)^3 (4.2),
+ * FEM_TARGET_SINE_PLUS_ONE (4.3), and FEM_TARGET_BUMPS: sum_b a_b exp(-|x-c_b|^2/(2 w_b^2))
+ * (synthetic batched/serving targets).  Arrays are host pointers of length nb (3*nb for
+ * centres); nb <= 64. */
+typedef enum {
+  FEM_TARGET_SINE = 0,
+  FEM_TARGET_BOX = 1,
+  FEM_TARGET_BUMPS = 2,
+  FEM_TARGET_SINE_PLUS_ONE = 3
+} fem_target_kind;
+
+typedef struct {
+  int32_t kind;
+  int32_t nb;
+  const double* centers_host;
+  const double* widths_host;
+  const double* amps_host;
+  double lo, hi;
+} fem_target;
+
+/* Operator storage for the finest level. */
+typedef enum {
+  FEM_FMT_AUTO = 0,     /* 15-point stencil on the uniform grid, CSR4 otherwise */
+  FEM_FMT_STENCIL = 1,  /* matrix-free stencil (uniform grid only)              */
+  FEM_FMT_CSR = 2       /* CSR4 always                                           */
+} fem_format;
+
+typedef struct {
+  int32_t format;       /* fem_format                                            */
+  int32_t keep_pencil;  /* 1: keep K and M separately (needed by batched solves) */
+} fem_assemble_opts;
+
+typedef struct fem_system_s* fem_system;
+
+/* Assemble K, M and f = (int ubar phi_i)_i (Sec. 2, entries below eq. (linsys)) on the
+ * interior unknowns and form A = rho K + M (eq. (linsys)).  K and M come from the P1
+ * element matrices |tau| grad(lambda_a).grad(lambda_b) and |tau|(1+delta_ab)/20; f uses
+ * the 4-point degree-2 rule of Hammer and Stroud on each tetrahedron.  rho > 0.
+ * opts may be NULL (defaults: AUTO format, no pencil).  On success *out owns all
+ * device storage of the system. */
+fem_status fem_assemble(const fem_kuhn_desc* mesh, double rho, const fem_target* target,
+                        const fem_assemble_opts* opts, void* stream, fem_system* out);
+
+typedef struct {
+  int64_t n;          /* cells per side                                 */
+  int64_t N;          /* unknowns (n-1)^3                               */
+  int64_t nnz;        /* stored entries of the CSR4 form (with padding) */
+  double h, rho;
+  int32_t is_stencil; /* finest level applied matrix-free               */
+  int32_t has_pencil;
+} fem_system_info;
+
+fem_status fem_system_get_info(fem_system sys, fem_system_info* info);
+
+/* Copy the assembled load vector f (length N) into f_dev. */
+fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream);
+
+/* Export A = rho K + M (which = 0), K (1) or M (2) in CSR4: rowptr_dev int32[N+1],
+ * col_dev int32[nnz], val_dev double[nnz] with nnz from fem_system_get_info. */
+fem_status fem_system_export(fem_system sys, int32_t which, int32_t* rowptr_dev,
+                             int32_t* col_dev, double* val_dev, void* stream);
+
+/* y = A x for the system's operator, FP64 (the operator of eq. (linsys)). */
+fem_status fem_spmv(fem_system sys, const double* x_dev, double* y_dev, void* stream);
+
+void fem_system_destroy(fem_system sys);
+
+/* ------------------------------------------------------------------ AMG */
+
+typedef enum { AMG_SMOOTHER_CHEBYSHEV = 0, AMG_SMOOTHER_L1_JACOBI = 1 } amg_smoother;
+typedef enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_BF16 = 2 } amg_precision;
+
+/* Smoothed-aggregation set-up on the device; Sec. 3.1 coarsens by red-black colouring
+ * and averaging interpolation, this library by smoothed aggregation (rules below); both
+ * build A_c = P^T A P by Galerkin's method (Sec. 3.1).
+ *   strength: |a_ij| >= theta sqrt(a_ii a_jj); MIS-2 roots by hashed priorities (seed);
+ *   P = (I - omega D^{-1} A_F) P_tent, omega = 4/(3 lambda_F) (Gershgorin bound);
+ *   coarsest level (<= coarse_max unknowns): dense FP64 inverse.
+ * precision selects the V-cycle arithmetic: FP64, FP32, or BF16-stored matrix values
+ * with FP32 vectors/accumulation; the coarsest solve is FP64 in every case. */
+typedef struct {
+  double theta;          /* strength threshold, default 0.05                   */
+  int32_t smoother;      /* amg_smoother, default Chebyshev                     */
+  int32_t degree;        /* Chebyshev degree per smoothing step, default 2      */
+  double cheb_ratio;     /* interval [lambda/ratio, lambda], default 6          */
+  int32_t coarse_max;    /* default 256                                         */
+  int32_t max_levels;    /* default 16                                          */
+  int32_t precision;     /* amg_precision, default FP64                         */
+  uint32_t seed;         /* priority seed, default 0                            */
+} amg_opts;
+
+typedef struct amg_hier_s* amg_hier;
+
+/* opts may be NULL for defaults.  The hierarchy refers to sys's storage: destroy it
+ * before the system. */
+fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hier* out);
+
+/* Fill opts with the defaults. */
+void amg_default_opts(amg_opts* opts);
+
+typedef struct {
+  int32_t levels;
+  int64_t rows[32];      /* unknowns per level        */
+  int64_t nnz[32];       /* stored CSR4 entries       */
+  double lmax[32];       /* Gershgorin bound of D^-1 A per level */
+  double setup_ms;
+} amg_hier_info;
+
+fem_status amg_hier_get_info(amg_hier h, amg_hier_info* info);
+
+/* Export level l (0 = finest): which = 0 A_l, 1 P_l, 2 R_l = P_l^T (CSR4, FP64 values;
+ * sizes from amg_hier_get_info / the row counts of consecutive levels), which = 3 the
+ * aggregate of each node of level l (int32 in col_dev, -1 = isolated; rowptr/val unused). */
+fem_status amg_hier_export(amg_hier h, int32_t level, int32_t which, int32_t* rowptr_dev,
+                           int32_t* col_dev, double* val_dev, int64_t* nnz_out, void* stream);
+
+/* z = V(r): one V-cycle with zero initial guess (eq. (amgpre) applied recursively). */
+fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stream);
+
+void amg_hier_destroy(amg_hier h);
+
+/* ------------------------------------------------------------------ PCG */
+
+typedef enum { PCG_STOP_RESIDUAL = 0, PCG_STOP_PRECONDITIONED = 1 } pcg_stop;
+
+typedef struct {
+  double tol;               /* default 1e-8                                           */
+  int32_t max_iter;         /* default 1000                                           */
+  int32_t stop;             /* PCG_STOP_RESIDUAL: ||r||/||f|| <= tol (default);
+                               PCG_STOP_PRECONDITIONED: sqrt(<r,z>/<r0,z0>) <= tol     */
+  int32_t flexible;         /* -1 auto (on for FP32/BF16 V-cycles), 0 off, 1 on        */
+  int32_t use_x0;           /* 1: u_dev holds the initial guess, 0: start from zero    */
+  int32_t use_graph;        /* 1: replay iterations as a CUDA graph (default 1)       */
+  const volatile int32_t* cancel_host; /* optional host flag; nonzero cancels          */
+} pcg_opts;
+
+typedef struct {
+  int32_t iterations;
+  int32_t status;           /* fem_status of the solve                                 */
+  double relres;            /* ||f - A u|| / ||f||, recomputed in FP64 at the end      */
+  double prec_relres;       /* sqrt(<r,z>/<r0,z0>) at the last iteration               */
+  double solve_ms;          /* device time of the iterations (CUDA events)             */
+} pcg_result;
+
+void pcg_default_opts(pcg_opts* opts);
+
+/* Solve (rho K + M) u = f by CG preconditioned with the V-cycle of hier (Sec. 4), or
+ * with the diagonal when hier is NULL.  f_dev NULL means the assembled load vector.
+ * nrhs = 1: u_dev is length N.  nrhs > 1: f_dev/u_dev are [N][nrhs] row-major and
+ * rho_k_host gives one rho per column (the system must keep its pencil, the hierarchy
+ * must come from amg_setup on it); each column is an independent solve.  res points to
+ * nrhs results.  Returns FEM_OK when every column converged. */
+fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double* u_dev,
+                     int32_t nrhs, const double* rho_k_host, const pcg_opts* opts,
+                     void* stream, pcg_result* res);
+
+/* ------------------------------------------------------------------ batched sessions */
+
+/* A batch session holds up to `slots` independent solves on one system/hierarchy, each
+ * with its own rho and right-hand side, advanced together one CG iteration per step
+ * (multi-vector SpMM-PCG, no counterpart in the paper).  Slots are admitted and retired
+ * between steps, so new solves join while others are in flight (continuous batching).
+ * Results of a slot do not depend on the other slots. */
+typedef struct pcg_batch_s* pcg_batch;
+
+fem_status pcg_batch_create(fem_system sys, amg_hier hier, int32_t slots, const pcg_opts* opts,
+                            void* stream, pcg_batch* out);
+/* Load f_dev (length N) and rho into a free slot; *slot_out receives its index. */
+fem_status pcg_batch_admit(pcg_batch b, const double* f_dev, double rho, int32_t* slot_out,
+                           void* stream);
+/* Run `iters` CG iterations for every active slot (one CUDA-graph replay per iteration). */
+fem_status pcg_batch_step(pcg_batch b, int32_t iters, void* stream);
+/* Host snapshot per slot: status (-1 free, 0 running, 1 converged, 2 failed), iterations,
+ * recurrence residual ||r||/||f||.  Arrays of length slots. */
+fem_status pcg_batch_poll(pcg_batch b, int32_t* state_host, int32_t* iters_host,
+                          double* relres_host, void* stream);
+/* Copy the slot's iterate into u_dev (length N), free the slot. */
+fem_status pcg_batch_retire(pcg_batch b, int32_t slot, double* u_dev, void* stream);
+/* Bytes of device memory a session with these sizes allocates (admission control). */
+int64_t pcg_batch_footprint(fem_system sys, amg_hier hier, int32_t slots);
+void pcg_batch_destroy(pcg_batch b);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Message of the last failure on this thread ("" if none). */
+const char* fem_last_error(void);
+
+/* Autotuner cache as JSON text (choices and timings per kernel shape). The string is
+ * owned by the library and valid until the next call. */
+const char* fem_autotune_report(void);
+
+/* Library version string. */
+const char* fem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEMAMG_H */

@@ -1,0 +1,332 @@
+"""ctypes declarations of include/femamg.h and one Python function per entry point.
+
+Device buffers are torch CUDA tensors (contiguous; float64 vectors, int32 index arrays);
+``stream`` defaults to torch's current stream.  Failures raise :class:`FemError` with the
+library's status and message, except FEM_ENOCONV from ``pcg_solve``, which is reported in
+the returned result (the best iterate is written).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfemamg.so")
+
+FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_ENOCONV = 0, 1, 2, 3, 4
+FEM_EBREAKDOWN, FEM_ECANCELLED, FEM_EDEVCHECK, FEM_EUNSUPPORTED = 5, 6, 7, 8
+STATUS_NAMES = {0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_ENOMEM", 3: "FEM_ECUDA", 4: "FEM_ENOCONV",
+                5: "FEM_EBREAKDOWN", 6: "FEM_ECANCELLED", 7: "FEM_EDEVCHECK",
+                8: "FEM_EUNSUPPORTED"}
+FEM_TARGET = {"sine": 0, "box": 1, "bumps": 2, "sine_plus_one": 3}
+FEM_FMT_AUTO, FEM_FMT_STENCIL, FEM_FMT_CSR = 0, 1, 2
+AMG_SMOOTHER_CHEBYSHEV, AMG_SMOOTHER_L1_JACOBI = 0, 1
+AMG_PREC_FP64, AMG_PREC_FP32, AMG_PREC_BF16 = 0, 1, 2
+PCG_STOP_RESIDUAL, PCG_STOP_PRECONDITIONED = 0, 1
+
+
+class FemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class KuhnDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("xyz_host", C.POINTER(C.c_double))]
+
+
+class Target(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nb", C.c_int32), ("centers_host", C.POINTER(C.c_double)),
+                ("widths_host", C.POINTER(C.c_double)), ("amps_host", C.POINTER(C.c_double)),
+                ("lo", C.c_double), ("hi", C.c_double)]
+
+
+class AssembleOpts(C.Structure):
+    _fields_ = [("format", C.c_int32), ("keep_pencil", C.c_int32)]
+
+
+class SystemInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("N", C.c_int64), ("nnz", C.c_int64), ("h", C.c_double),
+                ("rho", C.c_double), ("is_stencil", C.c_int32), ("has_pencil", C.c_int32)]
+
+
+class AmgOpts(C.Structure):
+    _fields_ = [("theta", C.c_double), ("smoother", C.c_int32), ("degree", C.c_int32),
+                ("cheb_ratio", C.c_double), ("coarse_max", C.c_int32),
+                ("max_levels", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint32)]
+
+
+class HierInfo(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("rows", C.c_int64 * 32), ("nnz", C.c_int64 * 32),
+                ("lmax", C.c_double * 32), ("setup_ms", C.c_double)]
+
+
+class PcgOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("stop", C.c_int32),
+                ("flexible", C.c_int32), ("use_x0", C.c_int32), ("use_graph", C.c_int32),
+                ("cancel_host", C.POINTER(C.c_int32))]
+
+
+class PcgResult(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("relres", C.c_double),
+                ("prec_relres", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "status": STATUS_NAMES.get(self.status),
+                "relres": self.relres, "prec_relres": self.prec_relres,
+                "solve_ms": self.solve_ms}
+
+
+_lock = threading.Lock()
+_lib = None
+VP = C.c_void_p
+P = C.POINTER
+
+# name -> (restype, argtypes); this list mirrors include/femamg.h
+SIGNATURES = {
+    "fem_assemble": (C.c_int, [P(KuhnDesc), C.c_double, P(Target), P(AssembleOpts), VP, P(VP)]),
+    "fem_system_get_info": (C.c_int, [VP, P(SystemInfo)]),
+    "fem_system_get_rhs": (C.c_int, [VP, VP, VP]),
+    "fem_system_export": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
+    "fem_spmv": (C.c_int, [VP, VP, VP, VP]),
+    "fem_system_destroy": (None, [VP]),
+    "amg_setup": (C.c_int, [VP, P(AmgOpts), VP, P(VP)]),
+    "amg_default_opts": (None, [P(AmgOpts)]),
+    "amg_hier_get_info": (C.c_int, [VP, P(HierInfo)]),
+    "amg_hier_export": (C.c_int, [VP, C.c_int32, C.c_int32, VP, VP, VP, P(C.c_int64), VP]),
+    "amg_vcycle": (C.c_int, [VP, VP, VP, VP]),
+    "amg_hier_destroy": (None, [VP]),
+    "pcg_default_opts": (None, [P(PcgOpts)]),
+    "pcg_solve": (C.c_int, [VP, VP, VP, VP, C.c_int32, P(C.c_double), P(PcgOpts), VP,
+                            P(PcgResult)]),
+    "pcg_batch_create": (C.c_int, [VP, VP, C.c_int32, P(PcgOpts), VP, P(VP)]),
+    "pcg_batch_admit": (C.c_int, [VP, VP, C.c_double, P(C.c_int32), VP]),
+    "pcg_batch_step": (C.c_int, [VP, C.c_int32, VP]),
+    "pcg_batch_poll": (C.c_int, [VP, P(C.c_int32), P(C.c_int32), P(C.c_double), VP]),
+    "pcg_batch_retire": (C.c_int, [VP, C.c_int32, VP, VP]),
+    "pcg_batch_footprint": (C.c_int64, [VP, VP, C.c_int32]),
+    "pcg_batch_destroy": (None, [VP]),
+    "fem_last_error": (C.c_char_p, []),
+    "fem_autotune_report": (C.c_char_p, []),
+    "fem_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libfemamg.so is not built (run paper_2102_03515_gb300.build)")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != FEM_OK:
+        raise FemError(status, lib().fem_last_error().decode() or what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return VP(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return VP(stream)
+    return VP(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_contiguous(), "device buffers must be contiguous"
+    return VP(t.data_ptr())
+
+
+def _dp(a):
+    return a.ctypes.data_as(P(C.c_double))
+
+
+def fem_last_error() -> str:
+    return lib().fem_last_error().decode()
+
+
+def fem_version() -> str:
+    return lib().fem_version().decode()
+
+
+def fem_autotune_report() -> str:
+    return lib().fem_autotune_report().decode()
+
+
+# ------------------------------------------------------------------ system
+
+def fem_assemble(n: int, rho: float, target: dict, xyz=None, fmt: int = FEM_FMT_AUTO,
+                 keep_pencil: bool = False, stream=None):
+    """Assemble (rho K + M) u = f on the Kuhn mesh; returns the system handle."""
+    keep = []
+    d = KuhnDesc()
+    d.n = n
+    if xyz is not None:
+        xa = np.ascontiguousarray(xyz, dtype=np.float64)
+        assert xa.size == 3 * (n + 1) ** 3
+        keep.append(xa)
+        d.xyz_host = _dp(xa)
+    t = Target()
+    t.kind = FEM_TARGET[target["kind"]]
+    t.lo = float(target.get("lo", 0.25))
+    t.hi = float(target.get("hi", 0.75))
+    if target["kind"] == "bumps":
+        c = np.ascontiguousarray(target["centers"], dtype=np.float64)
+        w = np.ascontiguousarray(target["widths"], dtype=np.float64)
+        a = np.ascontiguousarray(target["amps"], dtype=np.float64)
+        keep += [c, w, a]
+        t.nb = len(w)
+        t.centers_host, t.widths_host, t.amps_host = _dp(c), _dp(w), _dp(a)
+    o = AssembleOpts(fmt, 1 if keep_pencil else 0)
+    h = VP()
+    _check(lib().fem_assemble(C.byref(d), rho, C.byref(t), C.byref(o), _stream(stream),
+                              C.byref(h)), "fem_assemble")
+    return h
+
+
+def fem_system_get_info(sys) -> dict:
+    i = SystemInfo()
+    _check(lib().fem_system_get_info(sys, C.byref(i)), "fem_system_get_info")
+    return {"n": i.n, "N": i.N, "nnz": i.nnz, "h": i.h, "rho": i.rho,
+            "is_stencil": bool(i.is_stencil), "has_pencil": bool(i.has_pencil)}
+
+
+def fem_system_get_rhs(sys, f, stream=None):
+    _check(lib().fem_system_get_rhs(sys, _ptr(f), _stream(stream)), "fem_system_get_rhs")
+
+
+def fem_system_export(sys, which, rowptr, col, val, stream=None):
+    _check(lib().fem_system_export(sys, which, _ptr(rowptr), _ptr(col), _ptr(val),
+                                   _stream(stream)), "fem_system_export")
+
+
+def fem_spmv(sys, x, y, stream=None):
+    _check(lib().fem_spmv(sys, _ptr(x), _ptr(y), _stream(stream)), "fem_spmv")
+
+
+def fem_system_destroy(sys):
+    lib().fem_system_destroy(sys)
+
+
+# ------------------------------------------------------------------ AMG
+
+def amg_default_opts(**kw) -> AmgOpts:
+    o = AmgOpts()
+    lib().amg_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def amg_setup(sys, stream=None, **kw):
+    o = amg_default_opts(**kw)
+    h = VP()
+    _check(lib().amg_setup(sys, C.byref(o), _stream(stream), C.byref(h)), "amg_setup")
+    return h
+
+
+def amg_hier_get_info(h) -> dict:
+    i = HierInfo()
+    _check(lib().amg_hier_get_info(h, C.byref(i)), "amg_hier_get_info")
+    L = i.levels
+    return {"levels": L, "rows": list(i.rows[:L]), "nnz": list(i.nnz[:L]),
+            "lmax": list(i.lmax[:L]), "setup_ms": i.setup_ms}
+
+
+def amg_hier_export(h, level, which, rowptr=None, col=None, val=None, stream=None) -> int:
+    nnz = C.c_int64(0)
+    _check(lib().amg_hier_export(h, level, which, _ptr(rowptr), _ptr(col), _ptr(val),
+                                 C.byref(nnz), _stream(stream)), "amg_hier_export")
+    return nnz.value
+
+
+def amg_vcycle(h, r, z, stream=None):
+    _check(lib().amg_vcycle(h, _ptr(r), _ptr(z), _stream(stream)), "amg_vcycle")
+
+
+def amg_hier_destroy(h):
+    lib().amg_hier_destroy(h)
+
+
+# ------------------------------------------------------------------ PCG
+
+def pcg_default_opts(**kw) -> PcgOpts:
+    o = PcgOpts()
+    lib().pcg_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def pcg_solve(sys, hier, f, u, nrhs: int = 1, rho_k=None, stream=None, **kw):
+    """Solve; returns a list of per-column result dicts (one for nrhs = 1)."""
+    o = pcg_default_opts(**kw)
+    res = (PcgResult * nrhs)()
+    rk = None
+    if rho_k is not None:
+        rk = np.ascontiguousarray(rho_k, dtype=np.float64)
+        assert len(rk) == nrhs
+    st = lib().pcg_solve(sys, hier, _ptr(f), _ptr(u), nrhs, _dp(rk) if rk is not None else None,
+                         C.byref(o), _stream(stream), res)
+    out = [res[i].as_dict() for i in range(nrhs)]
+    if st not in (FEM_OK, FEM_ENOCONV):
+        raise FemError(st, fem_last_error())
+    return out
+
+
+# ------------------------------------------------------------------ batch sessions
+
+def pcg_batch_create(sys, hier, slots: int, stream=None, **kw):
+    o = pcg_default_opts(**kw)
+    h = VP()
+    _check(lib().pcg_batch_create(sys, hier, slots, C.byref(o), _stream(stream), C.byref(h)),
+           "pcg_batch_create")
+    return h
+
+
+def pcg_batch_admit(b, f, rho: float, stream=None) -> int:
+    slot = C.c_int32(-1)
+    _check(lib().pcg_batch_admit(b, _ptr(f), rho, C.byref(slot), _stream(stream)),
+           "pcg_batch_admit")
+    return slot.value
+
+
+def pcg_batch_step(b, iters: int = 1, stream=None):
+    _check(lib().pcg_batch_step(b, iters, _stream(stream)), "pcg_batch_step")
+
+
+def pcg_batch_poll(b, slots: int, stream=None):
+    st = np.zeros(slots, dtype=np.int32)
+    it = np.zeros(slots, dtype=np.int32)
+    rr = np.zeros(slots, dtype=np.float64)
+    _check(lib().pcg_batch_poll(b, st.ctypes.data_as(P(C.c_int32)),
+                                it.ctypes.data_as(P(C.c_int32)), _dp(rr), _stream(stream)),
+           "pcg_batch_poll")
+    return st, it, rr
+
+
+def pcg_batch_retire(b, slot: int, u, stream=None):
+    _check(lib().pcg_batch_retire(b, slot, _ptr(u), _stream(stream)), "pcg_batch_retire")
+
+
+def pcg_batch_footprint(sys, hier, slots: int) -> int:
+    return int(lib().pcg_batch_footprint(sys, hier, slots))
+
+
+def pcg_batch_destroy(b):
+    lib().pcg_batch_destroy(b)

@@ -1,0 +1,967 @@
+// Smoothed-aggregation AMG set-up on the device.
+//
+// The paper (Sec. 3.1) coarsens by red-black colouring with averaging interpolation and
+// forms A_c = P^T A P by Galerkin's method.  This library keeps the Galerkin product and
+// replaces the coarsening by smoothed aggregation with these rules:
+//  * strength: i != j strong iff a_ij != 0 and |a_ij| >= theta sqrt(a_ii a_jj);
+//    nodes without strong neighbours are isolated and not aggregated;
+//  * MIS-2: node keys (state, priority), IN > UNDECIDED > OUT, priority
+//    (fmix32(i xor s) >> 1) * 2^31 + i with fmix32 the MurmurHash3 finaliser and
+//    s = 0x9E3779B9 (seed + level + 1); per round each node takes the largest key within
+//    distance 2; an UNDECIDED node whose own key wins enters, one whose winner is IN leaves;
+//  * aggregates: roots numbered in index order; phase 1: strong neighbours of a root join
+//    it; phase 2: every other non-isolated node joins the phase-1 aggregate it has the
+//    most strong edges to (ties: smaller aggregate id);
+//  * P = P_t - omega D^{-1} A_F P_t, A_F = diagonal + strong entries, omega = 4/(3 lambda_F),
+//    lambda_F = max_i sum_j |A_F(i,j)| / a_ii;
+//  * coarsest level: dense FP64 inverse (Gauss-Jordan, SPD so no pivoting).
+// Everything is deterministic: integer atomics only, fixed summation orders.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "solver.cuh"
+
+namespace fem {
+namespace {
+
+// ------------------------------------------------------------------ scan
+
+// Exclusive prefix sum of int64 counts (three passes: block sums, scan of block sums,
+// add block offsets).  out[n] receives the total.
+constexpr int SCAN_B = 1024;
+
+__global__ void k_scan_blocks(const int64_t* in, int64_t n, int64_t* out, int64_t* bsum) {
+  __shared__ int64_t sh[SCAN_B];
+  int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  int64_t v = i < n ? in[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < SCAN_B; o <<= 1) {
+    int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = sh[threadIdx.x] - v;
+  if (threadIdx.x == SCAN_B - 1) bsum[blockIdx.x] = sh[SCAN_B - 1];
+}
+
+__global__ void k_scan_single(int64_t* bsum, int64_t nb) {
+  // one block; sequential chunks
+  __shared__ int64_t sh[SCAN_B];
+  int64_t carry = 0;
+  for (int64_t base = 0; base < nb; base += SCAN_B) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < nb ? bsum[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < SCAN_B; o <<= 1) {
+      int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    carry += sh[SCAN_B - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* bsum) {
+  int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  if (i < n) out[i] += bsum[blockIdx.x];
+  if (i == n - 1) out[n] = bsum[gridDim.x];
+}
+
+// out[0..n]: exclusive scan of in[0..n-1] and the total in out[n].  Returns the total.
+int64_t exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st) {
+  if (n == 0) {
+    FEM_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+    return 0;
+  }
+  int64_t nb = (n + SCAN_B - 1) / SCAN_B;
+  DevBuf<int64_t> bsum(nb + 1, st);
+  k_scan_blocks<<<(unsigned)nb, SCAN_B, 0, st>>>(in, n, out, bsum);
+  FEM_CHECK_LAUNCH();
+  k_scan_single<<<1, SCAN_B, 0, st>>>(bsum, nb);
+  FEM_CHECK_LAUNCH();
+  k_scan_add<<<(unsigned)nb, SCAN_B, 0, st>>>(out, n, bsum);
+  FEM_CHECK_LAUNCH();
+  int64_t total = 0;
+  FEM_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  return total;
+}
+
+__global__ void k_to_rowptr(const int64_t* in, int64_t n, int32_t* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) out[i] = (int32_t)in[i];
+}
+
+// CSR4 row pointer from per-row real counts (each padded to a multiple of 4).
+__global__ void k_pad4(const int64_t* cnt, int64_t n, int64_t* padded) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) padded[i] = (cnt[i] + 3) & ~(int64_t)3;
+}
+
+void rowptr_from_counts(const int64_t* cnt, int64_t n, Csr4& C, cudaStream_t st) {
+  DevBuf<int64_t> padded(n, st), scan(n + 1, st);
+  k_pad4<<<grid_for(n, 256), 256, 0, st>>>(cnt, n, padded);
+  FEM_CHECK_LAUNCH();
+  int64_t total = exclusive_scan(padded, n, scan, st);
+  FEM_REQUIRE(total < ((int64_t)1 << 31), FEM_EUNSUPPORTED, "matrix with more than 2^31 entries");
+  C.rowptr.alloc(n + 1);
+  k_to_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(scan, n, C.rowptr);
+  FEM_CHECK_LAUNCH();
+  C.nnz = total;
+  C.col.alloc(total);
+}
+
+// ------------------------------------------------------------------ small kernels
+
+__global__ void k_diag(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
+                       double* d) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double x = 0.0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++)
+    if (col[e] == r) x = v[e];
+  d[r] = x;
+}
+
+__global__ void k_recip(int64_t N, const double* d, double* o, float* o32) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double v = 1.0 / d[r];
+  o[r] = v;
+  if (o32) o32[r] = (float)v;
+}
+
+// Row sums of |a_ij| over entries selected by mask (null: all), divided by a_ii; block
+// maxima into bmax.  Optionally the l1 norms themselves.
+__global__ void k_rowabs(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
+                         const uint8_t* mask, const double* d, double* bmax, double* l1) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double q = -1.0;
+  if (r < N) {
+    double s = 0.0;
+    for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+      if (col[e] < 0) continue;
+      if (mask && !mask[e] && col[e] != r) continue;
+      s += fabs(v[e]);
+    }
+    if (l1) l1[r] = s;
+    q = s / d[r];
+  }
+  q = block_max(q);
+  if (threadIdx.x == 0) bmax[blockIdx.x] = q;
+}
+
+__global__ void k_max_reduce(const double* in, int n, double* out) {
+  double q = -1.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) q = fmax(q, in[i]);
+  q = block_max(q);
+  if (threadIdx.x == 0) *out = q;
+}
+
+template <typename S, typename D>
+__global__ void k_convert(int64_t n, const S* in, D* out);
+template <>
+__global__ void k_convert<double, float>(int64_t n, const double* in, float* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+template <>
+__global__ void k_convert<double, __nv_bfloat16>(int64_t n, const double* in, __nv_bfloat16* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __float2bfloat16_rn((float)in[i]);
+}
+
+// ------------------------------------------------------------------ strength + MIS-2
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ uint64_t prio_of(int64_t i, uint32_t s) {
+  uint32_t h = fmix32((uint32_t)i ^ s);
+  return ((uint64_t)(h >> 1) << 31) | (uint64_t)i;
+}
+
+enum : uint8_t { ST_OUT = 0, ST_UND = 1, ST_IN = 2 };
+
+__global__ void k_strength(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
+                           const double* d, double theta, uint8_t* smask, int64_t* scount) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int64_t c = 0;
+  const double dr = d[r];
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    int j = col[e];
+    uint8_t s = 0;
+    if (j >= 0 && j != r) {
+      double a = v[e];
+      s = (a != 0.0) && (fabs(a) >= theta * sqrt(dr * d[j]));
+    }
+    smask[e] = s;
+    c += s;
+  }
+  scount[r] = c;
+}
+
+__global__ void k_strength_fill(int64_t N, const int32_t* rowptr, const int32_t* col,
+                                const uint8_t* smask, const int64_t* sptr, int32_t* scol) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int64_t p = sptr[r];
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++)
+    if (smask[e]) scol[p++] = col[e];
+}
+
+__global__ void k_mis_init(int64_t N, const int64_t* sptr, uint8_t* state) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  state[r] = (sptr[r + 1] == sptr[r]) ? ST_OUT : ST_UND;
+}
+
+__global__ void k_mis_m1(int64_t N, const int64_t* sptr, const int32_t* scol,
+                         const uint8_t* state, uint32_t s, uint64_t* m1) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  uint64_t best = ((uint64_t)state[r] << 62) | prio_of(r, s);
+  for (int64_t e = sptr[r]; e < sptr[r + 1]; e++) {
+    int j = scol[e];
+    uint64_t kj = ((uint64_t)state[j] << 62) | prio_of(j, s);
+    best = kj > best ? kj : best;
+  }
+  m1[r] = best;
+}
+
+__global__ void k_mis_m2(int64_t N, const int64_t* sptr, const int32_t* scol, const uint64_t* m1,
+                         uint32_t s, uint8_t* state_in, uint8_t* state_out,
+                         unsigned long long* undecided) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  uint8_t st = state_in[r];
+  uint64_t best = m1[r];
+  for (int64_t e = sptr[r]; e < sptr[r + 1]; e++) {
+    uint64_t kj = m1[scol[e]];
+    best = kj > best ? kj : best;
+  }
+  uint8_t ns = st;
+  if (st == ST_UND) {
+    uint64_t key = ((uint64_t)ST_UND << 62) | prio_of(r, s);
+    if (best == key)
+      ns = ST_IN;
+    else if ((best >> 62) == ST_IN)
+      ns = ST_OUT;
+    else
+      atomicAdd(undecided, 1ull);
+  }
+  state_out[r] = ns;
+}
+
+__global__ void k_root_flags(int64_t N, const uint8_t* state, int64_t* flag) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N) flag[r] = state[r] == ST_IN;
+}
+
+__global__ void k_agg_phase1(int64_t N, const int64_t* sptr, const int32_t* scol,
+                             const uint8_t* state, const int64_t* rootid, int32_t* agg,
+                             uint8_t* p1, unsigned long long* err) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int32_t a = -1;
+  if (state[r] == ST_IN) {
+    a = (int32_t)rootid[r];
+  } else {
+    int found = 0;
+    for (int64_t e = sptr[r]; e < sptr[r + 1]; e++) {
+      int j = scol[e];
+      if (state[j] == ST_IN) {
+        if (found) atomicAdd(err, 1ull);  // two roots within distance 1: MIS-2 violated
+        a = (int32_t)rootid[j];
+        found = 1;
+      }
+    }
+  }
+  agg[r] = a;
+  p1[r] = a >= 0;
+}
+
+__global__ void k_agg_phase2(int64_t N, const int64_t* sptr, const int32_t* scol, const uint8_t* p1,
+                             int32_t* agg, unsigned long long* err) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  if (p1[r]) return;
+  const int64_t e0 = sptr[r], e1 = sptr[r + 1];
+  if (e0 == e1) return;  // isolated
+  int32_t best = -1;
+  int bestc = 0;
+  for (int64_t e = e0; e < e1; e++) {
+    int j = scol[e];
+    if (!p1[j]) continue;
+    int32_t a = agg[j];
+    int c = 0;
+    for (int64_t f = e0; f < e1; f++) {
+      int q = scol[f];
+      if (p1[q] && agg[q] == a) c++;
+    }
+    if (c > bestc || (c == bestc && a < best)) {
+      best = a;
+      bestc = c;
+    }
+  }
+  if (best < 0) atomicAdd(err, 1ull);
+  agg[r] = best;
+}
+
+// tentative prolongator, 4 slots per row
+__global__ void k_tentative(int64_t N, const int32_t* agg, int32_t* rowptr, int32_t* col,
+                            double* val) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > N) return;
+  rowptr[r] = (int32_t)(4 * r);
+  if (r == N) return;
+  int32_t a = agg[r];
+  col[4 * r] = a;
+  val[4 * r] = a >= 0 ? 1.0 : 0.0;
+  for (int q = 1; q < 4; q++) {
+    col[4 * r + q] = -1;
+    val[4 * r + q] = 0.0;
+  }
+}
+
+// D^{-1} A_F on A's pattern (weak entries become padding).
+__global__ void k_scaled_filtered(int64_t N, const int32_t* rowptr, const int32_t* col,
+                                  const double* v, const uint8_t* smask, const double* dinv,
+                                  int32_t* ocol, double* oval) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    int j = col[e];
+    bool keep = (j == r) || smask[e];
+    ocol[e] = keep ? j : -1;
+    oval[e] = keep ? __dmul_rn(v[e], dinv[r]) : 0.0;
+  }
+}
+
+// P = P_t - omega B on B's pattern.
+__global__ void k_smooth_p(int64_t N, const int32_t* rowptr, const int32_t* col, double* val,
+                           const int32_t* agg, double omega) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    if (col[e] < 0) continue;
+    double t = __dmul_rn(-omega, val[e]);
+    val[e] = (col[e] == agg[r]) ? __dadd_rn(1.0, t) : t;
+  }
+}
+
+// ------------------------------------------------------------------ SpGEMM
+
+// Warp per output row; per-warp hash tables in shared memory.
+constexpr int HT = 1024;             // table slots per warp (power of two)
+constexpr int HMAX = HT / 2;         // distinct columns per row handled
+constexpr int SG_WARPS = 4;
+constexpr size_t SG_SMEM = SG_WARPS * (HT * 4 + HT * 4 + HMAX * 8 + HMAX * 4);
+
+__device__ __forceinline__ uint32_t hslot(int key, int mask) {
+  return ((uint32_t)key * 2654435761u) & (uint32_t)mask;
+}
+
+struct WarpTab {
+  int* keys;
+  int* rank;
+  double* acc;
+  int* list;
+};
+
+__device__ __forceinline__ WarpTab warp_tab(char* smem, int w) {
+  char* base = smem + (size_t)w * (HT * 4 + HT * 4 + HMAX * 8 + HMAX * 4);
+  WarpTab t;
+  t.keys = reinterpret_cast<int*>(base);
+  t.rank = reinterpret_cast<int*>(base + HT * 4);
+  t.acc = reinterpret_cast<double*>(base + HT * 8);
+  t.list = reinterpret_cast<int*>(base + HT * 8 + HMAX * 8);
+  return t;
+}
+
+// Insert every product column of row r of A*B into the table; returns the number of
+// distinct keys (lane-uniform), or HMAX+1 on overflow.
+__device__ int warp_insert(const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
+                           const int32_t* Bcol, int64_t r, const WarpTab& t, int tsize,
+                           int lane) {
+  const int mask = tsize - 1;
+  for (int q = lane; q < tsize; q += 32) t.keys[q] = -1;
+  __syncwarp();
+  int count = 0;
+  for (int e = Arp[r]; e < Arp[r + 1]; e++) {
+    int k = Acol[e];
+    if (k < 0) continue;
+    for (int f = Brp[k] + lane; f < Brp[k + 1]; f += 32) {
+      int j = Bcol[f];
+      if (j < 0) continue;
+      uint32_t h = hslot(j, mask);
+      for (int probe = 0; probe < tsize; probe++) {
+        int old = atomicCAS(&t.keys[h], -1, j);
+        if (old == -1) {
+          count++;
+          break;
+        }
+        if (old == j) break;
+        h = (h + 1) & mask;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
+  __syncwarp();
+  return count;
+}
+
+__device__ __forceinline__ int table_size_for(int64_t ub) {
+  int64_t t = 64;
+  while (t < 2 * ub && t < HT) t <<= 1;
+  return (int)t;
+}
+
+__device__ int64_t row_products(const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
+                                int64_t r, int lane) {
+  int64_t ub = 0;
+  for (int e = Arp[r] + lane; e < Arp[r + 1]; e += 32) {
+    int k = Acol[e];
+    if (k >= 0) ub += Brp[k + 1] - Brp[k];
+  }
+  for (int o = 16; o > 0; o >>= 1) ub += __shfl_xor_sync(0xffffffffu, ub, o);
+  return ub;
+}
+
+__global__ void __launch_bounds__(32 * SG_WARPS)
+    k_spgemm_count(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
+                   const int32_t* Bcol, int64_t* cnt, unsigned long long* overflow) {
+  extern __shared__ char smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * SG_WARPS + w;
+  if (r >= nrows) return;
+  WarpTab t = warp_tab(smem, w);
+  int64_t ub = row_products(Arp, Acol, Brp, r, lane);
+  int c = warp_insert(Arp, Acol, Brp, Bcol, r, t, table_size_for(ub), lane);
+  if (lane == 0) {
+    if (c > HMAX) atomicAdd(overflow, 1ull);
+    cnt[r] = c;
+  }
+}
+
+// Columns (sorted) and, with values, the sums sum_e a_e b_(k_e, j) taken in the order of
+// A's row: lanes split a row of B, whose columns are distinct, so each step adds at most
+// once per output entry.
+__global__ void __launch_bounds__(32 * SG_WARPS)
+    k_spgemm_fill(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const double* Aval,
+                  const int32_t* Brp, const int32_t* Bcol, const double* Bval, const int32_t* Crp,
+                  int32_t* Ccol, double* Cval) {
+  extern __shared__ char smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * SG_WARPS + w;
+  if (r >= nrows) return;
+  WarpTab t = warp_tab(smem, w);
+  int64_t ub = row_products(Arp, Acol, Brp, r, lane);
+  const int tsize = table_size_for(ub);
+  const int mask = tsize - 1;
+  int c = warp_insert(Arp, Acol, Brp, Bcol, r, t, tsize, lane);
+  // compact keys into list (order of table slots)
+  int base = 0;
+  for (int q0 = 0; q0 < tsize; q0 += 32) {
+    int q = q0 + lane;
+    int k = q < tsize ? t.keys[q] : -1;
+    unsigned bal = __ballot_sync(0xffffffffu, k >= 0);
+    if (k >= 0) t.list[base + __popc(bal & ((1u << lane) - 1))] = k;
+    base += __popc(bal);
+  }
+  __syncwarp();
+  // rank sort: position = number of smaller keys
+  const int64_t out0 = Crp[r];
+  for (int a = lane; a < c; a += 32) {
+    int key = t.list[a];
+    int rk = 0;
+    for (int b = 0; b < c; b++) rk += t.list[b] < key;
+    Ccol[out0 + rk] = key;
+    uint32_t h = hslot(key, mask);
+    while (t.keys[h] != key) h = (h + 1) & mask;
+    t.rank[h] = rk;
+    if (Cval) t.acc[rk] = 0.0;
+  }
+  const int64_t out1 = Crp[r + 1];
+  for (int64_t q = out0 + c + lane; q < out1; q += 32) {
+    Ccol[q] = -1;
+    if (Cval) Cval[q] = 0.0;
+  }
+  __syncwarp();
+  if (!Cval) return;
+  for (int e = Arp[r]; e < Arp[r + 1]; e++) {
+    int k = Acol[e];
+    if (k < 0) continue;
+    double a = Aval[e];
+    for (int f = Brp[k] + lane; f < Brp[k + 1]; f += 32) {
+      int j = Bcol[f];
+      if (j < 0) continue;
+      uint32_t h = hslot(j, mask);
+      while (t.keys[h] != j) h = (h + 1) & mask;
+      int rk = t.rank[h];
+      t.acc[rk] = __dadd_rn(t.acc[rk], __dmul_rn(a, Bval[f]));
+    }
+    __syncwarp();
+  }
+  for (int a = lane; a < c; a += 32) Cval[out0 + a] = t.acc[a];
+}
+
+// Numeric product on a known output pattern (sorted real columns per row).
+__global__ void __launch_bounds__(32 * SG_WARPS)
+    k_spgemm_numeric(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const double* Aval,
+                     const int32_t* Brp, const int32_t* Bcol, const double* Bval,
+                     const int32_t* Crp, const int32_t* Ccol, double* Cval) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * SG_WARPS + w;
+  if (r >= nrows) return;
+  const int c0 = Crp[r], c1 = Crp[r + 1];
+  int cl = c1;
+  while (cl > c0 && Ccol[cl - 1] < 0) cl--;
+  for (int q = c0 + lane; q < c1; q += 32) Cval[q] = 0.0;
+  __syncwarp();
+  for (int e = Arp[r]; e < Arp[r + 1]; e++) {
+    int k = Acol[e];
+    if (k < 0) continue;
+    double a = Aval[e];
+    for (int f = Brp[k] + lane; f < Brp[k + 1]; f += 32) {
+      int j = Bcol[f];
+      if (j < 0) continue;
+      int lo = c0, hi = cl - 1;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (Ccol[mid] < j) lo = mid + 1; else hi = mid;
+      }
+      Cval[lo] = __dadd_rn(Cval[lo], __dmul_rn(a, Bval[f]));
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ transpose
+
+__global__ void k_col_count(int64_t nnz, const int32_t* col, unsigned long long* cnt) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnz && col[e] >= 0) atomicAdd(&cnt[col[e]], 1ull);
+}
+__global__ void k_u64_to_i64(int64_t n, const unsigned long long* a, int64_t* b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (int64_t)a[i];
+}
+__global__ void k_scatter_t(int64_t nrows, const int32_t* rowptr, const int32_t* col,
+                            const double* val, const int32_t* Trp, unsigned long long* fill,
+                            int32_t* Tcol, double* Tval) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    int c = col[e];
+    if (c < 0) continue;
+    unsigned long long p = atomicAdd(&fill[c], 1ull);
+    Tcol[Trp[c] + p] = (int32_t)r;
+    Tval[Trp[c] + p] = val[e];
+  }
+}
+// sort each row by column (rank sort in a warp), pad
+constexpr int TMAX = 1024;
+__global__ void k_sort_rows(int64_t nrows, const int32_t* rp, const int64_t* cnt, int32_t* col,
+                            double* val, unsigned long long* err) {
+  __shared__ int sc[4][TMAX];
+  __shared__ double sv[4][TMAX];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * 4 + w;
+  if (r >= nrows) return;
+  const int c = (int)cnt[r];
+  const int o = rp[r];
+  if (c > TMAX) {
+    if (lane == 0) atomicAdd(err, 1ull);
+    return;
+  }
+  for (int a = lane; a < c; a += 32) {
+    sc[w][a] = col[o + a];
+    sv[w][a] = val[o + a];
+  }
+  __syncwarp();
+  for (int a = lane; a < c; a += 32) {
+    int key = sc[w][a];
+    int rk = 0;
+    for (int b = 0; b < c; b++) rk += sc[w][b] < key;
+    col[o + rk] = key;
+    val[o + rk] = sv[w][a];
+  }
+  for (int q = o + c + lane; q < rp[r + 1]; q += 32) {
+    col[q] = -1;
+    val[q] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ dense coarsest
+
+__global__ void k_dense_from_csr(int64_t N, const int32_t* rowptr, const int32_t* col,
+                                 const double* v, double* D) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  for (int64_t c = 0; c < N; c++) D[r * N + c] = 0.0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++)
+    if (col[e] >= 0) D[r * N + col[e]] += v[e];
+}
+
+// Gauss-Jordan step k of the in-place inversion (no pivoting: A is SPD).
+__global__ void k_gj_save(int64_t N, int64_t k, const double* D, double* rowk, double* colk) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  rowk[i] = D[k * N + i];
+  colk[i] = D[i * N + k];
+}
+__global__ void k_gj_update(int64_t N, int64_t k, double* D, const double* rowk,
+                            const double* colk) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * N) return;
+  int64_t i = t / N, j = t % N;
+  double p = rowk[k];
+  double v;
+  if (i == k && j == k)
+    v = 1.0 / p;
+  else if (i == k)
+    v = rowk[j] / p;
+  else if (j == k)
+    v = -colk[i] / p;
+  else
+    v = D[t] - colk[i] * rowk[j] / p;
+  D[t] = v;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host wrappers
+
+void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
+            cudaStream_t st, bool values) {
+  const int64_t nr = A.nrows;
+  C.nrows = A.nrows;
+  C.ncols = B.ncols;
+  static bool attr = false;
+  if (!attr) {
+    FEM_CUDA(cudaFuncSetAttribute(k_spgemm_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SG_SMEM));
+    FEM_CUDA(cudaFuncSetAttribute(k_spgemm_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SG_SMEM));
+    attr = true;
+  }
+  DevBuf<int64_t> cnt(nr, st);
+  DevBuf<unsigned long long> ovf(1, st);
+  FEM_CUDA(cudaMemsetAsync(ovf, 0, 8, st));
+  unsigned g = (unsigned)((nr + SG_WARPS - 1) / SG_WARPS);
+  if (nr > 0) {
+    k_spgemm_count<<<g, 32 * SG_WARPS, SG_SMEM, st>>>(nr, A.rowptr, A.col, B.rowptr, B.col, cnt,
+                                                      ovf);
+    FEM_CHECK_LAUNCH();
+  }
+  unsigned long long hov = 0;
+  FEM_CUDA(cudaMemcpyAsync(&hov, ovf, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(hov == 0, FEM_EUNSUPPORTED,
+              "spgemm: a product row has more than 512 distinct columns");
+  rowptr_from_counts(cnt, nr, C, st);
+  if (values) C.val.alloc(C.nnz);
+  if (nr > 0) {
+    k_spgemm_fill<<<g, 32 * SG_WARPS, SG_SMEM, st>>>(nr, A.rowptr, A.col, Aval, B.rowptr, B.col,
+                                                     Bval, C.rowptr, C.col,
+                                                     values ? C.val.p : nullptr);
+    FEM_CHECK_LAUNCH();
+  }
+}
+
+// C's pattern must be that of A*B.
+void spgemm_numeric(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval,
+                    const Csr4& C, double* Cval, cudaStream_t st) {
+  const int64_t nr = A.nrows;
+  if (nr == 0) return;
+  unsigned g = (unsigned)((nr + SG_WARPS - 1) / SG_WARPS);
+  k_spgemm_numeric<<<g, 32 * SG_WARPS, 0, st>>>(nr, A.rowptr, A.col, Aval, B.rowptr, B.col,
+                                                Bval, C.rowptr, C.col, Cval);
+  FEM_CHECK_LAUNCH();
+}
+
+void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st) {
+  T.nrows = (int32_t)ncols;
+  T.ncols = A.nrows;
+  DevBuf<unsigned long long> cnt(ncols, st), fill(ncols, st);
+  FEM_CUDA(cudaMemsetAsync(cnt, 0, 8 * ncols, st));
+  FEM_CUDA(cudaMemsetAsync(fill, 0, 8 * ncols, st));
+  if (A.nnz > 0) {
+    k_col_count<<<grid_for(A.nnz, 256), 256, 0, st>>>(A.nnz, A.col, cnt);
+    FEM_CHECK_LAUNCH();
+  }
+  DevBuf<int64_t> c64(ncols, st);
+  if (ncols > 0) {
+    k_u64_to_i64<<<grid_for(ncols, 256), 256, 0, st>>>(ncols, cnt, c64);
+    FEM_CHECK_LAUNCH();
+  }
+  rowptr_from_counts(c64, ncols, T, st);
+  T.val.alloc(T.nnz);
+  if (A.nrows > 0) {
+    k_scatter_t<<<grid_for(A.nrows, 256), 256, 0, st>>>(A.nrows, A.rowptr, A.col, A.val, T.rowptr,
+                                                        fill, T.col, T.val);
+    FEM_CHECK_LAUNCH();
+  }
+  DevBuf<unsigned long long> err(1, st);
+  FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+  if (ncols > 0) {
+    k_sort_rows<<<(unsigned)((ncols + 3) / 4), 128, 0, st>>>(ncols, T.rowptr, c64, T.col, T.val, err);
+    FEM_CHECK_LAUNCH();
+  }
+  unsigned long long he = 0;
+  FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(he == 0, FEM_EUNSUPPORTED, "transpose: a row has more than 1024 entries");
+}
+
+static double rowabs_max(const Csr4& A, const double* val, const uint8_t* mask, const double* d,
+                         double* l1, cudaStream_t st) {
+  const int64_t N = A.nrows;
+  unsigned g = grid_for(N, 256);
+  DevBuf<double> bmax(g, st), out(1, st);
+  k_rowabs<<<g, 256, 0, st>>>(N, A.rowptr, A.col, val, mask, d, bmax, l1);
+  FEM_CHECK_LAUNCH();
+  k_max_reduce<<<1, 1024, 0, st>>>(bmax, (int)g, out);
+  FEM_CHECK_LAUNCH();
+  double h = 0;
+  FEM_CUDA(cudaMemcpyAsync(&h, out, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  return h;
+}
+
+double gershgorin(const Csr4& A, const double* val, cudaStream_t st) {
+  DevBuf<double> d(A.nrows, st);
+  k_diag<<<grid_for(A.nrows, 256), 256, 0, st>>>(A.nrows, A.rowptr, A.col, val, d);
+  FEM_CHECK_LAUNCH();
+  return rowabs_max(A, val, nullptr, d, nullptr, st);
+}
+
+void dense_inverse(const Csr4& A, const double* val, DevBuf<double>& Ainv, cudaStream_t st) {
+  const int64_t N = A.nrows;
+  Ainv.alloc(N * N);
+  if (N == 0) return;
+  k_dense_from_csr<<<grid_for(N, 128), 128, 0, st>>>(N, A.rowptr, A.col, val, Ainv);
+  FEM_CHECK_LAUNCH();
+  DevBuf<double> rowk(N, st), colk(N, st);
+  for (int64_t k = 0; k < N; k++) {
+    k_gj_save<<<grid_for(N, 256), 256, 0, st>>>(N, k, Ainv, rowk, colk);
+    k_gj_update<<<grid_for(N * N, 256), 256, 0, st>>>(N, k, Ainv, rowk, colk);
+  }
+  FEM_CHECK_LAUNCH();
+}
+
+namespace {
+
+struct Aggregation {
+  DevBuf<int32_t> agg;
+  DevBuf<uint8_t> smask;
+  int64_t nagg = 0;
+};
+
+Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t seed_s,
+                      cudaStream_t st) {
+  const int64_t N = A.nrows;
+  Aggregation R;
+  R.smask.alloc(A.nnz);
+  DevBuf<int64_t> scount(N, st), sptr(N + 1, st);
+  unsigned g = grid_for(N, 256);
+  k_strength<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, d, theta, R.smask, scount);
+  FEM_CHECK_LAUNCH();
+  int64_t snnz = exclusive_scan(scount, N, sptr, st);
+  DevBuf<int32_t> scol(snnz > 0 ? snnz : 1, st);
+  k_strength_fill<<<g, 256, 0, st>>>(N, A.rowptr, A.col, R.smask, sptr, scol);
+  FEM_CHECK_LAUNCH();
+  DevBuf<uint8_t> s0(N, st), s1(N, st);
+  DevBuf<uint64_t> m1(N, st);
+  DevBuf<unsigned long long> und(1, st);
+  k_mis_init<<<g, 256, 0, st>>>(N, sptr, s0);
+  FEM_CHECK_LAUNCH();
+  uint8_t* cur = s0;
+  uint8_t* nxt = s1;
+  bool finished = false;
+  for (int round = 0; round < 10000; round++) {
+    FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+    k_mis_m1<<<g, 256, 0, st>>>(N, sptr, scol, cur, seed_s, m1);
+    k_mis_m2<<<g, 256, 0, st>>>(N, sptr, scol, m1, seed_s, cur, nxt, und);
+    FEM_CHECK_LAUNCH();
+    std::swap(cur, nxt);
+    unsigned long long hu = 0;
+    FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    if (hu == 0) {
+      finished = true;
+      break;
+    }
+  }
+  FEM_REQUIRE(finished, FEM_EDEVCHECK, "aggregation: MIS-2 did not terminate");
+  DevBuf<int64_t> flag(N, st), rootid(N + 1, st);
+  k_root_flags<<<g, 256, 0, st>>>(N, cur, flag);
+  FEM_CHECK_LAUNCH();
+  R.nagg = exclusive_scan(flag, N, rootid, st);
+  R.agg.alloc(N);
+  DevBuf<uint8_t> p1(N, st);
+  DevBuf<unsigned long long> err(1, st);
+  FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+  k_agg_phase1<<<g, 256, 0, st>>>(N, sptr, scol, cur, rootid, R.agg, p1, err);
+  k_agg_phase2<<<g, 256, 0, st>>>(N, sptr, scol, p1, R.agg, err);
+  FEM_CHECK_LAUNCH();
+  unsigned long long he = 0;
+  FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(he == 0, FEM_EDEVCHECK, "aggregation: inconsistent MIS-2 / aggregate assignment");
+  return R;
+}
+
+void make_lowp(Csr4& A, int prec, cudaStream_t st) {
+  if (prec == AMG_PREC_FP32 || prec == AMG_PREC_BF16) {
+    A.val32.alloc(A.nnz);
+    if (A.nnz)
+      k_convert<double, float><<<grid_for(A.nnz, 256), 256, 0, st>>>(A.nnz, A.val, A.val32);
+    FEM_CHECK_LAUNCH();
+  }
+  if (prec == AMG_PREC_BF16) {
+    A.val16.alloc(A.nnz);
+    if (A.nnz)
+      k_convert<double, __nv_bfloat16><<<grid_for(A.nnz, 256), 256, 0, st>>>(A.nnz, A.val, A.val16);
+    FEM_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace
+
+void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st) {
+  H.sys = &S;
+  H.o = o;
+  H.L.clear();
+  const int prec = o.precision;
+  const bool lowp = prec != AMG_PREC_FP64;
+  auto cur = std::make_unique<Level>();
+  cur->A = &S.A;
+  cur->stencil = S.stencil;
+  cur->st = S.stA;
+  for (int lev = 0;; lev++) {
+    Level& Lv = *cur;
+    const Csr4* Acur = Lv.A;
+    Lv.N = Acur->nrows;
+    const int64_t N = Lv.N;
+    unsigned g = grid_for(N, 256);
+    DevBuf<double> d(N, st);
+    k_diag<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, d);
+    FEM_CHECK_LAUNCH();
+    Lv.dinv.alloc(N);
+    if (lowp) Lv.dinv32.alloc(N);
+    Lv.scalar_sinv = Lv.stencil && o.smoother == AMG_SMOOTHER_CHEBYSHEV;
+    if (o.smoother == AMG_SMOOTHER_L1_JACOBI) {
+      DevBuf<double> l1(N, st);
+      rowabs_max(*Acur, Acur->val, nullptr, d, l1, st);
+      k_recip<<<g, 256, 0, st>>>(N, l1, Lv.dinv, lowp ? Lv.dinv32.p : nullptr);
+      Lv.lmax = 1.0;
+    } else {
+      k_recip<<<g, 256, 0, st>>>(N, d, Lv.dinv, lowp ? Lv.dinv32.p : nullptr);
+      Lv.lmax = rowabs_max(*Acur, Acur->val, nullptr, d, nullptr, st);
+    }
+    FEM_CHECK_LAUNCH();
+    if (lowp) {
+      Csr4& Am = lev == 0 ? S.A : Lv.Aown;
+      if (!(lev == 0 && Lv.stencil)) {
+        if (!Am.val32.p) make_lowp(Am, AMG_PREC_FP32, st);
+        if (prec == AMG_PREC_BF16 && !Am.val16.p) make_lowp(Am, AMG_PREC_BF16, st);
+      }
+    }
+
+    bool last = (N <= o.coarse_max) || (lev == o.max_levels - 1);
+    Aggregation ag;
+    if (!last) {
+      uint32_t s = (uint32_t)(0x9E3779B9u * (uint32_t)(o.seed + lev + 1));
+      ag = aggregate(*Acur, d, o.theta, s, st);
+      if (ag.nagg == 0 || (double)ag.nagg >= 0.9 * (double)N) last = true;
+    }
+    if (last) {
+      Lv.coarsest = true;
+      if (N <= 4096) dense_inverse(*Acur, Acur->val, Lv.Ainv, st);
+      H.L.push_back(std::move(cur));
+      break;
+    }
+    // smoothed prolongator P = P_t - omega D^{-1} A_F P_t
+    Lv.agg = std::move(ag.agg);
+    Csr4 Pt;
+    Pt.nrows = (int32_t)N;
+    Pt.ncols = (int32_t)ag.nagg;
+    Pt.nnz = 4 * N;
+    Pt.rowptr.alloc(N + 1);
+    Pt.col.alloc(4 * N);
+    Pt.val.alloc(4 * N);
+    k_tentative<<<grid_for(N + 1, 256), 256, 0, st>>>(N, Lv.agg, Pt.rowptr, Pt.col, Pt.val);
+    FEM_CHECK_LAUNCH();
+    const double lamF = rowabs_max(*Acur, Acur->val, ag.smask, d, nullptr, st);
+    const double omega = 4.0 / (3.0 * lamF);
+    Csr4 DF;
+    DF.nrows = DF.ncols = (int32_t)N;
+    DF.nnz = Acur->nnz;
+    DF.rowptr.alloc(N + 1);
+    DF.col.alloc(DF.nnz);
+    DF.val.alloc(DF.nnz);
+    FEM_CUDA(cudaMemcpyAsync(DF.rowptr, Acur->rowptr, 4 * (N + 1), cudaMemcpyDeviceToDevice, st));
+    {
+      DevBuf<double> dinvA(N, st);
+      k_recip<<<g, 256, 0, st>>>(N, d, dinvA, nullptr);
+      k_scaled_filtered<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, ag.smask,
+                                           dinvA, DF.col, DF.val);
+      FEM_CHECK_LAUNCH();
+    }
+    spgemm(DF, DF.val, Pt, Pt.val, Lv.P, st, true);
+    Lv.P.ncols = (int32_t)ag.nagg;
+    k_smooth_p<<<g, 256, 0, st>>>(N, Lv.P.rowptr, Lv.P.col, Lv.P.val, Lv.agg, omega);
+    FEM_CHECK_LAUNCH();
+    transpose(Lv.P, Lv.R, ag.nagg, st);
+    if (lowp) {
+      make_lowp(Lv.P, AMG_PREC_FP32, st);
+      make_lowp(Lv.R, AMG_PREC_FP32, st);
+      if (prec == AMG_PREC_BF16) {
+        make_lowp(Lv.P, AMG_PREC_BF16, st);
+        make_lowp(Lv.R, AMG_PREC_BF16, st);
+      }
+    }
+    // Galerkin coarse operator A_c = R (A P)  (Sec. 3.1)
+    Csr4 AP;
+    spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true);
+    auto nxt = std::make_unique<Level>();
+    spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true);
+    nxt->Aown.ncols = (int32_t)ag.nagg;
+    nxt->A = &nxt->Aown;
+    if (S.pencil) {
+      // with P fixed, R (rho K + M) P = rho R K P + R M P: keep both pencil parts
+      const double* Kv = lev == 0 ? S.Kv.p : Lv.Kv.p;
+      const double* Mv = lev == 0 ? S.Mv.p : Lv.Mv.p;
+      DevBuf<double> KP(AP.nnz, st), MP(AP.nnz, st);
+      spgemm_numeric(*Acur, Kv, Lv.P, Lv.P.val, AP, KP, st);
+      spgemm_numeric(*Acur, Mv, Lv.P, Lv.P.val, AP, MP, st);
+      nxt->Kv.alloc(nxt->Aown.nnz);
+      nxt->Mv.alloc(nxt->Aown.nnz);
+      spgemm_numeric(Lv.R, Lv.R.val, AP, KP, nxt->Aown, nxt->Kv, st);
+      spgemm_numeric(Lv.R, Lv.R.val, AP, MP, nxt->Aown, nxt->Mv, st);
+    }
+    H.L.push_back(std::move(cur));
+    cur = std::move(nxt);
+  }
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace fem

@@ -1,0 +1,490 @@
+// Device assembly of K, M, f for P1 elements on the Kuhn mesh of the unit cube
+// (arXiv 2102.03515, Sec. 2: K_ij = int grad phi_j . grad phi_i, M_ij = int phi_j phi_i,
+// f_i = int ubar phi_i; A = rho K + M, eq. (linsys)).
+//
+// Layout.  Unknowns are the interior vertices (i,j,k), 1..n-1 per axis, numbered
+// (i-1) + m((j-1) + m(k-1)), m = n-1.  In the Kuhn mesh vertex v is joined to
+// v +- e_d, v +- (e_a + e_b) and v +- (1,1,1): 14 neighbours, so every CSR4 row has at
+// most 15 entries and is stored with 16 slots (rowptr[r] = 16 r), real entries first in
+// increasing column order, then (col -1, value 0) padding.
+//
+// Element arithmetic is done without FMA contraction (this file is compiled with
+// -fmad=false) so that sums of element contributions follow plain IEEE rounding.
+#include <cmath>
+
+#include "solver.cuh"
+
+namespace fem {
+namespace {
+
+// The 15 stencil slots in increasing linear-offset order (di + m dj + m^2 dk).
+__constant__ int kSlotOff[15][3] = {
+    {-1, -1, -1}, {0, -1, -1}, {-1, 0, -1}, {0, 0, -1}, {-1, -1, 0}, {0, -1, 0}, {-1, 0, 0},
+    {0, 0, 0},    {1, 0, 0},   {0, 1, 0},   {1, 1, 0},  {0, 0, 1},   {1, 0, 1},  {0, 1, 1},
+    {1, 1, 1}};
+// Slot type: 0 centre, 1 axis, 2 face diagonal, 3 body diagonal.
+__constant__ int kSlotType[15] = {3, 2, 2, 1, 2, 1, 1, 0, 1, 1, 2, 1, 2, 2, 3};
+// Tet paths: permutation p steps along kPerm[p][0], then [1], then [2].
+__constant__ int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+__device__ __forceinline__ int slot_of(int di, int dj, int dk) {
+  // inverse of kSlotOff for Kuhn neighbours; -1 if not a neighbour
+  int code = (di + 1) + 3 * (dj + 1) + 9 * (dk + 1);
+  switch (code) {
+    case 0: return 0;   // (-1,-1,-1)
+    case 1: return 1;   // (0,-1,-1)
+    case 3: return 2;   // (-1,0,-1)
+    case 4: return 3;   // (0,0,-1)
+    case 9: return 4;   // (-1,-1,0)
+    case 10: return 5;  // (0,-1,0)
+    case 12: return 6;  // (-1,0,0)
+    case 13: return 7;  // (0,0,0)
+    case 14: return 8;  // (1,0,0)
+    case 16: return 9;  // (0,1,0)
+    case 17: return 10; // (1,1,0)
+    case 22: return 11; // (0,0,1)
+    case 23: return 12; // (1,0,1)
+    case 25: return 13; // (0,1,1)
+    case 26: return 14; // (1,1,1)
+  }
+  return -1;
+}
+
+// det J and barycentric gradients of a tet (rows of J^{-1}; grad lambda_0 = -sum).
+__device__ double tet_grads(const double X[4][3], double g[4][3]) {
+  double J[3][3];
+  for (int r = 0; r < 3; r++)
+    for (int c = 0; c < 3; c++) J[r][c] = X[c + 1][r] - X[0][r];
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  for (int d = 0; d < 3; d++) {
+    g[1][d] = inv[0][d];
+    g[2][d] = inv[1][d];
+    g[3][d] = inv[2][d];
+    g[0][d] = -(inv[0][d] + inv[1][d] + inv[2][d]);
+  }
+  return det;
+}
+
+struct Coords {
+  const double* xyz;  // null: uniform grid
+  int n;
+  double h;
+  __device__ void get(int i, int j, int k, double out[3]) const {
+    if (xyz) {
+      int64_t v = (int64_t)i + (int64_t)(n + 1) * ((int64_t)j + (int64_t)(n + 1) * k);
+      out[0] = xyz[3 * v];
+      out[1] = xyz[3 * v + 1];
+      out[2] = xyz[3 * v + 2];
+    } else {
+      out[0] = i * h;
+      out[1] = j * h;
+      out[2] = k * h;
+    }
+  }
+};
+
+// Row r of K and M (15 slots each) for the interior vertex (i,j,k): element
+// contributions of its 24 tets, visited in increasing tet index (cube id, then path).
+__device__ void vertex_row(const Coords& C, int i, int j, int k, double kv[15], double mv[15]) {
+  for (int s = 0; s < 15; s++) kv[s] = mv[s] = 0.0;
+  for (int dd = 7; dd >= 0; dd--) {
+    const int ci = i - (dd & 1), cj = j - ((dd >> 1) & 1), ck = k - ((dd >> 2) & 1);
+    if (ci < 0 || cj < 0 || ck < 0 || ci >= C.n || cj >= C.n || ck >= C.n) continue;
+    for (int p = 0; p < 6; p++) {
+      int v[4][3];
+      v[0][0] = ci; v[0][1] = cj; v[0][2] = ck;
+      for (int s = 0; s < 3; s++) {
+        for (int d = 0; d < 3; d++) v[s + 1][d] = v[s][d];
+        v[s + 1][kPerm[p][s]] += 1;
+      }
+      int loc = -1;
+      for (int a = 0; a < 4; a++)
+        if (v[a][0] == i && v[a][1] == j && v[a][2] == k) loc = a;
+      if (loc < 0) continue;
+      double X[4][3], g[4][3];
+      for (int a = 0; a < 4; a++) C.get(v[a][0], v[a][1], v[a][2], X[a]);
+      double det = tet_grads(X, g);
+      double vol = fabs(det) / 6.0;
+      for (int b = 0; b < 4; b++) {
+        int s = slot_of(v[b][0] - i, v[b][1] - j, v[b][2] - k);
+        double ke = vol * (g[loc][0] * g[b][0] + g[loc][1] * g[b][1] + g[loc][2] * g[b][2]);
+        double me = vol * (loc == b ? 2.0 : 1.0) / 20.0;
+        kv[s] += ke;
+        mv[s] += me;
+      }
+    }
+  }
+}
+
+// One interior vertex's row on the uniform grid gives the stencils of K and M.
+__global__ void k_uniform_row(int n, double* out /* 30: K slots, M slots */) {
+  Coords C{nullptr, n, 1.0 / n};
+  double kv[15], mv[15];
+  vertex_row(C, 1, 1, 1, kv, mv);
+  for (int s = 0; s < 15; s++) {
+    out[s] = kv[s];
+    out[15 + s] = mv[s];
+  }
+}
+
+// CSR4 rows (16 slots) with values from per-type stencil coefficients.
+__global__ void k_csr_uniform(int m, double rho, Stencil sk, Stencil sm, int32_t* rowptr,
+                              int32_t* col, double* aval, double* kval, double* mval) {
+  int64_t N = (int64_t)m * m * m;
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > N) return;
+  rowptr[r] = (int32_t)(16 * r);
+  if (r == N) return;
+  int i = (int)(r % m), j = (int)((r / m) % m), k = (int)(r / ((int64_t)m * m));
+  double kt[4] = {sk.c0, sk.ca, sk.cf, sk.cb}, mt[4] = {sm.c0, sm.ca, sm.cf, sm.cb};
+  int64_t e = 16 * r;
+  int cnt = 0;
+  for (int s = 0; s < 15; s++) {
+    int ii = i + kSlotOff[s][0], jj = j + kSlotOff[s][1], kk = k + kSlotOff[s][2];
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= m || jj >= m || kk >= m) continue;
+    int t = kSlotType[s];
+    col[e + cnt] = (int32_t)(ii + (int64_t)m * (jj + (int64_t)m * kk));
+    double kvv = kt[t], mvv = mt[t];
+    aval[e + cnt] = rho * kvv + mvv;
+    if (kval) kval[e + cnt] = kvv;
+    if (mval) mval[e + cnt] = mvv;
+    cnt++;
+  }
+  for (; cnt < 16; cnt++) {
+    col[e + cnt] = -1;
+    aval[e + cnt] = 0.0;
+    if (kval) kval[e + cnt] = 0.0;
+    if (mval) mval[e + cnt] = 0.0;
+  }
+}
+
+// CSR4 rows on a general (jittered) vertex grid with Kuhn connectivity.
+__global__ void k_csr_general(int n, const double* xyz, double rho, int32_t* rowptr,
+                              int32_t* col, double* aval, double* kval, double* mval) {
+  const int m = n - 1;
+  int64_t N = (int64_t)m * m * m;
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > N) return;
+  rowptr[r] = (int32_t)(16 * r);
+  if (r == N) return;
+  int i = (int)(r % m), j = (int)((r / m) % m), k = (int)(r / ((int64_t)m * m));
+  Coords C{xyz, n, 1.0 / n};
+  double kv[15], mv[15];
+  vertex_row(C, i + 1, j + 1, k + 1, kv, mv);
+  int64_t e = 16 * r;
+  int cnt = 0;
+  for (int s = 0; s < 15; s++) {
+    int ii = i + kSlotOff[s][0], jj = j + kSlotOff[s][1], kk = k + kSlotOff[s][2];
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= m || jj >= m || kk >= m) continue;
+    col[e + cnt] = (int32_t)(ii + (int64_t)m * (jj + (int64_t)m * kk));
+    aval[e + cnt] = rho * kv[s] + mv[s];
+    if (kval) kval[e + cnt] = kv[s];
+    if (mval) mval[e + cnt] = mv[s];
+    cnt++;
+  }
+  for (; cnt < 16; cnt++) {
+    col[e + cnt] = -1;
+    aval[e + cnt] = 0.0;
+    if (kval) kval[e + cnt] = 0.0;
+    if (mval) mval[e + cnt] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ load vector
+
+struct TargetDev {
+  int kind;
+  int nb;
+  const double* c;  // nb*3
+  const double* w;
+  const double* a;
+  double lo, hi;
+};
+
+__device__ double target_eval(const TargetDev& T, double x, double y, double z) {
+  switch (T.kind) {
+    case FEM_TARGET_SINE:
+      return sinpi(x) * sinpi(y) * sinpi(z);
+    case FEM_TARGET_SINE_PLUS_ONE:
+      return 1.0 + sinpi(x) * sinpi(y) * sinpi(z);
+    case FEM_TARGET_BOX:
+      return (x > T.lo && x < T.hi && y > T.lo && y < T.hi && z > T.lo && z < T.hi) ? 1.0 : 0.0;
+    case FEM_TARGET_BUMPS: {
+      double s = 0.0;
+      for (int b = 0; b < T.nb; b++) {
+        double dx = x - T.c[3 * b], dy = y - T.c[3 * b + 1], dz = z - T.c[3 * b + 2];
+        double r2 = dx * dx + dy * dy + dz * dz;
+        s += T.a[b] * exp(-r2 / (2.0 * T.w[b] * T.w[b]));
+      }
+      return s;
+    }
+  }
+  return 0.0;
+}
+
+// On the uniform grid every target here is a sum of separable terms
+//   ubar(x) = sum_t alpha_t g_t0(x) g_t1(y) g_t2(z),
+// and a quadrature point of the 4-point rule in a Kuhn tet sits at h*(c_d + o) along each
+// axis with o one of 6 offsets; tab[(t*3 + d)*n*6 + c*6 + o] = g_td(h*(c + o)).
+__device__ __forceinline__ double qoff(int o) {
+  const double A = (5.0 + 3.0 * sqrt(5.0)) / 20.0, B = (5.0 - sqrt(5.0)) / 20.0;
+  switch (o) {
+    case 0: return B;
+    case 1: return A;
+    case 2: return 2.0 * B;
+    case 3: return A + B;
+    case 4: return 3.0 * B;
+    default: return A + 2.0 * B;
+  }
+}
+
+__global__ void k_target_tables(TargetDev T, int n, int nterms, double* tab, double* alpha) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int total = nterms * 3 * n * 6;
+  if (idx < nterms) {
+    if (T.kind == FEM_TARGET_BUMPS) alpha[idx] = T.a[idx];
+    else alpha[idx] = 1.0;
+  }
+  if (idx >= total) return;
+  int o = idx % 6, c = (idx / 6) % n, d = (idx / (6 * n)) % 3, t = idx / (18 * n);
+  double x = (c + qoff(o)) / n;
+  double v = 1.0;
+  switch (T.kind) {
+    case FEM_TARGET_SINE: v = sinpi(x); break;
+    case FEM_TARGET_SINE_PLUS_ONE: v = (t == 0) ? 1.0 : sinpi(x); break;
+    case FEM_TARGET_BOX: v = (x > T.lo && x < T.hi) ? 1.0 : 0.0; break;
+    case FEM_TARGET_BUMPS: {
+      double dx = x - T.c[3 * t + d], w = T.w[t];
+      v = exp(-dx * dx / (2.0 * w * w));
+    } break;
+  }
+  tab[idx] = v;
+}
+
+// Per-cube load contributions: cube c gets cf[c*8 + local vertex] with local vertex
+// dx + 2 dy + 4 dz, summing w_q |tau| ubar(x_q) lambda_a(x_q) over its 6 tets and the
+// 4 points of each (Hammer-Stroud, barycentric (A,B,B,B) permutations, weight 1/4).
+template <bool UNIFORM>
+__global__ void k_cube_load(int n, const double* xyz, TargetDev T, const double* tab,
+                            const double* alpha, int nterms, double* cf) {
+  int64_t nc = (int64_t)n * n * n;
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int ci = (int)(c % n), cj = (int)((c / n) % n), ck = (int)(c / ((int64_t)n * n));
+  const double A = (5.0 + 3.0 * sqrt(5.0)) / 20.0, B = (5.0 - sqrt(5.0)) / 20.0;
+  double acc[8];
+  for (int a = 0; a < 8; a++) acc[a] = 0.0;
+  double Xc[8][3];
+  if (!UNIFORM) {
+    Coords C{xyz, n, 1.0 / n};
+    for (int a = 0; a < 8; a++) C.get(ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1), Xc[a]);
+  }
+  const double h = 1.0 / n;
+  const int cc[3] = {ci, cj, ck};
+  for (int p = 0; p < 6; p++) {
+    int lv[4];
+    lv[0] = 0;
+    for (int s = 0; s < 3; s++) lv[s + 1] = lv[s] | (1 << kPerm[p][s]);
+    double vol;
+    if (UNIFORM) {
+      vol = h * h * h / 6.0;
+    } else {
+      double X[4][3], g[4][3];
+      for (int a = 0; a < 4; a++)
+        for (int d = 0; d < 3; d++) X[a][d] = Xc[lv[a]][d];
+      vol = fabs(tet_grads(X, g)) / 6.0;
+    }
+    for (int q = 0; q < 4; q++) {
+      double mu[4] = {B, B, B, B};
+      mu[q] = A;
+      double u;
+      if (UNIFORM) {
+        // offset index along kPerm[p][0] (1 - mu0), kPerm[p][1] (mu2 + mu3), kPerm[p][2] (mu3)
+        int oax[3];
+        oax[kPerm[p][0]] = (q == 0) ? 4 : 5;
+        oax[kPerm[p][1]] = (q >= 2) ? 3 : 2;
+        oax[kPerm[p][2]] = (q == 3) ? 1 : 0;
+        u = 0.0;
+        for (int t = 0; t < nterms; t++) {
+          double g0 = tab[((t * 3 + 0) * n + cc[0]) * 6 + oax[0]];
+          double g1 = tab[((t * 3 + 1) * n + cc[1]) * 6 + oax[1]];
+          double g2 = tab[((t * 3 + 2) * n + cc[2]) * 6 + oax[2]];
+          u += alpha[t] * (g0 * g1 * g2);
+        }
+      } else {
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < 4; a++)
+          for (int d = 0; d < 3; d++) x[d] += mu[a] * Xc[lv[a]][d];
+        u = target_eval(T, x[0], x[1], x[2]);
+      }
+      double wu = 0.25 * u;
+      for (int a = 0; a < 4; a++) acc[lv[a]] += vol * (wu * mu[a]);
+    }
+  }
+  for (int a = 0; a < 8; a++) cf[8 * c + a] = acc[a];
+}
+
+__global__ void k_gather_load(int n, const double* cf, double* f) {
+  const int m = n - 1;
+  int64_t N = (int64_t)m * m * m;
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int i = (int)(r % m) + 1, j = (int)((r / m) % m) + 1, k = (int)(r / ((int64_t)m * m)) + 1;
+  double s = 0.0;
+  for (int dd = 7; dd >= 0; dd--) {
+    int ci = i - (dd & 1), cj = j - ((dd >> 1) & 1), ck = k - ((dd >> 2) & 1);
+    int64_t c = ci + (int64_t)n * (cj + (int64_t)n * ck);
+    s += cf[8 * c + dd];
+  }
+  f[r] = s;
+}
+
+__global__ void k_diag_inv(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
+                           double* dinv) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double d = 0.0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++)
+    if (col[e] == r) d = v[e];
+  dinv[r] = 1.0 / d;
+}
+
+}  // namespace
+
+void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem_target& t,
+                     const fem_assemble_opts& o, cudaStream_t st) {
+  const int n = mesh.n;
+  FEM_REQUIRE(n >= 2 && n <= 1290, FEM_EINVAL, "fem_assemble: n must be in [2, 1290]");
+  FEM_REQUIRE(rho > 0.0 && std::isfinite(rho), FEM_EINVAL, "fem_assemble: rho must be > 0");
+  FEM_REQUIRE(t.kind >= 0 && t.kind <= 3, FEM_EINVAL, "fem_assemble: unknown target kind");
+  FEM_REQUIRE(t.kind != FEM_TARGET_BUMPS || (t.nb >= 1 && t.nb <= 64 && t.centers_host &&
+                                             t.widths_host && t.amps_host),
+              FEM_EINVAL, "fem_assemble: bumps need 1..64 centres/widths/amplitudes");
+  FEM_REQUIRE(o.format >= 0 && o.format <= 2, FEM_EINVAL, "fem_assemble: bad format");
+  const int m = n - 1;
+  const int64_t N = (int64_t)m * m * m;
+  FEM_REQUIRE(16 * N < ((int64_t)1 << 31), FEM_EUNSUPPORTED,
+              "fem_assemble: more than 2^31 stored entries");
+  S.n = n;
+  S.N = N;
+  S.h = 1.0 / n;
+  S.rho = rho;
+  S.uniform = (mesh.xyz_host == nullptr);
+  FEM_REQUIRE(!(o.format == FEM_FMT_STENCIL && !S.uniform), FEM_EINVAL,
+              "fem_assemble: the stencil format needs the uniform grid");
+  S.stencil = S.uniform && o.format != FEM_FMT_CSR;
+  S.pencil = o.keep_pencil != 0;
+
+  // target on the device
+  DevBuf<double> tc, tw, ta;
+  TargetDev T{t.kind, 0, nullptr, nullptr, nullptr, t.lo, t.hi};
+  if (t.kind == FEM_TARGET_BUMPS) {
+    tc.alloc_async(3 * t.nb, st);
+    tw.alloc_async(t.nb, st);
+    ta.alloc_async(t.nb, st);
+    FEM_CUDA(cudaMemcpyAsync(tc, t.centers_host, 24 * t.nb, cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(tw, t.widths_host, 8 * t.nb, cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(ta, t.amps_host, 8 * t.nb, cudaMemcpyHostToDevice, st));
+    T.nb = t.nb;
+    T.c = tc;
+    T.w = tw;
+    T.a = ta;
+  }
+
+  // operator
+  S.A.nrows = S.A.ncols = (int32_t)N;
+  S.A.nnz = 16 * N;
+  S.A.rowptr.alloc(N + 1);
+  S.A.col.alloc(16 * N);
+  S.A.val.alloc(16 * N);
+  if (S.pencil) {
+    S.Kv.alloc(16 * N);
+    S.Mv.alloc(16 * N);
+  }
+  DevBuf<double> xyz;
+  if (S.uniform) {
+    DevBuf<double> row(30, st);
+    k_uniform_row<<<1, 1, 0, st>>>(n, row);
+    FEM_CHECK_LAUNCH();
+    double hrow[30];
+    FEM_CUDA(cudaMemcpyAsync(hrow, row, sizeof(hrow), cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    // per-type coefficients: centre slot 7, axis +x slot 8, face (1,1,0) slot 10,
+    // body (1,1,1) slot 14; all slots of one type agree (checked)
+    const int rep[4] = {7, 8, 10, 14};
+    const int type_of[15] = {3, 2, 2, 1, 2, 1, 1, 0, 1, 1, 2, 1, 2, 2, 3};
+    for (int s = 0; s < 15; s++) {
+      for (int w = 0; w < 2; w++) {
+        double a = hrow[15 * w + s], b = hrow[15 * w + rep[type_of[s]]];
+        double scale = fabs(hrow[15 * w + 7]);
+        FEM_REQUIRE(fabs(a - b) <= 1e-12 * scale, FEM_EDEVCHECK,
+                    "fem_assemble: uniform stencil slots of one type disagree");
+      }
+    }
+    auto mk = [&](int w) {
+      Stencil s;
+      s.m = m;
+      s.c0 = hrow[15 * w + 7];
+      s.ca = hrow[15 * w + 8];
+      s.cf = hrow[15 * w + 10];
+      s.cb = hrow[15 * w + 14];
+      return s;
+    };
+    S.stK = mk(0);
+    S.stM = mk(1);
+    S.stA.m = m;
+    S.stA.c0 = rho * S.stK.c0 + S.stM.c0;
+    S.stA.ca = rho * S.stK.ca + S.stM.ca;
+    S.stA.cf = rho * S.stK.cf + S.stM.cf;
+    S.stA.cb = rho * S.stK.cb + S.stM.cb;
+    k_csr_uniform<<<grid_for(N + 1, 256), 256, 0, st>>>(m, rho, S.stK, S.stM, S.A.rowptr,
+                                                         S.A.col, S.A.val, S.Kv.p, S.Mv.p);
+    FEM_CHECK_LAUNCH();
+  } else {
+    int64_t nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
+    xyz.alloc_async(3 * nv, st);
+    FEM_CUDA(cudaMemcpyAsync(xyz, mesh.xyz_host, 24 * nv, cudaMemcpyHostToDevice, st));
+    k_csr_general<<<grid_for(N + 1, 128), 128, 0, st>>>(n, xyz, rho, S.A.rowptr, S.A.col,
+                                                         S.A.val, S.Kv.p, S.Mv.p);
+    FEM_CHECK_LAUNCH();
+  }
+
+  // load vector
+  S.f.alloc(N);
+  int64_t ncube = (int64_t)n * n * n;
+  DevBuf<double> cf(8 * ncube, st);
+  if (S.uniform) {
+    int nterms = (t.kind == FEM_TARGET_BUMPS) ? t.nb : (t.kind == FEM_TARGET_SINE_PLUS_ONE ? 2 : 1);
+    DevBuf<double> tab((size_t)nterms * 3 * n * 6, st), alpha(nterms, st);
+    int total = nterms * 3 * n * 6;
+    k_target_tables<<<grid_for(total, 256), 256, 0, st>>>(T, n, nterms, tab, alpha);
+    FEM_CHECK_LAUNCH();
+    k_cube_load<true><<<grid_for(ncube, 128), 128, 0, st>>>(n, nullptr, T, tab, alpha, nterms, cf);
+    FEM_CHECK_LAUNCH();
+  } else {
+    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, xyz, T, nullptr, nullptr, 0, cf);
+    FEM_CHECK_LAUNCH();
+  }
+  k_gather_load<<<grid_for(N, 256), 256, 0, st>>>(n, cf, S.f);
+  FEM_CHECK_LAUNCH();
+
+  S.dinv.alloc(N);
+  k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);
+  FEM_CHECK_LAUNCH();
+  // temporaries are freed stream-ordered; make sure the caller's data is complete
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace fem

@@ -1,0 +1,290 @@
+// extern "C" entry points of include/femamg.h: argument checks, handles, and the
+// translation of internal failures into fem_status codes with a per-thread message.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "solver.cuh"
+
+namespace fem {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+[[noreturn]] void fail(fem_status s, const std::string& msg) { throw Error{s, msg}; }
+
+void alloc_level_vectors(Hierarchy& H);
+void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_opts& o,
+                cudaStream_t user, pcg_result& res);
+fem_status pcg_multi(System& S, Hierarchy& H, const double* f, double* u, int nrhs,
+                     const double* rho_k, const pcg_opts& o, cudaStream_t user, pcg_result* res);
+
+template <typename F>
+static fem_status guarded(F&& f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const Error& e) {
+    g_last_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return FEM_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return FEM_EINVAL;
+  }
+}
+
+}  // namespace fem
+
+struct fem_system_s {
+  fem::System S;
+};
+struct amg_hier_s {
+  fem::Hierarchy H;
+  fem_system_s* sys = nullptr;
+};
+
+using namespace fem;
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char* fem_last_error(void) { return g_last_error.c_str(); }
+
+const char* fem_version(void) { return "femamg 0.1 (sm_103a)"; }
+
+fem_status fem_assemble(const fem_kuhn_desc* mesh, double rho, const fem_target* target,
+                        const fem_assemble_opts* opts, void* stream, fem_system* out) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(mesh && target && out, FEM_EINVAL, "fem_assemble: null argument");
+    *out = nullptr;
+    fem_assemble_opts o{FEM_FMT_AUTO, 0};
+    if (opts) o = *opts;
+    auto* h = new fem_system_s();
+    try {
+      assemble_system(h->S, *mesh, rho, *target, o, as_stream(stream));
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return FEM_OK;
+  });
+}
+
+fem_status fem_system_get_info(fem_system sys, fem_system_info* info) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && info, FEM_EINVAL, "fem_system_get_info: null argument");
+    const System& S = sys->S;
+    info->n = S.n;
+    info->N = S.N;
+    info->nnz = S.A.nnz;
+    info->h = S.h;
+    info->rho = S.rho;
+    info->is_stencil = S.stencil;
+    info->has_pencil = S.pencil;
+    return FEM_OK;
+  });
+}
+
+fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && f_dev, FEM_EINVAL, "fem_system_get_rhs: null argument");
+    FEM_CUDA(cudaMemcpyAsync(f_dev, sys->S.f, 8 * sys->S.N, cudaMemcpyDeviceToDevice,
+                             as_stream(stream)));
+    FEM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    return FEM_OK;
+  });
+}
+
+fem_status fem_system_export(fem_system sys, int32_t which, int32_t* rowptr_dev, int32_t* col_dev,
+                             double* val_dev, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && rowptr_dev && col_dev && val_dev, FEM_EINVAL,
+                "fem_system_export: null argument");
+    const System& S = sys->S;
+    const double* v = nullptr;
+    if (which == 0) v = S.A.val;
+    else if (which == 1) v = S.Kv.p;
+    else if (which == 2) v = S.Mv.p;
+    FEM_REQUIRE(which >= 0 && which <= 2, FEM_EINVAL, "fem_system_export: which must be 0, 1, 2");
+    FEM_REQUIRE(v, FEM_EINVAL, "fem_system_export: K and M need keep_pencil at assembly");
+    cudaStream_t st = as_stream(stream);
+    FEM_CUDA(cudaMemcpyAsync(rowptr_dev, S.A.rowptr, 4 * (S.N + 1), cudaMemcpyDeviceToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(col_dev, S.A.col, 4 * S.A.nnz, cudaMemcpyDeviceToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(val_dev, v, 8 * S.A.nnz, cudaMemcpyDeviceToDevice, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    return FEM_OK;
+  });
+}
+
+fem_status fem_spmv(fem_system sys, const double* x_dev, double* y_dev, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && x_dev && y_dev, FEM_EINVAL, "fem_spmv: null argument");
+    Level L;
+    system_level(sys->S, L);
+    op_apply_d(L, x_dev, y_dev, nullptr, nullptr, as_stream(stream));
+    FEM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    return FEM_OK;
+  });
+}
+
+void fem_system_destroy(fem_system sys) {
+  if (!sys) return;
+  cudaDeviceSynchronize();
+  delete sys;
+}
+
+void amg_default_opts(amg_opts* o) {
+  if (!o) return;
+  o->theta = 0.05;
+  o->smoother = AMG_SMOOTHER_CHEBYSHEV;
+  o->degree = 2;
+  o->cheb_ratio = 6.0;
+  o->coarse_max = 256;
+  o->max_levels = 16;
+  o->precision = AMG_PREC_FP64;
+  o->seed = 0;
+}
+
+fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hier* out) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && out, FEM_EINVAL, "amg_setup: null argument");
+    *out = nullptr;
+    amg_opts o;
+    amg_default_opts(&o);
+    if (opts) o = *opts;
+    FEM_REQUIRE(o.theta >= 0.0 && o.theta < 1.0, FEM_EINVAL, "amg_setup: theta in [0, 1)");
+    FEM_REQUIRE(o.degree >= 1 && o.degree <= 15, FEM_EINVAL, "amg_setup: degree in [1, 15]");
+    FEM_REQUIRE(o.cheb_ratio > 1.0, FEM_EINVAL, "amg_setup: cheb_ratio > 1");
+    FEM_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= 4096, FEM_EINVAL,
+                "amg_setup: coarse_max in [1, 4096]");
+    FEM_REQUIRE(o.max_levels >= 1 && o.max_levels <= 32, FEM_EINVAL,
+                "amg_setup: max_levels in [1, 32]");
+    FEM_REQUIRE(o.precision >= 0 && o.precision <= 2, FEM_EINVAL, "amg_setup: bad precision");
+    FEM_REQUIRE(o.smoother == 0 || o.smoother == 1, FEM_EINVAL, "amg_setup: bad smoother");
+    cudaStream_t st = as_stream(stream);
+    auto* h = new amg_hier_s();
+    h->sys = sys;
+    try {
+      cudaEvent_t e0, e1;
+      FEM_CUDA(cudaEventCreate(&e0));
+      FEM_CUDA(cudaEventCreate(&e1));
+      FEM_CUDA(cudaEventRecord(e0, st));
+      build_hierarchy(h->H, sys->S, o, st);
+      alloc_level_vectors(h->H);
+      FEM_CUDA(cudaEventRecord(e1, st));
+      FEM_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      h->H.setup_ms = ms;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return FEM_OK;
+  });
+}
+
+fem_status amg_hier_get_info(amg_hier h, amg_hier_info* info) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(h && info, FEM_EINVAL, "amg_hier_get_info: null argument");
+    std::memset(info, 0, sizeof(*info));
+    info->levels = (int32_t)h->H.L.size();
+    for (size_t l = 0; l < h->H.L.size() && l < 32; l++) {
+      info->rows[l] = h->H.L[l]->N;
+      info->nnz[l] = h->H.L[l]->A->nnz;
+      info->lmax[l] = h->H.L[l]->lmax;
+    }
+    info->setup_ms = h->H.setup_ms;
+    return FEM_OK;
+  });
+}
+
+fem_status amg_hier_export(amg_hier h, int32_t level, int32_t which, int32_t* rowptr_dev,
+                           int32_t* col_dev, double* val_dev, int64_t* nnz_out, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(h, FEM_EINVAL, "amg_hier_export: null handle");
+    FEM_REQUIRE(level >= 0 && level < (int)h->H.L.size(), FEM_EINVAL, "amg_hier_export: bad level");
+    Level& L = *h->H.L[level];
+    cudaStream_t st = as_stream(stream);
+    if (which == 3) {
+      FEM_REQUIRE(!L.coarsest, FEM_EINVAL, "amg_hier_export: the coarsest level has no aggregates");
+      if (nnz_out) *nnz_out = L.N;
+      if (col_dev) FEM_CUDA(cudaMemcpyAsync(col_dev, L.agg, 4 * L.N, cudaMemcpyDeviceToDevice, st));
+      FEM_CUDA(cudaStreamSynchronize(st));
+      return FEM_OK;
+    }
+    const Csr4* M = nullptr;
+    if (which == 0) M = L.A;
+    else if (which == 1 || which == 2) {
+      FEM_REQUIRE(!L.coarsest, FEM_EINVAL, "amg_hier_export: the coarsest level has no P/R");
+      M = which == 1 ? &L.P : &L.R;
+    }
+    FEM_REQUIRE(M, FEM_EINVAL, "amg_hier_export: which must be 0..3");
+    if (nnz_out) *nnz_out = M->nnz;
+    if (rowptr_dev)
+      FEM_CUDA(cudaMemcpyAsync(rowptr_dev, M->rowptr, 4 * ((int64_t)M->nrows + 1),
+                               cudaMemcpyDeviceToDevice, st));
+    if (col_dev) FEM_CUDA(cudaMemcpyAsync(col_dev, M->col, 4 * M->nnz, cudaMemcpyDeviceToDevice, st));
+    if (val_dev) FEM_CUDA(cudaMemcpyAsync(val_dev, M->val, 8 * M->nnz, cudaMemcpyDeviceToDevice, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    return FEM_OK;
+  });
+}
+
+fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(h && r_dev && z_dev, FEM_EINVAL, "amg_vcycle: null argument");
+    vcycle(h->H, r_dev, z_dev, as_stream(stream), nullptr);
+    FEM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    return FEM_OK;
+  });
+}
+
+void amg_hier_destroy(amg_hier h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  delete h;
+}
+
+void pcg_default_opts(pcg_opts* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->max_iter = 1000;
+  o->stop = PCG_STOP_RESIDUAL;
+  o->flexible = -1;
+  o->use_x0 = 0;
+  o->use_graph = 1;
+  o->cancel_host = nullptr;
+}
+
+fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double* u_dev,
+                     int32_t nrhs, const double* rho_k_host, const pcg_opts* opts, void* stream,
+                     pcg_result* res) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && u_dev && res, FEM_EINVAL, "pcg_solve: null argument");
+    FEM_REQUIRE(nrhs >= 1, FEM_EINVAL, "pcg_solve: nrhs >= 1");
+    FEM_REQUIRE(!hier || hier->sys == sys, FEM_EINVAL, "pcg_solve: hierarchy of another system");
+    pcg_opts o;
+    pcg_default_opts(&o);
+    if (opts) o = *opts;
+    FEM_REQUIRE(o.tol > 0.0 && o.max_iter >= 0, FEM_EINVAL, "pcg_solve: tol > 0, max_iter >= 0");
+    if (nrhs == 1 && !rho_k_host) {
+      pcg_single(sys->S, hier ? &hier->H : nullptr, f_dev, u_dev, o, as_stream(stream), res[0]);
+      return (fem_status)res[0].status;
+    }
+    FEM_REQUIRE(hier && rho_k_host && f_dev, FEM_EINVAL,
+                "pcg_solve: several right-hand sides need a hierarchy, rho_k and f");
+    return pcg_multi(sys->S, hier->H, f_dev, u_dev, nrhs, rho_k_host, o, as_stream(stream), res);
+  });
+}
+
+}  // extern "C"

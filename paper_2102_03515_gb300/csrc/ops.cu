@@ -1,0 +1,565 @@
+// Operator applications of the V-cycle and of CG: the matrix-free 15-point stencil of
+// A = rho K + M on the uniform Kuhn grid and CSR4 SpMV, each with a fused epilogue
+// (plain product, residual, Chebyshev / l1-Jacobi smoothing step, dot products).
+//
+// Smoothing (one "step" of the paper's V-cycle, Sec. 3.1 and Sec. 4) is a Chebyshev
+// polynomial of degree k in D^{-1}A over [lambda/ratio, lambda], lambda the Gershgorin
+// bound, run by the three-term recurrence
+//     r_0 = D^{-1}(b - A x_0),  d_0 = r_0 / theta,  x_1 = x_0 + d_0,
+//     r_i = r_{i-1} - D^{-1} A d_{i-1},  d_i = c1_i d_{i-1} + c2_i r_i,  x_{i+1} = x_i + d_i,
+// (theta, delta the centre and half-width of the interval, sigma = theta/delta,
+// rho_0 = 1/sigma, rho_i = 1/(2 sigma - rho_{i-1}), c1_i = rho_i rho_{i-1}, c2_i = 2 rho_i/delta).
+// One l1-Jacobi step is the degree-1 case with D replaced by the l1 row norms, theta = 1.
+#include <algorithm>
+#include <cmath>
+
+#include "solver.cuh"
+
+namespace fem {
+
+ChebCoef cheb_coefficients(double lmax, double ratio, int degree) {
+  ChebCoef c;
+  c.degree = degree;
+  double a = lmax / ratio, b = lmax;
+  double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
+  double sigma = theta / delta;
+  c.inv_theta = 1.0 / theta;
+  double rho_old = 1.0 / sigma;
+  for (int i = 1; i < degree && i < 16; i++) {
+    double rho_new = 1.0 / (2.0 * sigma - rho_old);
+    c.c1[i] = rho_new * rho_old;
+    c.c2[i] = 2.0 * rho_new / delta;
+    rho_old = rho_new;
+  }
+  return c;
+}
+
+namespace {
+
+enum EpiMode { E_STORE = 0, E_RESIDUAL = 1, E_CHEB_STEP = 2, E_CHEB_INIT = 3, E_ADD = 4 };
+
+// Fused epilogue applied to (row, (A v)_row).  Modes:
+//   E_STORE     y = Av              (dot: <v, Av> with v = vin)
+//   E_ADD       y += Av
+//   E_RESIDUAL  y = b - Av
+//   E_CHEB_INIT r = s (b - Av); d_new = c2 r                       (v = x, x not written)
+//   E_CHEB_STEP r -= s Av; d_new = c1 d_old + c2 r; x += [d_old] + d_new   (v = d_old)
+// s is the smoother's diagonal inverse (scalar sinv_c when sinv is null).  When z64 is
+// set, the final x is also written in FP64 and <z, r1>, <z, r2> are accumulated.
+template <typename T>
+struct Epi {
+  int mode;
+  T* y;
+  const T* b;
+  T* r;
+  const T* dold;
+  T* dnew;
+  T* x;
+  const T* sinv;
+  T sinv_c;
+  T c1, c2;
+  int add_prev;
+  const T* vin;
+  int want_dot;
+  double* z64;
+  const double* r1;
+  const double* r2;
+
+  __device__ __forceinline__ void operator()(int64_t row, typename Arith<T>::type av,
+                                             double acc[2]) const {
+    using AT = typename Arith<T>::type;
+    switch (mode) {
+      case E_STORE:
+        y[row] = (T)av;
+        if (want_dot) acc[0] += (double)vin[row] * (double)av;
+        break;
+      case E_ADD:
+        y[row] = (T)((AT)y[row] + av);
+        break;
+      case E_RESIDUAL:
+        y[row] = (T)((AT)b[row] - av);
+        break;
+      case E_CHEB_INIT: {
+        AT s = sinv ? (AT)sinv[row] : (AT)sinv_c;
+        AT rr = s * ((AT)b[row] - av);
+        r[row] = (T)rr;
+        dnew[row] = (T)((AT)c2 * rr);
+      } break;
+      case E_CHEB_STEP: {
+        AT s = sinv ? (AT)sinv[row] : (AT)sinv_c;
+        AT rr = (AT)r[row] - s * av;
+        AT dl = (AT)dold[row];
+        AT dn = (AT)c1 * dl + (AT)c2 * rr;
+        r[row] = (T)rr;
+        dnew[row] = (T)dn;
+        AT xv = (AT)x[row] + (add_prev ? dl : (AT)0) + dn;
+        x[row] = (T)xv;
+        if (z64) {
+          double z = (double)xv;
+          z64[row] = z;
+          acc[0] += z * r1[row];
+          if (r2) acc[1] += z * r2[row];
+        }
+      } break;
+    }
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void write_partials(double (&acc)[2], double* partials, int want,
+                                               int nblocks) {
+  if (!want) return;
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    partials[bid] = acc[0];
+    partials[nblocks + bid] = acc[1];
+  }
+}
+
+// ------------------------------------------------------------------ stencil
+
+constexpr int TX = 32, TY = 8, KZ = 16;
+
+template <typename T>
+struct SC {
+  T c0, ca, cf, cb;
+};
+
+// 2.5D tiling: a block owns a 32 x 8 column of the (i, j) plane and marches KZ planes in
+// k, keeping planes k-1, k, k+1 (with a one-point halo) in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(TX* TY) k_stencil(const T* __restrict__ v, int m, SC<T> c,
+                                                    Epi<T> epi, double* partials, int nblocks,
+                                                    const int* done) {
+  using AT = typename Arith<T>::type;
+  if (done && *done) return;
+  __shared__ T pl[3][TY + 2][TX + 2];
+  const int tx = threadIdx.x & (TX - 1), ty = threadIdx.x / TX;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KZ;
+  const int i = i0 + tx, j = j0 + ty;
+  const int64_t mm = (int64_t)m * m;
+  auto load = [&](int k) {
+    const int slot = (k - k0 + 1 + 3) % 3;
+    for (int t = threadIdx.x; t < (TY + 2) * (TX + 2); t += TX * TY) {
+      const int a = t % (TX + 2), b = t / (TX + 2);
+      const int ii = i0 + a - 1, jj = j0 + b - 1;
+      T val = (T)0;
+      if (k >= 0 && k < m && ii >= 0 && ii < m && jj >= 0 && jj < m)
+        val = v[ii + (int64_t)m * jj + mm * k];
+      pl[slot][b][a] = val;
+    }
+  };
+  double acc[2] = {0.0, 0.0};
+  const int kend = min(k0 + KZ, m);
+  load(k0 - 1);
+  load(k0);
+  const AT c0 = (AT)c.c0, ca = (AT)c.ca, cf = (AT)c.cf, cb = (AT)c.cb;
+  for (int k = k0; k < kend; k++) {
+    load(k + 1);
+    __syncthreads();
+    const int sm = (k - k0 + 3) % 3, s0 = (k - k0 + 1) % 3, sp = (k - k0 + 2) % 3;
+    if (i < m && j < m) {
+      const int a = tx + 1, b = ty + 1;
+      AT axis = (AT)pl[s0][b][a - 1] + (AT)pl[s0][b][a + 1] + (AT)pl[s0][b - 1][a] +
+                (AT)pl[s0][b + 1][a] + (AT)pl[sm][b][a] + (AT)pl[sp][b][a];
+      AT face = (AT)pl[s0][b + 1][a + 1] + (AT)pl[s0][b - 1][a - 1] + (AT)pl[sp][b][a + 1] +
+                (AT)pl[sm][b][a - 1] + (AT)pl[sp][b + 1][a] + (AT)pl[sm][b - 1][a];
+      AT body = (AT)pl[sp][b + 1][a + 1] + (AT)pl[sm][b - 1][a - 1];
+      AT av = c0 * (AT)pl[s0][b][a] + ca * axis + cf * face + cb * body;
+      epi((int64_t)i + (int64_t)m * j + mm * k, av, acc);
+    }
+    __syncthreads();
+  }
+  write_partials<T>(acc, partials, partials != nullptr, nblocks);
+}
+
+template <typename T>
+int launch_stencil(const Stencil& s, const T* v, const Epi<T>& epi, double* partials,
+                   cudaStream_t st, const int* done = nullptr) {
+  const int m = s.m;
+  dim3 grid((m + TX - 1) / TX, (m + TY - 1) / TY, (m + KZ - 1) / KZ);
+  int nb = grid.x * grid.y * grid.z;
+  FEM_REQUIRE(!partials || nb <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "stencil grid too large");
+  SC<T> c{(T)s.c0, (T)s.ca, (T)s.cf, (T)s.cb};
+  k_stencil<T><<<grid, TX * TY, 0, st>>>(v, m, c, epi, partials, nb, done);
+  FEM_CHECK_LAUNCH();
+  return nb;
+}
+
+// ------------------------------------------------------------------ CSR4
+
+template <typename VT>
+struct Vals4;
+template <>
+struct Vals4<double> {
+  __device__ static void load(const double* p, double o[4]) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+};
+template <>
+struct Vals4<float> {
+  __device__ static void load(const float* p, float o[4]) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
+};
+template <>
+struct Vals4<__nv_bfloat16> {
+  __device__ static void load(const __nv_bfloat16* p, float o[4]) {
+    uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
+  }
+};
+
+// TPR lanes per row; every lane loads 4 consecutive entries (int4 of columns and
+// 16/32 bytes of values) per iteration: coalesced 128-bit loads along the rows.
+template <int TPR, typename VT, typename T>
+__global__ void __launch_bounds__(256) k_csr(int nrows, const int32_t* __restrict__ rowptr,
+                                             const int32_t* __restrict__ col,
+                                             const VT* __restrict__ val, const T* __restrict__ v,
+                                             Epi<T> epi, double* partials, int nblocks,
+                                             const int* done) {
+  using AT = typename Arith<T>::type;
+  if (done && *done) return;
+  const int lane = threadIdx.x % TPR;
+  const int rows_per_block = blockDim.x / TPR;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t base = (int64_t)blockIdx.x * rows_per_block; base < nrows;
+       base += (int64_t)gridDim.x * rows_per_block) {
+    const int64_t row = base + threadIdx.x / TPR;
+    AT sum = 0;
+    if (row < nrows) {
+      const int e0 = rowptr[row], e1 = rowptr[row + 1];
+      for (int e = e0 + 4 * lane; e < e1; e += 4 * TPR) {
+        int4 c4 = __ldg(reinterpret_cast<const int4*>(col + e));
+        AT w[4];
+        Vals4<VT>::load(val + e, w);
+        const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (cs[q] >= 0) sum += w[q] * (AT)__ldg(v + cs[q]);
+      }
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, TPR);
+    if (row < nrows && lane == 0) epi(row, sum, acc);
+  }
+  write_partials<T>(acc, partials, partials != nullptr, nblocks);
+}
+
+template <typename VT, typename T>
+int launch_csr(const Csr4& M, const VT* val, const T* v, const Epi<T>& epi, double* partials,
+               cudaStream_t st, const int* done = nullptr) {
+  const int64_t nr = M.nrows;
+  if (nr == 0) return 0;
+  const double avg = (double)M.nnz / (double)nr;
+  const int block = 256;
+  int tpr = avg <= 16 ? 4 : (avg <= 32 ? 8 : (avg <= 96 ? 16 : 32));
+  const int rpb = block / tpr;
+  unsigned grid = persistent_grid((nr + rpb - 1) / rpb * block, block, 16);
+  FEM_REQUIRE(!partials || (int)grid <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "grid too large");
+  switch (tpr) {
+    case 4:
+      k_csr<4, VT, T><<<grid, block, 0, st>>>(M.nrows, M.rowptr, M.col, val, v, epi, partials, grid, done);
+      break;
+    case 8:
+      k_csr<8, VT, T><<<grid, block, 0, st>>>(M.nrows, M.rowptr, M.col, val, v, epi, partials, grid, done);
+      break;
+    case 16:
+      k_csr<16, VT, T><<<grid, block, 0, st>>>(M.nrows, M.rowptr, M.col, val, v, epi, partials, grid, done);
+      break;
+    default:
+      k_csr<32, VT, T><<<grid, block, 0, st>>>(M.nrows, M.rowptr, M.col, val, v, epi, partials, grid, done);
+  }
+  FEM_CHECK_LAUNCH();
+  return (int)grid;
+}
+
+// Level operator with the precision's value array.
+template <typename T>
+int launch_op(const Level& Lv, int prec, const T* v, const Epi<T>& epi, double* partials,
+              cudaStream_t st, const int* done = nullptr);
+
+template <>
+int launch_op<double>(const Level& Lv, int prec, const double* v, const Epi<double>& epi,
+                      double* partials, cudaStream_t st, const int* done) {
+  (void)prec;
+  if (Lv.stencil) return launch_stencil<double>(Lv.st, v, epi, partials, st, done);
+  return launch_csr<double, double>(*Lv.A, Lv.A->val.p, v, epi, partials, st, done);
+}
+template <>
+int launch_op<float>(const Level& Lv, int prec, const float* v, const Epi<float>& epi,
+                     double* partials, cudaStream_t st, const int* done) {
+  if (Lv.stencil) return launch_stencil<float>(Lv.st, v, epi, partials, st, done);
+  if (prec == AMG_PREC_BF16 && Lv.A->val16.p)
+    return launch_csr<__nv_bfloat16, float>(*Lv.A, Lv.A->val16.p, v, epi, partials, st, done);
+  return launch_csr<float, float>(*Lv.A, Lv.A->val32.p, v, epi, partials, st, done);
+}
+
+template <typename T>
+Epi<T> epi_base(int mode) {
+  Epi<T> e;
+  e.mode = mode;
+  e.y = nullptr;
+  e.b = nullptr;
+  e.r = nullptr;
+  e.dold = nullptr;
+  e.dnew = nullptr;
+  e.x = nullptr;
+  e.sinv = nullptr;
+  e.sinv_c = (T)0;
+  e.c1 = e.c2 = (T)0;
+  e.add_prev = 0;
+  e.vin = nullptr;
+  e.want_dot = 0;
+  e.z64 = nullptr;
+  e.r1 = e.r2 = nullptr;
+  return e;
+}
+
+template <typename T>
+const T* level_sinv(const Level& Lv);
+template <>
+const double* level_sinv<double>(const Level& Lv) { return Lv.scalar_sinv ? nullptr : Lv.dinv.p; }
+template <>
+const float* level_sinv<float>(const Level& Lv) { return Lv.scalar_sinv ? nullptr : Lv.dinv32.p; }
+
+// ------------------------------------------------------------------ elementwise
+
+// Chebyshev start from x = 0: r = s b, d = r / theta, x = d.  With b64 given the FP64
+// right-hand side is converted into b as well (mixed precision, finest level).
+template <typename T>
+__global__ void k_cheb_zero(int64_t N, const T* __restrict__ b, const double* __restrict__ b64,
+                            T* bout, const T* __restrict__ sinv, T sinv_c, T inv_theta, T* r,
+                            T* d, T* x, const int* done) {
+  using AT = typename Arith<T>::type;
+  if (done && *done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    AT bv;
+    if (b64) {
+      bv = (AT)b64[i];
+      bout[i] = (T)bv;
+    } else {
+      bv = (AT)b[i];
+    }
+    AT s = sinv ? (AT)sinv[i] : (AT)sinv_c;
+    AT rr = s * bv;
+    AT dd = (AT)inv_theta * rr;
+    r[i] = (T)rr;
+    d[i] = (T)dd;
+    x[i] = (T)dd;
+  }
+}
+
+// x += d; optional FP64 output of x with <z, r1>, <z, r2>.
+template <typename T>
+__global__ void k_add_out(int64_t N, const T* __restrict__ d, T* x, double* z64,
+                          const double* r1, const double* r2, double* partials, int nblocks,
+                          const int* done) {
+  using AT = typename Arith<T>::type;
+  if (done && *done) return;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    AT xv = (AT)x[i] + (AT)d[i];
+    x[i] = (T)xv;
+    if (z64) {
+      double z = (double)xv;
+      z64[i] = z;
+      acc[0] += z * r1[i];
+      if (r2) acc[1] += z * r2[i];
+    }
+  }
+  write_partials<T>(acc, partials, partials != nullptr, nblocks);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ public launchers
+
+void system_level(System& S, Level& Lv) {
+  Lv.N = S.N;
+  Lv.A = &S.A;
+  Lv.stencil = S.stencil;
+  Lv.st = S.stA;
+}
+
+void op_apply_d(const Level& Lv, const double* x, double* y, double* partials, int* nblocks,
+                cudaStream_t st) {
+  Epi<double> e = epi_base<double>(E_STORE);
+  e.y = y;
+  e.vin = x;
+  e.want_dot = partials != nullptr;
+  int nb = launch_op<double>(Lv, AMG_PREC_FP64, x, e, partials, st);
+  if (nblocks) *nblocks = nb;
+}
+
+void op_apply_d_done(const Level& Lv, const double* x, double* y, double* partials, int* nblocks,
+                     cudaStream_t st, const int* done) {
+  Epi<double> e = epi_base<double>(E_STORE);
+  e.y = y;
+  e.vin = x;
+  e.want_dot = partials != nullptr;
+  int nb = launch_op<double>(Lv, AMG_PREC_FP64, x, e, partials, st, done);
+  if (nblocks) *nblocks = nb;
+}
+
+template <typename T>
+void op_residual(const Level& Lv, int prec, const T* b, const T* x, T* r, cudaStream_t st) {
+  Epi<T> e = epi_base<T>(E_RESIDUAL);
+  e.y = r;
+  e.b = b;
+  launch_op<T>(Lv, prec, x, e, nullptr, st, Lv.done);
+}
+
+template <>
+void csr_spmv<double>(const Csr4& M, int prec, const double* x, double* y, bool accumulate,
+                      cudaStream_t st, const int* done) {
+  (void)prec;
+  Epi<double> e = epi_base<double>(accumulate ? E_ADD : E_STORE);
+  e.y = y;
+  launch_csr<double, double>(M, M.val.p, x, e, nullptr, st, done);
+}
+template <>
+void csr_spmv<float>(const Csr4& M, int prec, const float* x, float* y, bool accumulate,
+                     cudaStream_t st, const int* done) {
+  Epi<float> e = epi_base<float>(accumulate ? E_ADD : E_STORE);
+  e.y = y;
+  if (prec == AMG_PREC_BF16 && M.val16.p)
+    launch_csr<__nv_bfloat16, float>(M, M.val16.p, x, e, nullptr, st, done);
+  else
+    launch_csr<float, float>(M, M.val32.p, x, e, nullptr, st, done);
+}
+
+// Pre-smoothing from the zero initial guess.
+template <typename T>
+void smooth_pre_zero(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& cc,
+                     const T* b, T* x, T* r, T* d0, T* d1, cudaStream_t st, const double* b64) {
+  const int64_t N = Lv.N;
+  const T* sinv = level_sinv<T>(Lv);
+  T sinv_c = Lv.scalar_sinv ? (T)(1.0 / Lv.st.c0) : (T)0;
+  unsigned g = persistent_grid(N, 256, 8);
+  k_cheb_zero<T><<<g, 256, 0, st>>>(N, b, b64, const_cast<T*>(b), sinv, sinv_c,
+                                    (T)cc.inv_theta, r, d0, x, Lv.done);
+  FEM_CHECK_LAUNCH();
+  T* dold = d0;
+  T* dnew = d1;
+  for (int i = 1; i < cc.degree; i++) {
+    Epi<T> e = epi_base<T>(E_CHEB_STEP);
+    e.r = r;
+    e.dold = dold;
+    e.dnew = dnew;
+    e.x = x;
+    e.sinv = sinv;
+    e.sinv_c = sinv_c;
+    e.c1 = (T)cc.c1[i];
+    e.c2 = (T)cc.c2[i];
+    e.add_prev = 0;
+    launch_op<T>(Lv, prec, dold, e, nullptr, st, Lv.done);
+    std::swap(dold, dnew);
+  }
+  (void)o;
+}
+
+// Post-smoothing from the current x; the last kernel may emit z (FP64) and dots.
+template <typename T>
+void smooth_post(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& cc, const T* b,
+                 T* x, T* r, T* d0, T* d1, cudaStream_t st, const DotOut* dot) {
+  const int64_t N = Lv.N;
+  const T* sinv = level_sinv<T>(Lv);
+  T sinv_c = Lv.scalar_sinv ? (T)(1.0 / Lv.st.c0) : (T)0;
+  const int* done = Lv.done;
+  {
+    Epi<T> e = epi_base<T>(E_CHEB_INIT);
+    e.b = b;
+    e.r = r;
+    e.dnew = d0;
+    e.sinv = sinv;
+    e.sinv_c = sinv_c;
+    e.c2 = (T)cc.inv_theta;
+    launch_op<T>(Lv, prec, x, e, nullptr, st, done);
+  }
+  if (cc.degree == 1) {
+    unsigned g = persistent_grid(N, 256, 8);
+    k_add_out<T><<<g, 256, 0, st>>>(N, d0, x, dot ? dot->z64 : nullptr, dot ? dot->r1 : nullptr,
+                                    dot ? dot->r2 : nullptr, dot ? dot->partials : nullptr, g,
+                                    done);
+    FEM_CHECK_LAUNCH();
+    if (dot && dot->nblocks) *dot->nblocks = (int)g;
+    return;
+  }
+  T* dold = d0;
+  T* dnew = d1;
+  for (int i = 1; i < cc.degree; i++) {
+    const bool last = (i == cc.degree - 1);
+    Epi<T> e = epi_base<T>(E_CHEB_STEP);
+    e.r = r;
+    e.dold = dold;
+    e.dnew = dnew;
+    e.x = x;
+    e.sinv = sinv;
+    e.sinv_c = sinv_c;
+    e.c1 = (T)cc.c1[i];
+    e.c2 = (T)cc.c2[i];
+    e.add_prev = (i == 1);
+    double* partials = nullptr;
+    if (last && dot) {
+      e.z64 = dot->z64;
+      e.r1 = dot->r1;
+      e.r2 = dot->r2;
+      partials = dot->partials;
+    }
+    int nb = launch_op<T>(Lv, prec, dold, e, partials, st, done);
+    if (last && dot && dot->nblocks) *dot->nblocks = nb;
+    std::swap(dold, dnew);
+  }
+  (void)o;
+}
+
+template void op_residual<double>(const Level&, int, const double*, const double*, double*,
+                                  cudaStream_t);
+template void op_residual<float>(const Level&, int, const float*, const float*, float*,
+                                 cudaStream_t);
+template void smooth_pre_zero<double>(const Level&, int, const amg_opts&, const ChebCoef&,
+                                      const double*, double*, double*, double*, double*,
+                                      cudaStream_t, const double*);
+template void smooth_pre_zero<float>(const Level&, int, const amg_opts&, const ChebCoef&,
+                                     const float*, float*, float*, float*, float*, cudaStream_t,
+                                     const double*);
+template void smooth_post<double>(const Level&, int, const amg_opts&, const ChebCoef&,
+                                  const double*, double*, double*, double*, double*,
+                                  cudaStream_t, const DotOut*);
+template void smooth_post<float>(const Level&, int, const amg_opts&, const ChebCoef&,
+                                 const float*, float*, float*, float*, float*, cudaStream_t,
+                                 const DotOut*);
+
+// ------------------------------------------------------------------ reductions
+
+namespace {
+__global__ void k_finalize(const double* partials, int nblocks, int nv, double* out,
+                           const int* done) {
+  if (done && *done) return;
+  for (int k = 0; k < nv; k++) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) v[0] += partials[(int64_t)k * nblocks + i];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) out[k] = v[0];
+    __syncthreads();
+  }
+}
+}  // namespace
+
+void finalize_sums(const double* partials, int nblocks, int nv, double* out, cudaStream_t st,
+                   const int* done) {
+  k_finalize<<<1, 1024, 0, st>>>(partials, nblocks, nv, out, done);
+  FEM_CHECK_LAUNCH();
+}
+
+}  // namespace fem

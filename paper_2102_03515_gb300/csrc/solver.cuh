@@ -1,0 +1,132 @@
+// Internal data structures of the solver library and the launchers shared between
+// translation units.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fem {
+
+// 15-point stencil of a matrix on the uniform Kuhn grid of interior points (m per axis):
+// c0 at the centre, ca on the 6 axis neighbours +-e_d, cf on the 6 face diagonals
+// +-(e_a + e_b), cb on the 2 body diagonals +-(1,1,1); neighbours outside the interior
+// grid are Dirichlet zeros.
+struct Stencil {
+  int m = 0;
+  double c0 = 0, ca = 0, cf = 0, cb = 0;
+};
+
+struct System {
+  int n = 0;
+  int64_t N = 0;
+  double h = 0, rho = 0;
+  bool uniform = false;   // vertex coordinates are the uniform grid
+  bool stencil = false;   // finest operator applied matrix-free
+  bool pencil = false;    // K and M values kept
+  Stencil stA, stK, stM;  // uniform grid only
+  Csr4 A;                 // A = rho K + M (CSR4, FP64), pattern shared by Kv/Mv
+  DevBuf<double> Kv, Mv;  // pencil values on A's pattern
+  DevBuf<double> f;       // load vector
+  DevBuf<double> dinv;    // 1 / a_ii
+};
+
+struct Level {
+  int64_t N = 0;
+  bool stencil = false;
+  Stencil st;
+  Csr4 Aown;                 // coarse levels own their matrix
+  const Csr4* A = nullptr;   // level matrix (the system's for level 0)
+  Csr4 P, R;                 // N x Nc and Nc x N
+  DevBuf<int32_t> agg;       // aggregate of each node (-1 isolated)
+  DevBuf<double> dinv;       // 1 / a_ii
+  DevBuf<float> dinv32;
+  double lmax = 0;           // Gershgorin bound of D^-1 A
+  bool scalar_sinv = false;  // smoother diagonal is the constant 1/c0 (stencil, Chebyshev)
+  const int* done = nullptr; // early-exit flag of the running solve (null: none)
+  bool coarsest = false;
+  DevBuf<double> Ainv;       // coarsest: dense inverse, N x N
+  // pencil (batched solves): values of P^T K P and P^T M P on A's pattern
+  DevBuf<double> Kv, Mv;
+  DevBuf<float> Kv32, Mv32;
+  double stK_c[4] = {0, 0, 0, 0}, stM_c[4] = {0, 0, 0, 0};
+  // single-vector work space (FP64 or FP32 according to the hierarchy precision)
+  DevBuf<double> x, b, r, d0, d1;
+  DevBuf<float> xf, bf, rf, d0f, d1f;
+};
+
+struct Hierarchy {
+  System* sys = nullptr;
+  amg_opts o;
+  std::vector<std::unique_ptr<Level>> L;
+  double setup_ms = 0;
+  DevBuf<double> partials;   // per-block partial sums of fused reductions
+  DevBuf<double> scal;       // small device scalars
+};
+
+// Partial-sum buffer size (doubles) any fused kernel may need: 4 dot products per block.
+constexpr int kMaxPartialBlocks = 1 << 16;
+
+// ------------------------------------------------------------------ assembly (assemble.cu)
+void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem_target& t,
+                     const fem_assemble_opts& o, cudaStream_t st);
+
+// ------------------------------------------------------------------ operators (ops.cu)
+// Chebyshev coefficients of one smoothing application of degree k on [lmax/ratio, lmax].
+struct ChebCoef {
+  int degree = 0;
+  double inv_theta = 0;          // 1/theta for the first step
+  double c1[16] = {0}, c2[16] = {0};   // d_i = c1[i] d_{i-1} + c2[i] r_i, i >= 1
+};
+ChebCoef cheb_coefficients(double lmax, double ratio, int degree);
+
+// y = A x (FP64) for a level / system operator; optional <x, y> partials.
+void op_apply_d(const Level& Lv, const double* x, double* y, double* partials, int* nblocks,
+                cudaStream_t st);
+void op_apply_d_done(const Level& Lv, const double* x, double* y, double* partials,
+                     int* nblocks, cudaStream_t st, const int* done);
+// Non-owning finest-level view of a system's operator.
+void system_level(System& S, Level& Lv);
+// r = b - A x
+template <typename T>
+void op_residual(const Level& Lv, int prec, const T* b, const T* x, T* r, cudaStream_t st);
+// y (+)= M x for a CSR4 matrix M (restriction / prolongation).
+template <typename T>
+void csr_spmv(const Csr4& M, int prec, const T* x, T* y, bool accumulate, cudaStream_t st,
+              const int* done = nullptr);
+
+// Smoother pieces used by the V-cycle.
+template <typename T>
+void smooth_pre_zero(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& cc,
+                     const T* b, T* x, T* r, T* d0, T* d1, cudaStream_t st,
+                     const double* b64 = nullptr);
+struct DotOut {   // fused dot products of the final smoothing kernel
+  double* z64 = nullptr;        // output z (FP64)
+  const double* r1 = nullptr;   // <z, r1>
+  const double* r2 = nullptr;   // <z, r2>
+  double* partials = nullptr;
+  int* nblocks = nullptr;
+  const int* done = nullptr;
+};
+template <typename T>
+void smooth_post(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& cc, const T* b,
+                 T* x, T* r, T* d0, T* d1, cudaStream_t st, const DotOut* dot = nullptr);
+
+// ------------------------------------------------------------------ setup (amg_setup.cu)
+void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st);
+void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
+            cudaStream_t st, bool values = true);
+void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st);
+double gershgorin(const Csr4& A, const double* val, cudaStream_t st);
+void dense_inverse(const Csr4& A, const double* val, DevBuf<double>& Ainv, cudaStream_t st);
+
+// ------------------------------------------------------------------ V-cycle (vcycle.cu)
+void vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t st, const DotOut* dot);
+
+// ------------------------------------------------------------------ utilities
+void finalize_sums(const double* partials, int nblocks, int nv, double* out, cudaStream_t st,
+                   const int* done = nullptr);
+
+}  // namespace fem
