@@ -1,0 +1,386 @@
+"""Benchmark: AMG-preconditioned CG for (rho K + M) u = f on the 256^3 Kuhn mesh.
+
+One step = fem_assemble + amg_setup + pcg_solve to ||f - A u|| / ||f|| <= 1e-8 on the
+unit cube with n = 256 cells per side (255^3 = 16,581,375 unknowns), rho = h^2, smooth
+sine target (the smooth-target experiment of arXiv 2102.03515, Sec. 4.1, at h = 1/256),
+with the FP32 V-cycle inside FP64 flexible CG.  The metric is dof-iterations per second
+of the whole step (unknowns x CG iterations / step time; setup included, as the paper's
+timings include coarsening).  FP64 and BF16 V-cycles of the same workload are reported
+beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs independent replicas (one per GPU, launched by torchrun); nothing is sharded.
+--impl reference times the FP64 CPU oracle (assembly, smoothed-aggregation hierarchy and
+AMG-PCG in numpy/scipy) on a smaller mesh of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 256
+TOL = 1e-8
+ORACLE_N = 48          # reference-arm step: the same workload on a 48^3 mesh
+BASELINE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
+# dominant kernel: the FP64 15-point stencil A p of every CG iteration; 2 flops per stored
+# stencil entry, FP64 peak from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def oracle_sample(n: int) -> dict:
+    """Run the oracle's full path (assemble, SA hierarchy, AMG-PCG to 1e-8) at n^3."""
+    import numpy as np  # noqa: F401
+    import fem_workloads as W
+    from oracle import amg, core
+    t0 = time.perf_counter()
+    s = core.assemble(n, W.sine_target())
+    rho = 1.0 / n ** 2
+    A = s.A(rho)
+    H = amg.build_hierarchy(A)
+    x, it, rr, _ = amg.pcg(A, s.f, lambda r: amg.vcycle(H, r), tol=TOL)
+    dt = time.perf_counter() - t0
+    N = A.shape[0]
+    return {"n": n, "N": N, "iterations": it, "seconds": dt, "relres": rr,
+            "value": N * it / dt}
+
+
+def oracle_subprocess(n: int, timeout: float = 600.0) -> dict:
+    """The oracle in a single-threaded child process (started before any GPU work)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(%d)))" % (ROOT, n))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         env=env, timeout=timeout, cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+
+    import fem_workloads as W
+    from paper_2102_03515_gb300 import build as B
+    B.build()
+    import paper_2102_03515_gb300 as fa
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # oracle first: no process is forked after the GPU is initialised
+        try:
+            cpu = oracle_subprocess(BASELINE_N)
+        except Exception as e:  # the GPU number stands on its own
+            cpu = {"error": str(e)[:300]}
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    rho = 1.0 / n ** 2
+    N = (n - 1) ** 3
+    target = W.sine_target()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(precision: int, u, tol=TOL):
+        sys_ = fa.fem_assemble(n, rho, target)
+        h = fa.amg_setup(sys_, precision=precision)
+        res = fa.pcg_solve(sys_, h, None, u, tol=tol)[0]
+        info = fa.amg_hier_get_info(h)
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+        return res, info
+
+    def timed(precision: int, steps: int, warmup: int, u):
+        for _ in range(warmup):
+            step(precision, u)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = fa.fem_kernel_launches()
+        results = []
+        e0.record(stream)
+        for _ in range(steps):
+            results.append(step(precision, u))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        return ms, results, fa.fem_kernel_launches() - l0
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    # ---- headline: FP32 V-cycle inside FP64 flexible CG
+    with Clocks(local) as clk:
+        ms, results, launches = timed(fa.AMG_PREC_FP32, args.steps, args.warmup, u)
+    ms = max_over_ranks(ms)
+    its = results[-1][0]["iterations"]
+    relres = max(r[0]["relres"] for r in results)
+    u_mixed = u.clone()
+    value = world * N * its / (ms / 1e3)
+    solve_ms = statistics.mean(r[0]["solve_ms"] for r in results)
+    setup_ms = statistics.mean(r[1]["setup_ms"] for r in results)
+
+    # ---- FP64 V-cycle (plain FP64 AMG-PCG) and BF16-stored V-cycle on the same workload
+    extra = {}
+    for name, prec in (("fp64", fa.AMG_PREC_FP64), ("bf16", fa.AMG_PREC_BF16)):
+        ms2, res2, _ = timed(prec, max(1, args.steps // 2), 1, u)
+        ms2 = max_over_ranks(ms2)
+        it2 = res2[-1][0]["iterations"]
+        extra[name] = {"value": world * N * it2 / (ms2 / 1e3), "ms_per_step": ms2,
+                       "iterations": it2, "relres": res2[-1][0]["relres"],
+                       "solve_ms": res2[-1][0]["solve_ms"], "setup_ms": res2[-1][1]["setup_ms"]}
+        if name == "fp64":
+            u_fp64 = u.clone()
+        else:
+            u_bf16 = u.clone()
+    # reference solution: FP64 V-cycle to 1e-12 (the FP64 path is parity-tested against
+    # the oracle on smaller meshes); error of each solve against it
+    step(fa.AMG_PREC_FP64, u, tol=1e-12)
+    ref = u.clone()
+    nref = torch.linalg.norm(ref).item()
+    errs = {"fp32": torch.linalg.norm(u_mixed - ref).item() / nref,
+            "fp64": torch.linalg.norm(u_fp64 - ref).item() / nref,
+            "bf16": torch.linalg.norm(u_bf16 - ref).item() / nref}
+
+    # ---- end to end through the C ABI with host buffers: the solution is read back
+    host_u = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps // 2)
+    for _ in range(e2e_steps):
+        step(fa.AMG_PREC_FP32, u)
+        host_u.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps)
+
+    # ---- dominant kernel: the FP64 stencil apply of every CG iteration, timed on the
+    # stream it is launched on
+    sys_ = fa.fem_assemble(n, rho, target)
+    x = torch.randn(N, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        fa.fem_spmv(sys_, x, y)
+    reps = 20
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        fa.fem_spmv(sys_, x, y)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / reps
+    fa.fem_system_destroy(sys_)
+    # stored entries of the Kuhn stencil that are not padding: the centre plus, for each of
+    # the 14 neighbour offsets, the points whose neighbour is interior
+    m = n - 1
+    real_nnz = m ** 3 + 6 * m * m * (m - 1) + 6 * m * (m - 1) ** 2 + 2 * (m - 1) ** 3
+    flops = 2.0 * real_nnz
+    achieved = flops / (kms * 1e-3) / 1e12
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "PCG dof-iters/s: assemble + AMG setup + PCG to ||r||/||f|| <= 1e-8 at "
+                  "255^3 = 16,581,375 dofs",
+        "value": value,
+        "unit": "dof-iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 CG + f32 V-cycle",
+        "data": "synthetic (seeded, generated on the device)",
+        "config": {"workload": "unit-cube Kuhn mesh 256^3, 16,581,375 interior dofs, rho=h^2, "
+                               "sine target, SA-AMG V-cycle (Chebyshev 2) in flexible CG, "
+                               "tol 1e-8, FP32 V-cycle",
+                   "n": n, "rho": rho, "tol": TOL,
+                   "l2": "inputs larger than L2 (about 10 GB of matrices and vectors)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": its,
+        "relres": relres,
+        "time_to_tol_ms": ms,
+        "setup_ms": setup_ms,
+        "solve_ms": solve_ms,
+        "solve_dof_iters_per_s": N * its / (solve_ms / 1e3),
+        "fp64": extra["fp64"],
+        "bf16": extra["bf16"],
+        "err_vs_fp64_ref": errs,
+        "e2e": {"value": world * N * its / (e2e_ms / 1e3), "unit": "dof-iters/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * N,
+                "ms_per_step": e2e_ms},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_stencil<double> (q = A p, FP64 15-point stencil)",
+                     "kernel_ms": kms, "flops_per_launch": flops,
+                     "peak_source": "FP64 unit counts x max SM clock (no FP64 entry in the "
+                                    "measured peaks)"},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if cpu is not None:
+        if "value" in cpu:
+            line["cpu_baseline"] = {"value": cpu["value"], "unit": "dof-iters/s", "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": "oracle assemble + SA hierarchy + AMG-PCG to 1e-8 "
+                                              "on the %d^3 mesh (%d dofs, %d iterations, %.1f s)"
+                                              % (cpu["n"], cpu["N"], cpu["iterations"],
+                                                 cpu["seconds"])}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "dof-iters/s", "cores": 1,
+                                    "kind": "oracle", "sample": cpu.get("error", "")}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    vals, samples = [], []
+    for _ in range(args.warmup):
+        oracle_sample(ORACLE_N)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = oracle_sample(ORACLE_N)
+        vals.append(s["value"])
+        samples.append(s)
+    dt = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference",
+        "metric": "PCG dof-iters/s: assemble + AMG setup + PCG to ||r||/||f|| <= 1e-8 at "
+                  "255^3 = 16,581,375 dofs",
+        "value": value,
+        "unit": "dof-iters/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / max(1, args.steps),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "unit-cube Kuhn mesh, rho=h^2, sine target, SA-AMG V-cycle in "
+                               "CG, tol 1e-8; each step a bounded sample on the %d^3 mesh "
+                               "(%d dofs)" % (ORACLE_N, samples[0]["N"] if samples else 0),
+                   "n": ORACLE_N},
+        "cpu_baseline": {"value": value, "unit": "dof-iters/s", "cores": 1, "kind": "oracle",
+                         "sample": "oracle full path on the %d^3 mesh per step" % ORACLE_N},
+        "e2e": {"value": value, "unit": "dof-iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_CELLS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -256,6 +256,10 @@ const char* fem_autotune_report(void);
 /* Library version string. */
 const char* fem_version(void);
 
+/* Number of this library's kernels launched so far in the process (CUDA-graph replays
+ * count every kernel they run). */
+int64_t fem_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,7 @@ SIGNATURES = {
     "fem_last_error": (C.c_char_p, []),
     "fem_autotune_report": (C.c_char_p, []),
     "fem_version": (C.c_char_p, []),
+    "fem_kernel_launches": (C.c_int64, []),
 }
 
 
@@ -162,6 +163,10 @@ def fem_last_error() -> str:
 
 def fem_version() -> str:
     return lib().fem_version().decode()
+
+
+def fem_kernel_launches() -> int:
+    return int(lib().fem_kernel_launches())
 
 
 def fem_autotune_report() -> str:

@@ -762,9 +762,10 @@ void dense_inverse(const Csr4& A, const double* val, DevBuf<double>& Ainv, cudaS
   DevBuf<double> rowk(N, st), colk(N, st);
   for (int64_t k = 0; k < N; k++) {
     k_gj_save<<<grid_for(N, 256), 256, 0, st>>>(N, k, Ainv, rowk, colk);
+    FEM_CHECK_LAUNCH();
     k_gj_update<<<grid_for(N * N, 256), 256, 0, st>>>(N, k, Ainv, rowk, colk);
+    FEM_CHECK_LAUNCH();
   }
-  FEM_CHECK_LAUNCH();
 }
 
 namespace {
@@ -799,6 +800,7 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
   for (int round = 0; round < 10000; round++) {
     FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
     k_mis_m1<<<g, 256, 0, st>>>(N, sptr, scol, cur, seed_s, m1);
+    FEM_CHECK_LAUNCH();
     k_mis_m2<<<g, 256, 0, st>>>(N, sptr, scol, m1, seed_s, cur, nxt, und);
     FEM_CHECK_LAUNCH();
     std::swap(cur, nxt);
@@ -820,6 +822,7 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
   DevBuf<unsigned long long> err(1, st);
   FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
   k_agg_phase1<<<g, 256, 0, st>>>(N, sptr, scol, cur, rootid, R.agg, p1, err);
+  FEM_CHECK_LAUNCH();
   k_agg_phase2<<<g, 256, 0, st>>>(N, sptr, scol, p1, R.agg, err);
   FEM_CHECK_LAUNCH();
   unsigned long long he = 0;
@@ -922,6 +925,7 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     {
       DevBuf<double> dinvA(N, st);
       k_recip<<<g, 256, 0, st>>>(N, d, dinvA, nullptr);
+      FEM_CHECK_LAUNCH();
       k_scaled_filtered<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, ag.smask,
                                            dinvA, DF.col, DF.val);
       FEM_CHECK_LAUNCH();

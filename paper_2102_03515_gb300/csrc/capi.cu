@@ -1,5 +1,6 @@
 // extern "C" entry points of include/femamg.h: argument checks, handles, and the
 // translation of internal failures into fem_status codes with a per-thread message.
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
@@ -9,6 +10,10 @@
 namespace fem {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_now() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
@@ -56,6 +61,8 @@ extern "C" {
 const char* fem_last_error(void) { return g_last_error.c_str(); }
 
 const char* fem_version(void) { return "femamg 0.1 (sm_103a)"; }
+
+int64_t fem_kernel_launches(void) { return (int64_t)launches_now(); }
 
 fem_status fem_assemble(const fem_kuhn_desc* mesh, double rho, const fem_target* target,
                         const fem_assemble_opts* opts, void* stream, fem_system* out) {

@@ -33,7 +33,14 @@ void set_last_error(const std::string& msg);
                       std::to_string(__LINE__) + ")");                                   \
   } while (0)
 
-#define FEM_CHECK_LAUNCH() FEM_CUDA(cudaGetLastError())
+// Every kernel launch site ends with FEM_CHECK_LAUNCH(), which also counts the launch
+// (the count is reported by fem_kernel_launches()).
+void count_launches(long long n);
+#define FEM_CHECK_LAUNCH()            \
+  do {                                \
+    FEM_CUDA(cudaGetLastError());     \
+    ::fem::count_launches(1);         \
+  } while (0)
 
 #define FEM_REQUIRE(cond, status, msg)           \
   do {                                           \

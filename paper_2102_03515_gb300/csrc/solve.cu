@@ -22,6 +22,7 @@
 #include "solver.cuh"
 
 namespace fem {
+long long launches_now();
 namespace {
 
 // x = Ainv b on the coarsest level, FP64 arithmetic; warp per row.
@@ -425,18 +426,23 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
     int nb_pq = 0;
     op_apply_d_done(L0, W.p, W.q, W.partials, &nb_pq, st, done);
     k_fin_pq<<<1, 1024, 0, st>>>(W.partials, nb_pq, W.state);
+    FEM_CHECK_LAUNCH();
     k_update_xr<<<gv, 256, 0, st>>>(N, u, W.p, W.r, W.q, flexible ? W.rprev.p : nullptr, W.state,
                                     W.partials);
+    FEM_CHECK_LAUNCH();
     k_fin_rr<<<1, 1024, 0, st>>>(W.partials, gv, W.state);
     FEM_CHECK_LAUNCH();
     precondition(done);
     k_fin_rz<<<1, 1024, 0, st>>>(W.partials, nb_rz, W.state);
+    FEM_CHECK_LAUNCH();
     k_update_p<<<gv, 256, 0, st>>>(N, W.z, W.p, W.state);
     FEM_CHECK_LAUNCH();
   };
 
   bool use_graph = o.use_graph != 0;
+  long long per_iter = 0;
   if (use_graph) {
+    const long long c0 = launches_now();
     FEM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     try {
       iteration();
@@ -448,12 +454,15 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
     }
     FEM_CUDA(cudaStreamEndCapture(st, &W.graph));
     FEM_CUDA(cudaGraphInstantiate(&W.exec, W.graph, 0));
+    per_iter = launches_now() - c0;   // captured, not run: counted again per replay
+    count_launches(-per_iter);
   }
   FEM_CUDA(cudaEventRecord(W.t0, st));
   // r = f - A x0  (or f)
   if (o.use_x0) {
     op_apply_d(L0, u, W.r, nullptr, nullptr, st);
     k_sub<<<gv, 256, 0, st>>>(N, f, W.r);
+    FEM_CHECK_LAUNCH();
   } else {
     FEM_CUDA(cudaMemsetAsync(u, 0, 8 * N, st));
     k_copy<<<gv, 256, 0, st>>>(N, f, W.r);
@@ -478,9 +487,10 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
   bool finished = false;
   while (!finished) {
     for (int c = 0; c < chunk; c++) {
-      if (use_graph)
+      if (use_graph) {
         FEM_CUDA(cudaGraphLaunch(W.exec, st));
-      else
+        count_launches(per_iter);
+      } else
         iteration();
       launched++;
     }
@@ -507,6 +517,7 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
   // true residual
   op_apply_d(L0, u, W.q, nullptr, nullptr, st);
   k_sub<<<gv, 256, 0, st>>>(N, f, W.q);
+  FEM_CHECK_LAUNCH();
   k_dot_self<<<gv, 256, 0, st>>>(N, W.q, f, W.partials);
   FEM_CHECK_LAUNCH();
   finalize_sums(W.partials, gv, 2, W.sums, st);
