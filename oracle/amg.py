@@ -9,7 +9,7 @@ coarse operators by Galerkin's method A_c = P^T A P (Sec. 3.1).  Its coarsening
 aggregation; every rule below is stated in the docstring that applies it, and
 the CUDA library follows the same rules in code of its own:
 
-* strength: i != j is a strong pair iff |a_ij| >= theta * sqrt(a_ii a_jj) and a_ij != 0;
+* strength: i != j is a strong pair iff |a_ij| >= theta sqrt(a_ii) sqrt(a_jj) and a_ij != 0;
   a node without strong neighbours is *isolated* and is not aggregated;
 * distance-2 maximal independent set by priorities (see :func:`mis2`);
 * aggregates: each MIS-2 root with its strong neighbours, then every other node
@@ -17,7 +17,9 @@ the CUDA library follows the same rules in code of its own:
 * tentative P_t(i, agg(i)) = 1; filtered A_F keeps the diagonal and strong entries;
 * P = P_t - omega D^{-1} A_F P_t, omega = 4 / (3 lambda_F), lambda_F the Gershgorin
   bound max_i sum_j |A_F(i,j)| / a_ii;
-* coarsest level: dense inverse (from a Cholesky factorisation) in FP64;
+* coarsest level: dense inverse (from a Cholesky factorisation) in FP64 when it has at
+  most coarse_max unknowns; when coarsening stops above that size (every node isolated,
+  or too few aggregates) the coarsest level is solved by the smoother alone;
 * smoother: Chebyshev of degree k on D^{-1}A over [lambda/ratio, lambda] with lambda the
   Gershgorin bound of D^{-1}A, or one l1-Jacobi step.
 """
@@ -129,11 +131,13 @@ def diagonal(A) -> np.ndarray:
 # ------------------------------------------------------------- setup
 
 def strength(A, theta: float) -> np.ndarray:
-    """Boolean over A's stored entries: True where (i, j), i != j, is a strong pair."""
+    """Boolean over A's stored entries: True where (i, j), i != j, is a strong pair:
+    |a_ij| >= (theta sqrt(a_ii)) sqrt(a_jj)."""
     d = diagonal(A)
+    sq = np.sqrt(d)
     r = rows_of(A)
     c = A.indices
-    return (r != c) & (A.data != 0.0) & (np.abs(A.data) >= theta * np.sqrt(d[r] * d[c]))
+    return (r != c) & (A.data != 0.0) & (np.abs(A.data) >= (theta * sq[r]) * sq[c])
 
 
 def _segmax(vals, indptr):
@@ -286,7 +290,7 @@ def build_hierarchy(A, opts: dict | None = None, K=None, M=None):
                 last = True
         if last:
             L.coarsest = True
-            if n <= 4096:
+            if n <= o["coarse_max"]:
                 Lc = np.linalg.cholesky(Al.toarray())
                 Li = np.linalg.inv(Lc)
                 L.Ainv = Li.T @ Li

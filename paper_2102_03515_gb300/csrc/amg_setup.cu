@@ -3,7 +3,7 @@
 // The paper (Sec. 3.1) coarsens by red-black colouring with averaging interpolation and
 // forms A_c = P^T A P by Galerkin's method.  This library keeps the Galerkin product and
 // replaces the coarsening by smoothed aggregation with these rules:
-//  * strength: i != j strong iff a_ij != 0 and |a_ij| >= theta sqrt(a_ii a_jj);
+//  * strength: i != j strong iff a_ij != 0 and |a_ij| >= theta sqrt(a_ii) sqrt(a_jj);
 //    nodes without strong neighbours are isolated and not aggregated;
 //  * MIS-2: node keys (state, priority), IN > UNDECIDED > OUT, priority
 //    (fmix32(i xor s) >> 1) * 2^31 + i with fmix32 the MurmurHash3 finaliser and
@@ -14,7 +14,8 @@
 //    most strong edges to (ties: smaller aggregate id);
 //  * P = P_t - omega D^{-1} A_F P_t, A_F = diagonal + strong entries, omega = 4/(3 lambda_F),
 //    lambda_F = max_i sum_j |A_F(i,j)| / a_ii;
-//  * coarsest level: dense FP64 inverse (Gauss-Jordan, SPD so no pivoting).
+//  * coarsest level: dense FP64 inverse (Gauss-Jordan, SPD so no pivoting) when it has at
+//    most coarse_max unknowns, else (coarsening stopped early) the smoother alone.
 // Everything is deterministic: integer atomics only, fixed summation orders.
 #include <algorithm>
 #include <cmath>
@@ -198,18 +199,24 @@ __device__ __forceinline__ uint64_t prio_of(int64_t i, uint32_t s) {
 
 enum : uint8_t { ST_OUT = 0, ST_UND = 1, ST_IN = 2 };
 
+__global__ void k_sqrt(int64_t N, const double* d, double* sq) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N) sq[r] = sqrt(d[r]);
+}
+
+// strong pair: a_ij != 0 and |a_ij| >= (theta sqrt(a_ii)) sqrt(a_jj)
 __global__ void k_strength(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
-                           const double* d, double theta, uint8_t* smask, int64_t* scount) {
+                           const double* sq, double theta, uint8_t* smask, int64_t* scount) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   int64_t c = 0;
-  const double dr = d[r];
+  const double tr = theta * sq[r];
   for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
     int j = col[e];
     uint8_t s = 0;
     if (j >= 0 && j != r) {
       double a = v[e];
-      s = (a != 0.0) && (fabs(a) >= theta * sqrt(dr * d[j]));
+      s = (a != 0.0) && (fabs(a) >= tr * sq[j]);
     }
     smask[e] = s;
     c += s;
@@ -368,161 +375,181 @@ __global__ void k_smooth_p(int64_t N, const int32_t* rowptr, const int32_t* col,
 
 // ------------------------------------------------------------------ SpGEMM
 
-// Warp per output row; per-warp hash tables in shared memory.
-constexpr int HT = 1024;             // table slots per warp (power of two)
-constexpr int HMAX = HT / 2;         // distinct columns per row handled
-constexpr int SG_WARPS = 4;
-constexpr size_t SG_SMEM = SG_WARPS * (HT * 4 + HT * 4 + HMAX * 8 + HMAX * 4);
+// G lanes per output row (a "group"), 256 / G groups per block.  Each group owns a hash
+// table of HT slots in shared memory.  The count pass inserts every product column and
+// counts distinct keys; the fill pass inserts again, sorts the keys (rank sort), and sums
+// the products of each output entry in the order of A's row: lanes split one row of B,
+// whose columns are distinct, so each step adds at most once to an output entry.
+constexpr int SG_BLOCK = 256;
+constexpr int kHTMax = 1024;
 
 __device__ __forceinline__ uint32_t hslot(int key, int mask) {
   return ((uint32_t)key * 2654435761u) & (uint32_t)mask;
 }
 
-struct WarpTab {
-  int* keys;
-  int* rank;
-  double* acc;
-  int* list;
-};
-
-__device__ __forceinline__ WarpTab warp_tab(char* smem, int w) {
-  char* base = smem + (size_t)w * (HT * 4 + HT * 4 + HMAX * 8 + HMAX * 4);
-  WarpTab t;
-  t.keys = reinterpret_cast<int*>(base);
-  t.rank = reinterpret_cast<int*>(base + HT * 4);
-  t.acc = reinterpret_cast<double*>(base + HT * 8);
-  t.list = reinterpret_cast<int*>(base + HT * 8 + HMAX * 8);
-  return t;
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  if (G == 32) return 0xffffffffu;
+  const int lw = threadIdx.x & 31;
+  return ((1u << G) - 1u) << (lw & ~(G - 1));
 }
 
-// Insert every product column of row r of A*B into the table; returns the number of
-// distinct keys (lane-uniform), or HMAX+1 on overflow.
-__device__ int warp_insert(const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
-                           const int32_t* Bcol, int64_t r, const WarpTab& t, int tsize,
-                           int lane) {
-  const int mask = tsize - 1;
-  for (int q = lane; q < tsize; q += 32) t.keys[q] = -1;
-  __syncwarp();
+template <int G>
+__device__ __forceinline__ int group_sum(int v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+  return v;
+}
+
+template <int G>
+__device__ int group_insert(const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
+                            const int32_t* Bcol, int64_t r, int* keys, int ht, int lane,
+                            unsigned mask) {
+  for (int q = lane; q < ht; q += G) keys[q] = -1;
+  __syncwarp(mask);
   int count = 0;
-  for (int e = Arp[r]; e < Arp[r + 1]; e++) {
-    int k = Acol[e];
-    if (k < 0) continue;
-    for (int f = Brp[k] + lane; f < Brp[k + 1]; f += 32) {
-      int j = Bcol[f];
-      if (j < 0) continue;
-      uint32_t h = hslot(j, mask);
-      for (int probe = 0; probe < tsize; probe++) {
-        int old = atomicCAS(&t.keys[h], -1, j);
-        if (old == -1) {
-          count++;
-          break;
+  const int ea = Arp[r], e1 = Arp[r + 1];
+  // each round the G lanes load G entries of A's row and their B row ranges at once
+  for (int e0 = ea; e0 < e1; e0 += G) {
+    const int e = e0 + lane;
+    const int k = e < e1 ? Acol[e] : -1;
+    const int fb = k >= 0 ? Brp[k] : 0, fe = k >= 0 ? Brp[k + 1] : 0;
+    const int nt = min(G, e1 - e0);
+    for (int t = 0; t < nt; t++) {
+      const int b0 = __shfl_sync(mask, fb, t, G), b1 = __shfl_sync(mask, fe, t, G);
+      for (int f = b0 + lane; f < b1; f += G) {
+        const int j = Bcol[f];
+        if (j < 0) continue;
+        uint32_t h = hslot(j, ht - 1);
+        for (int probe = 0; probe < ht; probe++) {
+          const int old = atomicCAS(&keys[h], -1, j);
+          if (old == -1) {
+            count++;
+            break;
+          }
+          if (old == j) break;
+          h = (h + 1) & (ht - 1);
         }
-        if (old == j) break;
-        h = (h + 1) & mask;
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
-  __syncwarp();
+  count = group_sum<G>(count, mask);
+  __syncwarp(mask);
   return count;
 }
 
-__device__ __forceinline__ int table_size_for(int64_t ub) {
-  int64_t t = 64;
-  while (t < 2 * ub && t < HT) t <<= 1;
-  return (int)t;
-}
-
-__device__ int64_t row_products(const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
-                                int64_t r, int lane) {
-  int64_t ub = 0;
-  for (int e = Arp[r] + lane; e < Arp[r + 1]; e += 32) {
-    int k = Acol[e];
-    if (k >= 0) ub += Brp[k + 1] - Brp[k];
-  }
-  for (int o = 16; o > 0; o >>= 1) ub += __shfl_xor_sync(0xffffffffu, ub, o);
-  return ub;
-}
-
-__global__ void __launch_bounds__(32 * SG_WARPS)
-    k_spgemm_count(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
-                   const int32_t* Bcol, int64_t* cnt, unsigned long long* overflow) {
-  extern __shared__ char smem[];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * SG_WARPS + w;
+template <int G, int HT>
+__global__ void __launch_bounds__(SG_BLOCK)
+    k_sg_count(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
+               const int32_t* Bcol, int64_t* cnt) {
+  extern __shared__ __align__(16) char smem[];
+  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
+  const int64_t r = (int64_t)blockIdx.x * (SG_BLOCK / G) + grp;
   if (r >= nrows) return;
-  WarpTab t = warp_tab(smem, w);
-  int64_t ub = row_products(Arp, Acol, Brp, r, lane);
-  int c = warp_insert(Arp, Acol, Brp, Bcol, r, t, table_size_for(ub), lane);
-  if (lane == 0) {
-    if (c > HMAX) atomicAdd(overflow, 1ull);
-    cnt[r] = c;
-  }
+  int* keys = reinterpret_cast<int*>(smem) + grp * HT;
+  const int c = group_insert<G>(Arp, Acol, Brp, Bcol, r, keys, HT, lane, group_mask<G>());
+  if (lane == 0) cnt[r] = c;
 }
 
-// Columns (sorted) and, with values, the sums sum_e a_e b_(k_e, j) taken in the order of
-// A's row: lanes split a row of B, whose columns are distinct, so each step adds at most
-// once per output entry.
-__global__ void __launch_bounds__(32 * SG_WARPS)
-    k_spgemm_fill(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const double* Aval,
-                  const int32_t* Brp, const int32_t* Bcol, const double* Bval, const int32_t* Crp,
-                  int32_t* Ccol, double* Cval) {
-  extern __shared__ char smem[];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * SG_WARPS + w;
+template <int G, int HT>
+__global__ void __launch_bounds__(SG_BLOCK)
+    k_sg_fill(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const double* Aval,
+              const int32_t* Brp, const int32_t* Bcol, const double* Bval, const int32_t* Crp,
+              int32_t* Ccol, double* Cval) {
+  extern __shared__ __align__(16) char smem[];
+  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
+  const int64_t r = (int64_t)blockIdx.x * (SG_BLOCK / G) + grp;
   if (r >= nrows) return;
-  WarpTab t = warp_tab(smem, w);
-  int64_t ub = row_products(Arp, Acol, Brp, r, lane);
-  const int tsize = table_size_for(ub);
-  const int mask = tsize - 1;
-  int c = warp_insert(Arp, Acol, Brp, Bcol, r, t, tsize, lane);
-  // compact keys into list (order of table slots)
-  int base = 0;
-  for (int q0 = 0; q0 < tsize; q0 += 32) {
-    int q = q0 + lane;
-    int k = q < tsize ? t.keys[q] : -1;
-    unsigned bal = __ballot_sync(0xffffffffu, k >= 0);
-    if (k >= 0) t.list[base + __popc(bal & ((1u << lane) - 1))] = k;
-    base += __popc(bal);
+  const unsigned mask = group_mask<G>();
+  char* base = smem + (size_t)grp * (14 * HT);
+  int* keys = reinterpret_cast<int*>(base);
+  int* rank = keys + HT;
+  double* acc = reinterpret_cast<double*>(base + 8 * HT);
+  int* list = reinterpret_cast<int*>(base + 12 * HT);
+  const int c = group_insert<G>(Arp, Acol, Brp, Bcol, r, keys, HT, lane, mask);
+  // compact the keys (order of table slots)
+  const int shift = (threadIdx.x & 31) & ~(G - 1);
+  int nb = 0;
+  for (int q0 = 0; q0 < HT; q0 += G) {
+    const int k = keys[q0 + lane];
+    const unsigned bal = (__ballot_sync(mask, k >= 0) >> shift) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
+    if (k >= 0) list[nb + __popc(bal & ((1u << lane) - 1u))] = k;
+    nb += __popc(bal);
   }
-  __syncwarp();
+  __syncwarp(mask);
   // rank sort: position = number of smaller keys
   const int64_t out0 = Crp[r];
-  for (int a = lane; a < c; a += 32) {
-    int key = t.list[a];
+  for (int a = lane; a < c; a += G) {
+    const int key = list[a];
     int rk = 0;
-    for (int b = 0; b < c; b++) rk += t.list[b] < key;
+    for (int b = 0; b < c; b++) rk += list[b] < key;
     Ccol[out0 + rk] = key;
-    uint32_t h = hslot(key, mask);
-    while (t.keys[h] != key) h = (h + 1) & mask;
-    t.rank[h] = rk;
-    if (Cval) t.acc[rk] = 0.0;
+    uint32_t h = hslot(key, HT - 1);
+    while (keys[h] != key) h = (h + 1) & (HT - 1);
+    rank[h] = rk;
+    if (Cval) acc[rk] = 0.0;
   }
   const int64_t out1 = Crp[r + 1];
-  for (int64_t q = out0 + c + lane; q < out1; q += 32) {
+  for (int64_t q = out0 + c + lane; q < out1; q += G) {
     Ccol[q] = -1;
     if (Cval) Cval[q] = 0.0;
   }
-  __syncwarp();
+  __syncwarp(mask);
   if (!Cval) return;
+  const int ea = Arp[r], e1 = Arp[r + 1];
+  for (int e0 = ea; e0 < e1; e0 += G) {
+    const int e = e0 + lane;
+    const int k = e < e1 ? Acol[e] : -1;
+    const int fb = k >= 0 ? Brp[k] : 0, fe = k >= 0 ? Brp[k + 1] : 0;
+    const double av = k >= 0 ? Aval[e] : 0.0;
+    const int nt = min(G, e1 - e0);
+    for (int t = 0; t < nt; t++) {
+      const int b0 = __shfl_sync(mask, fb, t, G), b1 = __shfl_sync(mask, fe, t, G);
+      const double a = __shfl_sync(mask, av, t, G);
+      for (int f = b0 + lane; f < b1; f += G) {
+        const int j = Bcol[f];
+        if (j < 0) continue;
+        uint32_t h = hslot(j, HT - 1);
+        while (keys[h] != j) h = (h + 1) & (HT - 1);
+        const int rk = rank[h];
+        acc[rk] = __dadd_rn(acc[rk], __dmul_rn(a, Bval[f]));
+      }
+      __syncwarp(mask);
+    }
+  }
+  __syncwarp(mask);
+  for (int a = lane; a < c; a += G) Cval[out0 + a] = acc[a];
+}
+
+// Upper bound of the products of each row of A*B (stored entries of B's rows).
+__global__ void k_row_ub(int64_t nrows, const int32_t* Arp, const int32_t* Acol,
+                         const int32_t* Brp, int64_t* ub) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int64_t s = 0;
   for (int e = Arp[r]; e < Arp[r + 1]; e++) {
     int k = Acol[e];
-    if (k < 0) continue;
-    double a = Aval[e];
-    for (int f = Brp[k] + lane; f < Brp[k + 1]; f += 32) {
-      int j = Bcol[f];
-      if (j < 0) continue;
-      uint32_t h = hslot(j, mask);
-      while (t.keys[h] != j) h = (h + 1) & mask;
-      int rk = t.rank[h];
-      t.acc[rk] = __dadd_rn(t.acc[rk], __dmul_rn(a, Bval[f]));
-    }
-    __syncwarp();
+    if (k >= 0) s += Brp[k + 1] - Brp[k];
   }
-  for (int a = lane; a < c; a += 32) Cval[out0 + a] = t.acc[a];
+  ub[r] = s;
+}
+
+__global__ void k_row_len(int64_t nrows, const int32_t* rp, int64_t* len) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrows) len[r] = rp[r + 1] - rp[r];
+}
+
+__global__ void k_max_i64(const int64_t* v, int64_t n, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)v[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 // Numeric product on a known output pattern (sorted real columns per row).
+constexpr int SG_WARPS = 4;
 __global__ void __launch_bounds__(32 * SG_WARPS)
     k_spgemm_numeric(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const double* Aval,
                      const int32_t* Brp, const int32_t* Bcol, const double* Bval,
@@ -550,6 +577,69 @@ __global__ void __launch_bounds__(32 * SG_WARPS)
       Cval[lo] = __dadd_rn(Cval[lo], __dmul_rn(a, Bval[f]));
     }
     __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ smoothed prolongator
+
+// P = P_t - omega D^{-1} A_F P_t row by row: the row's diagonal and strong entries give
+// (agg(j), a_ij / a_ii); they are stably sorted by aggregate, each run is summed in A's
+// order, and the entry of the row's own aggregate gets 1 - omega * sum, the others
+// -omega * sum.  Count pass (Pcol == null) writes the number of distinct aggregates.
+constexpr int PS_MAX = 32;
+__global__ void k_psmooth(int64_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+                          const uint8_t* smask, const int32_t* agg, const double* dinv,
+                          double omega, int64_t* cnt, const int32_t* Prp, int32_t* Pcol,
+                          double* Pval, unsigned long long* overflow) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int32_t ar = agg[r];
+  int keys[PS_MAX];
+  double vals[PS_MAX];
+  int m = 0;
+  if (ar >= 0) {
+    const double di = dinv[r];
+    for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+      const int j = col[e];
+      if (j < 0 || (j != r && !smask[e])) continue;
+      const int a = agg[j];
+      if (a < 0) continue;
+      if (m == PS_MAX) {
+        atomicAdd(overflow, 1ull);
+        return;
+      }
+      const double v = __dmul_rn(val[e], di);
+      int q = m++;
+      while (q > 0 && keys[q - 1] > a) {
+        keys[q] = keys[q - 1];
+        vals[q] = vals[q - 1];
+        q--;
+      }
+      keys[q] = a;
+      vals[q] = v;
+    }
+  }
+  if (!Pcol) {
+    int d = 0;
+    for (int q = 0; q < m; q++) d += (q == 0 || keys[q] != keys[q - 1]);
+    cnt[r] = d;
+    return;
+  }
+  int64_t o = Prp[r];
+  const int64_t o1 = Prp[r + 1];
+  int q = 0;
+  while (q < m) {
+    const int key = keys[q];
+    double sum = vals[q++];
+    while (q < m && keys[q] == key) sum = __dadd_rn(sum, vals[q++]);
+    const double t = __dmul_rn(-omega, sum);
+    Pcol[o] = key;
+    Pval[o] = key == ar ? __dadd_rn(1.0, t) : t;
+    o++;
+  }
+  for (; o < o1; o++) {
+    Pcol[o] = -1;
+    Pval[o] = 0.0;
   }
 }
 
@@ -620,69 +710,146 @@ __global__ void k_dense_from_csr(int64_t N, const int32_t* rowptr, const int32_t
     if (col[e] >= 0) D[r * N + col[e]] += v[e];
 }
 
-// Gauss-Jordan step k of the in-place inversion (no pivoting: A is SPD).
-__global__ void k_gj_save(int64_t N, int64_t k, const double* D, double* rowk, double* colk) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  rowk[i] = D[k * N + i];
-  colk[i] = D[i * N + k];
-}
-__global__ void k_gj_update(int64_t N, int64_t k, double* D, const double* rowk,
-                            const double* colk) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N * N) return;
-  int64_t i = t / N, j = t % N;
-  double p = rowk[k];
-  double v;
-  if (i == k && j == k)
-    v = 1.0 / p;
-  else if (i == k)
-    v = rowk[j] / p;
-  else if (j == k)
-    v = -colk[i] / p;
-  else
-    v = D[t] - colk[i] * rowk[j] / p;
-  D[t] = v;
+// Gauss-Jordan step k (no pivoting: A is SPD), from D into E:
+//   E_kk = 1/p, E_kj = D_kj / p, E_ik = -D_ik / p, E_ij = D_ij - D_ik D_kj / p,  p = D_kk.
+__global__ void k_gj_step(int64_t N, int64_t k, const double* __restrict__ D, double* __restrict__ E) {
+  __shared__ double inv_p;
+  if (threadIdx.x == 0) inv_p = 1.0 / D[k * N + k];
+  __syncthreads();
+  const double ip = inv_p;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N * N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / N, j = t % N;
+    double v;
+    if (i == k && j == k)
+      v = ip;
+    else if (i == k)
+      v = D[t] * ip;
+    else if (j == k)
+      v = -D[t] * ip;
+    else
+      v = D[t] - D[i * N + k] * (D[k * N + j] * ip);
+    E[t] = v;
+  }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ host wrappers
 
+static int64_t max_of(const int64_t* v, int64_t n, cudaStream_t st) {
+  DevBuf<unsigned long long> m(1, st);
+  FEM_CUDA(cudaMemsetAsync(m, 0, 8, st));
+  if (n > 0) {
+    k_max_i64<<<persistent_grid(n, 256, 4), 256, 0, st>>>(v, n, m);
+    FEM_CHECK_LAUNCH();
+  }
+  unsigned long long h = 0;
+  FEM_CUDA(cudaMemcpyAsync(&h, m, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  return (int64_t)h;
+}
+
+static int pow2_at_least(int64_t v, int lo) {
+  int64_t t = lo;
+  while (t < v) t <<= 1;
+  return (int)t;
+}
+
+template <int G, int HT>
+static void sg_count_launch(int64_t nr, const Csr4& A, const Csr4& B, int64_t* cnt,
+                            cudaStream_t st) {
+  const size_t smem = (size_t)(SG_BLOCK / G) * HT * 4;
+  static bool attr = false;
+  if (!attr) {
+    FEM_CUDA(cudaFuncSetAttribute(k_sg_count<G, HT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    attr = true;
+  }
+  unsigned g = (unsigned)((nr + SG_BLOCK / G - 1) / (SG_BLOCK / G));
+  k_sg_count<G, HT><<<g, SG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, B.rowptr, B.col, cnt);
+  FEM_CHECK_LAUNCH();
+}
+
+template <int G, int HT>
+static void sg_fill_launch(int64_t nr, const Csr4& A, const double* Aval, const Csr4& B,
+                           const double* Bval, Csr4& C, double* Cval, cudaStream_t st) {
+  const size_t smem = (size_t)(SG_BLOCK / G) * HT * 14;
+  static bool attr = false;
+  if (!attr) {
+    FEM_CUDA(cudaFuncSetAttribute(k_sg_fill<G, HT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    attr = true;
+  }
+  unsigned g = (unsigned)((nr + SG_BLOCK / G - 1) / (SG_BLOCK / G));
+  k_sg_fill<G, HT><<<g, SG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, Aval, B.rowptr, B.col, Bval,
+                                              C.rowptr, C.col, Cval);
+  FEM_CHECK_LAUNCH();
+}
+
+template <int G>
+static void sg_count_ht(int ht, int64_t nr, const Csr4& A, const Csr4& B, int64_t* cnt,
+                        cudaStream_t st) {
+  switch (ht) {
+    case 64: sg_count_launch<G, 64>(nr, A, B, cnt, st); break;
+    case 128: sg_count_launch<G, 128>(nr, A, B, cnt, st); break;
+    case 256: sg_count_launch<G, 256>(nr, A, B, cnt, st); break;
+    case 512: sg_count_launch<G, 512>(nr, A, B, cnt, st); break;
+    default: sg_count_launch<G, 1024>(nr, A, B, cnt, st); break;
+  }
+}
+
+template <int G>
+static void sg_fill_ht(int ht, int64_t nr, const Csr4& A, const double* Aval, const Csr4& B,
+                       const double* Bval, Csr4& C, double* Cval, cudaStream_t st) {
+  switch (ht) {
+    case 64: sg_fill_launch<G, 64>(nr, A, Aval, B, Bval, C, Cval, st); break;
+    case 128: sg_fill_launch<G, 128>(nr, A, Aval, B, Bval, C, Cval, st); break;
+    case 256: sg_fill_launch<G, 256>(nr, A, Aval, B, Bval, C, Cval, st); break;
+    case 512: sg_fill_launch<G, 512>(nr, A, Aval, B, Bval, C, Cval, st); break;
+    default: sg_fill_launch<G, 1024>(nr, A, Aval, B, Bval, C, Cval, st); break;
+  }
+}
+
 void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
             cudaStream_t st, bool values) {
   const int64_t nr = A.nrows;
   C.nrows = A.nrows;
   C.ncols = B.ncols;
-  static bool attr = false;
-  if (!attr) {
-    FEM_CUDA(cudaFuncSetAttribute(k_spgemm_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SG_SMEM));
-    FEM_CUDA(cudaFuncSetAttribute(k_spgemm_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SG_SMEM));
-    attr = true;
-  }
-  DevBuf<int64_t> cnt(nr, st);
-  DevBuf<unsigned long long> ovf(1, st);
-  FEM_CUDA(cudaMemsetAsync(ovf, 0, 8, st));
-  unsigned g = (unsigned)((nr + SG_WARPS - 1) / SG_WARPS);
+  DevBuf<int64_t> cnt(nr > 0 ? nr : 1, st);
+  int G = 32, htc = 64;
   if (nr > 0) {
-    k_spgemm_count<<<g, 32 * SG_WARPS, SG_SMEM, st>>>(nr, A.rowptr, A.col, B.rowptr, B.col, cnt,
-                                                      ovf);
+    // group width from B's longest row, count-table size from the product bound
+    DevBuf<int64_t> tmp(std::max<int64_t>(nr, B.nrows) + 1, st);
+    k_row_len<<<grid_for(B.nrows, 256), 256, 0, st>>>(B.nrows, B.rowptr, tmp);
     FEM_CHECK_LAUNCH();
+    const int64_t maxb = max_of(tmp, B.nrows, st);
+    k_row_ub<<<grid_for(nr, 256), 256, 0, st>>>(nr, A.rowptr, A.col, B.rowptr, tmp);
+    FEM_CHECK_LAUNCH();
+    const int64_t maxub = max_of(tmp, nr, st);
+    G = maxb <= 4 ? 4 : (maxb <= 8 ? 8 : (maxb <= 16 ? 16 : 32));
+    htc = pow2_at_least(std::min<int64_t>(2 * maxub, kHTMax), 64);
+    switch (G) {
+      case 4: sg_count_ht<4>(htc, nr, A, B, cnt, st); break;
+      case 8: sg_count_ht<8>(htc, nr, A, B, cnt, st); break;
+      case 16: sg_count_ht<16>(htc, nr, A, B, cnt, st); break;
+      default: sg_count_ht<32>(htc, nr, A, B, cnt, st); break;
+    }
   }
-  unsigned long long hov = 0;
-  FEM_CUDA(cudaMemcpyAsync(&hov, ovf, 8, cudaMemcpyDeviceToHost, st));
-  FEM_CUDA(cudaStreamSynchronize(st));
-  FEM_REQUIRE(hov == 0, FEM_EUNSUPPORTED,
+  const int64_t maxc = nr > 0 ? max_of(cnt, nr, st) : 0;
+  FEM_REQUIRE(maxc <= kHTMax / 2, FEM_EUNSUPPORTED,
               "spgemm: a product row has more than 512 distinct columns");
   rowptr_from_counts(cnt, nr, C, st);
   if (values) C.val.alloc(C.nnz);
   if (nr > 0) {
-    k_spgemm_fill<<<g, 32 * SG_WARPS, SG_SMEM, st>>>(nr, A.rowptr, A.col, Aval, B.rowptr, B.col,
-                                                     Bval, C.rowptr, C.col,
-                                                     values ? C.val.p : nullptr);
-    FEM_CHECK_LAUNCH();
+    const int htf = pow2_at_least(2 * maxc, 64);
+    double* cv = values ? C.val.p : nullptr;
+    switch (G) {
+      case 4: sg_fill_ht<4>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
+      case 8: sg_fill_ht<8>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
+      case 16: sg_fill_ht<16>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
+      default: sg_fill_ht<32>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
+    }
   }
 }
 
@@ -757,15 +924,19 @@ void dense_inverse(const Csr4& A, const double* val, DevBuf<double>& Ainv, cudaS
   const int64_t N = A.nrows;
   Ainv.alloc(N * N);
   if (N == 0) return;
+  DevBuf<double> other(N * N, st);
   k_dense_from_csr<<<grid_for(N, 128), 128, 0, st>>>(N, A.rowptr, A.col, val, Ainv);
   FEM_CHECK_LAUNCH();
-  DevBuf<double> rowk(N, st), colk(N, st);
+  double* src = Ainv.p;
+  double* dst = other.p;
+  const unsigned g = persistent_grid(N * N, 256, 4);
   for (int64_t k = 0; k < N; k++) {
-    k_gj_save<<<grid_for(N, 256), 256, 0, st>>>(N, k, Ainv, rowk, colk);
+    k_gj_step<<<g, 256, 0, st>>>(N, k, src, dst);
     FEM_CHECK_LAUNCH();
-    k_gj_update<<<grid_for(N * N, 256), 256, 0, st>>>(N, k, Ainv, rowk, colk);
-    FEM_CHECK_LAUNCH();
+    std::swap(src, dst);
   }
+  if (src != Ainv.p)
+    FEM_CUDA(cudaMemcpyAsync(Ainv.p, src, 8 * N * N, cudaMemcpyDeviceToDevice, st));
 }
 
 namespace {
@@ -783,7 +954,10 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
   R.smask.alloc(A.nnz);
   DevBuf<int64_t> scount(N, st), sptr(N + 1, st);
   unsigned g = grid_for(N, 256);
-  k_strength<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, d, theta, R.smask, scount);
+  DevBuf<double> sq(N, st);
+  k_sqrt<<<g, 256, 0, st>>>(N, d, sq);
+  FEM_CHECK_LAUNCH();
+  k_strength<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, sq, theta, R.smask, scount);
   FEM_CHECK_LAUNCH();
   int64_t snnz = exclusive_scan(scount, N, sptr, st);
   DevBuf<int32_t> scol(snnz > 0 ? snnz : 1, st);
@@ -855,6 +1029,7 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
   H.L.clear();
   const int prec = o.precision;
   const bool lowp = prec != AMG_PREC_FP64;
+  Tracer tr(st);
   auto cur = std::make_unique<Level>();
   cur->A = &S.A;
   cur->stencil = S.stencil;
@@ -889,52 +1064,80 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       }
     }
 
+    tr.mark("level: diagonal, lambda, low precision");
     bool last = (N <= o.coarse_max) || (lev == o.max_levels - 1);
     Aggregation ag;
     if (!last) {
       uint32_t s = (uint32_t)(0x9E3779B9u * (uint32_t)(o.seed + lev + 1));
       ag = aggregate(*Acur, d, o.theta, s, st);
+      tr.mark("level: aggregation");
       if (ag.nagg == 0 || (double)ag.nagg >= 0.9 * (double)N) last = true;
     }
     if (last) {
       Lv.coarsest = true;
-      if (N <= 4096) dense_inverse(*Acur, Acur->val, Lv.Ainv, st);
+      if (N <= o.coarse_max) dense_inverse(*Acur, Acur->val, Lv.Ainv, st);
+      tr.mark("coarsest: dense inverse");
       H.L.push_back(std::move(cur));
       break;
     }
     // smoothed prolongator P = P_t - omega D^{-1} A_F P_t
     Lv.agg = std::move(ag.agg);
-    Csr4 Pt;
-    Pt.nrows = (int32_t)N;
-    Pt.ncols = (int32_t)ag.nagg;
-    Pt.nnz = 4 * N;
-    Pt.rowptr.alloc(N + 1);
-    Pt.col.alloc(4 * N);
-    Pt.val.alloc(4 * N);
-    k_tentative<<<grid_for(N + 1, 256), 256, 0, st>>>(N, Lv.agg, Pt.rowptr, Pt.col, Pt.val);
-    FEM_CHECK_LAUNCH();
     const double lamF = rowabs_max(*Acur, Acur->val, ag.smask, d, nullptr, st);
     const double omega = 4.0 / (3.0 * lamF);
-    Csr4 DF;
-    DF.nrows = DF.ncols = (int32_t)N;
-    DF.nnz = Acur->nnz;
-    DF.rowptr.alloc(N + 1);
-    DF.col.alloc(DF.nnz);
-    DF.val.alloc(DF.nnz);
-    FEM_CUDA(cudaMemcpyAsync(DF.rowptr, Acur->rowptr, 4 * (N + 1), cudaMemcpyDeviceToDevice, st));
+    DevBuf<double> dinvA(N, st);
+    k_recip<<<g, 256, 0, st>>>(N, d, dinvA, nullptr);
+    FEM_CHECK_LAUNCH();
+    bool done_p = false;
     {
-      DevBuf<double> dinvA(N, st);
-      k_recip<<<g, 256, 0, st>>>(N, d, dinvA, nullptr);
+      DevBuf<int64_t> pc(N, st);
+      DevBuf<unsigned long long> ovf(1, st);
+      FEM_CUDA(cudaMemsetAsync(ovf, 0, 8, st));
+      k_psmooth<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, ag.smask, Lv.agg, dinvA,
+                                   omega, pc, nullptr, nullptr, nullptr, ovf);
       FEM_CHECK_LAUNCH();
+      unsigned long long hov = 0;
+      FEM_CUDA(cudaMemcpyAsync(&hov, ovf, 8, cudaMemcpyDeviceToHost, st));
+      FEM_CUDA(cudaStreamSynchronize(st));
+      if (hov == 0) {
+        Lv.P.nrows = (int32_t)N;
+        Lv.P.ncols = (int32_t)ag.nagg;
+        rowptr_from_counts(pc, N, Lv.P, st);
+        Lv.P.val.alloc(Lv.P.nnz);
+        k_psmooth<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, ag.smask, Lv.agg,
+                                     dinvA, omega, nullptr, Lv.P.rowptr, Lv.P.col, Lv.P.val, ovf);
+        FEM_CHECK_LAUNCH();
+        done_p = true;
+      }
+    }
+    if (!done_p) {
+      // long rows: D^{-1} A_F as a CSR4 matrix times the tentative prolongator
+      Csr4 Pt;
+      Pt.nrows = (int32_t)N;
+      Pt.ncols = (int32_t)ag.nagg;
+      Pt.nnz = 4 * N;
+      Pt.rowptr.alloc(N + 1);
+      Pt.col.alloc(4 * N);
+      Pt.val.alloc(4 * N);
+      k_tentative<<<grid_for(N + 1, 256), 256, 0, st>>>(N, Lv.agg, Pt.rowptr, Pt.col, Pt.val);
+      FEM_CHECK_LAUNCH();
+      Csr4 DF;
+      DF.nrows = DF.ncols = (int32_t)N;
+      DF.nnz = Acur->nnz;
+      DF.rowptr.alloc(N + 1);
+      DF.col.alloc(DF.nnz);
+      DF.val.alloc(DF.nnz);
+      FEM_CUDA(cudaMemcpyAsync(DF.rowptr, Acur->rowptr, 4 * (N + 1), cudaMemcpyDeviceToDevice, st));
       k_scaled_filtered<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, ag.smask,
                                            dinvA, DF.col, DF.val);
       FEM_CHECK_LAUNCH();
+      spgemm(DF, DF.val, Pt, Pt.val, Lv.P, st, true);
+      Lv.P.ncols = (int32_t)ag.nagg;
+      k_smooth_p<<<g, 256, 0, st>>>(N, Lv.P.rowptr, Lv.P.col, Lv.P.val, Lv.agg, omega);
+      FEM_CHECK_LAUNCH();
     }
-    spgemm(DF, DF.val, Pt, Pt.val, Lv.P, st, true);
-    Lv.P.ncols = (int32_t)ag.nagg;
-    k_smooth_p<<<g, 256, 0, st>>>(N, Lv.P.rowptr, Lv.P.col, Lv.P.val, Lv.agg, omega);
-    FEM_CHECK_LAUNCH();
+    tr.mark("level: P = (I - w D^-1 A_F) P_t");
     transpose(Lv.P, Lv.R, ag.nagg, st);
+    tr.mark("level: R = P^T");
     if (lowp) {
       make_lowp(Lv.P, AMG_PREC_FP32, st);
       make_lowp(Lv.R, AMG_PREC_FP32, st);
@@ -946,8 +1149,10 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     // Galerkin coarse operator A_c = R (A P)  (Sec. 3.1)
     Csr4 AP;
     spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true);
+    tr.mark("level: A P (spgemm)");
     auto nxt = std::make_unique<Level>();
     spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true);
+    tr.mark("level: R (A P) (spgemm)");
     nxt->Aown.ncols = (int32_t)ag.nagg;
     nxt->A = &nxt->Aown;
     if (S.pencil) {
@@ -962,6 +1167,7 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       spgemm_numeric(Lv.R, Lv.R.val, AP, KP, nxt->Aown, nxt->Kv, st);
       spgemm_numeric(Lv.R, Lv.R.val, AP, MP, nxt->Aown, nxt->Mv, st);
     }
+    tr.mark("level: pencil / low precision copies");
     H.L.push_back(std::move(cur));
     cur = std::move(nxt);
   }

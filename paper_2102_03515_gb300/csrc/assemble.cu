@@ -129,45 +129,44 @@ __device__ void vertex_row(const Coords& C, int i, int j, int k, double kv[15], 
 }
 
 // One interior vertex's row on the uniform grid gives the stencils of K and M.
-__global__ void k_uniform_row(int n, double* out /* 30: K slots, M slots */) {
+__global__ void k_uniform_row(int n, double rho, double* out /* 45: K, M, A slots */) {
   Coords C{nullptr, n, 1.0 / n};
   double kv[15], mv[15];
   vertex_row(C, 1, 1, 1, kv, mv);
   for (int s = 0; s < 15; s++) {
     out[s] = kv[s];
     out[15 + s] = mv[s];
+    out[30 + s] = rho * kv[s] + mv[s];
   }
 }
 
-// CSR4 rows (16 slots) with values from per-type stencil coefficients.
-__global__ void k_csr_uniform(int m, double rho, Stencil sk, Stencil sm, int32_t* rowptr,
+// CSR4 rows (16 slots) with values from per-type stencil coefficients; one thread per
+// stored entry (coalesced stores): slot p of row r holds the p-th existing neighbour.
+__global__ void k_csr_uniform(int m, Stencil sa, Stencil sk, Stencil sm, int32_t* rowptr,
                               int32_t* col, double* aval, double* kval, double* mval) {
-  int64_t N = (int64_t)m * m * m;
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r > N) return;
-  rowptr[r] = (int32_t)(16 * r);
-  if (r == N) return;
-  int i = (int)(r % m), j = (int)((r / m) % m), k = (int)(r / ((int64_t)m * m));
-  double kt[4] = {sk.c0, sk.ca, sk.cf, sk.cb}, mt[4] = {sm.c0, sm.ca, sm.cf, sm.cb};
-  int64_t e = 16 * r;
-  int cnt = 0;
+  const int64_t N = (int64_t)m * m * m;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < N + 1) rowptr[e] = (int32_t)(16 * e);
+  if (e >= 16 * N) return;
+  const int64_t r = e >> 4;
+  const int p = (int)(e & 15);
+  const int i = (int)(r % m), j = (int)((r / m) % m), k = (int)(r / ((int64_t)m * m));
+  int cnt = 0, cl = -1, t = 0;
   for (int s = 0; s < 15; s++) {
-    int ii = i + kSlotOff[s][0], jj = j + kSlotOff[s][1], kk = k + kSlotOff[s][2];
+    const int ii = i + kSlotOff[s][0], jj = j + kSlotOff[s][1], kk = k + kSlotOff[s][2];
     if (ii < 0 || jj < 0 || kk < 0 || ii >= m || jj >= m || kk >= m) continue;
-    int t = kSlotType[s];
-    col[e + cnt] = (int32_t)(ii + (int64_t)m * (jj + (int64_t)m * kk));
-    double kvv = kt[t], mvv = mt[t];
-    aval[e + cnt] = rho * kvv + mvv;
-    if (kval) kval[e + cnt] = kvv;
-    if (mval) mval[e + cnt] = mvv;
+    if (cnt == p) {
+      cl = (int)(ii + (int64_t)m * (jj + (int64_t)m * kk));
+      t = kSlotType[s];
+    }
     cnt++;
   }
-  for (; cnt < 16; cnt++) {
-    col[e + cnt] = -1;
-    aval[e + cnt] = 0.0;
-    if (kval) kval[e + cnt] = 0.0;
-    if (mval) mval[e + cnt] = 0.0;
-  }
+  const double at[4] = {sa.c0, sa.ca, sa.cf, sa.cb}, kt[4] = {sk.c0, sk.ca, sk.cf, sk.cb},
+               mt[4] = {sm.c0, sm.ca, sm.cf, sm.cb};
+  col[e] = cl;
+  aval[e] = cl >= 0 ? at[t] : 0.0;
+  if (kval) kval[e] = cl >= 0 ? kt[t] : 0.0;
+  if (mval) mval[e] = cl >= 0 ? mt[t] : 0.0;
 }
 
 // CSR4 rows on a general (jittered) vertex grid with Kuhn connectivity.
@@ -276,64 +275,80 @@ __global__ void k_target_tables(TargetDev T, int n, int nterms, double* tab, dou
 // Per-cube load contributions: cube c gets cf[c*8 + local vertex] with local vertex
 // dx + 2 dy + 4 dz, summing w_q |tau| ubar(x_q) lambda_a(x_q) over its 6 tets and the
 // 4 points of each (Hammer-Stroud, barycentric (A,B,B,B) permutations, weight 1/4).
+// Loops over tets and points are unrolled so that every local index is static.
 template <bool UNIFORM>
 __global__ void k_cube_load(int n, const double* xyz, TargetDev T, const double* tab,
                             const double* alpha, int nterms, double* cf) {
+  constexpr int PP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   int64_t nc = (int64_t)n * n * n;
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int ci = (int)(c % n), cj = (int)((c / n) % n), ck = (int)(c / ((int64_t)n * n));
   const double A = (5.0 + 3.0 * sqrt(5.0)) / 20.0, B = (5.0 - sqrt(5.0)) / 20.0;
   double acc[8];
+#pragma unroll
   for (int a = 0; a < 8; a++) acc[a] = 0.0;
   double Xc[8][3];
   if (!UNIFORM) {
     Coords C{xyz, n, 1.0 / n};
+#pragma unroll
     for (int a = 0; a < 8; a++) C.get(ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1), Xc[a]);
   }
   const double h = 1.0 / n;
   const int cc[3] = {ci, cj, ck};
+#pragma unroll
   for (int p = 0; p < 6; p++) {
     int lv[4];
     lv[0] = 0;
-    for (int s = 0; s < 3; s++) lv[s + 1] = lv[s] | (1 << kPerm[p][s]);
-    double vol;
-    if (UNIFORM) {
-      vol = h * h * h / 6.0;
-    } else {
+#pragma unroll
+    for (int s = 0; s < 3; s++) lv[s + 1] = lv[s] | (1 << PP[p][s]);
+    double vol = 0.0;
+    if (!UNIFORM) {
       double X[4][3], g[4][3];
+#pragma unroll
       for (int a = 0; a < 4; a++)
+#pragma unroll
         for (int d = 0; d < 3; d++) X[a][d] = Xc[lv[a]][d];
       vol = fabs(tet_grads(X, g)) / 6.0;
     }
+    double uq[4];
+#pragma unroll
     for (int q = 0; q < 4; q++) {
       double mu[4] = {B, B, B, B};
       mu[q] = A;
       double u;
       if (UNIFORM) {
-        // offset index along kPerm[p][0] (1 - mu0), kPerm[p][1] (mu2 + mu3), kPerm[p][2] (mu3)
+        // offset index along PP[p][0] (1 - mu0), PP[p][1] (mu2 + mu3), PP[p][2] (mu3)
         int oax[3];
-        oax[kPerm[p][0]] = (q == 0) ? 4 : 5;
-        oax[kPerm[p][1]] = (q >= 2) ? 3 : 2;
-        oax[kPerm[p][2]] = (q == 3) ? 1 : 0;
+        oax[PP[p][0]] = (q == 0) ? 4 : 5;
+        oax[PP[p][1]] = (q >= 2) ? 3 : 2;
+        oax[PP[p][2]] = (q == 3) ? 1 : 0;
         u = 0.0;
         for (int t = 0; t < nterms; t++) {
-          double g0 = tab[((t * 3 + 0) * n + cc[0]) * 6 + oax[0]];
-          double g1 = tab[((t * 3 + 1) * n + cc[1]) * 6 + oax[1]];
-          double g2 = tab[((t * 3 + 2) * n + cc[2]) * 6 + oax[2]];
+          double g0 = __ldg(tab + ((t * 3 + 0) * n + cc[0]) * 6 + oax[0]);
+          double g1 = __ldg(tab + ((t * 3 + 1) * n + cc[1]) * 6 + oax[1]);
+          double g2 = __ldg(tab + ((t * 3 + 2) * n + cc[2]) * 6 + oax[2]);
           u += alpha[t] * (g0 * g1 * g2);
         }
       } else {
         double x[3] = {0, 0, 0};
+#pragma unroll
         for (int a = 0; a < 4; a++)
+#pragma unroll
           for (int d = 0; d < 3; d++) x[d] += mu[a] * Xc[lv[a]][d];
         u = target_eval(T, x[0], x[1], x[2]);
       }
-      double wu = 0.25 * u;
-      for (int a = 0; a < 4; a++) acc[lv[a]] += vol * (wu * mu[a]);
+      uq[q] = u;
     }
+    // sum_q (|tau|/4) u_q lambda_a(x_q) with lambda_a(x_q) = B + (A - B) [q == a]
+    const double S = (uq[0] + uq[1]) + (uq[2] + uq[3]);
+    const double w = UNIFORM ? 1.0 : 0.25 * vol;
+#pragma unroll
+    for (int a = 0; a < 4; a++) acc[lv[a]] += w * (B * S + (A - B) * uq[a]);
   }
-  for (int a = 0; a < 8; a++) cf[8 * c + a] = acc[a];
+  const double scale = UNIFORM ? 0.25 * (h * h * h / 6.0) : 1.0;
+#pragma unroll
+  for (int a = 0; a < 8; a++) cf[8 * c + a] = scale * acc[a];
 }
 
 __global__ void k_gather_load(int n, const double* cf, double* f) {
@@ -387,6 +402,7 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
   S.stencil = S.uniform && o.format != FEM_FMT_CSR;
   S.pencil = o.keep_pencil != 0;
 
+  Tracer tr(st);
   // target on the device
   DevBuf<double> tc, tw, ta;
   TargetDev T{t.kind, 0, nullptr, nullptr, nullptr, t.lo, t.hi};
@@ -415,10 +431,10 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
   }
   DevBuf<double> xyz;
   if (S.uniform) {
-    DevBuf<double> row(30, st);
-    k_uniform_row<<<1, 1, 0, st>>>(n, row);
+    DevBuf<double> row(45, st);
+    k_uniform_row<<<1, 1, 0, st>>>(n, rho, row);
     FEM_CHECK_LAUNCH();
-    double hrow[30];
+    double hrow[45];
     FEM_CUDA(cudaMemcpyAsync(hrow, row, sizeof(hrow), cudaMemcpyDeviceToHost, st));
     FEM_CUDA(cudaStreamSynchronize(st));
     // per-type coefficients: centre slot 7, axis +x slot 8, face (1,1,0) slot 10,
@@ -426,7 +442,7 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
     const int rep[4] = {7, 8, 10, 14};
     const int type_of[15] = {3, 2, 2, 1, 2, 1, 1, 0, 1, 1, 2, 1, 2, 2, 3};
     for (int s = 0; s < 15; s++) {
-      for (int w = 0; w < 2; w++) {
+      for (int w = 0; w < 3; w++) {
         double a = hrow[15 * w + s], b = hrow[15 * w + rep[type_of[s]]];
         double scale = fabs(hrow[15 * w + 7]);
         FEM_REQUIRE(fabs(a - b) <= 1e-12 * scale, FEM_EDEVCHECK,
@@ -444,13 +460,9 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
     };
     S.stK = mk(0);
     S.stM = mk(1);
-    S.stA.m = m;
-    S.stA.c0 = rho * S.stK.c0 + S.stM.c0;
-    S.stA.ca = rho * S.stK.ca + S.stM.ca;
-    S.stA.cf = rho * S.stK.cf + S.stM.cf;
-    S.stA.cb = rho * S.stK.cb + S.stM.cb;
-    k_csr_uniform<<<grid_for(N + 1, 256), 256, 0, st>>>(m, rho, S.stK, S.stM, S.A.rowptr,
-                                                         S.A.col, S.A.val, S.Kv.p, S.Mv.p);
+    S.stA = mk(2);
+    k_csr_uniform<<<grid_for(16 * N + 1, 256), 256, 0, st>>>(m, S.stA, S.stK, S.stM, S.A.rowptr,
+                                                              S.A.col, S.A.val, S.Kv.p, S.Mv.p);
     FEM_CHECK_LAUNCH();
   } else {
     int64_t nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
@@ -461,6 +473,7 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
     FEM_CHECK_LAUNCH();
   }
 
+  tr.mark("assemble: operator (CSR4)");
   // load vector
   S.f.alloc(N);
   int64_t ncube = (int64_t)n * n * n;
@@ -480,6 +493,7 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
   k_gather_load<<<grid_for(N, 256), 256, 0, st>>>(n, cf, S.f);
   FEM_CHECK_LAUNCH();
 
+  tr.mark("assemble: load vector");
   S.dinv.alloc(N);
   k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);
   FEM_CHECK_LAUNCH();

@@ -1,6 +1,9 @@
 // extern "C" entry points of include/femamg.h: argument checks, handles, and the
 // translation of internal failures into fem_status codes with a per-thread message.
 #include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -11,6 +14,42 @@ namespace fem {
 
 static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
+
+Tracer::Tracer(cudaStream_t s) : st(s) {
+  const char* e = std::getenv("FEM_TRACE");
+  on = e && e[0] == '1';
+  if (on) {
+    cudaStreamSynchronize(st);
+    t = std::chrono::duration<double, std::milli>(
+            std::chrono::steady_clock::now().time_since_epoch()).count();
+  }
+}
+
+void Tracer::mark(const char* what) {
+  if (!on) return;
+  cudaStreamSynchronize(st);
+  double now = std::chrono::duration<double, std::milli>(
+                   std::chrono::steady_clock::now().time_since_epoch()).count();
+  std::fprintf(stderr, "[fem] %-40s %9.3f ms\n", what, now - t);
+  t = now;
+}
+
+void init_memory_pool() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  FEM_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  FEM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = UINT64_MAX;
+  FEM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  done = true;
+}
+
+cudaStream_t& current_alloc_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
 
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_now() { return g_launches.load(std::memory_order_relaxed); }
@@ -67,10 +106,12 @@ int64_t fem_kernel_launches(void) { return (int64_t)launches_now(); }
 fem_status fem_assemble(const fem_kuhn_desc* mesh, double rho, const fem_target* target,
                         const fem_assemble_opts* opts, void* stream, fem_system* out) {
   return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
     FEM_REQUIRE(mesh && target && out, FEM_EINVAL, "fem_assemble: null argument");
     *out = nullptr;
     fem_assemble_opts o{FEM_FMT_AUTO, 0};
     if (opts) o = *opts;
+    init_memory_pool();
     auto* h = new fem_system_s();
     try {
       assemble_system(h->S, *mesh, rho, *target, o, as_stream(stream));
@@ -131,6 +172,7 @@ fem_status fem_system_export(fem_system sys, int32_t which, int32_t* rowptr_dev,
 
 fem_status fem_spmv(fem_system sys, const double* x_dev, double* y_dev, void* stream) {
   return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
     FEM_REQUIRE(sys && x_dev && y_dev, FEM_EINVAL, "fem_spmv: null argument");
     Level L;
     system_level(sys->S, L);
@@ -160,6 +202,7 @@ void amg_default_opts(amg_opts* o) {
 
 fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hier* out) {
   return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
     FEM_REQUIRE(sys && out, FEM_EINVAL, "amg_setup: null argument");
     *out = nullptr;
     amg_opts o;
@@ -249,6 +292,7 @@ fem_status amg_hier_export(amg_hier h, int32_t level, int32_t which, int32_t* ro
 
 fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stream) {
   return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
     FEM_REQUIRE(h && r_dev && z_dev, FEM_EINVAL, "amg_vcycle: null argument");
     vcycle(h->H, r_dev, z_dev, as_stream(stream), nullptr);
     FEM_CUDA(cudaStreamSynchronize(as_stream(stream)));
@@ -277,6 +321,7 @@ fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double*
                      int32_t nrhs, const double* rho_k_host, const pcg_opts* opts, void* stream,
                      pcg_result* res) {
   return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
     FEM_REQUIRE(sys && u_dev && res, FEM_EINVAL, "pcg_solve: null argument");
     FEM_REQUIRE(nrhs >= 1, FEM_EINVAL, "pcg_solve: nrhs >= 1");
     FEM_REQUIRE(!hier || hier->sys == sys, FEM_EINVAL, "pcg_solve: hierarchy of another system");

@@ -49,6 +49,15 @@ void count_launches(long long n);
 
 // ------------------------------------------------------------------ buffers
 
+// Stream on which DevBuf::alloc places its stream-ordered allocations (thread-local; the
+// entry points set it to the caller's stream for the duration of a call).
+cudaStream_t& current_alloc_stream();
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s) : prev(current_alloc_stream()) { current_alloc_stream() = s; }
+  ~StreamScope() { current_alloc_stream() = prev; }
+};
+
 // Owning device buffer.  Allocations are stream-ordered when a stream is given.
 template <typename T>
 struct DevBuf {
@@ -76,11 +85,7 @@ struct DevBuf {
     std::swap(s, o.s);
     std::swap(async, o.async);
   }
-  void alloc(size_t count) {
-    release();
-    n = count;
-    if (count) FEM_CUDA(cudaMalloc(&p, count * sizeof(T)));
-  }
+  void alloc(size_t count) { alloc_async(count, current_alloc_stream()); }
   void alloc_async(size_t count, cudaStream_t st) {
     release();
     n = count;
@@ -119,6 +124,22 @@ struct Csr4 {
     return rowptr.bytes() + col.bytes() + val.bytes() + val32.bytes() + val16.bytes();
   }
 };
+
+// ------------------------------------------------------------------ tracing
+
+// Phase timer enabled by the environment variable FEM_TRACE=1: each mark synchronises
+// the stream and prints the wall time since the previous mark to stderr.
+struct Tracer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  double t = 0;
+  explicit Tracer(cudaStream_t s);
+  void mark(const char* what);
+};
+
+// Keep freed stream-ordered allocations in the device's default pool (no unmapping at
+// every synchronisation): repeated set-ups reuse the same memory.
+void init_memory_pool();
 
 // ------------------------------------------------------------------ launch helpers
 
