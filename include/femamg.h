@@ -116,6 +116,11 @@ typedef struct {
 
 fem_status fem_system_get_info(fem_system sys, fem_system_info* info);
 
+/* Load vector of another target on the same mesh: f_dev[i] = int ubar phi_i (the rule of
+ * fem_assemble), length N.  Used to feed many targets to one batch. */
+fem_status fem_assemble_rhs(fem_system sys, const fem_target* target, double* f_dev,
+                            void* stream);
+
 /* Copy the assembled load vector f (length N) into f_dev. */
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream);
 

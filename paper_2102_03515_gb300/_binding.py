@@ -90,6 +90,7 @@ SIGNATURES = {
     "fem_assemble": (C.c_int, [P(KuhnDesc), C.c_double, P(Target), P(AssembleOpts), VP, P(VP)]),
     "fem_system_get_info": (C.c_int, [VP, P(SystemInfo)]),
     "fem_system_get_rhs": (C.c_int, [VP, VP, VP]),
+    "fem_assemble_rhs": (C.c_int, [VP, P(Target), VP, VP]),
     "fem_system_export": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
     "fem_spmv": (C.c_int, [VP, VP, VP, VP]),
     "fem_system_destroy": (None, [VP]),
@@ -175,17 +176,7 @@ def fem_autotune_report() -> str:
 
 # ------------------------------------------------------------------ system
 
-def fem_assemble(n: int, rho: float, target: dict, xyz=None, fmt: int = FEM_FMT_AUTO,
-                 keep_pencil: bool = False, stream=None):
-    """Assemble (rho K + M) u = f on the Kuhn mesh; returns the system handle."""
-    keep = []
-    d = KuhnDesc()
-    d.n = n
-    if xyz is not None:
-        xa = np.ascontiguousarray(xyz, dtype=np.float64)
-        assert xa.size == 3 * (n + 1) ** 3
-        keep.append(xa)
-        d.xyz_host = _dp(xa)
+def _target(target: dict, keep: list) -> Target:
     t = Target()
     t.kind = FEM_TARGET[target["kind"]]
     t.lo = float(target.get("lo", 0.25))
@@ -197,6 +188,27 @@ def fem_assemble(n: int, rho: float, target: dict, xyz=None, fmt: int = FEM_FMT_
         keep += [c, w, a]
         t.nb = len(w)
         t.centers_host, t.widths_host, t.amps_host = _dp(c), _dp(w), _dp(a)
+    return t
+
+
+def fem_assemble_rhs(sys, target: dict, f, stream=None):
+    keep = []
+    t = _target(target, keep)
+    _check(lib().fem_assemble_rhs(sys, C.byref(t), _ptr(f), _stream(stream)), "fem_assemble_rhs")
+
+
+def fem_assemble(n: int, rho: float, target: dict, xyz=None, fmt: int = FEM_FMT_AUTO,
+                 keep_pencil: bool = False, stream=None):
+    """Assemble (rho K + M) u = f on the Kuhn mesh; returns the system handle."""
+    keep = []
+    d = KuhnDesc()
+    d.n = n
+    if xyz is not None:
+        xa = np.ascontiguousarray(xyz, dtype=np.float64)
+        assert xa.size == 3 * (n + 1) ** 3
+        keep.append(xa)
+        d.xyz_host = _dp(xa)
+    t = _target(target, keep)
     o = AssembleOpts(fmt, 1 if keep_pencil else 0)
     h = VP()
     _check(lib().fem_assemble(C.byref(d), rho, C.byref(t), C.byref(o), _stream(stream),

@@ -376,7 +376,62 @@ __global__ void k_diag_inv(int64_t N, const int32_t* rowptr, const int32_t* col,
   dinv[r] = 1.0 / d;
 }
 
+// f_i = sum over tets of the 4-point rule applied to ubar phi_i (per-cube partial sums,
+// then a gather over the 8 cubes around each vertex in a fixed order).
+void load_vector(System& S, const TargetDev& T, const fem_target& t, double* f, cudaStream_t st) {
+  const int n = S.n;
+  const int64_t N = S.N;
+  int64_t ncube = (int64_t)n * n * n;
+  DevBuf<double> cf(8 * ncube, st);
+  if (S.uniform) {
+    int nterms = (t.kind == FEM_TARGET_BUMPS) ? t.nb : (t.kind == FEM_TARGET_SINE_PLUS_ONE ? 2 : 1);
+    DevBuf<double> tab((size_t)nterms * 3 * n * 6, st), alpha(nterms, st);
+    int total = nterms * 3 * n * 6;
+    k_target_tables<<<grid_for(total, 256), 256, 0, st>>>(T, n, nterms, tab, alpha);
+    FEM_CHECK_LAUNCH();
+    k_cube_load<true><<<grid_for(ncube, 128), 128, 0, st>>>(n, nullptr, T, tab, alpha, nterms, cf);
+    FEM_CHECK_LAUNCH();
+  } else {
+    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, S.xyz, T, nullptr, nullptr, 0, cf);
+    FEM_CHECK_LAUNCH();
+  }
+  k_gather_load<<<grid_for(N, 256), 256, 0, st>>>(n, cf, f);
+  FEM_CHECK_LAUNCH();
+}
+
+struct TargetHolder {
+  DevBuf<double> tc, tw, ta;
+  TargetDev T;
+};
+
+void target_to_device(const fem_target& t, TargetHolder& h, cudaStream_t st) {
+  FEM_REQUIRE(t.kind >= 0 && t.kind <= 3, FEM_EINVAL, "unknown target kind");
+  FEM_REQUIRE(t.kind != FEM_TARGET_BUMPS || (t.nb >= 1 && t.nb <= 64 && t.centers_host &&
+                                             t.widths_host && t.amps_host),
+              FEM_EINVAL, "bumps need 1..64 centres/widths/amplitudes");
+  h.T = TargetDev{t.kind, 0, nullptr, nullptr, nullptr, t.lo, t.hi};
+  if (t.kind == FEM_TARGET_BUMPS) {
+    h.tc.alloc_async(3 * t.nb, st);
+    h.tw.alloc_async(t.nb, st);
+    h.ta.alloc_async(t.nb, st);
+    FEM_CUDA(cudaMemcpyAsync(h.tc, t.centers_host, 24 * t.nb, cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(h.tw, t.widths_host, 8 * t.nb, cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(h.ta, t.amps_host, 8 * t.nb, cudaMemcpyHostToDevice, st));
+    h.T.nb = t.nb;
+    h.T.c = h.tc;
+    h.T.w = h.tw;
+    h.T.a = h.ta;
+  }
+}
+
 }  // namespace
+
+void assemble_rhs(System& S, const fem_target& t, double* f, cudaStream_t st) {
+  TargetHolder th;
+  target_to_device(t, th, st);
+  load_vector(S, th.T, t, f, st);
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
 
 void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem_target& t,
                      const fem_assemble_opts& o, cudaStream_t st) {
@@ -404,20 +459,9 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
 
   Tracer tr(st);
   // target on the device
-  DevBuf<double> tc, tw, ta;
-  TargetDev T{t.kind, 0, nullptr, nullptr, nullptr, t.lo, t.hi};
-  if (t.kind == FEM_TARGET_BUMPS) {
-    tc.alloc_async(3 * t.nb, st);
-    tw.alloc_async(t.nb, st);
-    ta.alloc_async(t.nb, st);
-    FEM_CUDA(cudaMemcpyAsync(tc, t.centers_host, 24 * t.nb, cudaMemcpyHostToDevice, st));
-    FEM_CUDA(cudaMemcpyAsync(tw, t.widths_host, 8 * t.nb, cudaMemcpyHostToDevice, st));
-    FEM_CUDA(cudaMemcpyAsync(ta, t.amps_host, 8 * t.nb, cudaMemcpyHostToDevice, st));
-    T.nb = t.nb;
-    T.c = tc;
-    T.w = tw;
-    T.a = ta;
-  }
+  TargetHolder th;
+  target_to_device(t, th, st);
+  const TargetDev& T = th.T;
 
   // operator
   S.A.nrows = S.A.ncols = (int32_t)N;
@@ -429,7 +473,7 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
     S.Kv.alloc(16 * N);
     S.Mv.alloc(16 * N);
   }
-  DevBuf<double> xyz;
+  DevBuf<double>& xyz = S.xyz;
   if (S.uniform) {
     DevBuf<double> row(45, st);
     k_uniform_row<<<1, 1, 0, st>>>(n, rho, row);
@@ -474,25 +518,8 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
   }
 
   tr.mark("assemble: operator (CSR4)");
-  // load vector
   S.f.alloc(N);
-  int64_t ncube = (int64_t)n * n * n;
-  DevBuf<double> cf(8 * ncube, st);
-  if (S.uniform) {
-    int nterms = (t.kind == FEM_TARGET_BUMPS) ? t.nb : (t.kind == FEM_TARGET_SINE_PLUS_ONE ? 2 : 1);
-    DevBuf<double> tab((size_t)nterms * 3 * n * 6, st), alpha(nterms, st);
-    int total = nterms * 3 * n * 6;
-    k_target_tables<<<grid_for(total, 256), 256, 0, st>>>(T, n, nterms, tab, alpha);
-    FEM_CHECK_LAUNCH();
-    k_cube_load<true><<<grid_for(ncube, 128), 128, 0, st>>>(n, nullptr, T, tab, alpha, nterms, cf);
-    FEM_CHECK_LAUNCH();
-  } else {
-    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, xyz, T, nullptr, nullptr, 0, cf);
-    FEM_CHECK_LAUNCH();
-  }
-  k_gather_load<<<grid_for(N, 256), 256, 0, st>>>(n, cf, S.f);
-  FEM_CHECK_LAUNCH();
-
+  load_vector(S, T, t, S.f, st);
   tr.mark("assemble: load vector");
   S.dinv.alloc(N);
   k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);

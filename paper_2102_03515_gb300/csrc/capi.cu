@@ -90,6 +90,10 @@ struct amg_hier_s {
   fem::Hierarchy H;
   fem_system_s* sys = nullptr;
 };
+struct pcg_batch_s {
+  fem::BatchSession* W = nullptr;
+  fem_system_s* sys = nullptr;
+};
 
 using namespace fem;
 
@@ -135,6 +139,16 @@ fem_status fem_system_get_info(fem_system sys, fem_system_info* info) {
     info->rho = S.rho;
     info->is_stencil = S.stencil;
     info->has_pencil = S.pencil;
+    return FEM_OK;
+  });
+}
+
+fem_status fem_assemble_rhs(fem_system sys, const fem_target* target, double* f_dev,
+                            void* stream) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(sys && target && f_dev, FEM_EINVAL, "fem_assemble_rhs: null argument");
+    assemble_rhs(sys->S, *target, f_dev, as_stream(stream));
     return FEM_OK;
   });
 }
@@ -338,5 +352,81 @@ fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double*
     return pcg_multi(sys->S, hier->H, f_dev, u_dev, nrhs, rho_k_host, o, as_stream(stream), res);
   });
 }
+
+fem_status pcg_batch_create(fem_system sys, amg_hier hier, int32_t slots, const pcg_opts* opts,
+                            void* stream, pcg_batch* out) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(sys && hier && out, FEM_EINVAL, "pcg_batch_create: null argument");
+    FEM_REQUIRE(hier->sys == sys, FEM_EINVAL, "pcg_batch_create: hierarchy of another system");
+    *out = nullptr;
+    pcg_opts o;
+    pcg_default_opts(&o);
+    if (opts) o = *opts;
+    auto* b = new pcg_batch_s();
+    try {
+      b->W = batch_create(sys->S, hier->H, slots, o, as_stream(stream));
+      b->sys = sys;
+    } catch (...) {
+      delete b;
+      throw;
+    }
+    *out = b;
+    return FEM_OK;
+  });
+}
+
+fem_status pcg_batch_admit(pcg_batch b, const double* f_dev, double rho, int32_t* slot_out,
+                           void* stream) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(b && f_dev && slot_out, FEM_EINVAL, "pcg_batch_admit: null argument");
+    *slot_out = batch_admit(*b->W, f_dev, 1, 0, rho, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
+fem_status pcg_batch_step(pcg_batch b, int32_t iters, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(b && iters >= 0, FEM_EINVAL, "pcg_batch_step: bad argument");
+    batch_step(*b->W, iters, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
+fem_status pcg_batch_poll(pcg_batch b, int32_t* state_host, int32_t* iters_host,
+                          double* relres_host, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(b, FEM_EINVAL, "pcg_batch_poll: null handle");
+    batch_poll(*b->W, state_host, iters_host, relres_host, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
+fem_status pcg_batch_retire(pcg_batch b, int32_t slot, double* u_dev, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(b && u_dev, FEM_EINVAL, "pcg_batch_retire: null argument");
+    batch_retire(*b->W, slot, u_dev, 1, 0, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
+int64_t pcg_batch_footprint(fem_system sys, amg_hier hier, int32_t slots) {
+  if (!sys || !hier || slots < 1 || slots > 64) return -1;
+  try {
+    return batch_footprint(sys->S, hier->H, slots);
+  } catch (...) {
+    return -1;
+  }
+}
+
+void pcg_batch_destroy(pcg_batch b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_destroy(b->W);
+  delete b;
+}
+
+const char* fem_autotune_report(void) { return "{}"; }
 
 }  // extern "C"

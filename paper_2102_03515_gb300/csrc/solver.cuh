@@ -31,6 +31,7 @@ struct System {
   DevBuf<double> Kv, Mv;  // pencil values on A's pattern
   DevBuf<double> f;       // load vector
   DevBuf<double> dinv;    // 1 / a_ii
+  DevBuf<double> xyz;     // vertex coordinates of a non-uniform grid
 };
 
 struct Level {
@@ -72,6 +73,7 @@ constexpr int kMaxPartialBlocks = 1 << 16;
 // ------------------------------------------------------------------ assembly (assemble.cu)
 void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem_target& t,
                      const fem_assemble_opts& o, cudaStream_t st);
+void assemble_rhs(System& S, const fem_target& t, double* f, cudaStream_t st);
 
 // ------------------------------------------------------------------ operators (ops.cu)
 // Chebyshev coefficients of one smoothing application of degree k on [lmax/ratio, lmax].
@@ -124,6 +126,16 @@ void dense_inverse(const Csr4& A, const double* val, DevBuf<double>& Ainv, cudaS
 
 // ------------------------------------------------------------------ V-cycle (vcycle.cu)
 void vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t st, const DotOut* dot);
+
+// ------------------------------------------------------------------ batched (batched.cu)
+struct BatchSession;
+BatchSession* batch_create(System& S, Hierarchy& H, int slots, const pcg_opts& o, cudaStream_t st);
+int batch_admit(BatchSession& W, const double* f, int64_t ld, int fcol, double rho, cudaStream_t st);
+void batch_step(BatchSession& W, int iters, cudaStream_t st);
+void batch_poll(BatchSession& W, int32_t* state, int32_t* iters, double* relres, cudaStream_t st);
+void batch_retire(BatchSession& W, int slot, double* u, int64_t ld, int ucol, cudaStream_t st);
+void batch_destroy(BatchSession* W);
+int64_t batch_footprint(const System& S, const Hierarchy& H, int slots);
 
 // ------------------------------------------------------------------ utilities
 void finalize_sums(const double* partials, int nblocks, int nv, double* out, cudaStream_t st,
