@@ -156,6 +156,9 @@ typedef struct {
   int32_t max_levels;    /* default 16                                          */
   int32_t precision;     /* amg_precision, default FP64                         */
   uint32_t seed;         /* priority seed, default 0                            */
+  double rho_setup;      /* > 0: build the hierarchy from rho_setup K + M (needs the
+                            pencil; the finest operator of solves is unchanged);
+                            default 0 = the system's rho                        */
 } amg_opts;
 
 typedef struct amg_hier_s* amg_hier;

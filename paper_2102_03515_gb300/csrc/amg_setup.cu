@@ -332,6 +332,11 @@ __global__ void k_agg_phase2(int64_t N, const int64_t* sptr, const int32_t* scol
 }
 
 // tentative prolongator, 4 slots per row
+__global__ void k_axpby(int64_t n, double a, const double* x, const double* y, double* z) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a * x[i] + y[i];
+}
+
 __global__ void k_tentative(int64_t N, const int32_t* agg, int32_t* rowptr, int32_t* col,
                             double* val) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -750,6 +755,13 @@ static int64_t max_of(const int64_t* v, int64_t n, cudaStream_t st) {
   return (int64_t)h;
 }
 
+// Widest needed group first; wider groups (fewer per block) when the tables of a
+// 256-thread block would not fit in 200 KB of shared memory.
+static int group_for_smem(int G, int ht, int bytes_per_slot) {
+  while (G < 32 && (size_t)(SG_BLOCK / G) * ht * bytes_per_slot > 200 * 1024) G <<= 1;
+  return G;
+}
+
 static int pow2_at_least(int64_t v, int lo) {
   int64_t t = lo;
   while (t < v) t <<= 1;
@@ -829,7 +841,8 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
     const int64_t maxub = max_of(tmp, nr, st);
     G = maxb <= 4 ? 4 : (maxb <= 8 ? 8 : (maxb <= 16 ? 16 : 32));
     htc = pow2_at_least(std::min<int64_t>(2 * maxub, kHTMax), 64);
-    switch (G) {
+    const int Gc = group_for_smem(G, htc, 4);
+    switch (Gc) {
       case 4: sg_count_ht<4>(htc, nr, A, B, cnt, st); break;
       case 8: sg_count_ht<8>(htc, nr, A, B, cnt, st); break;
       case 16: sg_count_ht<16>(htc, nr, A, B, cnt, st); break;
@@ -844,7 +857,7 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
   if (nr > 0) {
     const int htf = pow2_at_least(2 * maxc, 64);
     double* cv = values ? C.val.p : nullptr;
-    switch (G) {
+    switch (group_for_smem(G, htf, 14)) {
       case 4: sg_fill_ht<4>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
       case 8: sg_fill_ht<8>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
       case 16: sg_fill_ht<16>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
@@ -1034,6 +1047,26 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
   cur->A = &S.A;
   cur->stencil = S.stencil;
   cur->st = S.stA;
+  if (o.rho_setup > 0.0 && o.rho_setup != S.rho) {
+    // finest level of the set-up from rho_setup K + M on the system's pattern
+    Csr4& A0 = cur->Aown;
+    A0.nrows = S.A.nrows;
+    A0.ncols = S.A.ncols;
+    A0.nnz = S.A.nnz;
+    A0.rowptr.alloc(A0.nrows + 1);
+    A0.col.alloc(A0.nnz);
+    A0.val.alloc(A0.nnz);
+    FEM_CUDA(cudaMemcpyAsync(A0.rowptr, S.A.rowptr, 4 * ((int64_t)A0.nrows + 1),
+                             cudaMemcpyDeviceToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(A0.col, S.A.col, 4 * A0.nnz, cudaMemcpyDeviceToDevice, st));
+    k_axpby<<<grid_for(A0.nnz, 256), 256, 0, st>>>(A0.nnz, o.rho_setup, S.Kv, S.Mv, A0.val);
+    FEM_CHECK_LAUNCH();
+    cur->A = &A0;
+    cur->st.c0 = o.rho_setup * S.stK.c0 + S.stM.c0;
+    cur->st.ca = o.rho_setup * S.stK.ca + S.stM.ca;
+    cur->st.cf = o.rho_setup * S.stK.cf + S.stM.cf;
+    cur->st.cb = o.rho_setup * S.stK.cb + S.stM.cb;
+  }
   for (int lev = 0;; lev++) {
     Level& Lv = *cur;
     const Csr4* Acur = Lv.A;
@@ -1057,7 +1090,7 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     }
     FEM_CHECK_LAUNCH();
     if (lowp) {
-      Csr4& Am = lev == 0 ? S.A : Lv.Aown;
+      Csr4& Am = (lev == 0 && Lv.A == &S.A) ? S.A : Lv.Aown;
       if (!(lev == 0 && Lv.stencil)) {
         if (!Am.val32.p) make_lowp(Am, AMG_PREC_FP32, st);
         if (prec == AMG_PREC_BF16 && !Am.val16.p) make_lowp(Am, AMG_PREC_BF16, st);

@@ -140,76 +140,76 @@ __device__ __forceinline__ void slot_partials(double (&acc)[NV], int B, double* 
   }
 }
 
+// grid: x over blocks of points along i, y strides over the (j, k) planes
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_mv_stencil(const T* __restrict__ v, int m, MvEpi<T> e,
                                                     double* partials, int nblocks) {
   using AT = typename Arith<T>::type;
   const int B = e.B;
-  const int64_t N = (int64_t)m * m * m;
-  const int b = threadIdx.x % B;
+  const int b = threadIdx.x & (B - 1);
   const int ppb = blockDim.x / B;
+  const int i = blockIdx.x * ppb + threadIdx.x / B;
   double acc[2] = {0.0, 0.0};
   const LevCoef& c = e.lc[e.level * B + b];
   const AT c0 = (AT)c.c0, ca = (AT)c.ca, cf = (AT)c.cf, cb = (AT)c.cb;
-  for (int64_t base = (int64_t)blockIdx.x * ppb; base < N; base += (int64_t)gridDim.x * ppb) {
-    const int64_t p = base + threadIdx.x / B;
-    if (p < N) {
-      const int i = (int)(p % m), j = (int)((p / m) % m), k = (int)(p / ((int64_t)m * m));
-      auto X = [&](int di, int dj, int dk) -> AT {
-        const int ii = i + di, jj = j + dj, kk = k + dk;
-        if (ii < 0 || jj < 0 || kk < 0 || ii >= m || jj >= m || kk >= m) return (AT)0;
-        return (AT)v[((int64_t)ii + (int64_t)m * ((int64_t)jj + (int64_t)m * kk)) * B + b];
-      };
-      AT axis = X(-1, 0, 0) + X(1, 0, 0) + X(0, -1, 0) + X(0, 1, 0) + X(0, 0, -1) + X(0, 0, 1);
-      AT face = X(1, 1, 0) + X(-1, -1, 0) + X(1, 0, 1) + X(-1, 0, -1) + X(0, 1, 1) + X(0, -1, -1);
-      AT body = X(1, 1, 1) + X(-1, -1, -1);
-      AT av = c0 * X(0, 0, 0) + ca * axis + cf * face + cb * body;
-      mv_epi<T>(e, p, b, av, acc);
+  const int64_t sj = (int64_t)m * B, sk = (int64_t)m * m * B;
+  for (int jk = blockIdx.y; jk < m * m; jk += gridDim.y) {
+    const int k = jk / m, j = jk - k * m;
+    if (i < m) {
+      const int64_t o = ((int64_t)i + (int64_t)m * j + (int64_t)m * m * k) * B + b;
+      const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1, km = k > 0, kp = k < m - 1;
+      auto X = [&](bool ok, int64_t off) -> AT { return ok ? (AT)v[o + off] : (AT)0; };
+      AT axis = X(im, -B) + X(ip, B) + X(jm, -sj) + X(jp, sj) + X(km, -sk) + X(kp, sk);
+      AT face = X(ip && jp, B + sj) + X(im && jm, -B - sj) + X(ip && kp, B + sk) +
+                X(im && km, -B - sk) + X(jp && kp, sj + sk) + X(jm && km, -sj - sk);
+      AT body = X(ip && jp && kp, B + sj + sk) + X(im && jm && km, -B - sj - sk);
+      AT av = c0 * (AT)v[o] + ca * axis + cf * face + cb * body;
+      mv_epi<T>(e, (int64_t)i + (int64_t)m * j + (int64_t)m * m * k, b, av, acc);
     }
   }
-  if (NV > 0 && partials) slot_partials<2>(acc, B, partials, nblocks, blockIdx.x);
+  if (NV > 0 && partials)
+    slot_partials<2>(acc, B, partials, nblocks, blockIdx.x + gridDim.x * blockIdx.y);
 }
 
-// FP64 stencil for q = A(rho_b) p with per-slot coefficients in FP64 and <p, q> per slot.
+// FP64 stencil for q = A(rho_b) p with per-slot coefficients in FP64 and <p, q> per slot
+// (slots null: every slot, no dots).
 __global__ void __launch_bounds__(256) k_mv_stencil64(const double* __restrict__ v, int m,
                                                       const double* coef /* [B][4] */, int B,
                                                       double* y, const SlotState* slots,
                                                       double* partials, int nblocks) {
-  const int64_t N = (int64_t)m * m * m;
-  const int b = threadIdx.x % B;
+  const int b = threadIdx.x & (B - 1);
   const int ppb = blockDim.x / B;
+  const int i = blockIdx.x * ppb + threadIdx.x / B;
   double acc[1] = {0.0};
   const bool live = !slots || (slots[b].active && !slots[b].done);
   const double c0 = coef[4 * b], ca = coef[4 * b + 1], cf = coef[4 * b + 2], cb = coef[4 * b + 3];
-  for (int64_t base = (int64_t)blockIdx.x * ppb; base < N; base += (int64_t)gridDim.x * ppb) {
-    const int64_t p = base + threadIdx.x / B;
-    if (p < N && live) {
-      const int i = (int)(p % m), j = (int)((p / m) % m), k = (int)(p / ((int64_t)m * m));
-      auto X = [&](int di, int dj, int dk) -> double {
-        const int ii = i + di, jj = j + dj, kk = k + dk;
-        if (ii < 0 || jj < 0 || kk < 0 || ii >= m || jj >= m || kk >= m) return 0.0;
-        return v[((int64_t)ii + (int64_t)m * ((int64_t)jj + (int64_t)m * kk)) * B + b];
-      };
-      double av = c0 * X(0, 0, 0);
-      av = fma(ca, X(-1, 0, 0), av);
-      av = fma(ca, X(1, 0, 0), av);
-      av = fma(ca, X(0, -1, 0), av);
-      av = fma(ca, X(0, 1, 0), av);
-      av = fma(ca, X(0, 0, -1), av);
-      av = fma(ca, X(0, 0, 1), av);
-      av = fma(cf, X(1, 1, 0), av);
-      av = fma(cf, X(-1, -1, 0), av);
-      av = fma(cf, X(1, 0, 1), av);
-      av = fma(cf, X(-1, 0, -1), av);
-      av = fma(cf, X(0, 1, 1), av);
-      av = fma(cf, X(0, -1, -1), av);
-      av = fma(cb, X(1, 1, 1), av);
-      av = fma(cb, X(-1, -1, -1), av);
-      y[p * B + b] = av;
-      acc[0] += v[p * B + b] * av;
+  const int64_t sj = (int64_t)m * B, sk = (int64_t)m * m * B;
+  for (int jk = blockIdx.y; jk < m * m; jk += gridDim.y) {
+    const int k = jk / m, j = jk - k * m;
+    if (i < m && live) {
+      const int64_t o = ((int64_t)i + (int64_t)m * j + (int64_t)m * m * k) * B + b;
+      const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1, km = k > 0, kp = k < m - 1;
+      auto X = [&](bool ok, int64_t off) -> double { return ok ? v[o + off] : 0.0; };
+      double av = c0 * v[o];
+      av = fma(ca, X(im, -B), av);
+      av = fma(ca, X(ip, B), av);
+      av = fma(ca, X(jm, -sj), av);
+      av = fma(ca, X(jp, sj), av);
+      av = fma(ca, X(km, -sk), av);
+      av = fma(ca, X(kp, sk), av);
+      av = fma(cf, X(ip && jp, B + sj), av);
+      av = fma(cf, X(im && jm, -B - sj), av);
+      av = fma(cf, X(ip && kp, B + sk), av);
+      av = fma(cf, X(im && km, -B - sk), av);
+      av = fma(cf, X(jp && kp, sj + sk), av);
+      av = fma(cf, X(jm && km, -sj - sk), av);
+      av = fma(cb, X(ip && jp && kp, B + sj + sk), av);
+      av = fma(cb, X(im && jm && km, -B - sj - sk), av);
+      y[o] = av;
+      acc[0] += v[o] * av;
     }
   }
-  if (slots) slot_partials<1>(acc, B, partials, nblocks, blockIdx.x);
+  if (slots) slot_partials<1>(acc, B, partials, nblocks, blockIdx.x + gridDim.x * blockIdx.y);
 }
 
 // ------------------------------------------------------------------ multivector CSR
@@ -258,8 +258,8 @@ __global__ void k_mv_cheb_zero(int64_t N, int B, const double* __restrict__ b64,
   using AT = typename Arith<T>::type;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N * B;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / B;
-    const int b = (int)(idx % B);
+    const int b = (int)(idx & (B - 1));
+    const int64_t i = idx >> (31 - __clz(B));
     const LevCoef& c = lc[level * B + b];
     AT bv;
     if (b64) {
@@ -497,7 +497,7 @@ __global__ void k_slot_fin_rr(SlotState* S, const double* partials, int nb, int 
 __global__ void k_mv_update_p(int64_t N, int B, const double* z, double* p, const SlotState* S) {
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N * B;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(idx % B);
+    const int b = (int)(idx & (B - 1));
     const SlotState& s = S[b];
     if (!s.active || s.done) continue;
     p[idx] = z[idx] + s.beta * p[idx];
@@ -629,6 +629,15 @@ unsigned mv_grid(int64_t N, int B) {
   return persistent_grid((N + ppb - 1) / ppb * 256, 256, 8);
 }
 
+// stencil grid: x covers the i-line in blocks of 256/B points, y strides over planes
+dim3 mv_sgrid(int m, int B) {
+  const int ppb = 256 / B;
+  const int gx = (m + ppb - 1) / ppb;
+  int gy = (8 * num_sms() + gx - 1) / gx;
+  if (gy > m * m) gy = m * m;
+  return dim3(gx, gy, 1);
+}
+
 // One V-cycle on all slots (FP32), levels lev.., with the finest-level right-hand side
 // given in FP64 (b64) and the output written to z64 with per-slot dots.
 void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
@@ -651,12 +660,16 @@ void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
   const unsigned g = mv_grid(N, B);
   const bool finest = lev == 0;
   double* part = W.partials;
+  const int m = W.S->n - 1;
+  const dim3 sg = mv_sgrid(m, B);
   auto op = [&](const float* v, MvEpi<float> e, bool dots) {
     if (L.stencil) {
-      if (dots)
-        k_mv_stencil<float, 2><<<g, 256, 0, st>>>(v, (int)round(cbrt((double)N)), e, part, g);
-      else
-        k_mv_stencil<float, 0><<<g, 256, 0, st>>>(v, (int)round(cbrt((double)N)), e, nullptr, g);
+      if (dots) {
+        k_mv_stencil<float, 2><<<sg, 256, 0, st>>>(v, m, e, part, sg.x * sg.y);
+        W.nb_fine = sg.x * sg.y;
+      } else {
+        k_mv_stencil<float, 0><<<sg, 256, 0, st>>>(v, m, e, nullptr, sg.x * sg.y);
+      }
     } else {
       if (dots)
         k_mv_csr<float, float, 2><<<g, 256, 0, st>>>(N, L.A->rowptr, L.A->col, L.Kv, L.Mv, v, e, 0,
@@ -767,7 +780,7 @@ void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
       e.r2 = W.rprev;
     }
     op(dold, e, last && finest);
-    if (last && finest) W.nb_fine = (int)g;
+    if (last && finest && !L.stencil) W.nb_fine = (int)g;
     std::swap(dold, dnew);
   }
 }
@@ -778,7 +791,11 @@ int mv_apply64(BatchSession& W, cudaStream_t st) {
   const int B = W.B;
   const unsigned g = mv_grid(W.N, B);
   if (L.stencil) {
-    k_mv_stencil64<<<g, 256, 0, st>>>(W.p, W.S->n - 1, W.coef64, B, W.q, W.state, W.partials, g);
+    const dim3 sg = mv_sgrid(W.S->n - 1, B);
+    k_mv_stencil64<<<sg, 256, 0, st>>>(W.p, W.S->n - 1, W.coef64, B, W.q, W.state, W.partials,
+                                       sg.x * sg.y);
+    FEM_CHECK_LAUNCH();
+    return (int)(sg.x * sg.y);
   } else {
     MvEpi<double> e;
     std::memset(&e, 0, sizeof(e));
@@ -916,7 +933,7 @@ BatchSession* batch_create(System& S, Hierarchy& H, int slots, const pcg_opts& o
   FEM_CUDA(cudaMemsetAsync(W->coef64, 0, 32 * B, st));
   FEM_CUDA(cudaMemsetAsync(W->lc, 0, sizeof(LevCoef) * H.L.size() * B, st));
   W->partials.alloc((size_t)2 * B * (8 * num_sms() + 1) + 4 * (size_t)kMaxPartialBlocks);
-  W->scratch.alloc(1024);
+  W->scratch.alloc(4 * 8 * (size_t)num_sms() + 64);
   FEM_CUDA(cudaMallocHost(&W->hstate, sizeof(SlotState) * B));
   W->in_use.assign(B, 0);
   // one iteration as a CUDA graph
@@ -988,7 +1005,10 @@ int batch_admit(BatchSession& W, const double* f, int64_t ld, int fcol, double r
       c.sinv = (float)(1.0 / a[0]);
       double coef[4] = {a[0], a[1], a[2], a[3]};
       FEM_CUDA(cudaMemcpyAsync(W.coef64.p + 4 * slot, coef, 32, cudaMemcpyHostToDevice, st));
-      lmax = slot_gershgorin(*Lv.A, kv, mv, rho, W.scratch, st);
+      // every row has the diagonal a[0] and a subset of the interior row's neighbours, so
+      // the Gershgorin bound is the interior row's sum
+      lmax = (std::fabs(a[0]) + 6 * std::fabs(a[1]) + 6 * std::fabs(a[2]) + 2 * std::fabs(a[3])) /
+             a[0];
     } else {
       lmax = slot_gershgorin(*Lv.A, kv, mv, rho, W.scratch, st);
     }
@@ -1073,7 +1093,9 @@ static void batch_true_residual(BatchSession& W, double* out, cudaStream_t st) {
   BatchLevel& L = *W.L[0];
   const unsigned g = mv_grid(N, B);
   if (L.stencil) {
-    k_mv_stencil64<<<g, 256, 0, st>>>(W.x, W.S->n - 1, W.coef64, B, W.q, nullptr, W.partials, g);
+    const dim3 sg = mv_sgrid(W.S->n - 1, B);
+    k_mv_stencil64<<<sg, 256, 0, st>>>(W.x, W.S->n - 1, W.coef64, B, W.q, nullptr, W.partials,
+                                       sg.x * sg.y);
   } else {
     MvEpi<double> e;
     std::memset(&e, 0, sizeof(e));

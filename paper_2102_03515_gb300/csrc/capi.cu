@@ -1,6 +1,7 @@
 // extern "C" entry points of include/femamg.h: argument checks, handles, and the
 // translation of internal failures into fem_status codes with a per-thread message.
 #include <atomic>
+#include <cmath>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -212,6 +213,7 @@ void amg_default_opts(amg_opts* o) {
   o->max_levels = 16;
   o->precision = AMG_PREC_FP64;
   o->seed = 0;
+  o->rho_setup = 0.0;
 }
 
 fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hier* out) {
@@ -231,6 +233,10 @@ fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hie
                 "amg_setup: max_levels in [1, 32]");
     FEM_REQUIRE(o.precision >= 0 && o.precision <= 2, FEM_EINVAL, "amg_setup: bad precision");
     FEM_REQUIRE(o.smoother == 0 || o.smoother == 1, FEM_EINVAL, "amg_setup: bad smoother");
+    FEM_REQUIRE(o.rho_setup >= 0.0 && std::isfinite(o.rho_setup), FEM_EINVAL,
+                "amg_setup: rho_setup >= 0");
+    FEM_REQUIRE(o.rho_setup == 0.0 || sys->S.pencil, FEM_EINVAL,
+                "amg_setup: rho_setup needs a system that keeps its pencil");
     cudaStream_t st = as_stream(stream);
     auto* h = new amg_hier_s();
     h->sys = sys;

@@ -397,7 +397,8 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
         for (auto& Lp : H->L) Lp->done = nullptr;
     }
   } done_reset{H};
-  Level& L0 = H ? *H->L[0] : sysL;
+  // CG's operator is always the system's (a hierarchy may be set up from another rho)
+  Level& L0 = sysL;
   const int* done = &W.state.p->done;
   const unsigned gv = persistent_grid(N, 256, 8);
   if (!f) f = S.f.p;
