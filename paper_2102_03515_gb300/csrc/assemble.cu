@@ -351,6 +351,55 @@ __global__ void k_cube_load(int n, const double* xyz, TargetDev T, const double*
   for (int a = 0; a < 8; a++) cf[8 * c + a] = scale * acc[a];
 }
 
+// Uniform grid: one block per row of cubes (j, k); the products alpha_t g_t1(y) g_t2(z) of
+// the row's quadrature offsets are staged in shared memory, so each point costs one
+// product per separable term of the target.
+__global__ void __launch_bounds__(128) k_cube_load_rows(int n, const double* __restrict__ tab,
+                                                        const double* __restrict__ alpha,
+                                                        int nterms, double* cf) {
+  constexpr int PP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  extern __shared__ double t12[];  // [nterms][6 (y offset)][6 (z offset)]
+  const int cj = blockIdx.x, ck = blockIdx.y;
+  for (int q = threadIdx.x; q < nterms * 36; q += blockDim.x) {
+    const int t = q / 36, oy = (q / 6) % 6, oz = q % 6;
+    t12[q] = alpha[t] * (tab[((t * 3 + 1) * n + cj) * 6 + oy] * tab[((t * 3 + 2) * n + ck) * 6 + oz]);
+  }
+  __syncthreads();
+  const double A = (5.0 + 3.0 * sqrt(5.0)) / 20.0, B = (5.0 - sqrt(5.0)) / 20.0;
+  const double h = 1.0 / n;
+  const double scale = 0.25 * (h * h * h / 6.0);
+  for (int ci = threadIdx.x; ci < n; ci += blockDim.x) {
+    double acc[8];
+#pragma unroll
+    for (int a = 0; a < 8; a++) acc[a] = 0.0;
+#pragma unroll
+    for (int p = 0; p < 6; p++) {
+      int lv[4];
+      lv[0] = 0;
+#pragma unroll
+      for (int s = 0; s < 3; s++) lv[s + 1] = lv[s] | (1 << PP[p][s]);
+      double uq[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        int oax[3];
+        oax[PP[p][0]] = (q == 0) ? 4 : 5;
+        oax[PP[p][1]] = (q >= 2) ? 3 : 2;
+        oax[PP[p][2]] = (q == 3) ? 1 : 0;
+        double u = 0.0;
+        for (int t = 0; t < nterms; t++)
+          u += __ldg(tab + ((t * 3 + 0) * n + ci) * 6 + oax[0]) * t12[t * 36 + oax[1] * 6 + oax[2]];
+        uq[q] = u;
+      }
+      const double S = (uq[0] + uq[1]) + (uq[2] + uq[3]);
+#pragma unroll
+      for (int a = 0; a < 4; a++) acc[lv[a]] += B * S + (A - B) * uq[a];
+    }
+    const int64_t c = ci + (int64_t)n * (cj + (int64_t)n * ck);
+#pragma unroll
+    for (int a = 0; a < 8; a++) cf[8 * c + a] = scale * acc[a];
+  }
+}
+
 __global__ void k_gather_load(int n, const double* cf, double* f) {
   const int m = n - 1;
   int64_t N = (int64_t)m * m * m;
@@ -389,7 +438,7 @@ void load_vector(System& S, const TargetDev& T, const fem_target& t, double* f, 
     int total = nterms * 3 * n * 6;
     k_target_tables<<<grid_for(total, 256), 256, 0, st>>>(T, n, nterms, tab, alpha);
     FEM_CHECK_LAUNCH();
-    k_cube_load<true><<<grid_for(ncube, 128), 128, 0, st>>>(n, nullptr, T, tab, alpha, nterms, cf);
+    k_cube_load_rows<<<dim3(n, n), 128, (size_t)nterms * 36 * 8, st>>>(n, tab, alpha, nterms, cf);
     FEM_CHECK_LAUNCH();
   } else {
     k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, S.xyz, T, nullptr, nullptr, 0, cf);

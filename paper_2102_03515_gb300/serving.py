@@ -1,10 +1,14 @@
 """Continuous-batching solve service on top of the C ABI's batch sessions.
 
-Requests (mesh size n, rho, target, tolerance) are grouped by (n, rho-bucket), the
-bucket being floor(log10 rho).  Per n there is one assembled system that keeps its
-pencil (K and M); per (n, bucket) a smoothed-aggregation hierarchy set up at the
-bucket's representative rho (10^(bucket + 1/2)) is built once and cached; per
-(n, bucket) one batch session with a fixed number of slots runs on its own CUDA stream,
+Requests (mesh size n, rho, target, tolerance) are grouped by (n, rho-bucket).  Buckets
+are decades of rho, floor(log10 rho), grouped per mesh into two regimes: stiffness-
+dominated (rho >= h^2) and mass-dominated (rho < h^2).  With the prolongators fixed, a
+bucket's operators are the pencil rho K_l + M_l, and prolongators set up at the largest
+rho of a regime serve every rho of it (coarse correction matters in the stiff regime and
+little in the mass regime, where the smoother does the work).  Per n there is one
+assembled system that keeps its pencil (K and M); per (n, regime) a smoothed-aggregation
+hierarchy is built once and cached; per (n, regime) one batch session with a fixed
+number of slots runs on its own CUDA stream,
 so sessions of different keys overlap on the device.  Every tick advances each busy
 session by a few CG iterations, retires the slots that finished, and admits waiting
 requests into free slots; a session is created only if its bytes fit in the HBM budget
@@ -46,7 +50,7 @@ class Request:
 class ServeConfig:
     slots: int = 16               # slots per (n, bucket) session
     steps_per_tick: int = 2       # CG iterations per session per tick
-    hbm_budget: int = 64 << 30    # bytes the service may hold on the device
+    hbm_budget: int = 160 << 30   # bytes the service may hold on the device
     precision: int = fa.AMG_PREC_FP32
     keep_solutions: bool = False  # keep each request's solution on the device
     max_iter: int = 500
@@ -55,6 +59,16 @@ class ServeConfig:
 
 def rho_bucket(rho: float) -> int:
     return int(math.floor(math.log10(rho) + 1e-12))
+
+
+def regime(n: int, bucket: int) -> int:
+    """1 for decades whose rho reaches h^2 = 1/n^2 or more (stiffness-dominated), 0 below."""
+    return 1 if 10.0 ** (bucket + 1) > 1.0 / n ** 2 else 0
+
+
+def regime_rho_setup(n: int, reg: int, rho_max: float = 1.0) -> float:
+    """Set-up rho of a regime: its largest rho (rho_max for the stiff regime, h^2 below)."""
+    return rho_max if reg == 1 else 1.0 / n ** 2
 
 
 @dataclass
@@ -94,13 +108,13 @@ class SolveService:
             self.systems[n] = s
         return s
 
-    def _hierarchy(self, n: int, bucket: int):
-        key = (n, bucket)
+    def _hierarchy(self, n: int, reg: int):
+        key = (n, reg)
         h = self.hier.get(key)
         if h is None:
             self.stats["hierarchy_builds"] += 1
             h = fa.amg_setup(self._system(n), precision=self.cfg.precision,
-                             coarse_max=self.cfg.coarse_max, rho_setup=10.0 ** (bucket + 0.5))
+                             coarse_max=self.cfg.coarse_max, rho_setup=regime_rho_setup(n, reg))
             self.bytes_in_use += self._hier_bytes(h)
             self.hier[key] = h
         else:
@@ -133,19 +147,20 @@ class SolveService:
         return self.bytes_in_use + need <= self.cfg.hbm_budget
 
     def _session(self, n: int, bucket: int):
-        key = (n, bucket)
+        key = (n, regime(n, bucket))
         sess = self.sessions.get(key)
         if sess is not None:
             self.sessions.move_to_end(key)
+            self.stats["hierarchy_hits"] += 1
             return sess
         sys_ = self._system(n)
-        h = self._hierarchy(n, bucket)
+        h = self._hierarchy(*key)
         need = fa.pcg_batch_footprint(sys_, h, self.cfg.slots)
         if need < 0:
             raise fa.FemError(fa.FEM_EINVAL, "no footprint for this session")
         if not self._evict_idle(need, key):
             if not any(s.members for s in self.sessions.values()):
-                raise MemoryError("a (n=%d, bucket=%d) session does not fit in the budget" % key)
+                raise MemoryError("a (n=%d, regime=%d) session does not fit in the budget" % key)
             return None
         stream = torch.cuda.Stream(device=self.device)
         handle = fa.pcg_batch_create(sys_, h, self.cfg.slots, stream=stream,

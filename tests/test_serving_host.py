@@ -16,6 +16,17 @@ def test_rho_buckets_cover_the_workload_range():
     assert {rho_bucket(10 ** (-k / 7.0)) for k in range(0, 57)} <= set(range(-8, 1))
 
 
+def test_regimes_split_at_h_squared():
+    from paper_2102_03515_gb300.serving import regime, regime_rho_setup, rho_bucket
+    n = 100  # h^2 = 1e-4
+    assert regime(n, rho_bucket(1e-4)) == 1
+    assert regime(n, rho_bucket(9.9e-5)) == 0   # its decade [1e-5, 1e-4) lies below h^2
+    assert regime(n, rho_bucket(9e-6)) == 0
+    assert regime(n, rho_bucket(1.0)) == 1
+    assert regime_rho_setup(n, 0) == pytest.approx(1e-4)
+    assert regime_rho_setup(n, 1) == 1.0
+
+
 def test_latency_percentiles():
     from paper_2102_03515_gb300 import serving as S
     svc = S.SolveService.__new__(S.SolveService)  # statistics only, no device state
