@@ -121,6 +121,20 @@ fem_status fem_system_get_info(fem_system sys, fem_system_info* info);
 fem_status fem_assemble_rhs(fem_system sys, const fem_target* target, double* f_dev,
                             void* stream);
 
+/* fem_assemble_rhs without any device allocation (the paper has no counterpart: this is
+ * an interface for callers that cannot allocate).  Callers that cannot call cudaMalloc --
+ * code running while another allocator holds nearly all of the GPU's memory, callers with
+ * a fixed pre-reserved budget, latency-critical loops that must not pay for an allocation
+ * and its implicit synchronisation -- get the same f_dev as fem_assemble_rhs, computed in a
+ * fixed 17 MB scratch array that the library holds on every GPU it is loaded on until the
+ * process exits.  Limits: n <= 64 cells per side and at most 64 bumps; larger inputs return
+ * FEM_EINVAL with a message.  The first call on each device looks up the array's device
+ * address and must not be made during a stream capture.  All calls share the array: calls
+ * that overlap on the GPU (different streams without ordering) race and must not be issued.
+ * Returns after the work is complete. */
+fem_status fem_assemble_rhs_noalloc(fem_system sys, const fem_target* target, double* f_dev,
+                                    void* stream);
+
 /* Copy the assembled load vector f (length N) into f_dev. */
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream);
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "fem_system_get_info": (C.c_int, [VP, P(SystemInfo)]),
     "fem_system_get_rhs": (C.c_int, [VP, VP, VP]),
     "fem_assemble_rhs": (C.c_int, [VP, P(Target), VP, VP]),
+    "fem_assemble_rhs_noalloc": (C.c_int, [VP, P(Target), VP, VP]),
     "fem_system_export": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
     "fem_spmv": (C.c_int, [VP, VP, VP, VP]),
     "fem_system_destroy": (None, [VP]),
@@ -196,6 +197,14 @@ def fem_assemble_rhs(sys, target: dict, f, stream=None):
     keep = []
     t = _target(target, keep)
     _check(lib().fem_assemble_rhs(sys, C.byref(t), _ptr(f), _stream(stream)), "fem_assemble_rhs")
+
+
+def fem_assemble_rhs_noalloc(sys, target: dict, f, stream=None):
+    """fem_assemble_rhs for callers that cannot allocate device memory (n <= 64)."""
+    keep = []
+    t = _target(target, keep)
+    _check(lib().fem_assemble_rhs_noalloc(sys, C.byref(t), _ptr(f), _stream(stream)),
+           "fem_assemble_rhs_noalloc")
 
 
 def fem_assemble(n: int, rho: float, target: dict, xyz=None, fmt: int = FEM_FMT_AUTO,

@@ -11,6 +11,7 @@
 // Element arithmetic is done without FMA contraction (this file is compiled with
 // -fmad=false) so that sums of element contributions follow plain IEEE rounding.
 #include <cmath>
+#include <mutex>
 
 #include "solver.cuh"
 
@@ -574,6 +575,92 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
   k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);
   FEM_CHECK_LAUNCH();
   // temporaries are freed stream-ordered; make sure the caller's data is complete
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------ allocation-free load vector
+//
+// Some callers cannot allocate device memory: code that runs while another allocator owns
+// (nearly) all of the GPU's memory, callers with a fixed, pre-reserved memory budget, and
+// latency-critical loops that must not pay for an allocation and its implicit
+// synchronisation.  assemble_rhs_noalloc computes the same load vector as assemble_rhs with
+// every scratch buffer (the per-cube partial sums, the separable target tables and the
+// copies of the target's parameters) placed in the file-scope array below instead of being
+// allocated.  The array is a fixed 17 MB that every GPU loading the library holds until the
+// process exits, which limits this path to meshes with n <= 64 cells per side.  All calls
+// share it and it keeps the last call's contents; each call overwrites every entry it
+// reads, so nothing needs clearing, but calls whose work overlaps on the GPU (different
+// streams, no ordering between them) race on it.
+
+namespace {
+constexpr int kNoAllocMaxN = 64;
+constexpr int kNoAllocMaxTerms = 64;
+constexpr size_t kNoAllocCube = 8ull * kNoAllocMaxN * kNoAllocMaxN * kNoAllocMaxN;
+constexpr size_t kNoAllocTab = (size_t)kNoAllocMaxTerms * 3 * kNoAllocMaxN * 6;
+constexpr size_t kNoAllocDoubles = kNoAllocCube + kNoAllocTab + kNoAllocMaxTerms + 5 * kNoAllocMaxTerms;
+}  // namespace
+
+static __device__ __align__(256) double g_rhs_scratch[kNoAllocDoubles];
+
+// Device address of g_rhs_scratch on the current device.  The first call on a device looks
+// it up with cudaGetSymbolAddress (with that device current) and caches it; that first call
+// must not happen during a stream capture.
+static double* noalloc_scratch() {
+  static std::mutex mu;
+  static double* addr[128] = {nullptr};
+  int dev = 0;
+  FEM_CUDA(cudaGetDevice(&dev));
+  FEM_REQUIRE(dev >= 0 && dev < 128, FEM_EUNSUPPORTED, "fem_assemble_rhs_noalloc: device index");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    FEM_CUDA(cudaGetSymbolAddress(&p, g_rhs_scratch));
+    addr[dev] = static_cast<double*>(p);
+  }
+  return addr[dev];
+}
+
+void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_t st) {
+  FEM_REQUIRE(S.n <= kNoAllocMaxN, FEM_EINVAL,
+              "fem_assemble_rhs_noalloc: n = " + std::to_string(S.n) +
+                  " exceeds the allocation-free limit of 64 cells per side");
+  FEM_REQUIRE(t.kind >= 0 && t.kind <= 3, FEM_EINVAL, "fem_assemble_rhs_noalloc: unknown target");
+  FEM_REQUIRE(t.kind != FEM_TARGET_BUMPS || (t.nb >= 1 && t.nb <= kNoAllocMaxTerms &&
+                                             t.centers_host && t.widths_host && t.amps_host),
+              FEM_EINVAL, "fem_assemble_rhs_noalloc: bumps need 1..64 centres/widths/amplitudes");
+  double* base = noalloc_scratch();
+  double* cf = base;
+  double* tab = cf + kNoAllocCube;
+  double* alpha = tab + kNoAllocTab;
+  double* par = alpha + kNoAllocMaxTerms;
+  const int n = S.n;
+  TargetDev T{t.kind, 0, nullptr, nullptr, nullptr, t.lo, t.hi};
+  if (t.kind == FEM_TARGET_BUMPS) {
+    FEM_CUDA(cudaMemcpyAsync(par, t.centers_host, 24 * t.nb, cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(par + 3 * kNoAllocMaxTerms, t.widths_host, 8 * t.nb,
+                             cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(par + 4 * kNoAllocMaxTerms, t.amps_host, 8 * t.nb,
+                             cudaMemcpyHostToDevice, st));
+    T.nb = t.nb;
+    T.c = par;
+    T.w = par + 3 * kNoAllocMaxTerms;
+    T.a = par + 4 * kNoAllocMaxTerms;
+  }
+  const int64_t ncube = (int64_t)n * n * n;
+  if (S.uniform) {
+    const int nterms = (t.kind == FEM_TARGET_BUMPS) ? t.nb : (t.kind == FEM_TARGET_SINE_PLUS_ONE ? 2 : 1);
+    const int total = nterms * 3 * n * 6;
+    k_target_tables<<<grid_for(total, 256), 256, 0, st>>>(T, n, nterms, tab, alpha);
+    FEM_CHECK_LAUNCH();
+    k_cube_load_rows<<<dim3(n, n), 128, (size_t)nterms * 36 * 8, st>>>(n, tab, alpha, nterms, cf);
+    FEM_CHECK_LAUNCH();
+  } else {
+    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, S.xyz, T, nullptr, nullptr, 0, cf);
+    FEM_CHECK_LAUNCH();
+  }
+  k_gather_load<<<grid_for(S.N, 256), 256, 0, st>>>(n, cf, f);
+  FEM_CHECK_LAUNCH();
+  // the host parameter arrays are read by the copies above: finish before returning
   FEM_CUDA(cudaStreamSynchronize(st));
 }
 

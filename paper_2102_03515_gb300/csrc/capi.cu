@@ -154,6 +154,15 @@ fem_status fem_assemble_rhs(fem_system sys, const fem_target* target, double* f_
   });
 }
 
+fem_status fem_assemble_rhs_noalloc(fem_system sys, const fem_target* target, double* f_dev,
+                                    void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && target && f_dev, FEM_EINVAL, "fem_assemble_rhs_noalloc: null argument");
+    assemble_rhs_noalloc(sys->S, *target, f_dev, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream) {
   return guarded([&]() -> fem_status {
     FEM_REQUIRE(sys && f_dev, FEM_EINVAL, "fem_system_get_rhs: null argument");

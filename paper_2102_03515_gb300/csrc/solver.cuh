@@ -74,6 +74,7 @@ constexpr int kMaxPartialBlocks = 1 << 16;
 void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem_target& t,
                      const fem_assemble_opts& o, cudaStream_t st);
 void assemble_rhs(System& S, const fem_target& t, double* f, cudaStream_t st);
+void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_t st);
 
 // ------------------------------------------------------------------ operators (ops.cu)
 // Chebyshev coefficients of one smoothing application of degree k on [lmax/ratio, lmax].
