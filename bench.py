@@ -34,6 +34,9 @@ BASELINE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
 # dominant kernel: the FP64 15-point stencil A p of every CG iteration; 2 flops per stored
 # stencil entry, FP64 peak from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one launch of that kernel at 255^3, from the ncu capture
+# summarised in profiles/k_stencil_fp64_n256.md
+STENCIL64_TRAFFIC = 133.181440e6 + 89.830144e6
 
 
 def _env_int(name, default):
@@ -384,7 +387,8 @@ def run_ours(args, rank: int, world: int):
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * N,
                 "ms_per_step": e2e_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": STENCIL64_TRAFFIC,
                      "kernel": "k_stencil<double> (q = A p, FP64 15-point stencil)",
                      "kernel_ms": kms, "flops_per_launch": flops,
                      "peak_source": "FP64 unit counts x max SM clock (no FP64 entry in the "
