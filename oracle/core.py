@@ -78,6 +78,10 @@ def _load():
             lib.ora_cholesky.restype = C.c_int
             lib.ora_cholesky_solve.argtypes = [C.c_int, P(C.c_double), P(C.c_double),
                                                P(C.c_double)]
+            lib.ora_kuhn_rows.argtypes = [C.c_int, P(C.c_double), P(_Target), C.c_int,
+                                          C.c_int64, P(C.c_int64), P(C.c_int32),
+                                          P(C.c_double), P(C.c_double), P(C.c_double)]
+            lib.ora_kuhn_rows.restype = C.c_int
             lib.ora_errors.argtypes = [C.c_int64, P(C.c_double), C.c_int64, P(C.c_int32),
                                        P(C.c_double), P(_Target), C.c_int, P(C.c_double),
                                        P(C.c_double)]
@@ -280,3 +284,30 @@ def errors(system: System, u: np.ndarray, exact: dict, qlevel: int = 1):
     _load().ora_errors(len(U), _dp(system.xyz), len(tets), _ip(tets), _dp(U), C.byref(t),
                        qlevel, C.byref(l2), C.byref(h1))
     return l2.value, h1.value
+
+
+def kuhn_rows(n: int, target: dict, rows, xyz: np.ndarray | None = None, qlevel: int = 0):
+    """Rows (unknown indices) of K, M and f for selected unknowns, without assembling the mesh.
+
+    Returns (cols [len, 15] with -1 padding, K [len, 15], M [len, 15], f [len])."""
+    m = n - 1
+    rows = np.asarray(rows, dtype=np.int64)
+    i = rows % m + 1
+    j = (rows // m) % m + 1
+    k = rows // (m * m) + 1
+    vtx = np.ascontiguousarray(i + (n + 1) * (j + (n + 1) * k), dtype=np.int64)
+    cols = np.empty((len(rows), 15), dtype=np.int32)
+    K = np.empty((len(rows), 15))
+    M = np.empty((len(rows), 15))
+    f = np.empty(len(rows))
+    t, keep = _target_struct(target)
+    xp = None
+    if xyz is not None:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        xp = _dp(xyz)
+    rc = _load().ora_kuhn_rows(n, xp, C.byref(t), qlevel, len(rows),
+                               vtx.ctypes.data_as(C.POINTER(C.c_int64)), _ip(cols), _dp(K),
+                               _dp(M), _dp(f))
+    if rc != 0:
+        raise ValueError("kuhn_rows: a vertex is not interior")
+    return cols, K, M, f

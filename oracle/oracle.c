@@ -559,3 +559,95 @@ void ora_errors(int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
   *l2sq = e2;
   *h1sq = g2;
 }
+
+/* ------------------------------------------------------------ single rows */
+
+/* Rows of K, M and f for selected interior vertices of the Kuhn mesh with n cells per side,
+ * each built from the tets of the 8 cubes around the vertex that contain it (the same
+ * element matrices and quadrature as ora_assemble, without building the whole mesh).
+ * xyz may be NULL (uniform grid).  vtx: vertex ids i + (n+1)(j + (n+1)k) of interior
+ * vertices.  Outputs per row: up to 15 unknown columns (sorted, -1 padded), K, M values and
+ * f.  Returns 0, or -1 if a vertex is not interior. */
+int ora_kuhn_rows(int n, const double *xyz, const target_t *T, int qlevel, int64_t nsel,
+                  const int64_t *vtx, int32_t *cols, double *Kout, double *Mout, double *fout) {
+  qrule_t Q = qrule_make(qlevel);
+  const int m = n - 1;
+  const double h = 1.0 / n;
+  for (int64_t s = 0; s < nsel; s++) {
+    int64_t v = vtx[s];
+    int i = (int)(v % (n + 1)), j = (int)((v / (n + 1)) % (n + 1)), k = (int)(v / ((int64_t)(n + 1) * (n + 1)));
+    if (i < 1 || j < 1 || k < 1 || i > m || j > m || k > m) {
+      qrule_free(&Q);
+      return -1;
+    }
+    int32_t rc[32];
+    double rk[32], rm[32];
+    int u = 0;
+    double fv = 0.0;
+    /* cubes with corner c = (i,j,k) - (a,b,d), in increasing cube id */
+    for (int dz = 1; dz >= 0; dz--)
+      for (int dy = 1; dy >= 0; dy--)
+        for (int dx = 1; dx >= 0; dx--) {
+          int c[3] = {i - dx, j - dy, k - dz};
+          if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= n || c[1] >= n || c[2] >= n) continue;
+          for (int p = 0; p < 6; p++) {
+            int w[4][3];
+            for (int d = 0; d < 3; d++) w[0][d] = c[d];
+            for (int st = 0; st < 3; st++) {
+              for (int d = 0; d < 3; d++) w[st + 1][d] = w[st][d];
+              w[st + 1][PERMS[p][st]] += 1;
+            }
+            int loc = -1;
+            for (int a = 0; a < 4; a++)
+              if (w[a][0] == i && w[a][1] == j && w[a][2] == k) loc = a;
+            if (loc < 0) continue;
+            double X[12], Ke[16], Me[16];
+            for (int a = 0; a < 4; a++) {
+              int64_t id = vid(n, w[a][0], w[a][1], w[a][2]);
+              for (int d = 0; d < 3; d++)
+                X[3 * a + d] = xyz ? xyz[3 * id + d] : w[a][d] * h;
+            }
+            double det = ora_element(X, Ke, Me);
+            double vol = fabs(det) / 6.0;
+            for (int b = 0; b < 4; b++) {
+              int bi = w[b][0], bj = w[b][1], bk = w[b][2];
+              if (bi < 1 || bj < 1 || bk < 1 || bi > m || bj > m || bk > m) continue;
+              int32_t col = (bi - 1) + m * ((bj - 1) + m * (bk - 1));
+              int q = 0;
+              while (q < u && rc[q] != col) q++;
+              if (q == u) {
+                rc[u] = col;
+                rk[u] = 0.0;
+                rm[u] = 0.0;
+                u++;
+              }
+              rk[q] += Ke[4 * loc + b];
+              rm[q] += Me[4 * loc + b];
+            }
+            double acc = 0.0;
+            for (int q = 0; q < Q.np; q++) {
+              double x[3] = {0, 0, 0};
+              for (int a = 0; a < 4; a++)
+                for (int d = 0; d < 3; d++) x[d] += Q.bary[4 * q + a] * X[3 * a + d];
+              acc += Q.wt[q] * target_eval(T, x) * Q.bary[4 * q + loc];
+            }
+            fv += vol * acc;
+          }
+        }
+    /* sort the row by column */
+    for (int a = 1; a < u; a++)
+      for (int b = a; b > 0 && rc[b - 1] > rc[b]; b--) {
+        int32_t tc = rc[b]; rc[b] = rc[b - 1]; rc[b - 1] = tc;
+        double tk = rk[b]; rk[b] = rk[b - 1]; rk[b - 1] = tk;
+        double tm = rm[b]; rm[b] = rm[b - 1]; rm[b - 1] = tm;
+      }
+    for (int q = 0; q < 15; q++) {
+      cols[15 * s + q] = q < u ? rc[q] : -1;
+      Kout[15 * s + q] = q < u ? rk[q] : 0.0;
+      Mout[15 * s + q] = q < u ? rm[q] : 0.0;
+    }
+    fout[s] = fv;
+  }
+  qrule_free(&Q);
+  return 0;
+}

@@ -149,9 +149,11 @@ __global__ void k_csr_uniform(int m, Stencil sa, Stencil sk, Stencil sm, int32_t
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < N + 1) rowptr[e] = (int32_t)(16 * e);
   if (e >= 16 * N) return;
-  const int64_t r = e >> 4;
+  // 32-bit index decode (16 N < 2^31 is checked at assembly)
+  const uint32_t r32 = (uint32_t)(e >> 4), um = (uint32_t)m;
+  const uint32_t q1 = r32 / um;
+  const int i = (int)(r32 - q1 * um), j = (int)(q1 % um), k = (int)(q1 / um);
   const int p = (int)(e & 15);
-  const int i = (int)(r % m), j = (int)((r / m) % m), k = (int)(r / ((int64_t)m * m));
   int cnt = 0, cl = -1, t = 0;
   for (int s = 0; s < 15; s++) {
     const int ii = i + kSlotOff[s][0], jj = j + kSlotOff[s][1], kk = k + kSlotOff[s][2];
@@ -406,7 +408,8 @@ __global__ void k_gather_load(int n, const double* cf, double* f) {
   int64_t N = (int64_t)m * m * m;
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
-  int i = (int)(r % m) + 1, j = (int)((r / m) % m) + 1, k = (int)(r / ((int64_t)m * m)) + 1;
+  const uint32_t r32 = (uint32_t)r, um = (uint32_t)m, q1 = r32 / um;
+  const int i = (int)(r32 - q1 * um) + 1, j = (int)(q1 % um) + 1, k = (int)(q1 / um) + 1;
   double s = 0.0;
   for (int dd = 7; dd >= 0; dd--) {
     int ci = i - (dd & 1), cj = j - ((dd >> 1) & 1), ck = k - ((dd >> 2) & 1);

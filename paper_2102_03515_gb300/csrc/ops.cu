@@ -174,6 +174,58 @@ __global__ void __launch_bounds__(TX* TY) k_stencil(const T* __restrict__ v, int
   write_partials<T>(acc, partials, partials != nullptr, nblocks);
 }
 
+// Column marching without shared memory: thread (i, j) walks k, carrying in registers the
+// values it needs again one plane later, and loads 7 values per point (plane k: the three
+// "minus" neighbours (i-1,j), (i,j-1), (i-1,j-1); plane k+1: (i,j), (i+1,j), (i,j+1),
+// (i+1,j+1)).  Warps run along i, so every load is coalesced; there are no barriers.
+template <typename T>
+__global__ void __launch_bounds__(TX* TY) k_stencil_col(const T* __restrict__ v, int m, SC<T> c,
+                                                        Epi<T> epi, double* partials,
+                                                        int nblocks, const int* done) {
+  using AT = typename Arith<T>::type;
+  if (done && *done) return;
+  const int i = blockIdx.x * TX + (threadIdx.x & (TX - 1));
+  const int j = blockIdx.y * TY + threadIdx.x / TX;
+  const int k0 = blockIdx.z * KZ;
+  const int kend = min(k0 + KZ, m);
+  double acc[2] = {0.0, 0.0};
+  if (i < m && j < m) {
+    const int64_t sj = m, sk = (int64_t)m * m;
+    const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1;
+    const T* col = v + (int64_t)i + sj * j;
+    auto ld = [&](bool ok, int k, int64_t off) -> AT {
+      return (ok && k >= 0 && k < m) ? (AT)__ldg(col + sk * k + off) : (AT)0;
+    };
+    // plane k0 - 1: centre and minus set; plane k0: centre and plus set
+    AT cm = ld(true, k0 - 1, 0);
+    AT m_im = ld(im, k0 - 1, -1), m_jm = ld(jm, k0 - 1, -sj), m_ijm = ld(im && jm, k0 - 1, -1 - sj);
+    AT c0v = ld(true, k0, 0);
+    AT p_ip = ld(ip, k0, 1), p_jp = ld(jp, k0, sj), p_ijp = ld(ip && jp, k0, 1 + sj);
+    const AT a0 = (AT)c.c0, aa = (AT)c.ca, af = (AT)c.cf, ab = (AT)c.cb;
+    for (int k = k0; k < kend; k++) {
+      // plane k minus set, plane k+1 centre and plus set
+      const AT z_im = ld(im, k, -1), z_jm = ld(jm, k, -sj), z_ijm = ld(im && jm, k, -1 - sj);
+      const AT cp = ld(true, k + 1, 0);
+      const AT n_ip = ld(ip, k + 1, 1), n_jp = ld(jp, k + 1, sj), n_ijp = ld(ip && jp, k + 1, 1 + sj);
+      const AT axis = z_im + p_ip + z_jm + p_jp + cm + cp;
+      const AT face = p_ijp + z_ijm + n_ip + m_im + n_jp + m_jm;
+      const AT body = n_ijp + m_ijm;
+      const AT av = a0 * c0v + aa * axis + af * face + ab * body;
+      epi((int64_t)i + sj * j + sk * k, av, acc);
+      // shift: plane k becomes k-1, plane k+1 becomes k
+      cm = c0v;
+      m_im = z_im;
+      m_jm = z_jm;
+      m_ijm = z_ijm;
+      c0v = cp;
+      p_ip = n_ip;
+      p_jp = n_jp;
+      p_ijp = n_ijp;
+    }
+  }
+  write_partials<T>(acc, partials, partials != nullptr, nblocks);
+}
+
 template <typename T>
 int launch_stencil(const Stencil& s, const T* v, const Epi<T>& epi, double* partials,
                    cudaStream_t st, const int* done = nullptr) {
@@ -182,7 +234,10 @@ int launch_stencil(const Stencil& s, const T* v, const Epi<T>& epi, double* part
   int nb = grid.x * grid.y * grid.z;
   FEM_REQUIRE(!partials || nb <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "stencil grid too large");
   SC<T> c{(T)s.c0, (T)s.ca, (T)s.cf, (T)s.cb};
-  k_stencil<T><<<grid, TX * TY, 0, st>>>(v, m, c, epi, partials, nb, done);
+  if (sizeof(T) == 4)  // bandwidth-bound: barrier-free column marching
+    k_stencil_col<T><<<grid, TX * TY, 0, st>>>(v, m, c, epi, partials, nb, done);
+  else  // FP64-ALU-bound: shared-memory planes
+    k_stencil<T><<<grid, TX * TY, 0, st>>>(v, m, c, epi, partials, nb, done);
   FEM_CHECK_LAUNCH();
   return nb;
 }

@@ -217,3 +217,22 @@ def test_load_vector_of_constant_target_is_lumped_mass():
     rowsum = np.asarray(full.M.sum(axis=1)).ravel()
     dof = core.interior_dof_map(n)
     np.testing.assert_allclose(s.f, rowsum[dof >= 0], rtol=1e-13)
+
+
+@pytest.mark.parametrize("jitter", [False, True])
+def test_single_rows_match_full_assembly(jitter):
+    # the row routine (used for sampled checks on meshes too large to assemble on the CPU)
+    # restates the same integrals: it must reproduce the assembled rows exactly
+    n = 9
+    xyz = W.jittered_xyz(n, 0.2, seed=4) if jitter else None
+    t = W.bump_target(12)
+    s = core.assemble(n, t, xyz=xyz)
+    rows = np.arange(s.K.shape[0])
+    cols, K, M, f = core.kuhn_rows(n, t, rows, xyz=xyz)
+    for r in rows:
+        sl = slice(s.K.indptr[r], s.K.indptr[r + 1])
+        ln = s.K.indptr[r + 1] - s.K.indptr[r]
+        assert np.array_equal(cols[r, :ln], s.K.indices[sl]) and np.all(cols[r, ln:] == -1)
+        np.testing.assert_allclose(K[r, :ln], s.K.data[sl], rtol=1e-13, atol=1e-16)
+        np.testing.assert_allclose(M[r, :ln], s.M.data[sl], rtol=1e-13, atol=1e-19)
+    np.testing.assert_allclose(f, s.f, rtol=1e-13, atol=1e-18)
