@@ -271,9 +271,32 @@ void pcg_batch_destroy(pcg_batch b);
 /* Message of the last failure on this thread ("" if none). */
 const char* fem_last_error(void);
 
-/* Autotuner cache as JSON text (choices and timings per kernel shape). The string is
- * owned by the library and valid until the next call. */
+/* Launch-shape autotuner (no counterpart in the paper).  Kernels with several launch
+ * shapes -- lanes per row of the CSR SpMV, tile rows and planes per block of the stencil,
+ * block shape of the multivector kernels -- are timed once per operator shape with CUDA
+ * events, inside amg_setup (single-vector kernels) and pcg_batch_create / batched
+ * pcg_solve (multivector kernels), never while a stream is being captured.  The fastest
+ * variant is cached for the process under (kernel, rows, stored entries, slots) and used
+ * by every later launch of that shape; untuned shapes take a fixed default.  A choice
+ * changes only the order of floating-point sums.  Environment: FEM_AUTOTUNE=0 disables
+ * timing (defaults everywhere); FEM_AUTOTUNE_CACHE=<file> reads choices from and appends
+ * new ones to a text file ("kernel rows entries slots variant" per line).
+ *
+ * fem_autotune_report: the cache as JSON text, {"enabled": bool, "entries": [{"kernel",
+ * "a", "b", "c", "source": "timed"|"file", "pick", "pick_name", "variants": [{"name",
+ * "us"}]}]}.  The string is owned by the library (thread-local) and valid until the
+ * thread's next call.
+ * fem_autotune_clear: forgets every choice and pin (later launches take defaults until
+ * tuned again); does not touch the cache file.
+ * fem_autotune_pin: forces variant `variant` of kernel family `kernel` for every shape
+ * ("stencil_f32", "stencil_f64": 0 shared-memory planes, 1..5 column marching;
+ * "csr_f64", "csr_f32", "csr_bf16": lanes per row 1 << variant; "mv_stencil_f32",
+ * "mv_stencil_f64", "mv_csr_f32", "mv_csr_f64": see fem_autotune_report's variant names);
+ * variant < 0 removes the pin.  A pin outside a family's range is ignored.  Returns
+ * FEM_EINVAL for a null kernel name. */
 const char* fem_autotune_report(void);
+void fem_autotune_clear(void);
+fem_status fem_autotune_pin(const char* kernel, int32_t variant);
 
 /* Library version string. */
 const char* fem_version(void);

@@ -114,6 +114,8 @@ SIGNATURES = {
     "pcg_batch_destroy": (None, [VP]),
     "fem_last_error": (C.c_char_p, []),
     "fem_autotune_report": (C.c_char_p, []),
+    "fem_autotune_clear": (None, []),
+    "fem_autotune_pin": (C.c_int, [C.c_char_p, C.c_int32]),
     "fem_version": (C.c_char_p, []),
     "fem_kernel_launches": (C.c_int64, []),
 }
@@ -172,8 +174,19 @@ def fem_kernel_launches() -> int:
     return int(lib().fem_kernel_launches())
 
 
-def fem_autotune_report() -> str:
-    return lib().fem_autotune_report().decode()
+def fem_autotune_report() -> dict:
+    """The autotuner's choices and timings (parsed JSON)."""
+    import json
+    return json.loads(lib().fem_autotune_report().decode())
+
+
+def fem_autotune_clear() -> None:
+    lib().fem_autotune_clear()
+
+
+def fem_autotune_pin(kernel: str, variant: int) -> None:
+    """Force `variant` of a kernel family for every shape (variant < 0: unpin)."""
+    _check(lib().fem_autotune_pin(kernel.encode(), int(variant)), "fem_autotune_pin")
 
 
 # ------------------------------------------------------------------ system

@@ -84,44 +84,95 @@ __device__ __forceinline__ float smoother_sinv(const MvEpi<T>& e, int64_t i, int
   return c.sinv;
 }
 
+// The epilogue in two parts, like the single-vector one: mv_load() fetches the operands of
+// (i, b) so that kernels can issue those loads early, mv_apply() finishes the entry;
+// "centre" is v[i][b] (dold in mode 2), which the stencil kernels hold in a register.
 template <typename T>
-__device__ __forceinline__ void mv_epi(const MvEpi<T>& e, int64_t i, int b, typename Arith<T>::type av,
-                                       double acc[2]) {
+struct MvOps {
+  typename Arith<T>::type a, x, s;
+  double r1, r2;
+};
+
+template <typename T>
+__device__ __forceinline__ MvOps<T> mv_load(const MvEpi<T>& e, int64_t i, int b) {
+  using AT = typename Arith<T>::type;
+  MvOps<T> o;
+  o.a = (AT)0;
+  o.x = (AT)0;
+  o.s = (AT)0;
+  o.r1 = 0.0;
+  o.r2 = 0.0;
+  const int64_t idx = i * e.B + b;
+  switch (e.mode) {
+    case 0:
+      if (e.want_dot) o.a = (AT)e.x[idx];
+      break;
+    case 1:
+      o.a = (AT)e.b[idx];
+      break;
+    case 3:
+      o.a = (AT)e.b[idx];
+      o.s = (AT)smoother_sinv(e, i, b);
+      break;
+    case 2:
+      o.a = (AT)e.r[idx];
+      o.s = (AT)smoother_sinv(e, i, b);
+      o.x = (AT)e.x[idx];
+      if (e.z64) {
+        o.r1 = e.r1[idx];
+        o.r2 = e.r2[idx];
+      }
+      break;
+  }
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void mv_apply(const MvEpi<T>& e, int64_t i, int b,
+                                         typename Arith<T>::type av,
+                                         typename Arith<T>::type centre, const MvOps<T>& o,
+                                         double acc[2]) {
   using AT = typename Arith<T>::type;
   const int64_t idx = i * e.B + b;
   switch (e.mode) {
     case 0:
       e.y[idx] = (T)av;
-      if (e.want_dot) acc[0] += (double)e.x[idx] * (double)av;
+      if (e.want_dot) acc[0] += (double)o.a * (double)av;
       break;
     case 1:
-      e.y[idx] = (T)((AT)e.b[idx] - av);
+      e.y[idx] = (T)(o.a - av);
       break;
     case 3: {
       const LevCoef& c = e.lc[e.level * e.B + b];
-      AT s = (AT)smoother_sinv(e, i, b);
-      AT rr = s * ((AT)e.b[idx] - av);
+      AT rr = o.s * (o.a - av);
       e.r[idx] = (T)rr;
       e.dnew[idx] = (T)((AT)c.inv_theta * rr);
     } break;
     case 2: {
       const LevCoef& c = e.lc[e.level * e.B + b];
-      AT s = (AT)smoother_sinv(e, i, b);
-      AT rr = (AT)e.r[idx] - s * av;
-      AT dl = (AT)e.dold[idx];
+      AT rr = o.a - o.s * av;
+      AT dl = centre;
       AT dn = (AT)c.c1 * dl + (AT)c.c2 * rr;
       e.r[idx] = (T)rr;
       e.dnew[idx] = (T)dn;
-      AT xv = (AT)e.x[idx] + (e.add_prev ? dl : (AT)0) + dn;
+      AT xv = o.x + (e.add_prev ? dl : (AT)0) + dn;
       e.x[idx] = (T)xv;
       if (e.z64) {
         double z = (double)xv;
         e.z64[idx] = z;
-        acc[0] += z * e.r1[idx];
-        acc[1] += z * e.r2[idx];
+        acc[0] += z * o.r1;
+        acc[1] += z * o.r2;
       }
     } break;
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void mv_epi(const MvEpi<T>& e, int64_t i, int b, typename Arith<T>::type av,
+                                       double acc[2]) {
+  using AT = typename Arith<T>::type;
+  const AT centre = e.mode == 2 ? (AT)e.dold[i * e.B + b] : (AT)0;
+  mv_apply<T>(e, i, b, av, centre, mv_load<T>(e, i, b), acc);
 }
 
 // per-slot block reduction: threads of a block cover (points x slots) with slot = tid % B
@@ -135,6 +186,28 @@ __device__ __forceinline__ void slot_partials(double (&acc)[NV], int B, double* 
     for (int k = 0; k < NV; k++) {
       double s = 0.0;
       for (int t = threadIdx.x; t < (int)blockDim.x; t += B) s += sh[k][t];
+      partials[((int64_t)k * B + threadIdx.x) * nblocks + bid] = s;
+    }
+  }
+}
+
+// The same reduction for kernels whose threads each hold VS consecutive slots of one row:
+// thread t covers row t / (B / VS) of the block and slots (t % (B / VS)) * VS + q.  The
+// partial sum of a slot adds the block's rows in ascending order, as above.
+template <int VS>
+__device__ __forceinline__ void slot_partials_vs(double (&acc)[VS][2], int nv, int B,
+                                                 double* partials, int nblocks, int bid) {
+  __shared__ double sh[2][256 * VS];
+  const int tpr = B / VS;
+  const int r = threadIdx.x / tpr, g = threadIdx.x % tpr;
+  const int rpb = blockDim.x / tpr;
+  for (int k = 0; k < nv; k++)
+    for (int q = 0; q < VS; q++) sh[k][r * B + g * VS + q] = acc[q][k];
+  __syncthreads();
+  if ((int)threadIdx.x < B) {
+    for (int k = 0; k < nv; k++) {
+      double s = 0.0;
+      for (int rr = 0; rr < rpb; rr++) s += sh[k][rr * B + threadIdx.x];
       partials[((int64_t)k * B + threadIdx.x) * nblocks + bid] = s;
     }
   }
@@ -169,6 +242,80 @@ __global__ void __launch_bounds__(256) k_mv_stencil(const T* __restrict__ v, int
   }
   if (NV > 0 && partials)
     slot_partials<2>(acc, B, partials, nblocks, blockIdx.x + gridDim.x * blockIdx.y);
+}
+
+// Column marching (as in the single-vector stencil): thread (point i, slot b) of a block
+// walks k over KZV planes of each of its rows j, keeping in registers the values it needs
+// again one plane later (7 loads per point instead of 15) and issuing the loads of point
+// k + 1 before finishing point k.  grid: x over groups of 256 / B points along i, y strides
+// over j, z over plane ranges.
+template <typename T, int NV, int KZV>
+__global__ void __launch_bounds__(256) k_mv_stencil_col(const T* __restrict__ v, int m, MvEpi<T> e,
+                                                        double* partials, int nblocks) {
+  using AT = typename Arith<T>::type;
+  using Ops = MvOps<T>;
+  const int B = e.B;
+  const int b = threadIdx.x & (B - 1);
+  const int ppb = blockDim.x / B;
+  const int i = blockIdx.x * ppb + threadIdx.x / B;
+  const int k0 = blockIdx.z * KZV;
+  const int kend = min(k0 + KZV, m);
+  double acc[2] = {0.0, 0.0};
+  const LevCoef& c = e.lc[e.level * B + b];
+  const AT a0 = (AT)c.c0, aa = (AT)c.ca, af = (AT)c.cf, ab = (AT)c.cb;
+  const int64_t sB = B, sj = (int64_t)m * B, sk = (int64_t)m * m * B, pk = (int64_t)m * m;
+  if (i < m) {
+    for (int j = blockIdx.y; j < m; j += gridDim.y) {
+      const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1;
+      const int64_t row0 = (int64_t)i + (int64_t)m * j;
+      const T* col = v + row0 * B + b;
+      auto ld = [&](bool ok, int k, int64_t off) -> AT {
+        return (ok && k >= 0 && k < m) ? (AT)__ldg(col + sk * k + off) : (AT)0;
+      };
+      AT cm = ld(true, k0 - 1, 0);
+      AT m_im = ld(im, k0 - 1, -sB), m_jm = ld(jm, k0 - 1, -sj), m_ijm = ld(im && jm, k0 - 1, -sB - sj);
+      AT c0v = ld(true, k0, 0);
+      AT p_ip = ld(ip, k0, sB), p_jp = ld(jp, k0, sj), p_ijp = ld(ip && jp, k0, sB + sj);
+      AT z_im = ld(im, k0, -sB), z_jm = ld(jm, k0, -sj), z_ijm = ld(im && jm, k0, -sB - sj);
+      AT cp = ld(true, k0 + 1, 0);
+      AT n_ip = ld(ip, k0 + 1, sB), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, sB + sj);
+      Ops op = mv_load<T>(e, row0 + pk * k0, b);
+      for (int k = k0; k < kend; k++) {
+        const bool more = k + 1 < kend;
+        const AT z2_im = ld(im && more, k + 1, -sB), z2_jm = ld(jm && more, k + 1, -sj),
+                 z2_ijm = ld(im && jm && more, k + 1, -sB - sj);
+        const AT cp2 = ld(more, k + 2, 0);
+        const AT n2_ip = ld(ip && more, k + 2, sB), n2_jp = ld(jp && more, k + 2, sj),
+                 n2_ijp = ld(ip && jp && more, k + 2, sB + sj);
+        Ops op2;
+        if (more) op2 = mv_load<T>(e, row0 + pk * (k + 1), b);
+        const AT axis = z_im + p_ip + z_jm + p_jp + cm + cp;
+        const AT face = p_ijp + z_ijm + n_ip + m_im + n_jp + m_jm;
+        const AT body = n_ijp + m_ijm;
+        const AT av = a0 * c0v + aa * axis + af * face + ab * body;
+        mv_apply<T>(e, row0 + pk * k, b, av, c0v, op, acc);
+        cm = c0v;
+        m_im = z_im;
+        m_jm = z_jm;
+        m_ijm = z_ijm;
+        c0v = cp;
+        p_ip = n_ip;
+        p_jp = n_jp;
+        p_ijp = n_ijp;
+        z_im = z2_im;
+        z_jm = z2_jm;
+        z_ijm = z2_ijm;
+        cp = cp2;
+        n_ip = n2_ip;
+        n_jp = n2_jp;
+        n_ijp = n2_ijp;
+        if (more) op = op2;
+      }
+    }
+  }
+  if (NV > 0 && partials)
+    slot_partials<2>(acc, B, partials, nblocks,
+                     blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
 // FP64 stencil for q = A(rho_b) p with per-slot coefficients in FP64 and <p, q> per slot
@@ -214,9 +361,47 @@ __global__ void __launch_bounds__(256) k_mv_stencil64(const double* __restrict__
 
 // ------------------------------------------------------------------ multivector CSR
 
+template <typename T, int VS>
+struct VecLd;
+template <typename T>
+struct VecLd<T, 1> {
+  __device__ static void load(const T* p, T o[1]) { o[0] = __ldg(p); }
+};
+template <>
+struct VecLd<float, 2> {
+  __device__ static void load(const float* p, float o[2]) {
+    float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    o[0] = a.x; o[1] = a.y;
+  }
+};
+template <>
+struct VecLd<float, 4> {
+  __device__ static void load(const float* p, float o[4]) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
+};
+template <>
+struct VecLd<double, 2> {
+  __device__ static void load(const double* p, double o[2]) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = a.x; o[1] = a.y;
+  }
+};
+template <>
+struct VecLd<double, 4> {
+  __device__ static void load(const double* p, double o[4]) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    double2 c = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+  }
+};
+
 // y[i][b] op ((rho_b K + M) v)[i][b] (pencil) or (Mat v)[i][b] (kv null: single values mv).
-// One thread per (row, slot): the row's entries are broadcast, the slot reads coalesce.
-template <typename T, typename VT, int NV>
+// B / VS threads per row, each holding VS consecutive slots (vector loads of v); the row's
+// entries are read once per thread and shared by its VS slots.  Per (row, slot) the sum
+// runs over the row's entries in stored order whatever VS is.
+template <typename T, typename VT, int NV, int VS>
 __global__ void __launch_bounds__(256) k_mv_csr(int64_t nrows, const int32_t* __restrict__ rowptr,
                                                 const int32_t* __restrict__ col,
                                                 const VT* __restrict__ kv, const VT* __restrict__ mv,
@@ -224,29 +409,47 @@ __global__ void __launch_bounds__(256) k_mv_csr(int64_t nrows, const int32_t* __
                                                 double* partials, int nblocks) {
   using AT = typename Arith<T>::type;
   const int B = e.B;
-  const int b = threadIdx.x % B;
-  const int rpb = blockDim.x / B;
-  const AT rb = kv ? (AT)e.rho[b] : (AT)0;
-  double acc[2] = {0.0, 0.0};
+  const int tpr = B / VS;
+  const int b0 = (threadIdx.x % tpr) * VS;
+  const int rpb = blockDim.x / tpr;
+  AT rb[VS];
+#pragma unroll
+  for (int q = 0; q < VS; q++) rb[q] = kv ? (AT)e.rho[b0 + q] : (AT)0;
+  double acc[VS][2];
+#pragma unroll
+  for (int q = 0; q < VS; q++) acc[q][0] = acc[q][1] = 0.0;
   for (int64_t base = (int64_t)blockIdx.x * rpb; base < nrows; base += (int64_t)gridDim.x * rpb) {
-    const int64_t i = base + threadIdx.x / B;
+    const int64_t i = base + threadIdx.x / tpr;
     if (i < nrows) {
-      AT s = 0;
-      for (int q = rowptr[i]; q < rowptr[i + 1]; q++) {
-        const int c = col[q];
+      AT s[VS];
+#pragma unroll
+      for (int q = 0; q < VS; q++) s[q] = (AT)0;
+      const int e1 = rowptr[i + 1];
+      for (int p = rowptr[i]; p < e1; p++) {
+        const int c = col[p];
         if (c < 0) continue;
-        const AT w = kv ? rb * (AT)kv[q] + (AT)mv[q] : (AT)mv[q];
-        s += w * (AT)v[(int64_t)c * B + b];
+        const AT kq = kv ? (AT)kv[p] : (AT)0;
+        const AT mq = (AT)mv[p];
+        T vv[VS];
+        VecLd<T, VS>::load(v + (int64_t)c * B + b0, vv);
+#pragma unroll
+        for (int q = 0; q < VS; q++) {
+          const AT w = kv ? rb[q] * kq + mq : mq;
+          s[q] += w * (AT)vv[q];
+        }
       }
-      if (accumulate) {
-        const int64_t idx = i * B + b;
-        e.y[idx] = (T)((AT)e.y[idx] + s);
-      } else {
-        mv_epi<T>(e, i, b, s, acc);
+#pragma unroll
+      for (int q = 0; q < VS; q++) {
+        if (accumulate) {
+          const int64_t idx = i * B + b0 + q;
+          e.y[idx] = (T)((AT)e.y[idx] + s[q]);
+        } else {
+          mv_epi<T>(e, i, b0 + q, s[q], acc[q]);
+        }
       }
     }
   }
-  if (NV > 0 && partials) slot_partials<2>(acc, B, partials, nblocks, blockIdx.x);
+  if (NV > 0 && partials) slot_partials_vs<VS>(acc, NV, B, partials, nblocks, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ elementwise
@@ -292,19 +495,27 @@ __global__ void k_mv_dense(int64_t Nc, int B, const double* Ainv, const T* rhs, 
   if (lane == 0) x[i * B + b] = (T)s;
 }
 
-// dense per-slot coarse matrices from the pencil: D_b = rho_b K + M
+// dense coarse matrices from the pencil, D = rho K + M, for the admitted slots (grid.y)
 __global__ void k_mv_dense_build(int64_t Nc, const int32_t* rowptr, const int32_t* col,
-                                 const double* kv, const double* mv, const double* rho, int slot,
-                                 double* D) {
+                                 const double* kv, const double* mv, const double* rho,
+                                 const int32_t* slots, double* Ainv) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= Nc) return;
-  double* Dr = D + r * Nc;
+  const double rh = rho[blockIdx.y];
+  double* Dr = Ainv + (int64_t)slots[blockIdx.y] * Nc * Nc + r * Nc;
   for (int64_t c = 0; c < Nc; c++) Dr[c] = 0.0;
   for (int e = rowptr[r]; e < rowptr[r + 1]; e++)
-    if (col[e] >= 0) Dr[col[e]] += rho[slot] * kv[e] + mv[e];
+    if (col[e] >= 0) Dr[col[e]] += rh * kv[e] + mv[e];
 }
 
-__global__ void k_gj_step_b(int64_t N, int64_t k, const double* __restrict__ D, double* __restrict__ E) {
+// One Gauss-Jordan step (pivot k) for the admitted slots (grid.y): between the slot's
+// matrix in Ainv and its ping-pong buffer in tmp, direction given by from_tmp.
+__global__ void k_gj_step_b(int64_t N, int64_t k, double* Ainv, double* tmp, const int32_t* slots,
+                            int from_tmp) {
+  const double* D = from_tmp ? tmp + (int64_t)blockIdx.y * N * N
+                             : Ainv + (int64_t)slots[blockIdx.y] * N * N;
+  double* E = from_tmp ? Ainv + (int64_t)slots[blockIdx.y] * N * N
+                       : tmp + (int64_t)blockIdx.y * N * N;
   __shared__ double inv_p;
   if (threadIdx.x == 0) inv_p = 1.0 / D[k * N + k];
   __syncthreads();
@@ -321,10 +532,20 @@ __global__ void k_gj_step_b(int64_t N, int64_t k, const double* __restrict__ D, 
   }
 }
 
-// Gershgorin bound of D^{-1} A(rho) for one slot: block maxima of sum_j |a_ij| / a_ii
+__global__ void k_gj_copy_back(int64_t N, const double* tmp, double* Ainv, const int32_t* slots) {
+  const double* src = tmp + (int64_t)blockIdx.y * N * N;
+  double* dst = Ainv + (int64_t)slots[blockIdx.y] * N * N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N * N;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = src[t];
+}
+
+// Gershgorin bounds of D^{-1} A(rho) for the admitted rho values (grid.y): block maxima of
+// sum_j |a_ij| / a_ii in bmax[y * nb + block]
 __global__ void k_mv_gersh(int64_t N, const int32_t* rowptr, const int32_t* col, const double* kv,
-                           const double* mv, double rho, double* bmax) {
+                           const double* mv, const double* rhos, double* bmax, int nb) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double rho = rhos[blockIdx.y];
   double q = -1.0;
   if (r < N) {
     double s = 0.0, d = 0.0;
@@ -337,14 +558,15 @@ __global__ void k_mv_gersh(int64_t N, const int32_t* rowptr, const int32_t* col,
     q = s / d;
   }
   q = block_max(q);
-  if (threadIdx.x == 0) bmax[blockIdx.x] = q;
+  if (threadIdx.x == 0) bmax[(int64_t)blockIdx.y * nb + blockIdx.x] = q;
 }
 
+// per-block maxima of row y (one block per row) -> out[y]
 __global__ void k_max_red(const double* in, int n, double* out) {
   double q = -1.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) q = fmax(q, in[i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) q = fmax(q, in[(int64_t)blockIdx.x * n + i]);
   q = block_max(q);
-  if (threadIdx.x == 0) *out = q;
+  if (threadIdx.x == 0) out[blockIdx.x] = q;
 }
 
 __global__ void k_diag_f(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
@@ -362,55 +584,94 @@ __global__ void k_to_f32(int64_t n, const double* a, float* b) {
   if (i < n) b[i] = (float)a[i];
 }
 
-// column copies between a [N][ld] user array and slot b of a [N][B] multivector
-__global__ void k_col_in(int64_t N, int B, int slot, const double* src, int64_t ld, int scol,
-                         double* dst) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) dst[i * B + slot] = src[i * ld + scol];
-}
-__global__ void k_col_out(int64_t N, int B, int slot, const double* src, double* dst, int64_t ld,
-                          int dcol) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) dst[i * ld + dcol] = src[i * B + slot];
-}
-__global__ void k_col_set(int64_t N, int B, int slot, double v, double* dst) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) dst[i * B + slot] = v;
+// admission of `count` columns: f and r of slot slots[k] from column c0 + k of the caller's
+// [N][ld] array, x = p = r_prev = 0, and the slot's rho.  Block (kx, ty): threadIdx.x = k,
+// so a warp reads consecutive columns of one row of the caller's array.
+__global__ void k_cols_admit(int64_t N, int B, int count, const int32_t* slots,
+                             const double* rhos, const double* src, int64_t ld, int c0, double* f,
+                             double* r, double* x, double* p, double* rprev, double* rho) {
+  const int k = threadIdx.x;
+  if (k >= count) return;
+  const int slot = slots[k];
+  if (blockIdx.x == 0 && threadIdx.y == 0) rho[slot] = rhos[k];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < N;
+       i += (int64_t)gridDim.x * blockDim.y) {
+    const double v = src[i * ld + c0 + k];
+    const int64_t idx = i * B + slot;
+    f[idx] = v;
+    r[idx] = v;
+    x[idx] = 0.0;
+    p[idx] = 0.0;
+    rprev[idx] = 0.0;
+  }
 }
 
-// per-slot dot products <a_b, a_b> (for ||f||) of one column
-__global__ void k_col_norm2(int64_t N, int B, int slot, const double* a, double* partials) {
+// retirement of `count` slots: column c0 + k of the caller's [N][ld] array = x of slots[k]
+__global__ void k_cols_out(int64_t N, int B, int count, const int32_t* slots, const double* src,
+                           double* dst, int64_t ld, int c0) {
+  const int k = threadIdx.x;
+  if (k >= count) return;
+  const int slot = slots[k];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < N;
+       i += (int64_t)gridDim.x * blockDim.y)
+    dst[i * ld + c0 + k] = src[i * B + slot];
+}
+
+// per-slot partial sums of <a_b, a_b> (for ||f||), every slot at once (the order of a
+// slot's sum does not depend on which slots are being admitted)
+__global__ void k_mv_norm2(int64_t N, int B, const double* a, double* partials, int nblocks) {
   double acc[1] = {0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double v = a[i * B + slot];
-    acc[0] += v * v;
+  const int b = threadIdx.x % B;
+  const int rpb = blockDim.x / B;
+  for (int64_t base = (int64_t)blockIdx.x * rpb; base < N; base += (int64_t)gridDim.x * rpb) {
+    const int64_t i = base + threadIdx.x / B;
+    if (i < N) {
+      const double v = a[i * B + b];
+      acc[0] += v * v;
+    }
   }
-  block_sum<1>(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+  slot_partials<1>(acc, B, partials, nblocks, blockIdx.x);
 }
 
-// partial sums of ||f_b - q_b||^2 and ||f_b||^2 for one slot
-__global__ void k_col_resid2(int64_t N, int B, int slot, const double* f, const double* q,
-                             double* partials) {
+// per-slot partial sums of ||f_b - q_b||^2 and ||f_b||^2, every slot at once
+__global__ void k_mv_resid2(int64_t N, int B, const double* f, const double* q, double* partials,
+                            int nblocks) {
   double acc[2] = {0.0, 0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double fv = f[i * B + slot], d = fv - q[i * B + slot];
-    acc[0] += d * d;
-    acc[1] += fv * fv;
+  const int b = threadIdx.x % B;
+  const int rpb = blockDim.x / B;
+  for (int64_t base = (int64_t)blockIdx.x * rpb; base < N; base += (int64_t)gridDim.x * rpb) {
+    const int64_t i = base + threadIdx.x / B;
+    if (i < N) {
+      const int64_t idx = i * B + b;
+      const double fv = f[idx], d = fv - q[idx];
+      acc[0] += d * d;
+      acc[1] += fv * fv;
+    }
   }
-  block_sum<2>(acc);
+  slot_partials<2>(acc, B, partials, nblocks, blockIdx.x);
+}
+
+// out[2 b + k] = sum over blocks of partial k of slot b (fixed order)
+__global__ void k_slot_sums2(const double* partials, int nb, int B, double* out) {
+  const int b = blockIdx.x;
+  double v[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    v[0] += partials[(int64_t)(0 * B + b) * nb + i];
+    v[1] += partials[(int64_t)(1 * B + b) * nb + i];
+  }
+  block_sum<2>(v);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = acc[0];
-    partials[gridDim.x + blockIdx.x] = acc[1];
+    out[2 * b] = v[0];
+    out[2 * b + 1] = v[1];
   }
 }
 
-__global__ void k_slot_admit(SlotState* S, int slot, const double* sums, int nb, double rho,
-                             double tol, int maxit) {
+__global__ void k_slot_admit(SlotState* S, const int32_t* slots, const double* sums, int nb,
+                             const double* rhos, double tol, int maxit) {
+  const int slot = slots[blockIdx.x];
+  const double rho = rhos[blockIdx.x];
   double v[1] = {0.0};
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) v[0] += sums[i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v[0] += sums[(int64_t)slot * nb + i];
   block_sum<1>(v);
   if (threadIdx.x == 0) {
     SlotState& s = S[slot];
@@ -638,6 +899,88 @@ dim3 mv_sgrid(int m, int B) {
   return dim3(gx, gy, 1);
 }
 
+// ------------------------------------------------------------------ tuned launches
+
+// FP32 multivector stencil variants: 0 one thread per (point, slot) striding over planes,
+// 1..3 column marching over 16, 32, 64 planes per block.
+constexpr int kMvStencilVariants = 4;
+const char* const kMvStencilNames[kMvStencilVariants] = {"point", "col_kz16", "col_kz32",
+                                                         "col_kz64"};
+// multivector CSR variants: 1, 2, 4 slots per thread
+constexpr int kMvCsrVariants = 3;
+const char* const kMvCsrNames[kMvCsrVariants] = {"vs1", "vs2", "vs4"};
+
+dim3 mv_colgrid(int m, int B, int kz) {
+  const int ppb = 256 / B;
+  const int gx = (m + ppb - 1) / ppb, gz = (m + kz - 1) / kz;
+  int gy = (8 * num_sms() + gx * gz - 1) / (gx * gz);
+  if (gy > m) gy = m;
+  if (gy < 1) gy = 1;
+  return dim3(gx, gy, gz);
+}
+
+dim3 mv_stencil_grid(int var, int m, int B) {
+  switch (var) {
+    case 1: return mv_colgrid(m, B, 16);
+    case 2: return mv_colgrid(m, B, 32);
+    case 3: return mv_colgrid(m, B, 64);
+    default: return mv_sgrid(m, B);
+  }
+}
+
+template <int NV>
+int launch_mv_stencil32(int var, const float* v, int m, const MvEpi<float>& e, double* part,
+                        cudaStream_t st) {
+  const dim3 g = mv_stencil_grid(var, m, e.B);
+  const int nb = (int)(g.x * g.y * g.z);
+  switch (var) {
+    case 1: k_mv_stencil_col<float, NV, 16><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 2: k_mv_stencil_col<float, NV, 32><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 3: k_mv_stencil_col<float, NV, 64><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    default: k_mv_stencil<float, NV><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+  }
+  FEM_CHECK_LAUNCH();
+  return nb;
+}
+
+int mv_stencil32(int m, const float* v, const MvEpi<float>& e, double* part, cudaStream_t st) {
+  const int var = tuned_variant("mv_stencil_f32", m, 0, e.B, 1, kMvStencilVariants);
+  return part ? launch_mv_stencil32<2>(var, v, m, e, part, st)
+              : launch_mv_stencil32<0>(var, v, m, e, nullptr, st);
+}
+
+template <typename T>
+const char* mv_csr_key() { return sizeof(T) == 8 ? "mv_csr_f64" : "mv_csr_f32"; }
+
+template <typename T, typename VT, int NV>
+int launch_mv_csr(int var, const Csr4& A, const VT* kv, const VT* mv, const T* v,
+                  const MvEpi<T>& e, int accumulate, double* part, cudaStream_t st) {
+  const int64_t N = A.nrows;
+  int vs = 1 << var;
+  if (vs > e.B) vs = e.B;
+  const int tpr = e.B / vs, rpb = 256 / tpr;
+  const unsigned g = persistent_grid((N + rpb - 1) / rpb * 256, 256, 8);
+  switch (vs) {
+    case 2:
+      k_mv_csr<T, VT, NV, 2><<<g, 256, 0, st>>>(N, A.rowptr, A.col, kv, mv, v, e, accumulate, part, g);
+      break;
+    case 4:
+      k_mv_csr<T, VT, NV, 4><<<g, 256, 0, st>>>(N, A.rowptr, A.col, kv, mv, v, e, accumulate, part, g);
+      break;
+    default:
+      k_mv_csr<T, VT, NV, 1><<<g, 256, 0, st>>>(N, A.rowptr, A.col, kv, mv, v, e, accumulate, part, g);
+  }
+  FEM_CHECK_LAUNCH();
+  return (int)g;
+}
+
+template <typename T, typename VT, int NV>
+int mv_csr(const Csr4& A, const VT* kv, const VT* mv, const T* v, const MvEpi<T>& e,
+           int accumulate, double* part, cudaStream_t st) {
+  const int var = tuned_variant(mv_csr_key<T>(), A.nrows, A.nnz, e.B, 0, kMvCsrVariants);
+  return launch_mv_csr<T, VT, NV>(var, A, kv, mv, v, e, accumulate, part, st);
+}
+
 // One V-cycle on all slots (FP32), levels lev.., with the finest-level right-hand side
 // given in FP64 (b64) and the output written to z64 with per-slot dots.
 void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
@@ -661,24 +1004,15 @@ void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
   const bool finest = lev == 0;
   double* part = W.partials;
   const int m = W.S->n - 1;
-  const dim3 sg = mv_sgrid(m, B);
   auto op = [&](const float* v, MvEpi<float> e, bool dots) {
-    if (L.stencil) {
-      if (dots) {
-        k_mv_stencil<float, 2><<<sg, 256, 0, st>>>(v, m, e, part, sg.x * sg.y);
-        W.nb_fine = sg.x * sg.y;
-      } else {
-        k_mv_stencil<float, 0><<<sg, 256, 0, st>>>(v, m, e, nullptr, sg.x * sg.y);
-      }
-    } else {
-      if (dots)
-        k_mv_csr<float, float, 2><<<g, 256, 0, st>>>(N, L.A->rowptr, L.A->col, L.Kv, L.Mv, v, e, 0,
-                                                     part, g);
-      else
-        k_mv_csr<float, float, 0><<<g, 256, 0, st>>>(N, L.A->rowptr, L.A->col, L.Kv, L.Mv, v, e, 0,
-                                                     nullptr, g);
-    }
-    FEM_CHECK_LAUNCH();
+    int nb;
+    if (L.stencil)
+      nb = mv_stencil32(m, v, e, dots ? part : nullptr, st);
+    else if (dots)
+      nb = mv_csr<float, float, 2>(*L.A, L.Kv.p, L.Mv.p, v, e, 0, part, st);
+    else
+      nb = mv_csr<float, float, 0>(*L.A, L.Kv.p, L.Mv.p, v, e, 0, nullptr, st);
+    if (dots) W.nb_fine = nb;
   };
   if (L.coarsest && L.dense) {
     if (finest) {
@@ -735,17 +1069,13 @@ void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
     MvEpi<float> e = base;
     e.y = C.b;
     e.mode = 0;
-    k_mv_csr<float, float, 0><<<mv_grid(C.N, B), 256, 0, st>>>(C.N, L.R->rowptr, L.R->col, nullptr,
-                                                               L.Rv, L.r, e, 0, nullptr, 0);
-    FEM_CHECK_LAUNCH();
+    mv_csr<float, float, 0>(*L.R, (const float*)nullptr, L.Rv.p, L.r, e, 0, nullptr, st);
   }
   mv_vcycle(W, lev + 1, nullptr, st);
   {
     MvEpi<float> e = base;
     e.y = L.x;
-    k_mv_csr<float, float, 0><<<g, 256, 0, st>>>(N, L.P->rowptr, L.P->col, nullptr, L.Pv, C.x, e, 1,
-                                                 nullptr, 0);
-    FEM_CHECK_LAUNCH();
+    mv_csr<float, float, 0>(*L.P, (const float*)nullptr, L.Pv.p, C.x, e, 1, nullptr, st);
   }
   // post-smoothing
   {
@@ -780,7 +1110,6 @@ void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
       e.r2 = W.rprev;
     }
     op(dold, e, last && finest);
-    if (last && finest && !L.stencil) W.nb_fine = (int)g;
     std::swap(dold, dnew);
   }
 }
@@ -789,7 +1118,6 @@ void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
 int mv_apply64(BatchSession& W, cudaStream_t st) {
   BatchLevel& L = *W.L[0];
   const int B = W.B;
-  const unsigned g = mv_grid(W.N, B);
   if (L.stencil) {
     const dim3 sg = mv_sgrid(W.S->n - 1, B);
     k_mv_stencil64<<<sg, 256, 0, st>>>(W.p, W.S->n - 1, W.coef64, B, W.q, W.state, W.partials,
@@ -805,11 +1133,8 @@ int mv_apply64(BatchSession& W, cudaStream_t st) {
     e.want_dot = 1;
     e.B = B;
     e.rho = W.rho;
-    k_mv_csr<double, double, 1><<<g, 256, 0, st>>>(W.N, L.A->rowptr, L.A->col, L.Kv64, L.Mv64, W.p,
-                                                   e, 0, W.partials, g);
+    return mv_csr<double, double, 1>(*L.A, L.Kv64, L.Mv64, W.p, e, 0, W.partials, st);
   }
-  FEM_CHECK_LAUNCH();
-  return (int)g;
 }
 
 void batch_iteration(BatchSession& W, cudaStream_t st) {
@@ -831,19 +1156,77 @@ void batch_iteration(BatchSession& W, cudaStream_t st) {
   FEM_CHECK_LAUNCH();
 }
 
-double slot_gershgorin(const Csr4& A, const double* kv, const double* mv, double rho,
-                       DevBuf<double>& scratch, cudaStream_t st) {
-  const int64_t N = A.nrows;
-  unsigned g = grid_for(N, 256);
-  if (scratch.n < g + 1) scratch.alloc(g + 1);
-  k_mv_gersh<<<g, 256, 0, st>>>(N, A.rowptr, A.col, kv, mv, rho, scratch);
-  FEM_CHECK_LAUNCH();
-  k_max_red<<<1, 1024, 0, st>>>(scratch, (int)g, scratch.p + g);
-  FEM_CHECK_LAUNCH();
-  double h = 0;
-  FEM_CUDA(cudaMemcpyAsync(&h, scratch.p + g, 8, cudaMemcpyDeviceToHost, st));
-  FEM_CUDA(cudaStreamSynchronize(st));
-  return h;
+
+// Launch shapes of the session's multivector kernels, timed on its scratch vectors
+// before the iteration is captured (a graph keeps the shapes it was captured with).
+void tune_session(BatchSession& W, cudaStream_t st) {
+  const int B = W.B;
+  const int m = W.S->n - 1;
+  for (size_t l = 0; l < W.L.size(); l++) {
+    BatchLevel& L = *W.L[l];
+    MvEpi<float> e;
+    std::memset(&e, 0, sizeof(e));
+    e.level = (int)l;
+    e.lc = W.lc;
+    e.B = B;
+    e.rho = W.rho;
+    if (L.stencil) {
+      e.mode = 2;
+      e.r = L.r;
+      e.dold = L.d0;
+      e.dnew = L.d1;
+      e.x = L.x;
+      autotune("mv_stencil_f32", m, 0, B, kMvStencilVariants, kMvStencilNames, 1, st,
+               [&](int v) { launch_mv_stencil32<0>(v, L.d0.p, m, e, nullptr, st); });
+    } else if (!(L.coarsest && L.dense) && L.A->nnz >= (1 << 16)) {
+      e.kd = L.kd;
+      e.md = L.md;
+      e.mode = 1;
+      e.y = L.r;
+      e.b = L.b;
+      autotune("mv_csr_f32", L.A->nrows, L.A->nnz, B, kMvCsrVariants, kMvCsrNames, 0, st,
+               [&](int v) {
+                 launch_mv_csr<float, float, 0>(v, *L.A, L.Kv.p, L.Mv.p, L.x.p, e, 0, nullptr, st);
+               });
+    }
+    if (!L.coarsest && l + 1 < W.L.size()) {
+      BatchLevel& C = *W.L[l + 1];
+      MvEpi<float> er;
+      std::memset(&er, 0, sizeof(er));
+      er.B = B;
+      er.y = C.b;
+      if (L.R->nnz >= (1 << 16))
+        autotune("mv_csr_f32", L.R->nrows, L.R->nnz, B, kMvCsrVariants, kMvCsrNames, 0, st,
+                 [&](int v) {
+                   launch_mv_csr<float, float, 0>(v, *L.R, (const float*)nullptr, L.Rv.p, L.r.p,
+                                                  er, 0, nullptr, st);
+                 });
+      MvEpi<float> ep = er;
+      ep.y = L.x;
+      if (L.P->nnz >= (1 << 16))
+        autotune("mv_csr_f32", L.P->nrows, L.P->nnz, B, kMvCsrVariants, kMvCsrNames, 0, st,
+                 [&](int v) {
+                   launch_mv_csr<float, float, 0>(v, *L.P, (const float*)nullptr, L.Pv.p, C.x.p,
+                                                  ep, 1, nullptr, st);
+                 });
+    }
+  }
+  BatchLevel& L0 = *W.L[0];
+  if (!L0.stencil && L0.A->nnz >= (1 << 16)) {
+    MvEpi<double> e;
+    std::memset(&e, 0, sizeof(e));
+    e.mode = 0;
+    e.y = W.q;
+    e.x = W.p;
+    e.want_dot = 1;
+    e.B = B;
+    e.rho = W.rho;
+    autotune("mv_csr_f64", L0.A->nrows, L0.A->nnz, B, kMvCsrVariants, kMvCsrNames, 0, st,
+             [&](int v) {
+               launch_mv_csr<double, double, 1>(v, *L0.A, L0.Kv64, L0.Mv64, W.p.p, e, 0,
+                                                W.partials.p, st);
+             });
+  }
 }
 
 }  // namespace
@@ -912,11 +1295,10 @@ BatchSession* batch_create(System& S, Hierarchy& H, int slots, const pcg_opts& o
       BL->dense = Lv.N <= H.o.coarse_max;
       if (BL->dense) BL->Ainv.alloc((size_t)B * Lv.N * Lv.N);
     }
-    BL->x.alloc(Lv.N * B);
-    BL->b.alloc(Lv.N * B);
-    BL->r.alloc(Lv.N * B);
-    BL->d0.alloc(Lv.N * B);
-    BL->d1.alloc(Lv.N * B);
+    for (auto* v : {&BL->x, &BL->b, &BL->r, &BL->d0, &BL->d1}) {
+      v->alloc(Lv.N * B);
+      FEM_CUDA(cudaMemsetAsync(v->p, 0, 4 * Lv.N * B, st));
+    }
     W->L.push_back(std::move(BL));
   }
   for (auto* v : {&W->x, &W->r, &W->rprev, &W->p, &W->q, &W->z, &W->f}) {
@@ -932,10 +1314,21 @@ BatchSession* batch_create(System& S, Hierarchy& H, int slots, const pcg_opts& o
   FEM_CUDA(cudaMemsetAsync(W->rho, 0, 8 * B, st));
   FEM_CUDA(cudaMemsetAsync(W->coef64, 0, 32 * B, st));
   FEM_CUDA(cudaMemsetAsync(W->lc, 0, sizeof(LevCoef) * H.L.size() * B, st));
-  W->partials.alloc((size_t)2 * B * (8 * num_sms() + 1) + 4 * (size_t)kMaxPartialBlocks);
+  // per-slot partial sums: the largest block count of any kernel that emits them
+  int64_t maxnb = 8 * (int64_t)num_sms() + 1;
+  if (S.stencil) {
+    for (int v = 0; v < kMvStencilVariants; v++) {
+      const dim3 gv = mv_stencil_grid(v, S.n - 1, B);
+      maxnb = std::max<int64_t>(maxnb, (int64_t)gv.x * gv.y * gv.z);
+    }
+    const dim3 g64 = mv_sgrid(S.n - 1, B);
+    maxnb = std::max<int64_t>(maxnb, (int64_t)g64.x * g64.y);
+  }
+  W->partials.alloc((size_t)2 * B * maxnb + 4 * (size_t)kMaxPartialBlocks);
   W->scratch.alloc(4 * 8 * (size_t)num_sms() + 64);
   FEM_CUDA(cudaMallocHost(&W->hstate, sizeof(SlotState) * B));
   W->in_use.assign(B, 0);
+  tune_session(*W, st);
   // one iteration as a CUDA graph
   cudaStream_t cs;
   FEM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -965,90 +1358,125 @@ BatchSession* batch_create(System& S, Hierarchy& H, int slots, const pcg_opts& o
   return W.release();
 }
 
-// Load f (length N, column fcol of an [N][ld] array) and rho into a free slot.
-int batch_admit(BatchSession& W, const double* f, int64_t ld, int fcol, double rho, cudaStream_t st) {
-  FEM_REQUIRE(rho > 0.0 && std::isfinite(rho), FEM_EINVAL, "pcg_batch_admit: rho > 0");
-  int slot = -1;
-  for (int b = 0; b < W.slots; b++)
-    if (!W.in_use[b]) {
-      slot = b;
-      break;
-    }
-  FEM_REQUIRE(slot >= 0, FEM_ENOMEM, "pcg_batch_admit: no free slot");
+// Admit `count` solves at once: column fcol0 + k of f ([N][ld]) with rho[k] goes into the
+// k-th free slot.  Every kernel covers all admitted slots (grid.y = admitted slot), and
+// each slot's arithmetic and reduction order is the same as when it is admitted alone.
+void batch_admit_many(BatchSession& W, const double* f, int64_t ld, int fcol0, const double* rho,
+                      int count, int* slots_out, cudaStream_t st) {
+  FEM_REQUIRE(count >= 1, FEM_EINVAL, "pcg_batch_admit: nothing to admit");
+  std::vector<int> slot;
+  for (int b = 0; b < W.slots && (int)slot.size() < count; b++)
+    if (!W.in_use[b]) slot.push_back(b);
+  FEM_REQUIRE((int)slot.size() == count, FEM_ENOMEM, "pcg_batch_admit: no free slot");
+  for (int k = 0; k < count; k++)
+    FEM_REQUIRE(rho[k] > 0.0 && std::isfinite(rho[k]), FEM_EINVAL, "pcg_batch_admit: rho > 0");
   const int B = W.B;
   const int64_t N = W.N;
   System& S = *W.S;
   Hierarchy& H = *W.H;
-  const unsigned g1 = grid_for(N, 256);
-  k_col_in<<<g1, 256, 0, st>>>(N, B, slot, f, ld, fcol, W.f);
-  k_col_in<<<g1, 256, 0, st>>>(N, B, slot, f, ld, fcol, W.r);
-  k_col_set<<<g1, 256, 0, st>>>(N, B, slot, 0.0, W.x);
-  k_col_set<<<g1, 256, 0, st>>>(N, B, slot, 0.0, W.p);
-  k_col_set<<<g1, 256, 0, st>>>(N, B, slot, 0.0, W.rprev);
-  FEM_CHECK_LAUNCH();
-  FEM_CUDA(cudaMemcpyAsync(W.rho.p + slot, &rho, 8, cudaMemcpyHostToDevice, st));
-  // per-level smoother coefficients for this rho
+  // admitted slots and their rho on the device
+  std::vector<double> hr(rho, rho + count);
+  DevBuf<int32_t> dslot(count, st);
+  DevBuf<double> drho(count, st);
+  FEM_CUDA(cudaMemcpyAsync(dslot, slot.data(), 4 * count, cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(drho, hr.data(), 8 * count, cudaMemcpyHostToDevice, st));
+  {
+    int kx = 1;
+    while (kx < count) kx <<= 1;
+    const dim3 blk(kx, 256 / kx);
+    k_cols_admit<<<persistent_grid(N * kx, 256, 8), blk, 0, st>>>(
+        N, B, count, dslot, drho, f, ld, fcol0, W.f, W.r, W.x, W.p, W.rprev, W.rho);
+    FEM_CHECK_LAUNCH();
+  }
+  // per-level smoother coefficients of every admitted rho
   for (size_t l = 0; l < H.L.size(); l++) {
     Level& Lv = *H.L[l];
     BatchLevel& BL = *W.L[l];
-    LevCoef c{};
-    double lmax;
     const double* kv = BL.Kv64;
     const double* mv = BL.Mv64;
+    std::vector<double> lmax(count);
     if (Lv.stencil) {
-      const double a[4] = {rho * S.stK.c0 + S.stM.c0, rho * S.stK.ca + S.stM.ca,
-                           rho * S.stK.cf + S.stM.cf, rho * S.stK.cb + S.stM.cb};
-      c.c0 = (float)a[0];
-      c.ca = (float)a[1];
-      c.cf = (float)a[2];
-      c.cb = (float)a[3];
-      c.sinv = (float)(1.0 / a[0]);
-      double coef[4] = {a[0], a[1], a[2], a[3]};
-      FEM_CUDA(cudaMemcpyAsync(W.coef64.p + 4 * slot, coef, 32, cudaMemcpyHostToDevice, st));
       // every row has the diagonal a[0] and a subset of the interior row's neighbours, so
       // the Gershgorin bound is the interior row's sum
-      lmax = (std::fabs(a[0]) + 6 * std::fabs(a[1]) + 6 * std::fabs(a[2]) + 2 * std::fabs(a[3])) /
-             a[0];
-    } else {
-      lmax = slot_gershgorin(*Lv.A, kv, mv, rho, W.scratch, st);
-    }
-    if (H.o.smoother == AMG_SMOOTHER_L1_JACOBI) {
-      c.inv_theta = 1.0f;
-    } else {
-      ChebCoef cc = cheb_coefficients(lmax, H.o.cheb_ratio, H.o.degree);
-      c.inv_theta = (float)cc.inv_theta;
-      c.c1 = (float)cc.c1[1];
-      c.c2 = (float)cc.c2[1];
-    }
-    W.hlc[l * B + slot] = c;
-    FEM_CUDA(cudaMemcpyAsync(W.lc.p + l * B + slot, &W.hlc[l * B + slot], sizeof(LevCoef),
-                             cudaMemcpyHostToDevice, st));
-    if (BL.coarsest && BL.dense) {
-      const int64_t Nc = Lv.N;
-      double* A0 = BL.Ainv.p + (int64_t)slot * Nc * Nc;
-      DevBuf<double> tmp(Nc * Nc, st);
-      k_mv_dense_build<<<grid_for(Nc, 128), 128, 0, st>>>(Nc, Lv.A->rowptr, Lv.A->col, kv, mv,
-                                                          W.rho, slot, A0);
-      FEM_CHECK_LAUNCH();
-      double* src = A0;
-      double* dst = tmp.p;
-      const unsigned gg = persistent_grid(Nc * Nc, 256, 4);
-      for (int64_t k = 0; k < Nc; k++) {
-        k_gj_step_b<<<gg, 256, 0, st>>>(Nc, k, src, dst);
-        FEM_CHECK_LAUNCH();
-        std::swap(src, dst);
+      for (int k = 0; k < count; k++) {
+        const double r = rho[k];
+        const double a[4] = {r * S.stK.c0 + S.stM.c0, r * S.stK.ca + S.stM.ca,
+                             r * S.stK.cf + S.stM.cf, r * S.stK.cb + S.stM.cb};
+        FEM_CUDA(cudaMemcpyAsync(W.coef64.p + 4 * slot[k], a, 32, cudaMemcpyHostToDevice, st));
+        lmax[k] = (std::fabs(a[0]) + 6 * std::fabs(a[1]) + 6 * std::fabs(a[2]) +
+                   2 * std::fabs(a[3])) / a[0];
+        LevCoef& c = W.hlc[l * B + slot[k]];
+        c = LevCoef{};
+        c.c0 = (float)a[0];
+        c.ca = (float)a[1];
+        c.cf = (float)a[2];
+        c.cb = (float)a[3];
+        c.sinv = (float)(1.0 / a[0]);
       }
-      if (src != A0) FEM_CUDA(cudaMemcpyAsync(A0, src, 8 * Nc * Nc, cudaMemcpyDeviceToDevice, st));
+      FEM_CUDA(cudaStreamSynchronize(st));   // the host arrays above go out of scope
+    } else {
+      const int64_t NL = Lv.N;
+      const unsigned g = grid_for(NL, 256);
+      DevBuf<double> bm((size_t)count * (g + 1), st);
+      k_mv_gersh<<<dim3(g, count), 256, 0, st>>>(NL, Lv.A->rowptr, Lv.A->col, kv, mv, drho, bm, g);
+      FEM_CHECK_LAUNCH();
+      k_max_red<<<count, 1024, 0, st>>>(bm, (int)g, bm.p + (size_t)count * g);
+      FEM_CHECK_LAUNCH();
+      FEM_CUDA(cudaMemcpyAsync(lmax.data(), bm.p + (size_t)count * g, 8 * count,
+                               cudaMemcpyDeviceToHost, st));
+      FEM_CUDA(cudaStreamSynchronize(st));
+      for (int k = 0; k < count; k++) W.hlc[l * B + slot[k]] = LevCoef{};
+    }
+    for (int k = 0; k < count; k++) {
+      LevCoef& c = W.hlc[l * B + slot[k]];
+      if (H.o.smoother == AMG_SMOOTHER_L1_JACOBI) {
+        c.inv_theta = 1.0f;
+      } else {
+        ChebCoef cc = cheb_coefficients(lmax[k], H.o.cheb_ratio, H.o.degree);
+        c.inv_theta = (float)cc.inv_theta;
+        c.c1 = (float)cc.c1[1];
+        c.c2 = (float)cc.c2[1];
+      }
+      FEM_CUDA(cudaMemcpyAsync(W.lc.p + l * B + slot[k], &c, sizeof(LevCoef),
+                               cudaMemcpyHostToDevice, st));
+    }
+    if (BL.coarsest && BL.dense) {
+      // dense coarse matrix of each rho, inverted by Gauss-Jordan (ping-pong buffers)
+      const int64_t Nc = Lv.N;
+      DevBuf<double> tmp((size_t)count * Nc * Nc, st);
+      k_mv_dense_build<<<dim3(grid_for(Nc, 128), count), 128, 0, st>>>(
+          Nc, Lv.A->rowptr, Lv.A->col, kv, mv, drho, dslot, BL.Ainv);
+      FEM_CHECK_LAUNCH();
+      const unsigned gg = persistent_grid(Nc * Nc, 256, 4);
+      bool in_tmp = false;
+      for (int64_t k = 0; k < Nc; k++) {
+        k_gj_step_b<<<dim3(gg, count), 256, 0, st>>>(Nc, k, BL.Ainv, tmp, dslot, in_tmp);
+        FEM_CHECK_LAUNCH();
+        in_tmp = !in_tmp;
+      }
+      if (in_tmp) {
+        k_gj_copy_back<<<dim3(gg, count), 256, 0, st>>>(Nc, tmp, BL.Ainv, dslot);
+        FEM_CHECK_LAUNCH();
+      }
     }
   }
-  // ||f|| and the slot's CG state
-  const unsigned gn = persistent_grid(N, 256, 4);
-  k_col_norm2<<<gn, 256, 0, st>>>(N, B, slot, W.f, W.scratch);
+  FEM_CUDA(cudaStreamSynchronize(st));
+  // ||f|| and the slots' CG state
+  const unsigned gn = mv_grid(N, B);
+  k_mv_norm2<<<gn, 256, 0, st>>>(N, B, W.f, W.partials, gn);
   FEM_CHECK_LAUNCH();
-  k_slot_admit<<<1, 256, 0, st>>>(W.state, slot, W.scratch, gn, rho, W.o.tol, W.o.max_iter);
+  k_slot_admit<<<count, 256, 0, st>>>(W.state, dslot, W.partials, gn, drho, W.o.tol, W.o.max_iter);
   FEM_CHECK_LAUNCH();
   FEM_CUDA(cudaStreamSynchronize(st));
-  W.in_use[slot] = 1;
+  for (int k = 0; k < count; k++) {
+    W.in_use[slot[k]] = 1;
+    if (slots_out) slots_out[k] = slot[k];
+  }
+}
+
+int batch_admit(BatchSession& W, const double* f, int64_t ld, int fcol, double rho, cudaStream_t st) {
+  int slot = -1;
+  batch_admit_many(W, f, ld, fcol, &rho, 1, &slot, st);
   return slot;
 }
 
@@ -1072,16 +1500,32 @@ void batch_poll(BatchSession& W, int32_t* state, int32_t* iters, double* relres,
   }
 }
 
-void batch_retire(BatchSession& W, int slot, double* u, int64_t ld, int ucol, cudaStream_t st) {
-  FEM_REQUIRE(slot >= 0 && slot < W.slots && W.in_use[slot], FEM_EINVAL,
-              "pcg_batch_retire: slot not in use");
-  k_col_out<<<grid_for(W.N, 256), 256, 0, st>>>(W.N, W.B, slot, W.x, u, ld, ucol);
+// Copy x of slots[k] to column c0 + k of u ([N][ld]) and free the slots.
+void batch_retire_many(BatchSession& W, const int* slots, int count, double* u, int64_t ld, int c0,
+                       cudaStream_t st) {
+  for (int k = 0; k < count; k++)
+    FEM_REQUIRE(slots[k] >= 0 && slots[k] < W.slots && W.in_use[slots[k]], FEM_EINVAL,
+                "pcg_batch_retire: slot not in use");
+  DevBuf<int32_t> dslot(count, st);
+  std::vector<int32_t> hs(slots, slots + count);
+  FEM_CUDA(cudaMemcpyAsync(dslot, hs.data(), 4 * count, cudaMemcpyHostToDevice, st));
+  int kx = 1;
+  while (kx < count) kx <<= 1;
+  k_cols_out<<<persistent_grid(W.N * kx, 256, 8), dim3(kx, 256 / kx), 0, st>>>(
+      W.N, W.B, count, dslot, W.x, u, ld, c0);
   FEM_CHECK_LAUNCH();
   // deactivate
-  SlotState off{};
-  FEM_CUDA(cudaMemcpyAsync(W.state.p + slot, &off, sizeof(SlotState), cudaMemcpyHostToDevice, st));
+  std::vector<SlotState> off(count);
+  std::memset(off.data(), 0, sizeof(SlotState) * count);
+  for (int k = 0; k < count; k++)
+    FEM_CUDA(cudaMemcpyAsync(W.state.p + slots[k], &off[k], sizeof(SlotState),
+                             cudaMemcpyHostToDevice, st));
   FEM_CUDA(cudaStreamSynchronize(st));
-  W.in_use[slot] = 0;
+  for (int k = 0; k < count; k++) W.in_use[slots[k]] = 0;
+}
+
+void batch_retire(BatchSession& W, int slot, double* u, int64_t ld, int ucol, cudaStream_t st) {
+  batch_retire_many(W, &slot, 1, u, ld, ucol, st);
 }
 
 void batch_destroy(BatchSession* W) { delete W; }
@@ -1091,11 +1535,11 @@ static void batch_true_residual(BatchSession& W, double* out, cudaStream_t st) {
   const int B = W.B;
   const int64_t N = W.N;
   BatchLevel& L = *W.L[0];
-  const unsigned g = mv_grid(N, B);
   if (L.stencil) {
     const dim3 sg = mv_sgrid(W.S->n - 1, B);
     k_mv_stencil64<<<sg, 256, 0, st>>>(W.x, W.S->n - 1, W.coef64, B, W.q, nullptr, W.partials,
                                        sg.x * sg.y);
+    FEM_CHECK_LAUNCH();
   } else {
     MvEpi<double> e;
     std::memset(&e, 0, sizeof(e));
@@ -1104,24 +1548,20 @@ static void batch_true_residual(BatchSession& W, double* out, cudaStream_t st) {
     e.x = W.x;
     e.B = B;
     e.rho = W.rho;
-    k_mv_csr<double, double, 0><<<g, 256, 0, st>>>(N, L.A->rowptr, L.A->col, L.Kv64, L.Mv64, W.x, e,
-                                                   0, nullptr, 0);
+    mv_csr<double, double, 0>(*L.A, L.Kv64, L.Mv64, W.x, e, 0, nullptr, st);
   }
+  const unsigned g = mv_grid(N, B);
+  k_mv_resid2<<<g, 256, 0, st>>>(N, B, W.f, W.q, W.partials, g);
   FEM_CHECK_LAUNCH();
-  const unsigned gn = persistent_grid(N, 256, 4);
-  std::vector<double> h(2 * gn);
+  DevBuf<double> sums(2 * B, st);
+  k_slot_sums2<<<B, 256, 0, st>>>(W.partials, g, B, sums);
+  FEM_CHECK_LAUNCH();
+  std::vector<double> h(2 * B);
+  FEM_CUDA(cudaMemcpyAsync(h.data(), sums, 16 * B, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
   for (int b = 0; b < W.slots; b++) {
     if (!W.in_use[b]) continue;
-    k_col_resid2<<<gn, 256, 0, st>>>(N, B, b, W.f, W.q, W.scratch);
-    FEM_CHECK_LAUNCH();
-    FEM_CUDA(cudaMemcpyAsync(h.data(), W.scratch, 16 * gn, cudaMemcpyDeviceToHost, st));
-    FEM_CUDA(cudaStreamSynchronize(st));
-    double rr = 0, ff = 0;
-    for (unsigned i = 0; i < gn; i++) {
-      rr += h[i];
-      ff += h[gn + i];
-    }
-    out[b] = ff > 0 ? std::sqrt(rr / ff) : 0.0;
+    out[b] = h[2 * b + 1] > 0 ? std::sqrt(h[2 * b] / h[2 * b + 1]) : 0.0;
   }
 }
 
@@ -1129,7 +1569,7 @@ fem_status pcg_multi(System& S, Hierarchy& H, const double* f, double* u, int nr
                      const double* rho_k, const pcg_opts& o, cudaStream_t user, pcg_result* res) {
   FEM_REQUIRE(nrhs >= 1 && nrhs <= MAXB, FEM_EINVAL, "pcg_solve: nrhs in [1, 64]");
   std::unique_ptr<BatchSession> W(batch_create(S, H, nrhs, o, user));
-  for (int k = 0; k < nrhs; k++) batch_admit(*W, f, nrhs, k, rho_k[k], user);
+  batch_admit_many(*W, f, nrhs, 0, rho_k, nrhs, nullptr, user);
   cudaEvent_t e0, e1;
   FEM_CUDA(cudaEventCreate(&e0));
   FEM_CUDA(cudaEventCreate(&e1));
@@ -1154,8 +1594,12 @@ fem_status pcg_multi(System& S, Hierarchy& H, const double* f, double* u, int nr
   fem_status all = FEM_OK;
   std::vector<double> trr(W->B, 0.0);
   batch_true_residual(*W, trr.data(), user);
+  {
+    std::vector<int> all_slots(nrhs);
+    for (int k = 0; k < nrhs; k++) all_slots[k] = k;
+    batch_retire_many(*W, all_slots.data(), nrhs, u, nrhs, 0, user);
+  }
   for (int k = 0; k < nrhs; k++) {
-    batch_retire(*W, k, u, nrhs, k, user);
     res[k].iterations = it[k];
     res[k].status = st[k] == 1 ? FEM_OK : (st[k] == 0 ? FEM_ENOCONV : W->hstate[k].status);
     res[k].relres = trr[k];

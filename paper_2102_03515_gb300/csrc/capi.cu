@@ -256,6 +256,7 @@ fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hie
       FEM_CUDA(cudaEventRecord(e0, st));
       build_hierarchy(h->H, sys->S, o, st);
       alloc_level_vectors(h->H);
+      tune_hierarchy(h->H, sys->S, st);
       FEM_CUDA(cudaEventRecord(e1, st));
       FEM_CUDA(cudaEventSynchronize(e1));
       float ms = 0;
@@ -442,6 +443,29 @@ void pcg_batch_destroy(pcg_batch b) {
   delete b;
 }
 
-const char* fem_autotune_report(void) { return "{}"; }
+const char* fem_autotune_report(void) {
+  static thread_local std::string rep;
+  try {
+    rep = autotune_report();
+  } catch (...) {
+    rep = "{}";
+  }
+  return rep.c_str();
+}
+
+fem_status fem_autotune_pin(const char* kernel, int32_t variant) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(kernel, FEM_EINVAL, "fem_autotune_pin: null kernel name");
+    autotune_pin(kernel, variant);
+    return FEM_OK;
+  });
+}
+
+void fem_autotune_clear(void) {
+  try {
+    autotune_clear();
+  } catch (...) {
+  }
+}
 
 }  // extern "C"

@@ -46,8 +46,18 @@ enum EpiMode { E_STORE = 0, E_RESIDUAL = 1, E_CHEB_STEP = 2, E_CHEB_INIT = 3, E_
 //   E_CHEB_STEP r -= s Av; d_new = c1 d_old + c2 r; x += [d_old] + d_new   (v = d_old)
 // s is the smoother's diagonal inverse (scalar sinv_c when sinv is null).  When z64 is
 // set, the final x is also written in FP64 and <z, r1>, <z, r2> are accumulated.
+//
+// The epilogue is split into load() (the row's operands, so that a kernel can issue these
+// loads early, together with its stencil loads) and apply(); "centre" is v[row], which
+// the stencil kernels already hold in a register (it is vin[row] in E_STORE and d_old[row]
+// in E_CHEB_STEP).
 template <typename T>
 struct Epi {
+  using AT = typename Arith<T>::type;
+  struct Ops {
+    AT a, x, s;
+    double r1, r2;
+  };
   int mode;
   T* y;
   const T* b;
@@ -65,43 +75,84 @@ struct Epi {
   const double* r1;
   const double* r2;
 
-  __device__ __forceinline__ void operator()(int64_t row, typename Arith<T>::type av,
-                                             double acc[2]) const {
-    using AT = typename Arith<T>::type;
+  __device__ __forceinline__ Ops load(int64_t row) const {
+    Ops o;
+    o.a = (AT)0;
+    o.x = (AT)0;
+    o.s = (AT)0;
+    o.r1 = 0.0;
+    o.r2 = 0.0;
+    switch (mode) {
+      case E_ADD:
+        o.a = (AT)y[row];
+        break;
+      case E_RESIDUAL:
+        o.a = (AT)b[row];
+        break;
+      case E_CHEB_INIT:
+        o.a = (AT)b[row];
+        o.s = sinv ? (AT)sinv[row] : (AT)sinv_c;
+        break;
+      case E_CHEB_STEP:
+        o.a = (AT)r[row];
+        o.s = sinv ? (AT)sinv[row] : (AT)sinv_c;
+        o.x = (AT)x[row];
+        if (z64) {
+          o.r1 = r1[row];
+          if (r2) o.r2 = r2[row];
+        }
+        break;
+      default:
+        break;
+    }
+    return o;
+  }
+
+  __device__ __forceinline__ void apply(int64_t row, AT av, AT centre, const Ops& o,
+                                        double acc[2]) const {
     switch (mode) {
       case E_STORE:
         y[row] = (T)av;
-        if (want_dot) acc[0] += (double)vin[row] * (double)av;
+        if (want_dot) acc[0] += (double)centre * (double)av;
         break;
       case E_ADD:
-        y[row] = (T)((AT)y[row] + av);
+        y[row] = (T)(o.a + av);
         break;
       case E_RESIDUAL:
-        y[row] = (T)((AT)b[row] - av);
+        y[row] = (T)(o.a - av);
         break;
       case E_CHEB_INIT: {
-        AT s = sinv ? (AT)sinv[row] : (AT)sinv_c;
-        AT rr = s * ((AT)b[row] - av);
+        AT rr = o.s * (o.a - av);
         r[row] = (T)rr;
         dnew[row] = (T)((AT)c2 * rr);
       } break;
       case E_CHEB_STEP: {
-        AT s = sinv ? (AT)sinv[row] : (AT)sinv_c;
-        AT rr = (AT)r[row] - s * av;
-        AT dl = (AT)dold[row];
+        AT rr = o.a - o.s * av;
+        AT dl = centre;
         AT dn = (AT)c1 * dl + (AT)c2 * rr;
         r[row] = (T)rr;
         dnew[row] = (T)dn;
-        AT xv = (AT)x[row] + (add_prev ? dl : (AT)0) + dn;
+        AT xv = o.x + (add_prev ? dl : (AT)0) + dn;
         x[row] = (T)xv;
         if (z64) {
           double z = (double)xv;
           z64[row] = z;
-          acc[0] += z * r1[row];
-          if (r2) acc[1] += z * r2[row];
+          acc[0] += z * o.r1;
+          if (r2) acc[1] += z * o.r2;
         }
       } break;
     }
+  }
+
+  // centre value of a kernel that does not hold v[row]
+  __device__ __forceinline__ AT centre_of(int64_t row) const {
+    if (mode == E_STORE && want_dot) return (AT)vin[row];
+    if (mode == E_CHEB_STEP) return (AT)dold[row];
+    return (AT)0;
+  }
+
+  __device__ __forceinline__ void operator()(int64_t row, AT av, double acc[2]) const {
+    apply(row, av, centre_of(row), load(row), acc);
   }
 };
 
@@ -178,21 +229,25 @@ __global__ void __launch_bounds__(TX* TY) k_stencil(const T* __restrict__ v, int
 // values it needs again one plane later, and loads 7 values per point (plane k: the three
 // "minus" neighbours (i-1,j), (i,j-1), (i-1,j-1); plane k+1: (i,j), (i+1,j), (i,j+1),
 // (i+1,j+1)).  Warps run along i, so every load is coalesced; there are no barriers.
-template <typename T>
-__global__ void __launch_bounds__(TX* TY) k_stencil_col(const T* __restrict__ v, int m, SC<T> c,
-                                                        Epi<T> epi, double* partials,
-                                                        int nblocks, const int* done) {
+// The loads of point k+1 (stencil values and the epilogue's operands) are issued before
+// point k is finished, so each thread keeps two points' loads in flight.
+template <typename T, int TYV, int KZV>
+__global__ void __launch_bounds__(TX* TYV) k_stencil_col(const T* __restrict__ v, int m, SC<T> c,
+                                                         Epi<T> epi, double* partials,
+                                                         int nblocks, const int* done) {
   using AT = typename Arith<T>::type;
+  using Ops = typename Epi<T>::Ops;
   if (done && *done) return;
   const int i = blockIdx.x * TX + (threadIdx.x & (TX - 1));
-  const int j = blockIdx.y * TY + threadIdx.x / TX;
-  const int k0 = blockIdx.z * KZ;
-  const int kend = min(k0 + KZ, m);
+  const int j = blockIdx.y * TYV + threadIdx.x / TX;
+  const int k0 = blockIdx.z * KZV;
+  const int kend = min(k0 + KZV, m);
   double acc[2] = {0.0, 0.0};
   if (i < m && j < m) {
     const int64_t sj = m, sk = (int64_t)m * m;
     const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1;
     const T* col = v + (int64_t)i + sj * j;
+    const int64_t row0 = (int64_t)i + sj * j;
     auto ld = [&](bool ok, int k, int64_t off) -> AT {
       return (ok && k >= 0 && k < m) ? (AT)__ldg(col + sk * k + off) : (AT)0;
     };
@@ -201,17 +256,27 @@ __global__ void __launch_bounds__(TX* TY) k_stencil_col(const T* __restrict__ v,
     AT m_im = ld(im, k0 - 1, -1), m_jm = ld(jm, k0 - 1, -sj), m_ijm = ld(im && jm, k0 - 1, -1 - sj);
     AT c0v = ld(true, k0, 0);
     AT p_ip = ld(ip, k0, 1), p_jp = ld(jp, k0, sj), p_ijp = ld(ip && jp, k0, 1 + sj);
+    // loads of the first point: plane k0 minus set, plane k0 + 1 centre and plus set
+    AT z_im = ld(im, k0, -1), z_jm = ld(jm, k0, -sj), z_ijm = ld(im && jm, k0, -1 - sj);
+    AT cp = ld(true, k0 + 1, 0);
+    AT n_ip = ld(ip, k0 + 1, 1), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, 1 + sj);
+    Ops op = epi.load(row0 + sk * k0);
     const AT a0 = (AT)c.c0, aa = (AT)c.ca, af = (AT)c.cf, ab = (AT)c.cb;
     for (int k = k0; k < kend; k++) {
-      // plane k minus set, plane k+1 centre and plus set
-      const AT z_im = ld(im, k, -1), z_jm = ld(jm, k, -sj), z_ijm = ld(im && jm, k, -1 - sj);
-      const AT cp = ld(true, k + 1, 0);
-      const AT n_ip = ld(ip, k + 1, 1), n_jp = ld(jp, k + 1, sj), n_ijp = ld(ip && jp, k + 1, 1 + sj);
+      // issue the next point's loads (beyond kend they are not used)
+      const bool more = k + 1 < kend;
+      const AT z2_im = ld(im && more, k + 1, -1), z2_jm = ld(jm && more, k + 1, -sj),
+               z2_ijm = ld(im && jm && more, k + 1, -1 - sj);
+      const AT cp2 = ld(more, k + 2, 0);
+      const AT n2_ip = ld(ip && more, k + 2, 1), n2_jp = ld(jp && more, k + 2, sj),
+               n2_ijp = ld(ip && jp && more, k + 2, 1 + sj);
+      Ops op2;
+      if (more) op2 = epi.load(row0 + sk * (k + 1));
       const AT axis = z_im + p_ip + z_jm + p_jp + cm + cp;
       const AT face = p_ijp + z_ijm + n_ip + m_im + n_jp + m_jm;
       const AT body = n_ijp + m_ijm;
       const AT av = a0 * c0v + aa * axis + af * face + ab * body;
-      epi((int64_t)i + sj * j + sk * k, av, acc);
+      epi.apply(row0 + sk * k, av, c0v, op, acc);
       // shift: plane k becomes k-1, plane k+1 becomes k
       cm = c0v;
       m_im = z_im;
@@ -221,25 +286,69 @@ __global__ void __launch_bounds__(TX* TY) k_stencil_col(const T* __restrict__ v,
       p_ip = n_ip;
       p_jp = n_jp;
       p_ijp = n_ijp;
+      z_im = z2_im;
+      z_jm = z2_jm;
+      z_ijm = z2_ijm;
+      cp = cp2;
+      n_ip = n2_ip;
+      n_jp = n2_jp;
+      n_ijp = n2_ijp;
+      if (more) op = op2;
     }
   }
   write_partials<T>(acc, partials, partials != nullptr, nblocks);
 }
 
+// Variants of the stencil launch (chosen per (precision, m) by the autotuner):
+//   0: shared-memory planes (32 x 8 tile, 16 planes); 1..5: column marching with
+//   (rows of the tile, planes per block) = (8,16), (8,32), (4,32), (16,16), (8,64).
+constexpr int kStencilVariants = 6;
+const char* const kStencilNames[kStencilVariants] = {"smem32x8x16", "col32x8x16", "col32x8x32",
+                                                     "col32x4x32", "col32x16x16", "col32x8x64"};
+
+template <typename T, int TYV, int KZV>
+int launch_col(const Stencil& s, SC<T> c, const T* v, const Epi<T>& epi, double* partials,
+               cudaStream_t st, const int* done) {
+  const int m = s.m;
+  dim3 grid((m + TX - 1) / TX, (m + TYV - 1) / TYV, (m + KZV - 1) / KZV);
+  int nb = grid.x * grid.y * grid.z;
+  FEM_REQUIRE(!partials || nb <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "stencil grid too large");
+  k_stencil_col<T, TYV, KZV><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+  FEM_CHECK_LAUNCH();
+  return nb;
+}
+
 template <typename T>
-int launch_stencil(const Stencil& s, const T* v, const Epi<T>& epi, double* partials,
-                   cudaStream_t st, const int* done = nullptr) {
+int launch_stencil_variant(int var, const Stencil& s, const T* v, const Epi<T>& epi,
+                           double* partials, cudaStream_t st, const int* done) {
+  SC<T> c{(T)s.c0, (T)s.ca, (T)s.cf, (T)s.cb};
+  switch (var) {
+    case 1: return launch_col<T, 8, 16>(s, c, v, epi, partials, st, done);
+    case 2: return launch_col<T, 8, 32>(s, c, v, epi, partials, st, done);
+    case 3: return launch_col<T, 4, 32>(s, c, v, epi, partials, st, done);
+    case 4: return launch_col<T, 16, 16>(s, c, v, epi, partials, st, done);
+    case 5: return launch_col<T, 8, 64>(s, c, v, epi, partials, st, done);
+    default: break;
+  }
   const int m = s.m;
   dim3 grid((m + TX - 1) / TX, (m + TY - 1) / TY, (m + KZ - 1) / KZ);
   int nb = grid.x * grid.y * grid.z;
   FEM_REQUIRE(!partials || nb <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "stencil grid too large");
-  SC<T> c{(T)s.c0, (T)s.ca, (T)s.cf, (T)s.cb};
-  if (sizeof(T) == 4)  // bandwidth-bound: barrier-free column marching
-    k_stencil_col<T><<<grid, TX * TY, 0, st>>>(v, m, c, epi, partials, nb, done);
-  else  // FP64-ALU-bound: shared-memory planes
-    k_stencil<T><<<grid, TX * TY, 0, st>>>(v, m, c, epi, partials, nb, done);
+  k_stencil<T><<<grid, TX * TY, 0, st>>>(v, m, c, epi, partials, nb, done);
   FEM_CHECK_LAUNCH();
   return nb;
+}
+
+template <typename T>
+const char* stencil_key() { return sizeof(T) == 8 ? "stencil_f64" : "stencil_f32"; }
+
+template <typename T>
+int launch_stencil(const Stencil& s, const T* v, const Epi<T>& epi, double* partials,
+                   cudaStream_t st, const int* done = nullptr) {
+  // untuned default: FP64 is ALU-bound (shared-memory planes), FP32 bandwidth-bound
+  const int def = sizeof(T) == 8 ? 0 : 1;
+  const int var = tuned_variant(stencil_key<T>(), s.m, 0, 0, def, kStencilVariants);
+  return launch_stencil_variant<T>(var, s, v, epi, partials, st, done);
 }
 
 // ------------------------------------------------------------------ CSR4
@@ -291,8 +400,25 @@ __global__ void __launch_bounds__(256) k_csr(int nrows, const int32_t* __restric
     AT sum = 0;
     if (row < nrows) {
       const int e0 = rowptr[row], e1 = rowptr[row + 1];
-      for (int e = e0 + 4 * lane; e < e1; e += 4 * TPR) {
-        int4 c4 = __ldg(reinterpret_cast<const int4*>(col + e));
+      int e = e0 + 4 * lane;
+      // two groups of 4 per step: 8 independent gathers in flight per lane
+      for (; e + 4 * TPR < e1; e += 8 * TPR) {
+        const int4 ca = __ldg(reinterpret_cast<const int4*>(col + e));
+        const int4 cb = __ldg(reinterpret_cast<const int4*>(col + e + 4 * TPR));
+        AT wa[4], wb[4];
+        Vals4<VT>::load(val + e, wa);
+        Vals4<VT>::load(val + e + 4 * TPR, wb);
+        const int cs[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+        AT xv[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) xv[q] = cs[q] >= 0 ? (AT)__ldg(v + cs[q]) : (AT)0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) sum += wa[q] * xv[q];
+#pragma unroll
+        for (int q = 0; q < 4; q++) sum += wb[q] * xv[4 + q];
+      }
+      if (e < e1) {
+        const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + e));
         AT w[4];
         Vals4<VT>::load(val + e, w);
         const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -308,18 +434,41 @@ __global__ void __launch_bounds__(256) k_csr(int nrows, const int32_t* __restric
   write_partials<T>(acc, partials, partials != nullptr, nblocks);
 }
 
+template <typename VT>
+const char* csr_key();
+template <>
+const char* csr_key<double>() { return "csr_f64"; }
+template <>
+const char* csr_key<float>() { return "csr_f32"; }
+template <>
+const char* csr_key<__nv_bfloat16>() { return "csr_bf16"; }
+
+// Variants of the CSR launch: lanes per row (TPR) 1, 2, 4, 8, 16, 32, 256-thread blocks.
+constexpr int kCsrVariants = 6;
+const char* const kCsrNames[kCsrVariants] = {"tpr1", "tpr2", "tpr4", "tpr8", "tpr16", "tpr32"};
+
+// untuned default from the average stored entries per row
+inline int csr_default_variant(double avg) {
+  return avg <= 8 ? 1 : (avg <= 16 ? 2 : (avg <= 32 ? 3 : (avg <= 96 ? 4 : 5)));
+}
+
 template <typename VT, typename T>
-int launch_csr(const Csr4& M, const VT* val, const T* v, const Epi<T>& epi, double* partials,
-               cudaStream_t st, const int* done = nullptr) {
+int launch_csr_variant(int var, const Csr4& M, const VT* val, const T* v, const Epi<T>& epi,
+                       double* partials, cudaStream_t st, const int* done) {
   const int64_t nr = M.nrows;
   if (nr == 0) return 0;
-  const double avg = (double)M.nnz / (double)nr;
   const int block = 256;
-  int tpr = avg <= 16 ? 4 : (avg <= 32 ? 8 : (avg <= 96 ? 16 : 32));
+  const int tpr = 1 << var;
   const int rpb = block / tpr;
   unsigned grid = persistent_grid((nr + rpb - 1) / rpb * block, block, 16);
   FEM_REQUIRE(!partials || (int)grid <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "grid too large");
   switch (tpr) {
+    case 1:
+      k_csr<1, VT, T><<<grid, block, 0, st>>>(M.nrows, M.rowptr, M.col, val, v, epi, partials, grid, done);
+      break;
+    case 2:
+      k_csr<2, VT, T><<<grid, block, 0, st>>>(M.nrows, M.rowptr, M.col, val, v, epi, partials, grid, done);
+      break;
     case 4:
       k_csr<4, VT, T><<<grid, block, 0, st>>>(M.nrows, M.rowptr, M.col, val, v, epi, partials, grid, done);
       break;
@@ -334,6 +483,15 @@ int launch_csr(const Csr4& M, const VT* val, const T* v, const Epi<T>& epi, doub
   }
   FEM_CHECK_LAUNCH();
   return (int)grid;
+}
+
+template <typename VT, typename T>
+int launch_csr(const Csr4& M, const VT* val, const T* v, const Epi<T>& epi, double* partials,
+               cudaStream_t st, const int* done = nullptr) {
+  if (M.nrows == 0) return 0;
+  const int def = csr_default_variant((double)M.nnz / (double)M.nrows);
+  const int var = tuned_variant(csr_key<VT>(), M.nrows, M.nnz, 0, def, kCsrVariants);
+  return launch_csr_variant<VT, T>(var, M, val, v, epi, partials, st, done);
 }
 
 // Level operator with the precision's value array.
@@ -594,6 +752,119 @@ template void smooth_post<double>(const Level&, int, const amg_opts&, const Cheb
 template void smooth_post<float>(const Level&, int, const amg_opts&, const ChebCoef&,
                                  const float*, float*, float*, float*, float*, cudaStream_t,
                                  const DotOut*);
+
+// ------------------------------------------------------------------ launch-shape tuning
+
+namespace {
+constexpr int64_t kTuneMinEntries = 1 << 18;   // smaller operators: launch-bound, default
+
+template <typename VT, typename T>
+void tune_csr(const Csr4& M, const VT* val, const T* x, T* y, int mode, cudaStream_t st) {
+  if (M.nrows == 0 || M.nnz < kTuneMinEntries || !val) return;
+  const int def = csr_default_variant((double)M.nnz / (double)M.nrows);
+  Epi<T> e = epi_base<T>(mode);
+  e.y = y;
+  autotune(csr_key<VT>(), M.nrows, M.nnz, 0, kCsrVariants, kCsrNames, def, st,
+           [&](int v) { launch_csr_variant<VT, T>(v, M, val, x, e, nullptr, st, nullptr); });
+}
+
+template <typename T>
+void tune_csr_prec(const Csr4& M, int prec, const T* x, T* y, int mode, cudaStream_t st);
+template <>
+void tune_csr_prec<double>(const Csr4& M, int prec, const double* x, double* y, int mode,
+                           cudaStream_t st) {
+  (void)prec;
+  tune_csr<double, double>(M, M.val.p, x, y, mode, st);
+}
+template <>
+void tune_csr_prec<float>(const Csr4& M, int prec, const float* x, float* y, int mode,
+                          cudaStream_t st) {
+  if (prec == AMG_PREC_BF16 && M.val16.p)
+    tune_csr<__nv_bfloat16, float>(M, M.val16.p, x, y, mode, st);
+  else
+    tune_csr<float, float>(M, M.val32.p, x, y, mode, st);
+}
+
+// Stencil: the FP32 shape is tuned on the Chebyshev step (the V-cycle's most frequent
+// launch), the FP64 shape on y = A x with <x, y> (the CG operator).
+void tune_stencil_f32(const Stencil& s, float* v, float* r, float* dn, float* x, cudaStream_t st) {
+  Epi<float> e = epi_base<float>(E_CHEB_STEP);
+  e.r = r;
+  e.dold = v;
+  e.dnew = dn;
+  e.x = x;
+  e.sinv_c = (float)(1.0 / s.c0);
+  e.c1 = 0.5f;
+  e.c2 = 0.5f;
+  autotune("stencil_f32", s.m, 0, 0, kStencilVariants, kStencilNames, 1, st,
+           [&](int var) { launch_stencil_variant<float>(var, s, v, e, nullptr, st, nullptr); });
+}
+
+void tune_stencil_f64(const Stencil& s, double* v, double* y, double* partials, cudaStream_t st) {
+  Epi<double> e = epi_base<double>(E_STORE);
+  e.y = y;
+  e.vin = v;
+  e.want_dot = 1;
+  autotune("stencil_f64", s.m, 0, 0, kStencilVariants, kStencilNames, 0, st,
+           [&](int var) { launch_stencil_variant<double>(var, s, v, e, partials, st, nullptr); });
+}
+
+template <typename T>
+void tune_levels(Hierarchy& H, cudaStream_t st, T* (*vec)(Level&, int)) {
+  const int prec = H.o.precision;
+  for (size_t l = 0; l < H.L.size(); l++) {
+    Level& L = *H.L[l];
+    T* x = vec(L, 0);
+    T* b = vec(L, 1);
+    T* r = vec(L, 2);
+    T* d0 = vec(L, 3);
+    T* d1 = vec(L, 4);
+    FEM_CUDA(cudaMemsetAsync(x, 0, L.N * sizeof(T), st));
+    FEM_CUDA(cudaMemsetAsync(r, 0, L.N * sizeof(T), st));
+    FEM_CUDA(cudaMemsetAsync(d0, 0, L.N * sizeof(T), st));
+    if (L.stencil) {
+      if (sizeof(T) == 4)
+        tune_stencil_f32(L.st, (float*)(void*)d0, (float*)(void*)r, (float*)(void*)d1,
+                         (float*)(void*)x, st);
+    } else if (!L.coarsest || !L.Ainv.p) {
+      tune_csr_prec<T>(*L.A, prec, x, b, E_STORE, st);
+    }
+    if (!L.coarsest && l + 1 < H.L.size()) {
+      Level& C = *H.L[l + 1];
+      T* cx = vec(C, 0);
+      T* cb = vec(C, 1);
+      FEM_CUDA(cudaMemsetAsync(cx, 0, C.N * sizeof(T), st));
+      tune_csr_prec<T>(L.R, prec, r, cb, E_STORE, st);
+      tune_csr_prec<T>(L.P, prec, cx, x, E_ADD, st);
+    }
+  }
+}
+
+float* vec_f(Level& L, int k) {
+  DevBuf<float>* v[5] = {&L.xf, &L.bf, &L.rf, &L.d0f, &L.d1f};
+  return v[k]->p;
+}
+double* vec_d(Level& L, int k) {
+  DevBuf<double>* v[5] = {&L.x, &L.b, &L.r, &L.d0, &L.d1};
+  return v[k]->p;
+}
+}  // namespace
+
+void tune_hierarchy(Hierarchy& H, System& S, cudaStream_t st) {
+  if (H.o.precision == AMG_PREC_FP64)
+    tune_levels<double>(H, st, vec_d);
+  else
+    tune_levels<float>(H, st, vec_f);
+  // the CG operator (FP64) on the finest level
+  const int64_t N = S.N;
+  if (N == 0) return;
+  DevBuf<double> tmp(2 * (size_t)N, st);
+  FEM_CUDA(cudaMemsetAsync(tmp.p, 0, 2 * (size_t)N * sizeof(double), st));
+  if (S.stencil)
+    tune_stencil_f64(S.stA, tmp.p, tmp.p + N, H.partials.p, st);
+  else
+    tune_csr<double, double>(S.A, S.A.val.p, tmp.p, tmp.p + N, E_STORE, st);
+}
 
 // ------------------------------------------------------------------ reductions
 

@@ -2,6 +2,7 @@
 // translation units.  Nothing here is part of the C ABI.
 #pragma once
 
+#include <functional>
 #include <map>
 #include <memory>
 #include <vector>
@@ -137,6 +138,22 @@ void batch_poll(BatchSession& W, int32_t* state, int32_t* iters, double* relres,
 void batch_retire(BatchSession& W, int slot, double* u, int64_t ld, int ucol, cudaStream_t st);
 void batch_destroy(BatchSession* W);
 int64_t batch_footprint(const System& S, const Hierarchy& H, int slots);
+
+// ------------------------------------------------------------------ autotuning (autotune.cu)
+// Variant cached for (kernel, a, b, c), else def (also when the cached index is not below
+// nvariants).
+int tuned_variant(const char* kernel, int64_t a, int64_t b, int c, int def, int nvariants);
+// Times every variant (run(v) launches variant v on st) and caches the fastest; returns
+// the cached or default choice without timing when tuning is off or st is capturing.
+int autotune(const char* kernel, int64_t a, int64_t b, int c, int nvariants,
+             const char* const* names, int def, cudaStream_t st,
+             const std::function<void(int)>& run);
+std::string autotune_report();
+void autotune_clear();
+void autotune_pin(const char* kernel, int variant);
+// Tunes the launch shapes of a hierarchy's operators (ops.cu); runs on scratch vectors
+// after the set-up, before any solve uses the hierarchy.
+void tune_hierarchy(Hierarchy& H, System& S, cudaStream_t st);
 
 // ------------------------------------------------------------------ utilities
 void finalize_sums(const double* partials, int nblocks, int nv, double* out, cudaStream_t st,
