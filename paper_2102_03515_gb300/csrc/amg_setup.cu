@@ -271,7 +271,7 @@ __global__ void k_mis_m2(int64_t N, const int64_t* sptr, const int32_t* scol, co
     else if ((best >> 62) == ST_IN)
       ns = ST_OUT;
     else
-      atomicAdd(undecided, 1ull);
+      *undecided = 1ull;  // any undecided node (a plain store: only "nonzero" is read)
   }
   state_out[r] = ns;
 }
@@ -1019,6 +1019,377 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
   return R;
 }
 
+// ------------------------------------------------------------------ uniform-grid level
+
+// On the finest level of a uniform Kuhn grid every row of A holds the same values at the
+// same offsets (a subset of them at the boundary), so the strength graph, the Gershgorin
+// bounds and the smoothed prolongator follow from one interior row.  The kernels below
+// walk the stencil's offsets instead of A's columns; they take the same decisions and do
+// the same arithmetic, in the same order, as the CSR kernels above.
+struct StencilRow {
+  int m = 0;
+  uint32_t present = 0;      // bit d: the interior row has an entry at direction d
+  uint32_t strong = 0;       // bit d: that entry is a strong pair (never the diagonal)
+  double a[27];              // value at direction d
+};
+// direction d = (dx + 1) + 3 (dy + 1) + 9 (dz + 1): increasing d is increasing column
+// offset dx + m dy + m^2 dz (m >= 3), i.e. A's column order; d = 13 is the diagonal.
+constexpr int ST_DIAG = 13;
+
+__device__ __forceinline__ bool st_inb(int i, int j, int k, int d, int m) {
+  const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+  return (unsigned)(i + dx) < (unsigned)m && (unsigned)(j + dy) < (unsigned)m &&
+         (unsigned)(k + dz) < (unsigned)m;
+}
+
+__device__ __forceinline__ int64_t st_off(int d, int m) {
+  return (int64_t)(d % 3 - 1) + (int64_t)m * (d / 3 % 3 - 1) + (int64_t)m * m * (d / 9 - 1);
+}
+
+// strong-direction test: compile-time mask when MASK != 0, else the runtime one
+template <uint32_t MASK>
+__device__ __forceinline__ bool st_sel(uint32_t strong, int d) {
+  return MASK ? ((MASK >> d) & 1u) != 0 : ((strong >> d) & 1u) != 0;
+}
+
+__device__ __forceinline__ void st_ijk(int64_t r, int m, int& i, int& j, int& k) {
+  const uint32_t rr = (uint32_t)r, mm = (uint32_t)m;
+  const uint32_t q = rr / mm;
+  i = (int)(rr - q * mm);
+  k = (int)(q / mm);
+  j = (int)(q - (uint32_t)k * mm);
+}
+
+template <uint32_t MASK>
+__global__ void k_st_mis_init(int64_t N, int m, uint32_t strong, uint8_t* state) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int i, j, k;
+  st_ijk(r, m, i, j, k);
+  bool any = false;
+#pragma unroll
+  for (int d = 0; d < 27; d++)
+    if (st_sel<MASK>(strong, d)) any |= st_inb(i, j, k, d, m);
+  state[r] = any ? ST_UND : ST_OUT;
+}
+
+template <uint32_t MASK>
+__global__ void k_st_mis_m1(int64_t N, int m, uint32_t strong, const uint8_t* state, uint32_t s,
+                            uint64_t* m1) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int i, j, k;
+  st_ijk(r, m, i, j, k);
+  uint64_t best = ((uint64_t)state[r] << 62) | prio_of(r, s);
+#pragma unroll
+  for (int d = 0; d < 27; d++) {
+    if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+    const int64_t q = r + st_off(d, m);
+    const uint64_t kq = ((uint64_t)state[q] << 62) | prio_of(q, s);
+    best = kq > best ? kq : best;
+  }
+  m1[r] = best;
+}
+
+template <uint32_t MASK>
+__global__ void k_st_mis_m2(int64_t N, int m, uint32_t strong, const uint64_t* m1, uint32_t s,
+                            const uint8_t* state_in, uint8_t* state_out,
+                            unsigned long long* undecided) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int i, j, k;
+  st_ijk(r, m, i, j, k);
+  const uint8_t st = state_in[r];
+  uint64_t best = m1[r];
+#pragma unroll
+  for (int d = 0; d < 27; d++) {
+    if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+    const uint64_t kq = m1[r + st_off(d, m)];
+    best = kq > best ? kq : best;
+  }
+  uint8_t ns = st;
+  if (st == ST_UND) {
+    const uint64_t key = ((uint64_t)ST_UND << 62) | prio_of(r, s);
+    if (best == key)
+      ns = ST_IN;
+    else if ((best >> 62) == ST_IN)
+      ns = ST_OUT;
+    else
+      *undecided = 1ull;  // any undecided node (a plain store: only "nonzero" is read)
+  }
+  state_out[r] = ns;
+}
+
+template <uint32_t MASK>
+__global__ void k_st_agg_phase1(int64_t N, int m, uint32_t strong, const uint8_t* state,
+                                const int64_t* rootid, int32_t* agg, uint8_t* p1,
+                                unsigned long long* err) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int i, j, k;
+  st_ijk(r, m, i, j, k);
+  int32_t a = -1;
+  if (state[r] == ST_IN) {
+    a = (int32_t)rootid[r];
+  } else {
+    int found = 0;
+#pragma unroll
+    for (int d = 0; d < 27; d++) {
+      if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+      const int64_t q = r + st_off(d, m);
+      if (state[q] == ST_IN) {
+        if (found) atomicAdd(err, 1ull);
+        a = (int32_t)rootid[q];
+        found = 1;
+      }
+    }
+  }
+  agg[r] = a;
+  p1[r] = a >= 0;
+}
+
+template <uint32_t MASK>
+__global__ void k_st_agg_phase2(int64_t N, int m, uint32_t strong, const uint8_t* p1, int32_t* agg,
+                                unsigned long long* err) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  if (p1[r]) return;
+  int i, j, k;
+  st_ijk(r, m, i, j, k);
+  // aggregate of each strong in-bounds neighbour that is in a phase-1 aggregate (-1 else)
+  int32_t na[27];
+  bool any = false;
+#pragma unroll
+  for (int d = 0; d < 27; d++) {
+    na[d] = -1;
+    if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+    any = true;
+    const int64_t q = r + st_off(d, m);
+    if (p1[q]) na[d] = agg[q];
+  }
+  if (!any) return;  // isolated
+  int32_t best = -1;
+  int bestc = 0;
+#pragma unroll
+  for (int d = 0; d < 27; d++) {
+    if (na[d] < 0) continue;
+    int c = 0;
+#pragma unroll
+    for (int f = 0; f < 27; f++) c += na[f] == na[d];
+    if (c > bestc || (c == bestc && na[d] < best)) {
+      best = na[d];
+      bestc = c;
+    }
+  }
+  if (best < 0) atomicAdd(err, 1ull);
+  agg[r] = best;
+}
+
+// k_psmooth on the stencil: the row's in-bounds diagonal and strong entries in column order
+template <uint32_t MASK>
+__global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double dinv,
+                             double omega, int64_t* cnt, const int32_t* Prp, int32_t* Pcol,
+                             double* Pval) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int i, j, k;
+  st_ijk(r, S.m, i, j, k);
+  const int32_t ar = agg[r];
+  int keys[27];
+  double vals[27];
+  int m = 0;
+  if (ar >= 0) {
+#pragma unroll
+    for (int d = 0; d < 27; d++) {
+      if ((d != ST_DIAG && !st_sel<MASK>(S.strong, d)) || !st_inb(i, j, k, d, S.m)) continue;
+      const int a = agg[r + st_off(d, S.m)];
+      if (a < 0) continue;
+      const double v = __dmul_rn(S.a[d], dinv);
+      int q = m++;
+      while (q > 0 && keys[q - 1] > a) {
+        keys[q] = keys[q - 1];
+        vals[q] = vals[q - 1];
+        q--;
+      }
+      keys[q] = a;
+      vals[q] = v;
+    }
+  }
+  if (!Pcol) {
+    int dd = 0;
+    for (int q = 0; q < m; q++) dd += (q == 0 || keys[q] != keys[q - 1]);
+    cnt[r] = dd;
+    return;
+  }
+  int64_t o = Prp[r];
+  const int64_t o1 = Prp[r + 1];
+  int q = 0;
+  while (q < m) {
+    const int key = keys[q];
+    double sum = vals[q++];
+    while (q < m && keys[q] == key) sum = __dadd_rn(sum, vals[q++]);
+    const double t = __dmul_rn(-omega, sum);
+    Pcol[o] = key;
+    Pval[o] = key == ar ? __dadd_rn(1.0, t) : t;
+    o++;
+  }
+  for (; o < o1; o++) {
+    Pcol[o] = -1;
+    Pval[o] = 0.0;
+  }
+}
+
+__global__ void k_fill(int64_t n, double v, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v;
+}
+
+// The interior row of A (centre of the grid) with its strong pairs, by the same test as
+// k_strength.  Returns false when the level does not have the uniform-stencil structure
+// this path relies on (then the CSR path runs).
+bool stencil_row(const Csr4& A, int m, double theta, StencilRow& R, cudaStream_t st) {
+  if (m < 3 || (int64_t)m * m * m != A.nrows) return false;
+  const int64_t c = (int64_t)(m / 2) * (1 + m + (int64_t)m * m);
+  int32_t rp[2];
+  FEM_CUDA(cudaMemcpyAsync(rp, A.rowptr.p + c, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  const int len = rp[1] - rp[0];
+  if (len <= 0 || len > 32) return false;
+  int32_t col[32];
+  double val[32];
+  FEM_CUDA(cudaMemcpyAsync(col, A.col.p + rp[0], 4 * len, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaMemcpyAsync(val, A.val.p + rp[0], 8 * len, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  R = StencilRow{};
+  R.m = m;
+  for (int d = 0; d < 27; d++) R.a[d] = 0.0;
+  double dg = 0.0;
+  for (int e = 0; e < len; e++)
+    if (col[e] == c) dg = val[e];
+  if (!(dg > 0.0)) return false;
+  const double sq = std::sqrt(dg), tr = theta * sq;
+  int64_t prev = -1;
+  for (int e = 0; e < len; e++) {
+    if (col[e] < 0) continue;
+    const int64_t t = (int64_t)col[e] - c + (1 + m + (int64_t)m * m);
+    if (t < 0 || col[e] <= prev) return false;
+    prev = col[e];
+    const int64_t ex = t % m, ey = (t / m) % m, ez = t / ((int64_t)m * m);
+    if (ex > 2 || ey > 2 || ez > 2) return false;
+    const int d = (int)(ex + 3 * ey + 9 * ez);
+    R.present |= 1u << d;
+    R.a[d] = val[e];
+    if (d != ST_DIAG && val[e] != 0.0 && std::fabs(val[e]) >= tr * sq) R.strong |= 1u << d;
+  }
+  return (R.present >> ST_DIAG) & 1u;
+}
+
+// Row-sum bound max_i sum_j |a_ij| / a_ii over the selected entries (all, or diagonal and
+// strong) in column order: attained on interior rows (boundary rows hold a subset of the
+// same terms).
+double stencil_rowabs(const StencilRow& R, bool strong_only) {
+  const uint32_t sel = strong_only ? (R.strong | (1u << ST_DIAG)) : R.present;
+  double s = 0.0;
+  for (int d = 0; d < 27; d++)
+    if ((sel >> d) & 1u) s += std::fabs(R.a[d]);
+  return s / R.a[ST_DIAG];
+}
+
+// Strong-direction sets of the Kuhn stencil by class (the kernels are compiled for each
+// combination; any other set runs with the mask read at run time).
+constexpr uint32_t kStAxis = (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
+constexpr uint32_t kStFace = (1u << 1) | (1u << 3) | (1u << 9) | (1u << 17) | (1u << 23) | (1u << 25);
+constexpr uint32_t kStBody = (1u << 0) | (1u << 26);
+
+template <uint32_t M>
+Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s, cudaStream_t st) {
+  Aggregation R;
+  const unsigned g = grid_for(N, 256);
+  DevBuf<uint8_t> s0(N, st), s1(N, st);
+  DevBuf<uint64_t> m1(N, st);
+  DevBuf<unsigned long long> und(1, st);
+  k_st_mis_init<M><<<g, 256, 0, st>>>(N, S.m, S.strong, s0);
+  FEM_CHECK_LAUNCH();
+  uint8_t* cur = s0;
+  uint8_t* nxt = s1;
+  bool finished = false;
+  for (int round = 0; round < 10000; round++) {
+    // two rounds per check of the undecided flag (a round after the last is a no-op)
+    FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+    for (int t = 0; t < 2; t++) {
+      k_st_mis_m1<M><<<g, 256, 0, st>>>(N, S.m, S.strong, cur, seed_s, m1);
+      FEM_CHECK_LAUNCH();
+      if (t == 1) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+      k_st_mis_m2<M><<<g, 256, 0, st>>>(N, S.m, S.strong, m1, seed_s, cur, nxt, und);
+      FEM_CHECK_LAUNCH();
+      std::swap(cur, nxt);
+    }
+    unsigned long long hu = 0;
+    FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    if (hu == 0) {
+      finished = true;
+      break;
+    }
+  }
+  FEM_REQUIRE(finished, FEM_EDEVCHECK, "aggregation: MIS-2 did not terminate");
+  DevBuf<int64_t> flag(N, st), rootid(N + 1, st);
+  k_root_flags<<<g, 256, 0, st>>>(N, cur, flag);
+  FEM_CHECK_LAUNCH();
+  R.nagg = exclusive_scan(flag, N, rootid, st);
+  R.agg.alloc(N);
+  DevBuf<uint8_t> p1(N, st);
+  DevBuf<unsigned long long> err(1, st);
+  FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+  k_st_agg_phase1<M><<<g, 256, 0, st>>>(N, S.m, S.strong, cur, rootid, R.agg, p1, err);
+  FEM_CHECK_LAUNCH();
+  k_st_agg_phase2<M><<<g, 256, 0, st>>>(N, S.m, S.strong, p1, R.agg, err);
+  FEM_CHECK_LAUNCH();
+  unsigned long long he = 0;
+  FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(he == 0, FEM_EDEVCHECK, "aggregation: inconsistent MIS-2 / aggregate assignment");
+  return R;
+}
+
+template <uint32_t M>
+void psmooth_stencil_t(int64_t N, const StencilRow& S, const int32_t* agg, double dinv,
+                       double omega, Csr4& P, int64_t nagg, cudaStream_t st) {
+  const unsigned g = grid_for(N, 256);
+  DevBuf<int64_t> pc(N, st);
+  k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, pc, nullptr, nullptr, nullptr);
+  FEM_CHECK_LAUNCH();
+  P.nrows = (int32_t)N;
+  P.ncols = (int32_t)nagg;
+  rowptr_from_counts(pc, N, P, st);
+  P.val.alloc(P.nnz);
+  k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, nullptr, P.rowptr, P.col, P.val);
+  FEM_CHECK_LAUNCH();
+}
+
+#define FEM_ST_DISPATCH(strong, F, ...)                                        \
+  switch (strong) {                                                           \
+    case kStAxis: F<kStAxis>(__VA_ARGS__); break;                               \
+    case kStFace: F<kStFace>(__VA_ARGS__); break;                               \
+    case kStBody: F<kStBody>(__VA_ARGS__); break;                               \
+    case kStAxis | kStFace: F<kStAxis | kStFace>(__VA_ARGS__); break;           \
+    case kStAxis | kStBody: F<kStAxis | kStBody>(__VA_ARGS__); break;           \
+    case kStFace | kStBody: F<kStFace | kStBody>(__VA_ARGS__); break;           \
+    case kStAxis | kStFace | kStBody: F<kStAxis | kStFace | kStBody>(__VA_ARGS__); break; \
+    default: F<0u>(__VA_ARGS__); break;                                         \
+  }
+
+Aggregation aggregate_stencil(int64_t N, const StencilRow& S, uint32_t seed_s, cudaStream_t st) {
+  Aggregation R;
+  FEM_ST_DISPATCH(S.strong, R = aggregate_stencil_t, N, S, seed_s, st);
+  return R;
+}
+
+void psmooth_stencil(int64_t N, const StencilRow& S, const int32_t* agg, double dinv, double omega,
+                     Csr4& P, int64_t nagg, cudaStream_t st) {
+  FEM_ST_DISPATCH(S.strong, psmooth_stencil_t, N, S, agg, dinv, omega, P, nagg, st);
+}
+
 void make_lowp(Csr4& A, int prec, cudaStream_t st) {
   if (prec == AMG_PREC_FP32 || prec == AMG_PREC_BF16) {
     A.val32.alloc(A.nnz);
@@ -1073,8 +1444,15 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     Lv.N = Acur->nrows;
     const int64_t N = Lv.N;
     unsigned g = grid_for(N, 256);
+    // uniform finest level: graph, bounds and prolongator from the stencil
+    StencilRow SR;
+    const bool st0 = lev == 0 && Lv.stencil && o.smoother == AMG_SMOOTHER_CHEBYSHEV &&
+                     N > o.coarse_max && stencil_row(*Acur, Lv.st.m, o.theta, SR, st);
     DevBuf<double> d(N, st);
-    k_diag<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, d);
+    if (st0)
+      k_fill<<<g, 256, 0, st>>>(N, SR.a[ST_DIAG], d);
+    else
+      k_diag<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, d);
     FEM_CHECK_LAUNCH();
     Lv.dinv.alloc(N);
     if (lowp) Lv.dinv32.alloc(N);
@@ -1086,7 +1464,8 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       Lv.lmax = 1.0;
     } else {
       k_recip<<<g, 256, 0, st>>>(N, d, Lv.dinv, lowp ? Lv.dinv32.p : nullptr);
-      Lv.lmax = rowabs_max(*Acur, Acur->val, nullptr, d, nullptr, st);
+      Lv.lmax = st0 ? stencil_rowabs(SR, false)
+                    : rowabs_max(*Acur, Acur->val, nullptr, d, nullptr, st);
     }
     FEM_CHECK_LAUNCH();
     if (lowp) {
@@ -1102,7 +1481,7 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     Aggregation ag;
     if (!last) {
       uint32_t s = (uint32_t)(0x9E3779B9u * (uint32_t)(o.seed + lev + 1));
-      ag = aggregate(*Acur, d, o.theta, s, st);
+      ag = st0 ? aggregate_stencil(N, SR, s, st) : aggregate(*Acur, d, o.theta, s, st);
       tr.mark("level: aggregation");
       if (ag.nagg == 0 || (double)ag.nagg >= 0.9 * (double)N) last = true;
     }
@@ -1115,13 +1494,21 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     }
     // smoothed prolongator P = P_t - omega D^{-1} A_F P_t
     Lv.agg = std::move(ag.agg);
-    const double lamF = rowabs_max(*Acur, Acur->val, ag.smask, d, nullptr, st);
+    const double lamF = st0 ? stencil_rowabs(SR, true)
+                            : rowabs_max(*Acur, Acur->val, ag.smask, d, nullptr, st);
     const double omega = 4.0 / (3.0 * lamF);
-    DevBuf<double> dinvA(N, st);
-    k_recip<<<g, 256, 0, st>>>(N, d, dinvA, nullptr);
-    FEM_CHECK_LAUNCH();
     bool done_p = false;
-    {
+    if (st0) {
+      psmooth_stencil(N, SR, Lv.agg, 1.0 / SR.a[ST_DIAG], omega, Lv.P, ag.nagg, st);
+      done_p = true;
+    }
+    DevBuf<double> dinvA;
+    if (!done_p) {
+      dinvA.alloc(N);
+      k_recip<<<g, 256, 0, st>>>(N, d, dinvA, nullptr);
+      FEM_CHECK_LAUNCH();
+    }
+    if (!done_p) {
       DevBuf<int64_t> pc(N, st);
       DevBuf<unsigned long long> ovf(1, st);
       FEM_CUDA(cudaMemsetAsync(ovf, 0, 8, st));
