@@ -186,6 +186,43 @@ def batched_sample(fa, torch, dev, n: int = 128, nrhs: int = 64):
             "speedup_vs_sequential_fp64": ts / tb, "max_rel_diff_vs_sequential_fp64": err}
 
 
+# The paper's Tables 1 and 2 at h = 1/256 (Sec. 4.1; another mesh, so context only)
+PAPER_TABLE_H256 = {1e-2: (8.9566e-6, 1.2731e-2), 1e-4: (8.4684e-6, 1.6453e-2)}
+
+
+def paper_tables_sample(fa, torch, dev, n: int):
+    """||u_rho - u_rho,h||_L2 and ||grad(u_rho - u_rho,h)||_L2 from GPU solves (FP64 V-cycle,
+    tol 1e-10) with the device error norms, next to the paper's Tables 1 and 2."""
+    import math
+    import fem_workloads as W
+    out = {"h": 1.0 / n, "rows": []}
+    N = (n - 1) ** 3
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    for rho, (pl2, ph1) in PAPER_TABLE_H256.items():
+        sys_ = fa.fem_assemble(n, rho, W.sine_target())
+        h = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP64)
+        res = fa.pcg_solve(sys_, h, None, u, tol=1e-10)[0]
+        scale = 1.0 / (3.0 * rho * math.pi ** 2 + 1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fa.fem_errors(sys_, u, W.sine_target(), scale=scale, qlevel=1)
+        te = time.perf_counter() - t0
+        z = torch.empty_like(u)
+        p = torch.empty_like(u)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fa.fem_recover(sys_, u, W.sine_target(), z, p)
+        tr = time.perf_counter() - t1
+        row = {"rho": rho, "iterations": res["iterations"], "l2": math.sqrt(r["l2sq"]),
+               "h1": math.sqrt(r["h1sq"]), "paper_l2": pl2 if n == 256 else None,
+               "paper_h1": ph1 if n == 256 else None, "errors_ms": te * 1e3,
+               "recover_ms": tr * 1e3}
+        out["rows"].append(row)
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+    return out
+
+
 def serving_sample(count: int, sizes=(32, 64, 96, 128, 192)):
     """Poisson stream of solve requests through the continuous-batching service."""
     import fem_workloads as W
@@ -347,8 +384,9 @@ def run_ours(args, rank: int, world: int):
     flops = 2.0 * real_nnz
     achieved = flops / (kms * 1e-3) / 1e12
 
-    batched = serving = None
+    batched = serving = tables = None
     if not args.no_extras:
+        tables = paper_tables_sample(fa, torch, dev, n)
         batched = batched_sample(fa, torch, dev)
         serving = serving_sample(args.serve_requests)
 
@@ -396,6 +434,8 @@ def run_ours(args, rank: int, world: int):
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
+    if tables is not None:
+        line["paper_tables"] = tables
     if batched is not None:
         line["batched"] = batched
     if serving is not None:

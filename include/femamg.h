@@ -148,6 +148,33 @@ fem_status fem_spmv(fem_system sys, const double* x_dev, double* y_dev, void* st
 
 void fem_system_destroy(fem_system sys);
 
+/* ------------------------------------------------------------------ post-processing */
+
+/* Errors of a discrete solution against w = scale * target (Sec. 4.1, Tables 1-3: with
+ * target = FEM_TARGET_SINE and scale = 1 / (3 rho pi^2 + 1), w is the exact u_rho of the
+ * reduced problem; with scale = 1, w is the target ubar itself):
+ *   l2sq = ||w - u_h||^2_{L2},  h1sq = ||grad (w - u_h)||^2_{L2},
+ * u_h the P1 function with the nodal values u_dev (length N, interior unknowns) and zero
+ * on the boundary.  Integrals run over every tet of the mesh with the 4-point
+ * Hammer-Stroud rule applied on each child of qlevel (0..2) rounds of Bey's red
+ * refinement (4 * 8^qlevel points per tet), in FP64 with a fixed-order reduction.  h1sq is
+ * NaN for targets without a gradient here (box, bumps).  Errors: FEM_EINVAL (null
+ * argument, qlevel out of range, bad target). */
+typedef struct {
+  double l2sq;
+  double h1sq;
+} fem_errors_result;
+fem_status fem_errors(fem_system sys, const double* u_dev, const fem_target* target,
+                      double scale, int32_t qlevel, void* stream, fem_errors_result* out);
+
+/* Control and adjoint of the optimal control problem recovered from the state u_h
+ * (Sec. 2: z = (ubar - u) / rho from the gradient equation, p = -rho u): at every
+ * unknown's vertex x_i, z_i = (ubar(x_i) - u_i) / rho and p_i = -rho u_i, rho the
+ * system's.  u_dev, z_dev, p_dev: device arrays of length N (z_dev or p_dev may be
+ * null).  Errors: FEM_EINVAL (null sys / u_dev / target, bad target). */
+fem_status fem_recover(fem_system sys, const double* u_dev, const fem_target* target,
+                       double* z_dev, double* p_dev, void* stream);
+
 /* ------------------------------------------------------------------ AMG */
 
 typedef enum { AMG_SMOOTHER_CHEBYSHEV = 0, AMG_SMOOTHER_L1_JACOBI = 1 } amg_smoother;

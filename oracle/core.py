@@ -82,6 +82,8 @@ def _load():
                                           C.c_int64, P(C.c_int64), P(C.c_int32),
                                           P(C.c_double), P(C.c_double), P(C.c_double)]
             lib.ora_kuhn_rows.restype = C.c_int
+            lib.ora_target_values.argtypes = [P(_Target), C.c_int64, P(C.c_double),
+                                              P(C.c_double)]
             lib.ora_errors.argtypes = [C.c_int64, P(C.c_double), C.c_int64, P(C.c_int32),
                                        P(C.c_double), P(_Target), C.c_int, P(C.c_double),
                                        P(C.c_double)]
@@ -284,6 +286,28 @@ def errors(system: System, u: np.ndarray, exact: dict, qlevel: int = 1):
     _load().ora_errors(len(U), _dp(system.xyz), len(tets), _ip(tets), _dp(U), C.byref(t),
                        qlevel, C.byref(l2), C.byref(h1))
     return l2.value, h1.value
+
+
+def target_values(target: dict, pts: np.ndarray) -> np.ndarray:
+    """ubar at the given points (npts x 3)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    t, keep = _target_struct(target)
+    out = np.empty(len(pts))
+    _load().ora_target_values(C.byref(t), len(pts), _dp(pts), _dp(out))
+    return out
+
+
+def recover(system: System, rho: float, u: np.ndarray, target: dict):
+    """Control and adjoint from the state (Sec. 2: the gradient equation gives
+    z = (ubar - u) / rho, the adjoint p = -rho u), as nodal values at the unknowns'
+    vertices: z_i = (ubar(x_i) - u_i) / rho, p_i = -rho u_i."""
+    verts = np.flatnonzero(system.dof >= 0)
+    order = np.argsort(system.dof[verts])
+    x = system.xyz[verts[order]]
+    ub = target_values(target, x)
+    z = (ub - u) / rho
+    p = -rho * u
+    return z, p
 
 
 def kuhn_rows(n: int, target: dict, rows, xyz: np.ndarray | None = None, qlevel: int = 0):

@@ -560,6 +560,14 @@ void ora_errors(int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
   *h1sq = g2;
 }
 
+/* ------------------------------------------------------------ post-processing */
+
+/* Target values at points (npts x 3 coordinates); used for the control recovery of
+ * Sec. 2, z = (ubar - u) / rho, evaluated at the vertices. */
+void ora_target_values(const target_t *T, int64_t npts, const double *xyz, double *out) {
+  for (int64_t i = 0; i < npts; i++) out[i] = target_eval(T, xyz + 3 * i);
+}
+
 /* ------------------------------------------------------------ single rows */
 
 /* Rows of K, M and f for selected interior vertices of the Kuhn mesh with n cells per side,

@@ -87,12 +87,18 @@ VP = C.c_void_p
 P = C.POINTER
 
 # name -> (restype, argtypes); this list mirrors include/femamg.h
+class ErrorsResult(C.Structure):
+    _fields_ = [("l2sq", C.c_double), ("h1sq", C.c_double)]
+
+
 SIGNATURES = {
     "fem_assemble": (C.c_int, [P(KuhnDesc), C.c_double, P(Target), P(AssembleOpts), VP, P(VP)]),
     "fem_system_get_info": (C.c_int, [VP, P(SystemInfo)]),
     "fem_system_get_rhs": (C.c_int, [VP, VP, VP]),
     "fem_assemble_rhs": (C.c_int, [VP, P(Target), VP, VP]),
     "fem_assemble_rhs_noalloc": (C.c_int, [VP, P(Target), VP, VP]),
+    "fem_errors": (C.c_int, [VP, VP, P(Target), C.c_double, C.c_int32, VP, P(ErrorsResult)]),
+    "fem_recover": (C.c_int, [VP, VP, P(Target), VP, VP, VP]),
     "fem_system_export": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
     "fem_spmv": (C.c_int, [VP, VP, VP, VP]),
     "fem_system_destroy": (None, [VP]),
@@ -210,6 +216,24 @@ def fem_assemble_rhs(sys, target: dict, f, stream=None):
     keep = []
     t = _target(target, keep)
     _check(lib().fem_assemble_rhs(sys, C.byref(t), _ptr(f), _stream(stream)), "fem_assemble_rhs")
+
+
+def fem_errors(sys, u, target: dict, scale: float = 1.0, qlevel: int = 1, stream=None) -> dict:
+    """{"l2sq": ||w - u_h||^2, "h1sq": ||grad(w - u_h)||^2} for w = scale * target."""
+    keep = []
+    t = _target(target, keep)
+    r = ErrorsResult()
+    _check(lib().fem_errors(sys, _ptr(u), C.byref(t), float(scale), int(qlevel), _stream(stream),
+                            C.byref(r)), "fem_errors")
+    return {"l2sq": r.l2sq, "h1sq": r.h1sq}
+
+
+def fem_recover(sys, u, target: dict, z=None, p=None, stream=None):
+    """Control z = (ubar - u) / rho and adjoint p = -rho u at the unknowns."""
+    keep = []
+    t = _target(target, keep)
+    _check(lib().fem_recover(sys, _ptr(u), C.byref(t), _ptr(z) if z is not None else None,
+                             _ptr(p) if p is not None else None, _stream(stream)), "fem_recover")
 
 
 def fem_assemble_rhs_noalloc(sys, target: dict, f, stream=None):

@@ -12,6 +12,7 @@
 // -fmad=false) so that sums of element contributions follow plain IEEE rounding.
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "solver.cuh"
 
@@ -477,6 +478,138 @@ void target_to_device(const fem_target& t, TargetHolder& h, cudaStream_t st) {
   }
 }
 
+// ------------------------------------------------------------------ post-processing
+
+// Quadrature for the error norms: the 4-point Hammer-Stroud rule applied on each of the
+// 8^level children of `level` rounds of Bey's red refinement of the tet, as barycentric
+// points of the parent with weights summing to 1.
+void bey_rule(const double P[4][4], int level, double w, std::vector<double>& bary,
+              std::vector<double>& wt) {
+  if (level == 0) {
+    const double A = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, B = (5.0 - std::sqrt(5.0)) / 20.0;
+    for (int q = 0; q < 4; q++)
+      for (int d = 0; d < 4; d++) {
+        double s = 0.0;
+        for (int v = 0; v < 4; v++) s += (v == q ? A : B) * P[v][d];
+        bary.push_back(s);
+        if (d == 3) wt.push_back(0.25 * w);
+      }
+    return;
+  }
+  // edge midpoints mid(a, b); the 4 corner children and the 4 children of the inner
+  // octahedron split along the diagonal between the midpoints of edges 02 and 13
+  static const int kid[8][4][2] = {{{0, 0}, {0, 1}, {0, 2}, {0, 3}}, {{0, 1}, {1, 1}, {1, 2}, {1, 3}},
+                                   {{0, 2}, {1, 2}, {2, 2}, {2, 3}}, {{0, 3}, {1, 3}, {2, 3}, {3, 3}},
+                                   {{0, 1}, {0, 2}, {0, 3}, {1, 3}}, {{0, 1}, {0, 2}, {1, 2}, {1, 3}},
+                                   {{0, 2}, {0, 3}, {1, 3}, {2, 3}}, {{0, 2}, {1, 2}, {1, 3}, {2, 3}}};
+  for (int c = 0; c < 8; c++) {
+    double Q[4][4];
+    for (int v = 0; v < 4; v++)
+      for (int d = 0; d < 4; d++) Q[v][d] = 0.5 * (P[kid[c][v][0]][d] + P[kid[c][v][1]][d]);
+    bey_rule(Q, level - 1, w / 8.0, bary, wt);
+  }
+}
+
+// w = scale * target and its gradient (sine targets only)
+__device__ __forceinline__ void target_grad(const TargetDev& T, double scale, double x, double y,
+                                            double z, double g[3]) {
+  double s0, c0, s1, c1, s2, c2;
+  sincospi(x, &s0, &c0);
+  sincospi(y, &s1, &c1);
+  sincospi(z, &s2, &c2);
+  const double f = scale * 3.14159265358979323846;
+  g[0] = f * c0 * s1 * s2;
+  g[1] = f * s0 * c1 * s2;
+  g[2] = f * s0 * s1 * c2;
+}
+
+// ||w - u_h||^2 and ||grad(w - u_h)||^2 over the tets of one cube per thread (grid-stride,
+// fixed grid): u_h is the P1 function with nodal values u on interior vertices and 0 on the
+// boundary.  Per-block partial sums in partials[block], partials[nb + block].
+__global__ void k_errors(int n, const double* xyz, const double* __restrict__ u, TargetDev T,
+                         double scale, int grad, const double* __restrict__ qb,
+                         const double* __restrict__ qw, int np, double* partials) {
+  constexpr int PP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int64_t nc = (int64_t)n * n * n;
+  const int m = n - 1;
+  Coords C{xyz, n, 1.0 / n};
+  double acc[2] = {0.0, 0.0};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(c % n), cj = (int)((c / n) % n), ck = (int)(c / ((int64_t)n * n));
+    double Xc[8][3], Uc[8];
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+      const int vi = ci + (a & 1), vj = cj + ((a >> 1) & 1), vk = ck + ((a >> 2) & 1);
+      C.get(vi, vj, vk, Xc[a]);
+      const bool in = vi >= 1 && vj >= 1 && vk >= 1 && vi <= m && vj <= m && vk <= m;
+      Uc[a] = in ? u[(int64_t)(vi - 1) + (int64_t)m * ((vj - 1) + (int64_t)m * (vk - 1))] : 0.0;
+    }
+#pragma unroll
+    for (int p = 0; p < 6; p++) {
+      int lv[4];
+      lv[0] = 0;
+#pragma unroll
+      for (int s2 = 0; s2 < 3; s2++) lv[s2 + 1] = lv[s2] | (1 << PP[p][s2]);
+      double X[4][3], g[4][3], U[4];
+#pragma unroll
+      for (int a = 0; a < 4; a++) {
+        U[a] = Uc[lv[a]];
+#pragma unroll
+        for (int d = 0; d < 3; d++) X[a][d] = Xc[lv[a]][d];
+      }
+      const double vol = fabs(tet_grads(X, g)) / 6.0;
+      double guh[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) guh[d] += U[a] * g[a][d];
+      double e2 = 0.0, g2 = 0.0;
+      for (int q = 0; q < np; q++) {
+        double x[3] = {0.0, 0.0, 0.0}, uh = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+          const double b = qb[4 * q + a];
+#pragma unroll
+          for (int d = 0; d < 3; d++) x[d] += b * X[a][d];
+          uh += b * U[a];
+        }
+        const double diff = scale * target_eval(T, x[0], x[1], x[2]) - uh;
+        e2 += qw[q] * diff * diff;
+        if (grad) {
+          double ge[3];
+          target_grad(T, scale, x[0], x[1], x[2], ge);
+          const double d0 = ge[0] - guh[0], d1 = ge[1] - guh[1], d2 = ge[2] - guh[2];
+          g2 += qw[q] * (d0 * d0 + d1 * d1 + d2 * d2);
+        }
+      }
+      acc[0] += vol * e2;
+      acc[1] += vol * g2;
+    }
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc[0];
+    partials[gridDim.x + blockIdx.x] = acc[1];
+  }
+}
+
+// Control and adjoint at the unknowns' vertices: z = (ubar - u) / rho, p = -rho u.
+__global__ void k_recover(int n, const double* xyz, TargetDev T, double rho,
+                          const double* __restrict__ u, double* z, double* p) {
+  const int m = n - 1;
+  const int64_t N = (int64_t)m * m * m;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int i = (int)(r % m) + 1, j = (int)((r / m) % m) + 1, k = (int)(r / ((int64_t)m * m)) + 1;
+  Coords C{xyz, n, 1.0 / n};
+  double x[3];
+  C.get(i, j, k, x);
+  const double ur = u[r];
+  if (z) z[r] = (target_eval(T, x[0], x[1], x[2]) - ur) / rho;
+  if (p) p[r] = -rho * ur;
+}
+
 }  // namespace
 
 void assemble_rhs(System& S, const fem_target& t, double* f, cudaStream_t st) {
@@ -621,6 +754,41 @@ static double* noalloc_scratch() {
     addr[dev] = static_cast<double*>(p);
   }
   return addr[dev];
+}
+
+void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
+                     double out[2], cudaStream_t st) {
+  FEM_REQUIRE(qlevel >= 0 && qlevel <= 2, FEM_EINVAL, "fem_errors: qlevel in [0, 2]");
+  TargetHolder th;
+  target_to_device(t, th, st);
+  std::vector<double> bary, wt;
+  const double P[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+  bey_rule(P, qlevel, 1.0, bary, wt);
+  const int np = (int)wt.size();
+  DevBuf<double> qb(bary.size(), st), qw(wt.size(), st);
+  FEM_CUDA(cudaMemcpyAsync(qb, bary.data(), 8 * bary.size(), cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(qw, wt.data(), 8 * wt.size(), cudaMemcpyHostToDevice, st));
+  const int grad = (t.kind == FEM_TARGET_SINE || t.kind == FEM_TARGET_SINE_PLUS_ONE) ? 1 : 0;
+  const int64_t ncube = (int64_t)S.n * S.n * S.n;
+  const unsigned g = persistent_grid(ncube, 128, 8);
+  DevBuf<double> part(2 * (size_t)g, st), sums(2, st);
+  k_errors<<<g, 128, 0, st>>>(S.n, S.uniform ? nullptr : S.xyz.p, u, th.T, scale, grad, qb, qw,
+                              np, part);
+  FEM_CHECK_LAUNCH();
+  finalize_sums(part, (int)g, 2, sums, st);
+  FEM_CUDA(cudaMemcpyAsync(out, sums, 16, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  if (!grad) out[1] = std::nan("");
+}
+
+void fem_recovery(System& S, const double* u, const fem_target& t, double* z, double* p,
+                  cudaStream_t st) {
+  TargetHolder th;
+  target_to_device(t, th, st);
+  k_recover<<<grid_for(S.N, 256), 256, 0, st>>>(S.n, S.uniform ? nullptr : S.xyz.p, th.T, S.rho,
+                                                 u, z, p);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaStreamSynchronize(st));
 }
 
 void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_t st) {

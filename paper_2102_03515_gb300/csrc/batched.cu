@@ -93,7 +93,9 @@ struct MvOps {
   double r1, r2;
 };
 
-template <typename T>
+// MODE >= 0 fixes the mode at compile time (5: mode 2 with the FP64 output, 2: without);
+// -1 reads it at run time.
+template <typename T, int MODE = -1>
 __device__ __forceinline__ MvOps<T> mv_load(const MvEpi<T>& e, int64_t i, int b) {
   using AT = typename Arith<T>::type;
   MvOps<T> o;
@@ -103,7 +105,8 @@ __device__ __forceinline__ MvOps<T> mv_load(const MvEpi<T>& e, int64_t i, int b)
   o.r1 = 0.0;
   o.r2 = 0.0;
   const int64_t idx = i * e.B + b;
-  switch (e.mode) {
+  const bool zo = MODE == 5 || (MODE < 0 && e.z64 != nullptr);
+  switch (MODE >= 0 ? (MODE == 5 ? 2 : MODE) : e.mode) {
     case 0:
       if (e.want_dot) o.a = (AT)e.x[idx];
       break;
@@ -118,7 +121,7 @@ __device__ __forceinline__ MvOps<T> mv_load(const MvEpi<T>& e, int64_t i, int b)
       o.a = (AT)e.r[idx];
       o.s = (AT)smoother_sinv(e, i, b);
       o.x = (AT)e.x[idx];
-      if (e.z64) {
+      if (zo) {
         o.r1 = e.r1[idx];
         o.r2 = e.r2[idx];
       }
@@ -127,14 +130,15 @@ __device__ __forceinline__ MvOps<T> mv_load(const MvEpi<T>& e, int64_t i, int b)
   return o;
 }
 
-template <typename T>
+template <typename T, int MODE = -1>
 __device__ __forceinline__ void mv_apply(const MvEpi<T>& e, int64_t i, int b,
                                          typename Arith<T>::type av,
                                          typename Arith<T>::type centre, const MvOps<T>& o,
                                          double acc[2]) {
   using AT = typename Arith<T>::type;
   const int64_t idx = i * e.B + b;
-  switch (e.mode) {
+  const bool zo = MODE == 5 || (MODE < 0 && e.z64 != nullptr);
+  switch (MODE >= 0 ? (MODE == 5 ? 2 : MODE) : e.mode) {
     case 0:
       e.y[idx] = (T)av;
       if (e.want_dot) acc[0] += (double)o.a * (double)av;
@@ -157,7 +161,7 @@ __device__ __forceinline__ void mv_apply(const MvEpi<T>& e, int64_t i, int b,
       e.dnew[idx] = (T)dn;
       AT xv = o.x + (e.add_prev ? dl : (AT)0) + dn;
       e.x[idx] = (T)xv;
-      if (e.z64) {
+      if (zo) {
         double z = (double)xv;
         e.z64[idx] = z;
         acc[0] += z * o.r1;
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(256) k_mv_stencil(const T* __restrict__ v, int
 // again one plane later (7 loads per point instead of 15) and issuing the loads of point
 // k + 1 before finishing point k.  grid: x over groups of 256 / B points along i, y strides
 // over j, z over plane ranges.
-template <typename T, int NV, int KZV>
+template <typename T, int NV, int KZV, int MODE>
 __global__ void __launch_bounds__(256) k_mv_stencil_col(const T* __restrict__ v, int m, MvEpi<T> e,
                                                         double* partials, int nblocks) {
   using AT = typename Arith<T>::type;
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(256) k_mv_stencil_col(const T* __restrict__ v,
       AT z_im = ld(im, k0, -sB), z_jm = ld(jm, k0, -sj), z_ijm = ld(im && jm, k0, -sB - sj);
       AT cp = ld(true, k0 + 1, 0);
       AT n_ip = ld(ip, k0 + 1, sB), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, sB + sj);
-      Ops op = mv_load<T>(e, row0 + pk * k0, b);
+      Ops op = mv_load<T, MODE>(e, row0 + pk * k0, b);
       for (int k = k0; k < kend; k++) {
         const bool more = k + 1 < kend;
         const AT z2_im = ld(im && more, k + 1, -sB), z2_jm = ld(jm && more, k + 1, -sj),
@@ -288,12 +292,12 @@ __global__ void __launch_bounds__(256) k_mv_stencil_col(const T* __restrict__ v,
         const AT n2_ip = ld(ip && more, k + 2, sB), n2_jp = ld(jp && more, k + 2, sj),
                  n2_ijp = ld(ip && jp && more, k + 2, sB + sj);
         Ops op2;
-        if (more) op2 = mv_load<T>(e, row0 + pk * (k + 1), b);
+        if (more) op2 = mv_load<T, MODE>(e, row0 + pk * (k + 1), b);
         const AT axis = z_im + p_ip + z_jm + p_jp + cm + cp;
         const AT face = p_ijp + z_ijm + n_ip + m_im + n_jp + m_jm;
         const AT body = n_ijp + m_ijm;
         const AT av = a0 * c0v + aa * axis + af * face + ab * body;
-        mv_apply<T>(e, row0 + pk * k, b, av, c0v, op, acc);
+        mv_apply<T, MODE>(e, row0 + pk * k, b, av, c0v, op, acc);
         cm = c0v;
         m_im = z_im;
         m_jm = z_jm;
@@ -928,15 +932,30 @@ dim3 mv_stencil_grid(int var, int m, int B) {
   }
 }
 
+template <int NV, int KZV>
+void launch_mv_col(dim3 g, int nb, const float* v, int m, const MvEpi<float>& e, double* part,
+                   cudaStream_t st) {
+  switch (e.mode) {
+    case 0: k_mv_stencil_col<float, NV, KZV, 0><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 1: k_mv_stencil_col<float, NV, KZV, 1><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 3: k_mv_stencil_col<float, NV, KZV, 3><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    default:
+      if (e.z64)
+        k_mv_stencil_col<float, NV, KZV, 5><<<g, 256, 0, st>>>(v, m, e, part, nb);
+      else
+        k_mv_stencil_col<float, NV, KZV, 2><<<g, 256, 0, st>>>(v, m, e, part, nb);
+  }
+}
+
 template <int NV>
 int launch_mv_stencil32(int var, const float* v, int m, const MvEpi<float>& e, double* part,
                         cudaStream_t st) {
   const dim3 g = mv_stencil_grid(var, m, e.B);
   const int nb = (int)(g.x * g.y * g.z);
   switch (var) {
-    case 1: k_mv_stencil_col<float, NV, 16><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
-    case 2: k_mv_stencil_col<float, NV, 32><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
-    case 3: k_mv_stencil_col<float, NV, 64><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 1: launch_mv_col<NV, 16>(g, nb, v, m, e, part, st); break;
+    case 2: launch_mv_col<NV, 32>(g, nb, v, m, e, part, st); break;
+    case 3: launch_mv_col<NV, 64>(g, nb, v, m, e, part, st); break;
     default: k_mv_stencil<float, NV><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
   }
   FEM_CHECK_LAUNCH();

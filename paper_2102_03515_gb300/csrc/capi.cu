@@ -163,6 +163,29 @@ fem_status fem_assemble_rhs_noalloc(fem_system sys, const fem_target* target, do
   });
 }
 
+fem_status fem_errors(fem_system sys, const double* u_dev, const fem_target* target,
+                      double scale, int32_t qlevel, void* stream, fem_errors_result* out) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && u_dev && target && out, FEM_EINVAL, "fem_errors: null argument");
+    StreamScope scope(as_stream(stream));
+    double r[2] = {0.0, 0.0};
+    fem_error_norms(sys->S, u_dev, *target, scale, qlevel, r, as_stream(stream));
+    out->l2sq = r[0];
+    out->h1sq = r[1];
+    return FEM_OK;
+  });
+}
+
+fem_status fem_recover(fem_system sys, const double* u_dev, const fem_target* target,
+                       double* z_dev, double* p_dev, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && u_dev && target, FEM_EINVAL, "fem_recover: null argument");
+    StreamScope scope(as_stream(stream));
+    fem_recovery(sys->S, u_dev, *target, z_dev, p_dev, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream) {
   return guarded([&]() -> fem_status {
     FEM_REQUIRE(sys && f_dev, FEM_EINVAL, "fem_system_get_rhs: null argument");

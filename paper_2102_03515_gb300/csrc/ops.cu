@@ -37,6 +37,9 @@ ChebCoef cheb_coefficients(double lmax, double ratio, int degree) {
 namespace {
 
 enum EpiMode { E_STORE = 0, E_RESIDUAL = 1, E_CHEB_STEP = 2, E_CHEB_INIT = 3, E_ADD = 4 };
+// compile-time variants of E_CHEB_STEP for kernels specialised on the mode: without the
+// FP64 output (z64 null) and with it
+constexpr int E_CHEB_STEP_NOZ = 2, E_CHEB_STEP_Z = 5;
 
 // Fused epilogue applied to (row, (A v)_row).  Modes:
 //   E_STORE     y = Av              (dot: <v, Av> with v = vin)
@@ -75,6 +78,8 @@ struct Epi {
   const double* r1;
   const double* r2;
 
+  // MODE >= 0: the mode fixed at compile time (the switch folds away); -1: run time.
+  template <int MODE = -1>
   __device__ __forceinline__ Ops load(int64_t row) const {
     Ops o;
     o.a = (AT)0;
@@ -82,7 +87,8 @@ struct Epi {
     o.s = (AT)0;
     o.r1 = 0.0;
     o.r2 = 0.0;
-    switch (mode) {
+    const bool zo = MODE == E_CHEB_STEP_Z || (MODE < 0 && z64 != nullptr);
+    switch (MODE >= 0 ? (MODE == E_CHEB_STEP_Z ? E_CHEB_STEP : MODE) : mode) {
       case E_ADD:
         o.a = (AT)y[row];
         break;
@@ -97,7 +103,7 @@ struct Epi {
         o.a = (AT)r[row];
         o.s = sinv ? (AT)sinv[row] : (AT)sinv_c;
         o.x = (AT)x[row];
-        if (z64) {
+        if (zo) {
           o.r1 = r1[row];
           if (r2) o.r2 = r2[row];
         }
@@ -108,9 +114,11 @@ struct Epi {
     return o;
   }
 
+  template <int MODE = -1>
   __device__ __forceinline__ void apply(int64_t row, AT av, AT centre, const Ops& o,
                                         double acc[2]) const {
-    switch (mode) {
+    const bool zo = MODE == E_CHEB_STEP_Z || (MODE < 0 && z64 != nullptr);
+    switch (MODE >= 0 ? (MODE == E_CHEB_STEP_Z ? E_CHEB_STEP : MODE) : mode) {
       case E_STORE:
         y[row] = (T)av;
         if (want_dot) acc[0] += (double)centre * (double)av;
@@ -134,7 +142,7 @@ struct Epi {
         dnew[row] = (T)dn;
         AT xv = o.x + (add_prev ? dl : (AT)0) + dn;
         x[row] = (T)xv;
-        if (z64) {
+        if (zo) {
           double z = (double)xv;
           z64[row] = z;
           acc[0] += z * o.r1;
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(TX* TY) k_stencil(const T* __restrict__ v, int
 // (i+1,j+1)).  Warps run along i, so every load is coalesced; there are no barriers.
 // The loads of point k+1 (stencil values and the epilogue's operands) are issued before
 // point k is finished, so each thread keeps two points' loads in flight.
-template <typename T, int TYV, int KZV>
+template <typename T, int TYV, int KZV, int MODE>
 __global__ void __launch_bounds__(TX* TYV) k_stencil_col(const T* __restrict__ v, int m, SC<T> c,
                                                          Epi<T> epi, double* partials,
                                                          int nblocks, const int* done) {
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(TX* TYV) k_stencil_col(const T* __restrict__ v
     AT z_im = ld(im, k0, -1), z_jm = ld(jm, k0, -sj), z_ijm = ld(im && jm, k0, -1 - sj);
     AT cp = ld(true, k0 + 1, 0);
     AT n_ip = ld(ip, k0 + 1, 1), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, 1 + sj);
-    Ops op = epi.load(row0 + sk * k0);
+    Ops op = epi.template load<MODE>(row0 + sk * k0);
     const AT a0 = (AT)c.c0, aa = (AT)c.ca, af = (AT)c.cf, ab = (AT)c.cb;
     for (int k = k0; k < kend; k++) {
       // issue the next point's loads (beyond kend they are not used)
@@ -271,12 +279,12 @@ __global__ void __launch_bounds__(TX* TYV) k_stencil_col(const T* __restrict__ v
       const AT n2_ip = ld(ip && more, k + 2, 1), n2_jp = ld(jp && more, k + 2, sj),
                n2_ijp = ld(ip && jp && more, k + 2, 1 + sj);
       Ops op2;
-      if (more) op2 = epi.load(row0 + sk * (k + 1));
+      if (more) op2 = epi.template load<MODE>(row0 + sk * (k + 1));
       const AT axis = z_im + p_ip + z_jm + p_jp + cm + cp;
       const AT face = p_ijp + z_ijm + n_ip + m_im + n_jp + m_jm;
       const AT body = n_ijp + m_ijm;
       const AT av = a0 * c0v + aa * axis + af * face + ab * body;
-      epi.apply(row0 + sk * k, av, c0v, op, acc);
+      epi.template apply<MODE>(row0 + sk * k, av, c0v, op, acc);
       // shift: plane k becomes k-1, plane k+1 becomes k
       cm = c0v;
       m_im = z_im;
@@ -313,7 +321,29 @@ int launch_col(const Stencil& s, SC<T> c, const T* v, const Epi<T>& epi, double*
   dim3 grid((m + TX - 1) / TX, (m + TYV - 1) / TYV, (m + KZV - 1) / KZV);
   int nb = grid.x * grid.y * grid.z;
   FEM_REQUIRE(!partials || nb <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "stencil grid too large");
-  k_stencil_col<T, TYV, KZV><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+  if (sizeof(T) == 8) {  // ALU-bound: one kernel for every epilogue
+    k_stencil_col<T, TYV, KZV, -1><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+  } else {
+    switch (epi.mode) {
+      case E_STORE:
+        k_stencil_col<T, TYV, KZV, E_STORE><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+        break;
+      case E_RESIDUAL:
+        k_stencil_col<T, TYV, KZV, E_RESIDUAL><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+        break;
+      case E_CHEB_STEP:
+        if (epi.z64)
+          k_stencil_col<T, TYV, KZV, E_CHEB_STEP_Z><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+        else
+          k_stencil_col<T, TYV, KZV, E_CHEB_STEP_NOZ><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+        break;
+      case E_CHEB_INIT:
+        k_stencil_col<T, TYV, KZV, E_CHEB_INIT><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+        break;
+      default:
+        k_stencil_col<T, TYV, KZV, E_ADD><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+    }
+  }
   FEM_CHECK_LAUNCH();
   return nb;
 }

@@ -76,6 +76,12 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
                      const fem_assemble_opts& o, cudaStream_t st);
 void assemble_rhs(System& S, const fem_target& t, double* f, cudaStream_t st);
 void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_t st);
+// ||scale*t - u_h||^2 and ||grad(scale*t - u_h)||^2 (NaN without a gradient) by quadrature
+void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
+                     double out[2], cudaStream_t st);
+// z = (ubar - u) / rho and p = -rho u at the unknowns (either output may be null)
+void fem_recovery(System& S, const double* u, const fem_target& t, double* z, double* p,
+                  cudaStream_t st);
 
 // ------------------------------------------------------------------ operators (ops.cu)
 // Chebyshev coefficients of one smoothing application of degree k on [lmax/ratio, lmax].
