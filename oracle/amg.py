@@ -22,6 +22,17 @@ the CUDA library follows the same rules in code of its own:
   or too few aggregates) the coarsest level is solved by the smoother alone;
 * smoother: Chebyshev of degree k on D^{-1}A over [lambda/ratio, lambda] with lambda the
   Gershgorin bound of D^{-1}A, or one l1-Jacobi step.
+
+The paper's own coarsening is restated as well (``coarsening="kf"``, Sec. 3.1 after
+KF1998): red-black colouring (visit the unknowns in a fixed order; an unmarked one
+becomes coarse and its unmarked matrix-graph neighbours fine), interpolation of a fine
+unknown by the average over its coarse neighbours, Galerkin A_c = P^T A P, and symmetric
+Gauss-Seidel smoothing (``smoother="sgs"``: one forward sweep before the coarse-grid
+correction, one backward sweep after it).  The paper leaves the visiting order open; here
+it is decreasing hash priority (:func:`priority`).  Gauss-Seidel runs in the order of a
+greedy colouring of the matrix graph (colour classes in increasing order forward,
+decreasing backward; the unknowns of one class do not couple, so their order within the
+class does not matter).
 """
 from __future__ import annotations
 
@@ -30,7 +41,7 @@ import scipy.sparse as sp
 
 UNDECIDED, IN, OUT = 1, 2, 0
 DEFAULTS = dict(theta=0.05, smoother="chebyshev", degree=2, cheb_ratio=6.0,
-                coarse_max=256, max_levels=16, seed=0, min_ratio=0.9)
+                coarse_max=256, max_levels=16, seed=0, min_ratio=0.9, coarsening="sa")
 
 
 # ------------------------------------------------------------- utilities
@@ -261,6 +272,94 @@ def smoothed_prolongator(A, smask, agg, nagg):
     return add_struct(Pt, B, 1.0, -omega), omega
 
 
+# ------------------------------------------------------------- red-black coarsening
+
+def neighbours(A, i):
+    """Matrix-graph neighbours of i: columns j != i of stored nonzero a_ij (column order)."""
+    lo, hi = A.indptr[i], A.indptr[i + 1]
+    cols = A.indices[lo:hi]
+    vals = A.data[lo:hi]
+    return cols[(cols != i) & (vals != 0.0)]
+
+
+def red_black(A, seed: int) -> np.ndarray:
+    """Red-black colouring (Sec. 3.1, after KF1998 Algorithm 2): visit the unknowns by
+    decreasing priority; an unmarked one is marked black (coarse) and its unmarked
+    neighbours red (fine).  Returns the boolean coarse mask."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    mark = np.zeros(n, dtype=np.int8)  # 0 unmarked, 1 black, 2 red
+    for i in np.argsort(priority(n, seed))[::-1]:  # priorities are unique
+        if mark[i]:
+            continue
+        mark[i] = 1
+        nb = neighbours(A, i)
+        mark[nb[mark[nb] == 0]] = 2
+    return mark == 1
+
+
+def averaging_prolongator(A, coarse: np.ndarray):
+    """P: a coarse unknown keeps its value (P(i, c(i)) = 1, coarse unknowns numbered in
+    increasing order); a fine unknown is the average over its coarse neighbours
+    (P(i, c(j)) = 1 / #C_i for j in C_i) (Sec. 3.1)."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    cid = np.cumsum(coarse) - 1
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        if coarse[i]:
+            rows.append(i)
+            cols.append(cid[i])
+            vals.append(1.0)
+            continue
+        nb = neighbours(A, i)
+        cn = nb[coarse[nb]]
+        if len(cn) == 0:
+            raise RuntimeError("fine unknown without a coarse neighbour")
+        w = 1.0 / len(cn)
+        for j in cn:
+            rows.append(i)
+            cols.append(cid[j])
+            vals.append(w)
+    P = sp.csr_matrix((np.array(vals), (np.array(rows), np.array(cols))),
+                      shape=(n, int(coarse.sum())))
+    P.sort_indices()
+    return P
+
+
+def greedy_colouring(A, seed: int) -> np.ndarray:
+    """Colour of each unknown: visit by decreasing priority and take the smallest colour
+    not used by an already coloured neighbour."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    col = np.full(n, -1, dtype=np.int64)
+    for i in np.argsort(priority(n, seed))[::-1]:  # priorities are unique
+        used = set(col[neighbours(A, i)].tolist())
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return col
+
+
+def gauss_seidel(A, b, x, colours, forward: bool):
+    """One Gauss-Seidel sweep in colour order: for each colour class (increasing when
+    forward, decreasing otherwise) x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii, the sum over
+    A's stored entries in column order."""
+    A = sp.csr_matrix(A)
+    d = diagonal(A)
+    off = A.copy()
+    off.setdiag(0.0)
+    off.eliminate_zeros()
+    x = np.zeros_like(b) if x is None else x.copy()
+    ncol = int(colours.max()) + 1 if len(colours) else 0
+    order = range(ncol) if forward else range(ncol - 1, -1, -1)
+    for c in order:
+        idx = np.flatnonzero(colours == c)
+        x[idx] = (b[idx] - off[idx] @ x) / d[idx]
+    return x
+
+
 class Level:
     pass
 
@@ -283,9 +382,16 @@ def build_hierarchy(A, opts: dict | None = None, K=None, M=None):
         L.l1 = np.add.reduceat(np.abs(Al.data), Al.indptr[:-1])
         levels.append(L)
         n = Al.shape[0]
+        if o["smoother"] == "sgs":
+            L.colours = greedy_colouring(Al, o["seed"] + lev)
         last = n <= o["coarse_max"] or lev == o["max_levels"] - 1
+        kf = o["coarsening"] == "kf"
         if not last:
-            agg, nagg, smask = aggregate(Al, o["theta"], o["seed"] + lev)
+            if kf:
+                coarse = red_black(Al, o["seed"] + lev)
+                nagg = int(coarse.sum())
+            else:
+                agg, nagg, smask = aggregate(Al, o["theta"], o["seed"] + lev)
             if nagg == 0 or nagg >= o["min_ratio"] * n:
                 last = True
         if last:
@@ -298,8 +404,12 @@ def build_hierarchy(A, opts: dict | None = None, K=None, M=None):
                 L.Ainv = None  # smoother-only coarsest level
             return levels
         L.coarsest = False
-        L.agg, L.nagg = agg, nagg
-        L.P, L.omega = smoothed_prolongator(Al, smask, agg, nagg)
+        if kf:
+            L.coarse, L.nagg = coarse, nagg
+            L.P = averaging_prolongator(Al, coarse)
+        else:
+            L.agg, L.nagg = agg, nagg
+            L.P, L.omega = smoothed_prolongator(Al, smask, agg, nagg)
         L.R = sp.csr_matrix(L.P.T)
         L.R.sort_indices()
         Al = spgemm(L.R, spgemm(Al, L.P))
@@ -343,9 +453,11 @@ def l1_jacobi(A, l1, b, x):
     return x + (b - A @ x) / l1
 
 
-def smooth(L, b, x, o):
+def smooth(L, b, x, o, forward=True):
     if o["smoother"] == "chebyshev":
         return chebyshev(L.A, L.dinv, b, x, L.lmax, o["cheb_ratio"], o["degree"])
+    if o["smoother"] == "sgs":
+        return gauss_seidel(L.A, b, x, L.colours, forward)
     return l1_jacobi(L.A, L.l1, b, x)
 
 
@@ -360,11 +472,11 @@ def vcycle(levels, b, opts: dict | None = None, lev: int = 0):
         if L.Ainv is not None:
             return L.Ainv @ b
         return smooth(L, b, None, o)
-    x = smooth(L, b, None, o)
+    x = smooth(L, b, None, o, forward=True)
     r = b - L.A @ x
     xc = vcycle(levels, L.R @ r, o, lev + 1)
     x = x + L.P @ xc
-    return smooth(L, b, x, o)
+    return smooth(L, b, x, o, forward=False)
 
 
 # ------------------------------------------------------------- Krylov

@@ -1,0 +1,114 @@
+"""Pins of the oracle's restatement of the paper's own AMG (Sec. 3.1, after KF1998):
+red-black coarsening, averaging interpolation, greedy colouring and symmetric
+Gauss-Seidel smoothing.  Each check follows from the definitions in the paper or from
+textbook facts, not from re-running the oracle's formula.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+import fem_workloads as W
+from oracle import amg, core
+
+
+def _A(n, rho=None, jit=False):
+    xyz = W.jittered_xyz(n, 0.2, seed=n) if jit else None
+    s = core.assemble(n, W.sine_target(), xyz=xyz)
+    return s, s.A(rho if rho is not None else 1.0 / n ** 2).tocsr()
+
+
+@pytest.mark.parametrize("n,jit", [(10, False), (9, True)])
+def test_red_black_is_the_greedy_maximal_independent_set(n, jit):
+    _, A = _A(n, jit=jit)
+    coarse = amg.red_black(A, seed=3)
+    prio = amg.priority(A.shape[0], 3)
+    for i in range(A.shape[0]):
+        nb = amg.neighbours(A, i)
+        if coarse[i]:
+            assert not coarse[nb].any()           # independent (no black pair)
+        else:
+            # red because a black neighbour was visited first (higher priority)
+            assert (coarse[nb] & (prio[nb] > prio[i])).any()
+
+
+def test_averaging_prolongator_reproduces_constants():
+    _, A = _A(10)
+    coarse = amg.red_black(A, seed=1)
+    P = amg.averaging_prolongator(A, coarse)
+    assert np.allclose(P @ np.ones(P.shape[1]), 1.0, rtol=0, atol=1e-15)
+    cid = np.cumsum(coarse) - 1
+    for i in range(A.shape[0]):
+        row = P.getrow(i)
+        if coarse[i]:
+            assert row.nnz == 1 and row.indices[0] == cid[i] and row.data[0] == 1.0
+        else:
+            nb = amg.neighbours(A, i)
+            cn = cid[nb[coarse[nb]]]
+            assert sorted(row.indices) == sorted(cn)
+            assert np.all(row.data == 1.0 / len(cn))
+
+
+@pytest.mark.parametrize("n", [9, 12])
+def test_greedy_colouring_is_proper_and_greedy(n):
+    _, A = _A(n)
+    col = amg.greedy_colouring(A, seed=2)
+    prio = amg.priority(A.shape[0], 2)
+    maxdeg = max(len(amg.neighbours(A, i)) for i in range(A.shape[0]))
+    assert col.max() <= maxdeg
+    for i in range(A.shape[0]):
+        nb = amg.neighbours(A, i)
+        assert not np.any(col[nb] == col[i])
+        earlier = set(col[nb[prio[nb] > prio[i]]].tolist())
+        c = 0
+        while c in earlier:
+            c += 1
+        assert col[i] == c
+
+
+def test_gauss_seidel_is_the_triangular_sweep():
+    # one colour per unknown in natural order: the forward sweep is x = (D + L)^{-1} b from
+    # x = 0, the backward sweep x = (D + U)^{-1} (b - L x)
+    _, A = _A(7, jit=True)
+    n = A.shape[0]
+    b = W.random_vector(n, 5)
+    colours = np.arange(n)
+    x = amg.gauss_seidel(A, b, None, colours, forward=True)
+    lower = sp.tril(A, format="csr")
+    assert np.allclose(x, spl.spsolve_triangular(lower, b, lower=True), rtol=1e-13, atol=0)
+    y = amg.gauss_seidel(A, b, x, colours, forward=False)
+    upper = sp.triu(A, format="csr")
+    rhs = b - sp.tril(A, k=-1, format="csr") @ x
+    assert np.allclose(y, spl.spsolve_triangular(upper, rhs, lower=False), rtol=1e-13, atol=0)
+    # a diagonal matrix is solved in one sweep
+    D = sp.diags(np.arange(1.0, 6.0)).tocsr()
+    assert np.array_equal(amg.gauss_seidel(D, np.ones(5), None, np.zeros(5, int), True),
+                          1.0 / np.arange(1.0, 6.0))
+
+
+@pytest.mark.parametrize("coarsening", ["kf", "sa"])
+def test_sgs_vcycle_is_symmetric_positive(coarsening):
+    # forward sweep down, backward sweep up: the V-cycle is a symmetric operator
+    _, A = _A(11)
+    o = {"coarsening": coarsening, "smoother": "sgs", "coarse_max": 40}
+    L = amg.build_hierarchy(A, o)
+    n = A.shape[0]
+    r1, r2 = W.random_vector(n, 1), W.random_vector(n, 2)
+    v1, v2 = amg.vcycle(L, r1, o), amg.vcycle(L, r2, o)
+    assert abs(v1 @ r2 - r1 @ v2) <= 1e-12 * abs(v1 @ r2)
+    assert v1 @ r1 > 0 and v2 @ r2 > 0
+
+
+def test_kf_hierarchy_is_galerkin_and_pcg_converges():
+    s, A = _A(12)
+    o = {"coarsening": "kf", "smoother": "sgs", "coarse_max": 64}
+    L = amg.build_hierarchy(A, o)
+    for lev in range(len(L) - 1):
+        P = L[lev].P
+        Ac = (P.T @ L[lev].A @ P).toarray()
+        assert np.allclose(L[lev + 1].A.toarray(), Ac, rtol=0, atol=1e-13 * np.abs(Ac).max())
+        assert L[lev + 1].A.shape[0] < 0.5 * L[lev].A.shape[0]
+    x, it, rr, _ = amg.pcg(A, s.f, lambda r: amg.vcycle(L, r, o), tol=1e-10)
+    ref = spl.spsolve(A.tocsc(), s.f)
+    assert rr <= 1e-10 and np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert it <= 15
