@@ -177,7 +177,21 @@ fem_status fem_recover(fem_system sys, const double* u_dev, const fem_target* ta
 
 /* ------------------------------------------------------------------ AMG */
 
-typedef enum { AMG_SMOOTHER_CHEBYSHEV = 0, AMG_SMOOTHER_L1_JACOBI = 1 } amg_smoother;
+/* Smoothers: Chebyshev of degree `degree` on D^{-1}A, one l1-Jacobi step, or symmetric
+ * Gauss-Seidel as in Sec. 3.1 (one forward sweep on the way down, one backward sweep on
+ * the way up), run class by class over a greedy colouring of the matrix graph (nodes
+ * visited by decreasing hash priority, each taking the smallest colour unused by its
+ * already coloured neighbours). */
+typedef enum {
+  AMG_SMOOTHER_CHEBYSHEV = 0,
+  AMG_SMOOTHER_L1_JACOBI = 1,
+  AMG_SMOOTHER_SGS = 2
+} amg_smoother;
+/* Coarsening: smoothed aggregation (default), or the paper's red-black colouring with
+ * averaging interpolation (Sec. 3.1 after KF1998: visit the unknowns by decreasing hash
+ * priority; an unmarked one becomes coarse and its unmarked matrix-graph neighbours fine;
+ * a fine unknown is interpolated by the average of its coarse neighbours). */
+typedef enum { AMG_COARSEN_SA = 0, AMG_COARSEN_RED_BLACK = 1 } amg_coarsening;
 typedef enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_BF16 = 2 } amg_precision;
 
 /* Smoothed-aggregation set-up on the device; Sec. 3.1 coarsens by red-black colouring
@@ -200,6 +214,7 @@ typedef struct {
   double rho_setup;      /* > 0: build the hierarchy from rho_setup K + M (needs the
                             pencil; the finest operator of solves is unchanged);
                             default 0 = the system's rho                        */
+  int32_t coarsening;    /* amg_coarsening, default smoothed aggregation         */
 } amg_opts;
 
 typedef struct amg_hier_s* amg_hier;
@@ -223,7 +238,9 @@ fem_status amg_hier_get_info(amg_hier h, amg_hier_info* info);
 
 /* Export level l (0 = finest): which = 0 A_l, 1 P_l, 2 R_l = P_l^T (CSR4, FP64 values;
  * sizes from amg_hier_get_info / the row counts of consecutive levels), which = 3 the
- * aggregate of each node of level l (int32 in col_dev, -1 = isolated; rowptr/val unused). */
+ * aggregate of each node of level l (int32 in col_dev, -1 = isolated; with red-black
+ * coarsening the coarse index of coarse nodes and -1 for fine ones; rowptr/val unused),
+ * which = 4 the Gauss-Seidel colour of each node (int32 in col_dev; SGS smoother only). */
 fem_status amg_hier_export(amg_hier h, int32_t level, int32_t which, int32_t* rowptr_dev,
                            int32_t* col_dev, double* val_dev, int64_t* nnz_out, void* stream);
 

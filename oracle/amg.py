@@ -471,7 +471,10 @@ def vcycle(levels, b, opts: dict | None = None, lev: int = 0):
     if L.coarsest:
         if L.Ainv is not None:
             return L.Ainv @ b
-        return smooth(L, b, None, o)
+        x = smooth(L, b, None, o, forward=True)
+        if o["smoother"] == "sgs":  # both sweeps meet here: keep the V-cycle symmetric
+            x = smooth(L, b, x, o, forward=False)
+        return x
     x = smooth(L, b, None, o, forward=True)
     r = b - L.A @ x
     xc = vcycle(levels, L.R @ r, o, lev + 1)

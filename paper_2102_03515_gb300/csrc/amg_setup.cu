@@ -1019,6 +1019,165 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
   return R;
 }
 
+// ------------------------------------------------------------------ red-black coarsening
+
+// The paper's coarsening (Sec. 3.1, after KF1998): visit the unknowns in a fixed order
+// (decreasing hash priority); an unmarked one becomes coarse and its unmarked matrix-graph
+// neighbours fine.  The greedy result is computed in rounds: an undecided node becomes
+// coarse when it has the largest key among itself and its neighbours (IN > UNDECIDED >
+// OUT, then priority) and fine when a neighbour is already coarse -- the same set as the
+// sequential visit.  Neighbours: columns j != i of stored nonzero a_ij.
+__global__ void k_rb_round(int64_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+                           uint32_t s, const uint8_t* state_in, uint8_t* state_out,
+                           unsigned long long* undecided) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const uint8_t st = state_in[r];
+  if (st != ST_UND) {
+    state_out[r] = st;
+    return;
+  }
+  const uint64_t key = ((uint64_t)ST_UND << 62) | prio_of(r, s);
+  uint64_t best = key;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    const int j = col[e];
+    if (j < 0 || j == r || val[e] == 0.0) continue;
+    const uint64_t kj = ((uint64_t)state_in[j] << 62) | prio_of(j, s);
+    best = kj > best ? kj : best;
+  }
+  uint8_t ns = ST_UND;
+  if (best == key)
+    ns = ST_IN;
+  else if ((best >> 62) == ST_IN)
+    ns = ST_OUT;
+  else
+    *undecided = 1ull;
+  state_out[r] = ns;
+}
+
+// Averaging interpolation: coarse i -> (cid(i), 1); fine i -> (cid(j), 1 / #C_i) for its
+// coarse neighbours j in column order (cid increases with j).  Count pass when Pcol is null.
+__global__ void k_rb_prolong(int64_t N, const int32_t* rowptr, const int32_t* col,
+                             const double* val, const uint8_t* state, const int64_t* cid,
+                             int64_t* cnt, const int32_t* Prp, int32_t* Pcol, double* Pval,
+                             unsigned long long* err) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  if (state[r] == ST_IN) {
+    if (!Pcol) {
+      cnt[r] = 1;
+      return;
+    }
+    int64_t o = Prp[r];
+    Pcol[o] = (int32_t)cid[r];
+    Pval[o++] = 1.0;
+    for (; o < Prp[r + 1]; o++) {
+      Pcol[o] = -1;
+      Pval[o] = 0.0;
+    }
+    return;
+  }
+  int c = 0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    const int j = col[e];
+    if (j >= 0 && j != r && val[e] != 0.0 && state[j] == ST_IN) c++;
+  }
+  if (!Pcol) {
+    if (c == 0) atomicAdd(err, 1ull);
+    cnt[r] = c;
+    return;
+  }
+  const double w = 1.0 / (double)c;
+  int64_t o = Prp[r];
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    const int j = col[e];
+    if (j >= 0 && j != r && val[e] != 0.0 && state[j] == ST_IN) {
+      Pcol[o] = (int32_t)cid[j];
+      Pval[o++] = w;
+    }
+  }
+  for (; o < Prp[r + 1]; o++) {
+    Pcol[o] = -1;
+    Pval[o] = 0.0;
+  }
+}
+
+__global__ void k_rb_cid(int64_t N, const uint8_t* state, const int64_t* cid, int32_t* out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N) out[r] = state[r] == ST_IN ? (int32_t)cid[r] : -1;
+}
+
+// ------------------------------------------------------------------ greedy colouring
+
+// Colour of each node: the smallest colour not used by its higher-priority neighbours,
+// assigned once all of them are coloured (the same colouring as a sequential visit by
+// decreasing priority).  In place: a colour never changes once written.
+constexpr int kMaxColours = 256;
+__global__ void k_colour_round(int64_t N, const int32_t* rowptr, const int32_t* col,
+                               const double* val, uint32_t s, int32_t* colour,
+                               unsigned long long* pending, unsigned long long* overflow) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N || colour[r] >= 0) return;
+  const uint64_t pr = prio_of(r, s);
+  uint64_t used[kMaxColours / 64] = {0, 0, 0, 0};
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    const int j = col[e];
+    if (j < 0 || j == r || val[e] == 0.0) continue;
+    if (prio_of(j, s) < pr) continue;
+    const int cj = ((volatile int32_t*)colour)[j];
+    if (cj < 0) {
+      *pending = 1ull;
+      return;
+    }
+    used[cj >> 6] |= 1ull << (cj & 63);
+  }
+  int c = 0;
+  while (c < kMaxColours && ((used[c >> 6] >> (c & 63)) & 1ull)) c++;
+  if (c == kMaxColours) {
+    atomicAdd(overflow, 1ull);
+    c = kMaxColours - 1;
+  }
+  colour[r] = c;
+}
+
+// per-colour counts (block histograms in shared memory, one atomic per colour per block)
+__global__ void k_colour_count(int64_t N, const int32_t* colour, unsigned long long* cnt) {
+  __shared__ unsigned int h[kMaxColours];
+  for (int c = threadIdx.x; c < kMaxColours; c += blockDim.x) h[c] = 0;
+  __syncthreads();
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[colour[r]], 1u);
+  __syncthreads();
+  for (int c = threadIdx.x; c < kMaxColours; c += blockDim.x)
+    if (h[c]) atomicAdd(&cnt[c], (unsigned long long)h[c]);
+}
+
+// node lists per colour: each block reserves a range per colour, then fills it (the order
+// inside a colour is irrelevant: its nodes do not couple)
+__global__ void k_colour_scatter(int64_t N, const int32_t* colour, unsigned long long* cursor,
+                                 int32_t* nodes) {
+  __shared__ unsigned int h[kMaxColours];
+  __shared__ unsigned long long base[kMaxColours];
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < N; r0 += (int64_t)gridDim.x * blockDim.x) {
+    for (int c = threadIdx.x; c < kMaxColours; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    const int64_t r = r0 + threadIdx.x;
+    unsigned int slot = 0;
+    int c = -1;
+    if (r < N) {
+      c = colour[r];
+      slot = atomicAdd(&h[c], 1u);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kMaxColours; q += blockDim.x)
+      if (h[q]) base[q] = atomicAdd(&cursor[q], (unsigned long long)h[q]);
+    __syncthreads();
+    if (r < N) nodes[base[c] + slot] = (int32_t)r;
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ uniform-grid level
 
 // On the finest level of a uniform Kuhn grid every row of A holds the same values at the
@@ -1390,6 +1549,93 @@ void psmooth_stencil(int64_t N, const StencilRow& S, const int32_t* agg, double 
   FEM_ST_DISPATCH(S.strong, psmooth_stencil_t, N, S, agg, dinv, omega, P, nagg, st);
 }
 
+// Red-black split of a level: state (IN = coarse), coarse ids cid (exclusive scan of the
+// coarse flags); returns the number of coarse nodes.
+int64_t red_black_split(const Csr4& A, uint32_t s, DevBuf<uint8_t>& state, DevBuf<int64_t>& cid,
+                        cudaStream_t st) {
+  const int64_t N = A.nrows;
+  const unsigned g = grid_for(N, 256);
+  DevBuf<uint8_t> s0(N, st), s1(N, st);
+  DevBuf<unsigned long long> und(1, st);
+  FEM_CUDA(cudaMemsetAsync(s0, ST_UND, N, st));
+  uint8_t* cur = s0;
+  uint8_t* nxt = s1;
+  bool finished = false;
+  for (int round = 0; round < 100000; round++) {
+    FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+    for (int t = 0; t < 4; t++) {  // several rounds per check (extra rounds are no-ops)
+      if (t == 3) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+      k_rb_round<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, s, cur, nxt, und);
+      FEM_CHECK_LAUNCH();
+      std::swap(cur, nxt);
+    }
+    unsigned long long hu = 0;
+    FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    if (hu == 0) {
+      finished = true;
+      break;
+    }
+  }
+  FEM_REQUIRE(finished, FEM_EDEVCHECK, "red-black coarsening did not terminate");
+  state.alloc(N);
+  FEM_CUDA(cudaMemcpyAsync(state, cur, N, cudaMemcpyDeviceToDevice, st));
+  DevBuf<int64_t> flag(N, st);
+  k_root_flags<<<g, 256, 0, st>>>(N, state, flag);
+  FEM_CHECK_LAUNCH();
+  cid.alloc(N + 1);
+  return exclusive_scan(flag, N, cid, st);
+}
+
+// Greedy colouring of a level's matrix graph and the node lists per colour.
+void colour_level(Level& Lv, const Csr4& A, uint32_t s, cudaStream_t st) {
+  const int64_t N = A.nrows;
+  const unsigned g = grid_for(N, 256);
+  Lv.colour.alloc(N);
+  FEM_CUDA(cudaMemsetAsync(Lv.colour, 0xff, 4 * N, st));
+  DevBuf<unsigned long long> flags(2, st);
+  FEM_CUDA(cudaMemsetAsync(flags.p + 1, 0, 8, st));
+  bool finished = false;
+  for (int round = 0; round < 100000; round++) {
+    FEM_CUDA(cudaMemsetAsync(flags, 0, 8, st));
+    for (int t = 0; t < 4; t++) {
+      if (t == 3) FEM_CUDA(cudaMemsetAsync(flags, 0, 8, st));
+      k_colour_round<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, s, Lv.colour, flags,
+                                        flags.p + 1);
+      FEM_CHECK_LAUNCH();
+    }
+    unsigned long long hf[2] = {0, 0};
+    FEM_CUDA(cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    FEM_REQUIRE(hf[1] == 0, FEM_EUNSUPPORTED, "colouring: more than 256 colours");
+    if (hf[0] == 0) {
+      finished = true;
+      break;
+    }
+  }
+  FEM_REQUIRE(finished, FEM_EDEVCHECK, "colouring did not terminate");
+  DevBuf<unsigned long long> cnt(kMaxColours, st), cursor(kMaxColours, st);
+  FEM_CUDA(cudaMemsetAsync(cnt, 0, 8 * kMaxColours, st));
+  const unsigned gp = persistent_grid(N, 256, 4);
+  k_colour_count<<<gp, 256, 0, st>>>(N, Lv.colour, cnt);
+  FEM_CHECK_LAUNCH();
+  std::vector<unsigned long long> hc(kMaxColours);
+  FEM_CUDA(cudaMemcpyAsync(hc.data(), cnt, 8 * kMaxColours, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  int ncol = 0;
+  for (int c = 0; c < kMaxColours; c++)
+    if (hc[c]) ncol = c + 1;
+  Lv.coff.assign(ncol + 1, 0);
+  for (int c = 0; c < ncol; c++) Lv.coff[c + 1] = Lv.coff[c] + (int64_t)hc[c];
+  std::vector<unsigned long long> hcur(kMaxColours, 0);
+  for (int c = 0; c < ncol; c++) hcur[c] = (unsigned long long)Lv.coff[c];
+  FEM_CUDA(cudaMemcpyAsync(cursor, hcur.data(), 8 * kMaxColours, cudaMemcpyHostToDevice, st));
+  Lv.cnodes.alloc(N > 0 ? N : 1);
+  k_colour_scatter<<<gp, 256, 0, st>>>(N, Lv.colour, cursor, Lv.cnodes);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
 void make_lowp(Csr4& A, int prec, cudaStream_t st) {
   if (prec == AMG_PREC_FP32 || prec == AMG_PREC_BF16) {
     A.val32.alloc(A.nnz);
@@ -1446,7 +1692,9 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     unsigned g = grid_for(N, 256);
     // uniform finest level: graph, bounds and prolongator from the stencil
     StencilRow SR;
-    const bool st0 = lev == 0 && Lv.stencil && o.smoother == AMG_SMOOTHER_CHEBYSHEV &&
+    const bool rb = o.coarsening == AMG_COARSEN_RED_BLACK;
+    const uint32_t seed_s = (uint32_t)(0x9E3779B9u * (uint32_t)(o.seed + lev + 1));
+    const bool st0 = lev == 0 && Lv.stencil && o.smoother == AMG_SMOOTHER_CHEBYSHEV && !rb &&
                      N > o.coarse_max && stencil_row(*Acur, Lv.st.m, o.theta, SR, st);
     DevBuf<double> d(N, st);
     if (st0)
@@ -1470,18 +1718,26 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     FEM_CHECK_LAUNCH();
     if (lowp) {
       Csr4& Am = (lev == 0 && Lv.A == &S.A) ? S.A : Lv.Aown;
-      if (!(lev == 0 && Lv.stencil)) {
+      if (!(lev == 0 && Lv.stencil) || o.smoother == AMG_SMOOTHER_SGS) {
         if (!Am.val32.p) make_lowp(Am, AMG_PREC_FP32, st);
         if (prec == AMG_PREC_BF16 && !Am.val16.p) make_lowp(Am, AMG_PREC_BF16, st);
       }
     }
 
     tr.mark("level: diagonal, lambda, low precision");
+    if (o.smoother == AMG_SMOOTHER_SGS) {
+      colour_level(Lv, *Acur, seed_s, st);
+      tr.mark("level: colouring");
+    }
     bool last = (N <= o.coarse_max) || (lev == o.max_levels - 1);
     Aggregation ag;
+    DevBuf<uint8_t> rbstate;
+    DevBuf<int64_t> rbcid;
     if (!last) {
-      uint32_t s = (uint32_t)(0x9E3779B9u * (uint32_t)(o.seed + lev + 1));
-      ag = st0 ? aggregate_stencil(N, SR, s, st) : aggregate(*Acur, d, o.theta, s, st);
+      if (rb)
+        ag.nagg = red_black_split(*Acur, seed_s, rbstate, rbcid, st);
+      else
+        ag = st0 ? aggregate_stencil(N, SR, seed_s, st) : aggregate(*Acur, d, o.theta, seed_s, st);
       tr.mark("level: aggregation");
       if (ag.nagg == 0 || (double)ag.nagg >= 0.9 * (double)N) last = true;
     }
@@ -1492,12 +1748,37 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       H.L.push_back(std::move(cur));
       break;
     }
-    // smoothed prolongator P = P_t - omega D^{-1} A_F P_t
-    Lv.agg = std::move(ag.agg);
-    const double lamF = st0 ? stencil_rowabs(SR, true)
-                            : rowabs_max(*Acur, Acur->val, ag.smask, d, nullptr, st);
-    const double omega = 4.0 / (3.0 * lamF);
     bool done_p = false;
+    if (rb) {
+      // averaging interpolation of the red-black split (Sec. 3.1)
+      DevBuf<int64_t> pc(N, st);
+      DevBuf<unsigned long long> err(1, st);
+      FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+      k_rb_prolong<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, rbstate, rbcid, pc,
+                                      nullptr, nullptr, nullptr, err);
+      FEM_CHECK_LAUNCH();
+      Lv.P.nrows = (int32_t)N;
+      Lv.P.ncols = (int32_t)ag.nagg;
+      rowptr_from_counts(pc, N, Lv.P, st);
+      Lv.P.val.alloc(Lv.P.nnz);
+      k_rb_prolong<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, rbstate, rbcid,
+                                      nullptr, Lv.P.rowptr, Lv.P.col, Lv.P.val, err);
+      FEM_CHECK_LAUNCH();
+      Lv.agg.alloc(N);
+      k_rb_cid<<<g, 256, 0, st>>>(N, rbstate, rbcid, Lv.agg);
+      FEM_CHECK_LAUNCH();
+      unsigned long long he = 0;
+      FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+      FEM_CUDA(cudaStreamSynchronize(st));
+      FEM_REQUIRE(he == 0, FEM_EDEVCHECK, "red-black: a fine node without a coarse neighbour");
+      done_p = true;
+    }
+    // smoothed prolongator P = P_t - omega D^{-1} A_F P_t
+    if (!rb) Lv.agg = std::move(ag.agg);
+    const double lamF = rb ? 0.0
+                           : (st0 ? stencil_rowabs(SR, true)
+                                  : rowabs_max(*Acur, Acur->val, ag.smask, d, nullptr, st));
+    const double omega = rb ? 0.0 : 4.0 / (3.0 * lamF);
     if (st0) {
       psmooth_stencil(N, SR, Lv.agg, 1.0 / SR.a[ST_DIAG], omega, Lv.P, ag.nagg, st);
       done_p = true;

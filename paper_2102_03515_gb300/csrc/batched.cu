@@ -1269,6 +1269,8 @@ BatchSession* batch_create(System& S, Hierarchy& H, int slots, const pcg_opts& o
               "pcg_batch_create: the system must keep its pencil (keep_pencil at assembly)");
   FEM_REQUIRE(H.o.degree <= 2 || H.o.smoother == AMG_SMOOTHER_L1_JACOBI, FEM_EUNSUPPORTED,
               "pcg_batch_create: Chebyshev degree <= 2 in batched solves");
+  FEM_REQUIRE(H.o.smoother != AMG_SMOOTHER_SGS, FEM_EUNSUPPORTED,
+              "pcg_batch_create: batched solves smooth with Chebyshev or l1-Jacobi");
   auto W = std::make_unique<BatchSession>();
   W->S = &S;
   W->H = &H;

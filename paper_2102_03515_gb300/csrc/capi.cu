@@ -246,6 +246,7 @@ void amg_default_opts(amg_opts* o) {
   o->precision = AMG_PREC_FP64;
   o->seed = 0;
   o->rho_setup = 0.0;
+  o->coarsening = AMG_COARSEN_SA;
 }
 
 fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hier* out) {
@@ -264,7 +265,9 @@ fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hie
     FEM_REQUIRE(o.max_levels >= 1 && o.max_levels <= 32, FEM_EINVAL,
                 "amg_setup: max_levels in [1, 32]");
     FEM_REQUIRE(o.precision >= 0 && o.precision <= 2, FEM_EINVAL, "amg_setup: bad precision");
-    FEM_REQUIRE(o.smoother == 0 || o.smoother == 1, FEM_EINVAL, "amg_setup: bad smoother");
+    FEM_REQUIRE(o.smoother >= 0 && o.smoother <= 2, FEM_EINVAL, "amg_setup: bad smoother");
+    FEM_REQUIRE(o.coarsening == AMG_COARSEN_SA || o.coarsening == AMG_COARSEN_RED_BLACK,
+                FEM_EINVAL, "amg_setup: bad coarsening");
     FEM_REQUIRE(o.rho_setup >= 0.0 && std::isfinite(o.rho_setup), FEM_EINVAL,
                 "amg_setup: rho_setup >= 0");
     FEM_REQUIRE(o.rho_setup == 0.0 || sys->S.pencil, FEM_EINVAL,
@@ -318,6 +321,14 @@ fem_status amg_hier_export(amg_hier h, int32_t level, int32_t which, int32_t* ro
     FEM_REQUIRE(level >= 0 && level < (int)h->H.L.size(), FEM_EINVAL, "amg_hier_export: bad level");
     Level& L = *h->H.L[level];
     cudaStream_t st = as_stream(stream);
+    if (which == 4) {
+      FEM_REQUIRE(L.colour.p, FEM_EINVAL, "amg_hier_export: no colouring (SGS smoother only)");
+      if (nnz_out) *nnz_out = L.N;
+      if (col_dev)
+        FEM_CUDA(cudaMemcpyAsync(col_dev, L.colour, 4 * L.N, cudaMemcpyDeviceToDevice, st));
+      FEM_CUDA(cudaStreamSynchronize(st));
+      return FEM_OK;
+    }
     if (which == 3) {
       FEM_REQUIRE(!L.coarsest, FEM_EINVAL, "amg_hier_export: the coarsest level has no aggregates");
       if (nnz_out) *nnz_out = L.N;
@@ -331,7 +342,7 @@ fem_status amg_hier_export(amg_hier h, int32_t level, int32_t which, int32_t* ro
       FEM_REQUIRE(!L.coarsest, FEM_EINVAL, "amg_hier_export: the coarsest level has no P/R");
       M = which == 1 ? &L.P : &L.R;
     }
-    FEM_REQUIRE(M, FEM_EINVAL, "amg_hier_export: which must be 0..3");
+    FEM_REQUIRE(M, FEM_EINVAL, "amg_hier_export: which must be 0..4");
     if (nnz_out) *nnz_out = M->nnz;
     if (rowptr_dev)
       FEM_CUDA(cudaMemcpyAsync(rowptr_dev, M->rowptr, 4 * ((int64_t)M->nrows + 1),

@@ -783,6 +783,71 @@ template void smooth_post<float>(const Level&, int, const amg_opts&, const ChebC
                                  const float*, float*, float*, float*, float*, cudaStream_t,
                                  const DotOut*);
 
+// ------------------------------------------------------------------ Gauss-Seidel
+
+namespace {
+
+__device__ __forceinline__ double val_of(double v) { return v; }
+__device__ __forceinline__ float val_of(float v) { return v; }
+__device__ __forceinline__ float val_of(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii for the nodes of one colour class (thread per
+// node, the row's entries in column order; FP64 without contraction, as in the oracle).
+template <typename VT, typename T>
+__global__ void k_gs(int64_t cnt, const int32_t* __restrict__ nodes,
+                     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                     const VT* __restrict__ val, const T* __restrict__ b, T* x, const int* done) {
+  using AT = typename Arith<T>::type;
+  if (done && *done) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int i = nodes[t];
+  AT sum = (AT)0, dg = (AT)0;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; e++) {
+    const int j = col[e];
+    if (j < 0) continue;
+    const AT a = (AT)val_of(val[e]);
+    if (j == i) {
+      dg = a;
+    } else if (sizeof(AT) == 8) {
+      sum = (AT)__dadd_rn((double)sum, __dmul_rn((double)a, (double)x[j]));
+    } else {
+      sum += a * (AT)x[j];
+    }
+  }
+  x[i] = (T)(((AT)b[i] - sum) / dg);
+}
+
+template <typename VT, typename T>
+void gs_launch(const Level& Lv, const VT* val, const T* b, T* x, bool forward, cudaStream_t st) {
+  const int ncol = (int)Lv.coff.size() - 1;
+  for (int q = 0; q < ncol; q++) {
+    const int c = forward ? q : ncol - 1 - q;
+    const int64_t c0 = Lv.coff[c], cnt = Lv.coff[c + 1] - c0;
+    if (cnt == 0) continue;
+    k_gs<VT, T><<<grid_for(cnt, 256), 256, 0, st>>>(cnt, Lv.cnodes.p + c0, Lv.A->rowptr,
+                                                    Lv.A->col, val, b, x, Lv.done);
+    FEM_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace
+
+template <>
+void gs_sweep<double>(const Level& Lv, int prec, const double* b, double* x, bool forward,
+                      cudaStream_t st) {
+  (void)prec;
+  gs_launch<double, double>(Lv, Lv.A->val.p, b, x, forward, st);
+}
+template <>
+void gs_sweep<float>(const Level& Lv, int prec, const float* b, float* x, bool forward,
+                     cudaStream_t st) {
+  if (prec == AMG_PREC_BF16 && Lv.A->val16.p)
+    gs_launch<__nv_bfloat16, float>(Lv, Lv.A->val16.p, b, x, forward, st);
+  else
+    gs_launch<float, float>(Lv, Lv.A->val32.p, b, x, forward, st);
+}
+
 // ------------------------------------------------------------------ launch-shape tuning
 
 namespace {

@@ -59,6 +59,18 @@ __global__ void k_out_dots(int64_t N, const T* x, double* z64, const double* r1,
   }
 }
 
+// Start of the Gauss-Seidel pre-smoothing: x = 0 (and b from its FP64 form at the finest
+// level of a low-precision hierarchy).
+template <typename T>
+__global__ void k_sgs_start(int64_t N, const double* __restrict__ b64, T* b, T* x, const int* done) {
+  if (done && *done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (b64) b[i] = (T)b64[i];
+    x[i] = (T)0;
+  }
+}
+
 template <typename T>
 struct Bufs;
 template <>
@@ -88,6 +100,40 @@ ChebCoef level_cheb(const Level& L, const amg_opts& o) {
   return cheb_coefficients(L.lmax, o.cheb_ratio, o.degree);
 }
 
+template <typename T>
+void vc(Hierarchy& H, int lev, const T* b, T* x, const double* b64, const DotOut* dot,
+        cudaStream_t st);
+
+// V-cycle with symmetric Gauss-Seidel (Sec. 3.1): one forward sweep from x = 0 on the way
+// down, one backward sweep on the way up (both at a coarsest level without a dense
+// inverse), so that the preconditioner is symmetric.
+template <typename T>
+void vc_sgs(Hierarchy& H, int lev, const T* b, T* x, const double* b64, const DotOut* dot,
+            cudaStream_t st) {
+  Level& L = *H.L[lev];
+  const int prec = H.o.precision;
+  const int64_t N = L.N;
+  T* bb = const_cast<T*>(b);
+  k_sgs_start<T><<<persistent_grid(N, 256, 8), 256, 0, st>>>(N, b64, bb, x, L.done);
+  FEM_CHECK_LAUNCH();
+  gs_sweep<T>(L, prec, b, x, true, st);
+  if (!L.coarsest) {
+    T* r = Bufs<T>::r(L);
+    op_residual<T>(L, prec, b, x, r, st);
+    Level& C = *H.L[lev + 1];
+    csr_spmv<T>(L.R, prec, r, Bufs<T>::b(C), false, st, L.done);
+    vc<T>(H, lev + 1, Bufs<T>::b(C), Bufs<T>::x(C), nullptr, nullptr, st);
+    csr_spmv<T>(L.P, prec, Bufs<T>::x(C), x, true, st, L.done);
+  }
+  gs_sweep<T>(L, prec, b, x, false, st);
+  if (dot) {
+    unsigned g = persistent_grid(N, 256, 8);
+    k_out_dots<T><<<g, 256, 0, st>>>(N, x, dot->z64, dot->r1, dot->r2, dot->partials, g, L.done);
+    FEM_CHECK_LAUNCH();
+    if (dot->nblocks) *dot->nblocks = (int)g;
+  }
+}
+
 // One V-cycle on levels lev.. with right-hand side b (or b64 at the finest FP32 level) and
 // output x.  dot (finest level only) makes the last kernel emit z in FP64 with dot products.
 template <typename T>
@@ -97,6 +143,10 @@ void vc(Hierarchy& H, int lev, const T* b, T* x, const double* b64, const DotOut
   const int prec = H.o.precision;
   const amg_opts& o = H.o;
   const int64_t N = L.N;
+  if (o.smoother == AMG_SMOOTHER_SGS && !(L.coarsest && L.Ainv.p)) {
+    vc_sgs<T>(H, lev, b, x, b64, dot, st);
+    return;
+  }
   if (L.coarsest) {
     if (L.Ainv.p) {
       unsigned g = grid_for(N * 32, 256);

@@ -42,7 +42,11 @@ struct Level {
   Csr4 Aown;                 // coarse levels own their matrix
   const Csr4* A = nullptr;   // level matrix (the system's for level 0)
   Csr4 P, R;                 // N x Nc and Nc x N
-  DevBuf<int32_t> agg;       // aggregate of each node (-1 isolated)
+  DevBuf<int32_t> agg;       // aggregate of each node (-1 isolated); red-black: coarse id
+                             // of coarse nodes, -1 for fine ones
+  DevBuf<int32_t> colour;    // Gauss-Seidel colour of each node (SGS smoother)
+  DevBuf<int32_t> cnodes;    // nodes grouped by colour
+  std::vector<int64_t> coff; // colour c owns cnodes[coff[c] .. coff[c+1])
   DevBuf<double> dinv;       // 1 / a_ii
   DevBuf<float> dinv32;
   double lmax = 0;           // Gershgorin bound of D^-1 A
@@ -106,6 +110,11 @@ void op_residual(const Level& Lv, int prec, const T* b, const T* x, T* r, cudaSt
 template <typename T>
 void csr_spmv(const Csr4& M, int prec, const T* x, T* y, bool accumulate, cudaStream_t st,
               const int* done = nullptr);
+
+// One Gauss-Seidel sweep over the colour classes (increasing order when forward):
+// x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii.
+template <typename T>
+void gs_sweep(const Level& Lv, int prec, const T* b, T* x, bool forward, cudaStream_t st);
 
 // Smoother pieces used by the V-cycle.
 template <typename T>
