@@ -46,6 +46,42 @@ def _env_int(name, default):
         return default
 
 
+def _measured_hbm_gbs() -> float:
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except Exception:
+        return 6800.0   # the profiling recipe's fallback copy rate
+
+
+def vcycle_bytes(info: dict, flexible_r2: bool = False) -> float:
+    """Algorithmic bytes of one FP32 V-cycle (Chebyshev degree 2, matrix-free finest level,
+    FP32 CSR4 values on coarser levels, every vector access counted once): finest level
+    24 (start from the FP64 residual) + 24 (Chebyshev step) + 12 (residual) + 16 (post start)
+    + 40 (last step: x, r, d, FP64 z and <z, r>; + 8 with <z, r_prev>) bytes per row; a CSR
+    level 104 bytes of vectors per row and four passes over its matrix (8 bytes per stored
+    entry + 4 per row); R_l and P_l one pass each plus their vectors; the coarsest dense
+    inverse N^2 x 8 bytes."""
+    L = info["levels"]
+    rows, nnz, pnnz, rnnz = info["rows"], info["nnz"], info["pnnz"], info["rnnz"]
+    total = 0.0
+    for lev in range(L):
+        N = rows[lev]
+        coarsest = lev == L - 1
+        if coarsest:
+            total += 8.0 * N * N + 12.0 * N
+            continue
+        if lev == 0 and info["finest_stencil"]:
+            total += (116.0 + (8.0 if flexible_r2 else 0.0)) * N
+        else:
+            total += 104.0 * N + 4 * (8.0 * nnz[lev] + 4.0 * N)
+        Nc = rows[lev + 1]
+        total += 8.0 * rnnz[lev] + 4.0 * Nc + 4.0 * N + 4.0 * Nc      # restriction
+        total += 8.0 * pnnz[lev] + 4.0 * N + 8.0 * N + 4.0 * Nc       # prolongation
+    return total
+
+
 def oracle_sample(n: int) -> dict:
     """Run the oracle's full path (assemble, SA hierarchy, AMG-PCG to 1e-8) at n^3."""
     import numpy as np  # noqa: F401
@@ -264,6 +300,44 @@ def table4_sample(fa, torch, dev, n: int):
     return {"h": 1.0 / n, "precision": "FP32 V-cycle, FP64 CG", "rows": rows}
 
 
+def general_mesh_sample(fa, torch, dev, n: int = 32, refine: int = 2):
+    """An unstructured mesh through fem_assemble_mesh: the unit cube split into 5 tets per cube
+    (n^3 cubes), refined `refine` times by Bey's red refinement; FP32 V-cycle in FP64 flexible
+    CG to 1e-8 at rho = h^2 of the refined mesh (h = 1 / (n 2^refine))."""
+    import fem_workloads as W
+    mesh = W.five_tet_mesh(n)
+    for _ in range(refine):
+        mesh = W.bey_refine(*mesh)
+    xyz, tets, d = mesh
+    h = 1.0 / (n * 2 ** refine)
+    rho = h * h
+    out = {}
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sys_ = fa.fem_assemble_mesh(xyz, tets, d, rho, W.sine_target())
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        hh = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32)
+        info = fa.fem_system_get_info(sys_)
+        u = torch.zeros(info["N"], dtype=torch.float64, device=dev)
+        res = fa.pcg_solve(sys_, hh, None, u, tol=1e-8, flexible=1)[0]
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        hinfo = fa.amg_hier_get_info(hh)
+        fa.amg_hier_destroy(hh)
+        fa.fem_system_destroy(sys_)
+        out = {"workload": "five-tet cube mesh, n = %d, %d Bey refinements: %d tets, %d unknowns, "
+                           "rho = h^2, sine target, FP32 V-cycle, tol 1e-8" % (n, refine, len(tets),
+                                                                              info["N"]),
+               "value": info["N"] * res["iterations"] / (t2 - t0), "unit": "dof-iters/s",
+               "assemble_ms": (t1 - t0) * 1e3, "setup_ms": hinfo["setup_ms"],
+               "solve_ms": res["solve_ms"], "total_ms": (t2 - t0) * 1e3,
+               "iterations": res["iterations"], "relres": res["relres"],
+               "nnz_per_row": info["nnz"] / info["N"]}
+    return out
+
+
 def serving_sample(count: int, sizes=(32, 64, 96, 128, 192)):
     """Poisson stream of solve requests through the continuous-batching service."""
     import fem_workloads as W
@@ -425,10 +499,38 @@ def run_ours(args, rank: int, world: int):
     flops = 2.0 * real_nnz
     achieved = flops / (kms * 1e-3) / 1e12
 
-    batched = serving = tables = table4 = None
+    # ---- the V-cycle as a whole against the HBM roofline (FP32 hierarchy, warm, in situ)
+    sys_ = fa.fem_assemble(n, rho, target)
+    hv = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32)
+    vinfo = fa.amg_hier_get_info(hv)
+    rv = torch.randn(N, dtype=torch.float64, device=dev)
+    zv = torch.empty_like(rv)
+    for _ in range(3):
+        fa.amg_vcycle(hv, rv, zv)
+    v0 = torch.cuda.Event(enable_timing=True)
+    v1 = torch.cuda.Event(enable_timing=True)
+    vreps = 20
+    v0.record(stream)
+    for _ in range(vreps):
+        fa.amg_vcycle(hv, rv, zv)
+    v1.record(stream)
+    torch.cuda.synchronize()
+    vms = v0.elapsed_time(v1) / vreps
+    fa.amg_hier_destroy(hv)
+    fa.fem_system_destroy(sys_)
+    vbytes = vcycle_bytes(vinfo)
+    hbm = _measured_hbm_gbs()
+    vcycle_roof = {"bound": "hbm", "achieved": vbytes / (vms * 1e-3) / 1e9, "peak": hbm,
+                   "unit": "GB/s", "frac": vbytes / (vms * 1e-3) / 1e9 / hbm, "traffic": None,
+                   "kernel": "one FP32 V-cycle (all levels, amg_vcycle; host synchronisation "
+                             "per call included)",
+                   "ms": vms, "algorithmic_bytes": vbytes, "peak_source": "measured copy rate"}
+
+    batched = serving = tables = table4 = general = None
     if not args.no_extras:
         tables = paper_tables_sample(fa, torch, dev, n)
         table4 = table4_sample(fa, torch, dev, n)
+        general = general_mesh_sample(fa, torch, dev)
         batched = batched_sample(fa, torch, dev)
         serving = serving_sample(args.serve_requests)
 
@@ -473,6 +575,7 @@ def run_ours(args, rank: int, world: int):
                      "kernel_ms": kms, "flops_per_launch": flops,
                      "peak_source": "FP64 unit counts x max SM clock (no FP64 entry in the "
                                     "measured peaks)"},
+        "roofline_vcycle": vcycle_roof,
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
@@ -480,6 +583,8 @@ def run_ours(args, rank: int, world: int):
         line["paper_tables"] = tables
     if table4 is not None:
         line["paper_table4"] = table4
+    if general is not None:
+        line["general_mesh"] = general
     if batched is not None:
         line["batched"] = batched
     if serving is not None:

@@ -95,3 +95,117 @@ def random_vector(N: int, seed: int, nrhs: int = 1) -> np.ndarray:
     rng = np.random.default_rng(seed)
     v = rng.standard_normal(size=(N, nrhs) if nrhs > 1 else N)
     return np.ascontiguousarray(v)
+
+
+# ------------------------------------------------------------------ general tetrahedral meshes
+#
+# A mesh is (xyz [nv, 3], tets [nt, 4] vertex indices, dirichlet [nv] uint8 flags marking the
+# vertices on the boundary of the unit cube).  These generators only lay out vertices and
+# connectivity; element arithmetic is left to the oracle and the library.
+
+def _cube_vertex(n: int, i, j, k):
+    return i + (n + 1) * (j + (n + 1) * k)
+
+
+def _cube_boundary(xyz: np.ndarray) -> np.ndarray:
+    on = (xyz == 0.0) | (xyz == 1.0)
+    return on.any(axis=1).astype(np.uint8)
+
+
+def kuhn_mesh(n: int, xyz: np.ndarray | None = None):
+    """The Kuhn mesh as a general mesh: cube (i, j, k) (i fastest) is split into the 6 tets of
+    the paths 0 -> e_a -> e_a + e_b -> (1,1,1), permutations (a, b, c) in lexicographic order;
+    tet 6 c + p is path p of cube c."""
+    if xyz is None:
+        xyz = uniform_xyz(n)
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    c = np.arange(n ** 3)
+    ci, cj, ck = c % n, (c // n) % n, c // (n * n)
+    tets = np.empty((n ** 3, 6, 4), dtype=np.int32)
+    for p, perm in enumerate(perms):
+        off = np.zeros((n ** 3, 3), dtype=np.int64)
+        tets[:, p, 0] = _cube_vertex(n, ci, cj, ck)
+        for s, ax in enumerate(perm):
+            off[:, ax] += 1
+            tets[:, p, s + 1] = _cube_vertex(n, ci + off[:, 0], cj + off[:, 1], ck + off[:, 2])
+    grid = uniform_xyz(n)
+    return np.array(xyz, dtype=np.float64), tets.reshape(-1, 4), _cube_boundary(grid)
+
+
+def five_tet_mesh(n: int):
+    """Each cube split into 5 tets: 4 corner tets around a central one, the split alternating
+    with the parity of i + j + k so that neighbouring cubes share their face diagonals."""
+    xyz = uniform_xyz(n)
+    tets = []
+    corner_sets = {0: [(0, 1, 2, 4), (3, 1, 2, 7), (5, 1, 4, 7), (6, 2, 4, 7), (1, 2, 4, 7)],
+                   1: [(1, 0, 3, 5), (2, 0, 3, 6), (4, 0, 5, 6), (7, 3, 5, 6), (0, 3, 5, 6)]}
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                cv = [_cube_vertex(n, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))
+                      for a in range(8)]
+                for tset in corner_sets[(i + j + k) & 1]:
+                    tets.append([cv[a] for a in tset])
+    return xyz, np.array(tets, dtype=np.int32), _cube_boundary(xyz)
+
+
+def bey_refine(xyz: np.ndarray, tets: np.ndarray, dirichlet: np.ndarray):
+    """One round of Bey's red refinement: every tet into 8 (4 corner tets and 4 tets of the
+    inner octahedron cut along the diagonal between the midpoints of edges 02 and 13).  An
+    edge midpoint is a Dirichlet vertex when the edge lies on a boundary face (a face of one
+    tet only) whose three vertices are Dirichlet vertices."""
+    tets = np.asarray(tets, dtype=np.int64)
+    nv = len(xyz)
+    pairs = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    e = np.stack([np.sort(tets[:, list(p)], axis=1) for p in pairs], axis=1)   # [nt, 6, 2]
+    keys = e[:, :, 0] * nv + e[:, :, 1]
+    uk, inv = np.unique(keys.ravel(), return_inverse=True)
+    mid = nv + inv.reshape(-1, 6)
+    a, b = uk // nv, uk % nv
+    new_xyz = np.concatenate([xyz, 0.5 * (xyz[a] + xyz[b])])
+    # boundary faces
+    faces = np.sort(np.concatenate([tets[:, [1, 2, 3]], tets[:, [0, 2, 3]], tets[:, [0, 1, 3]],
+                                    tets[:, [0, 1, 2]]]), axis=1)
+    fk = (faces[:, 0] * nv + faces[:, 1]) * nv + faces[:, 2]
+    fu, fc = np.unique(fk, return_counts=True)
+    bf = fu[fc == 1]
+    f0, f1, f2 = bf // (nv * nv), (bf // nv) % nv, bf % nv
+    bedges = np.unique(np.concatenate([np.minimum(f0, f1) * nv + np.maximum(f0, f1),
+                                       np.minimum(f0, f2) * nv + np.maximum(f0, f2),
+                                       np.minimum(f1, f2) * nv + np.maximum(f1, f2)]))
+    d_f = np.asarray(dirichlet, dtype=bool)
+    face_dir = d_f[f0] & d_f[f1] & d_f[f2]
+    bedges_dir = np.unique(np.concatenate([
+        (np.minimum(f0, f1) * nv + np.maximum(f0, f1))[face_dir],
+        (np.minimum(f0, f2) * nv + np.maximum(f0, f2))[face_dir],
+        (np.minimum(f1, f2) * nv + np.maximum(f1, f2))[face_dir]]))
+    del bedges
+    new_dir = np.concatenate([d_f, np.isin(uk, bedges_dir)]).astype(np.uint8)
+    # children: vertex ids of the parent corners and edge midpoints
+    m = {p: mid[:, q] for q, p in enumerate(pairs)}
+    v = [tets[:, q] for q in range(4)]
+    def M(x, y):
+        return m[(min(x, y), max(x, y))]
+    kids = [(v[0], M(0, 1), M(0, 2), M(0, 3)), (M(0, 1), v[1], M(1, 2), M(1, 3)),
+            (M(0, 2), M(1, 2), v[2], M(2, 3)), (M(0, 3), M(1, 3), M(2, 3), v[3]),
+            (M(0, 1), M(0, 2), M(0, 3), M(1, 3)), (M(0, 1), M(0, 2), M(1, 2), M(1, 3)),
+            (M(0, 2), M(0, 3), M(1, 3), M(2, 3)), (M(0, 2), M(1, 2), M(1, 3), M(2, 3))]
+    new_tets = np.stack([np.stack(kd, axis=1) for kd in kids], axis=1).reshape(-1, 4)
+    return new_xyz, new_tets.astype(np.int32), new_dir
+
+
+def relabel_mesh(xyz, tets, dirichlet, seed: int = 0):
+    """Random renumbering of the vertices and the tets and a random order of each tet's
+    vertices (the mesh itself is unchanged)."""
+    rng = np.random.default_rng(seed)
+    nv = len(xyz)
+    perm = rng.permutation(nv)          # new index of old vertex v is inv[v]
+    inv = np.empty(nv, dtype=np.int64)
+    inv[perm] = np.arange(nv)
+    new_xyz = np.asarray(xyz)[perm]
+    new_dir = np.asarray(dirichlet)[perm]
+    t = inv[np.asarray(tets, dtype=np.int64)]
+    t = t[rng.permutation(len(t))]
+    order = np.argsort(rng.random(t.shape), axis=1)
+    t = np.take_along_axis(t, order, axis=1)
+    return new_xyz, t.astype(np.int32), new_dir

@@ -96,6 +96,19 @@ typedef struct {
 
 typedef struct fem_system_s* fem_system;
 
+/* A general conforming tetrahedral mesh (host arrays, read during the call only): nv
+ * vertices with coordinates xyz[3*nv]; nt tets given by 4 vertex indices each in tet[4*nt]
+ * (either orientation); dirichlet[nv] != 0 marks the vertices on which u = 0 (the boundary
+ * of Omega, Sec. 2: V_h = S_h^1 cap H_0^1).  The unknowns are the other vertices, numbered
+ * in increasing vertex order. */
+typedef struct {
+  int64_t nv;
+  int64_t nt;
+  const double* xyz;
+  const int32_t* tet;
+  const uint8_t* dirichlet;
+} fem_mesh_desc;
+
 /* Assemble K, M and f = (int ubar phi_i)_i (Sec. 2, entries below eq. (linsys)) on the
  * interior unknowns and form A = rho K + M (eq. (linsys)).  K and M come from the P1
  * element matrices |tau| grad(lambda_a).grad(lambda_b) and |tau|(1+delta_ab)/20; f uses
@@ -134,6 +147,16 @@ fem_status fem_assemble_rhs(fem_system sys, const fem_target* target, double* f_
  * Returns after the work is complete. */
 fem_status fem_assemble_rhs_noalloc(fem_system sys, const fem_target* target, double* f_dev,
                                     void* stream);
+
+/* fem_assemble on a general tetrahedral mesh: the same K, M (P1 element matrices) and f
+ * (4-point Hammer-Stroud rule per tet), rows built vertex by vertex over the incident tets in
+ * increasing tet order; CSR4 operator (no stencil).  Limits: at most 64 tets per vertex and
+ * 128 distinct neighbours per row (FEM_EUNSUPPORTED beyond), nt < 2^31.  A degenerate tet
+ * (zero volume) or a vertex index out of range gives FEM_EINVAL.  fem_errors, fem_recover,
+ * fem_assemble_rhs, the AMG variants and PCG accept the resulting system; batched sessions
+ * need keep_pencil as usual. */
+fem_status fem_assemble_mesh(const fem_mesh_desc* mesh, double rho, const fem_target* target,
+                             const fem_assemble_opts* opts, void* stream, fem_system* out);
 
 /* Copy the assembled load vector f (length N) into f_dev. */
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream);
@@ -232,6 +255,10 @@ typedef struct {
   int64_t nnz[32];       /* stored CSR4 entries       */
   double lmax[32];       /* Gershgorin bound of D^-1 A per level */
   double setup_ms;
+  int64_t pnnz[32];      /* stored CSR4 entries of P_l (0 on the coarsest level) */
+  int64_t rnnz[32];      /* stored CSR4 entries of R_l                            */
+  int32_t finest_stencil;/* 1: the finest level is applied matrix-free           */
+  int32_t colours[32];   /* Gauss-Seidel colours per level (SGS smoother; else 0) */
 } amg_hier_info;
 
 fem_status amg_hier_get_info(amg_hier h, amg_hier_info* info);

@@ -227,6 +227,41 @@ def assemble(n: int, target: dict, xyz: np.ndarray | None = None, qlevel: int = 
     return System(K, M, f, dof, n, xyz, tets)
 
 
+def assemble_mesh(xyz: np.ndarray, tets: np.ndarray, dirichlet: np.ndarray, target: dict,
+                  qlevel: int = 0) -> System:
+    """Assemble on a general tetrahedral mesh; the unknowns are the vertices not flagged in
+    ``dirichlet``, numbered in increasing vertex order."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    free = np.asarray(dirichlet) == 0
+    dof = np.full(len(xyz), -1, dtype=np.int32)
+    dof[free] = np.arange(int(free.sum()), dtype=np.int32)
+    ndof = int(free.sum())
+    t, keep = _target_struct(target)
+    s = _Sys()
+    rc = lib.ora_assemble(len(xyz), _dp(xyz), len(tets), _ip(tets), _ip(dof), ndof, C.byref(t),
+                          qlevel, C.byref(s))
+    if rc == -1:
+        raise MemoryError("oracle assembly: allocation failed")
+    try:
+        if rc == -2:
+            raise ValueError("oracle assembly: degenerate tetrahedron")
+        nnz = s.nnz
+        rowptr = np.ctypeslib.as_array(s.rowptr, (ndof + 1,)).copy()
+        col = np.ctypeslib.as_array(s.col, (nnz,)).copy()
+        Kv = np.ctypeslib.as_array(s.K, (nnz,)).copy()
+        Mv = np.ctypeslib.as_array(s.M, (nnz,)).copy()
+        f = np.ctypeslib.as_array(s.f, (ndof,)).copy()
+    finally:
+        lib.ora_sys_free(C.byref(s))
+    K = sp.csr_matrix((Kv, col, rowptr), shape=(ndof, ndof))
+    M = sp.csr_matrix((Mv, col.copy(), rowptr.copy()), shape=(ndof, ndof))
+    K.has_sorted_indices = True
+    M.has_sorted_indices = True
+    return System(K, M, f, dof, None, xyz, tets)
+
+
 def _sys_struct(system: System):
     K = system.K
     rowptr = np.ascontiguousarray(K.indptr, dtype=np.int64)

@@ -63,7 +63,9 @@ class AmgOpts(C.Structure):
 
 class HierInfo(C.Structure):
     _fields_ = [("levels", C.c_int32), ("rows", C.c_int64 * 32), ("nnz", C.c_int64 * 32),
-                ("lmax", C.c_double * 32), ("setup_ms", C.c_double)]
+                ("lmax", C.c_double * 32), ("setup_ms", C.c_double), ("pnnz", C.c_int64 * 32),
+                ("rnnz", C.c_int64 * 32), ("finest_stencil", C.c_int32),
+                ("colours", C.c_int32 * 32)]
 
 
 class PcgOpts(C.Structure):
@@ -88,6 +90,11 @@ VP = C.c_void_p
 P = C.POINTER
 
 # name -> (restype, argtypes); this list mirrors include/femamg.h
+class MeshDesc(C.Structure):
+    _fields_ = [("nv", C.c_int64), ("nt", C.c_int64), ("xyz", P(C.c_double)),
+                ("tet", P(C.c_int32)), ("dirichlet", P(C.c_uint8))]
+
+
 class ErrorsResult(C.Structure):
     _fields_ = [("l2sq", C.c_double), ("h1sq", C.c_double)]
 
@@ -98,6 +105,8 @@ SIGNATURES = {
     "fem_system_get_rhs": (C.c_int, [VP, VP, VP]),
     "fem_assemble_rhs": (C.c_int, [VP, P(Target), VP, VP]),
     "fem_assemble_rhs_noalloc": (C.c_int, [VP, P(Target), VP, VP]),
+    "fem_assemble_mesh": (C.c_int, [P(MeshDesc), C.c_double, P(Target), P(AssembleOpts), VP,
+                                    P(VP)]),
     "fem_errors": (C.c_int, [VP, VP, P(Target), C.c_double, C.c_int32, VP, P(ErrorsResult)]),
     "fem_recover": (C.c_int, [VP, VP, P(Target), VP, VP, VP]),
     "fem_system_export": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
@@ -264,6 +273,26 @@ def fem_assemble(n: int, rho: float, target: dict, xyz=None, fmt: int = FEM_FMT_
     return h
 
 
+def fem_assemble_mesh(xyz, tets, dirichlet, rho: float, target: dict, keep_pencil: bool = False,
+                      stream=None):
+    """Assemble (rho K + M) u = f on a general tetrahedral mesh (host arrays: xyz [nv, 3],
+    tets [nt, 4], dirichlet [nv] flags); returns the system handle."""
+    keep = []
+    xa = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    ta = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    da = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
+    assert len(da) == len(xa)
+    keep += [xa, ta, da]
+    d = MeshDesc(len(xa), len(ta), _dp(xa), ta.ctypes.data_as(P(C.c_int32)),
+                 da.ctypes.data_as(P(C.c_uint8)))
+    t = _target(target, keep)
+    o = AssembleOpts(FEM_FMT_CSR, 1 if keep_pencil else 0)
+    h = VP()
+    _check(lib().fem_assemble_mesh(C.byref(d), rho, C.byref(t), C.byref(o), _stream(stream),
+                                   C.byref(h)), "fem_assemble_mesh")
+    return h
+
+
 def fem_system_get_info(sys) -> dict:
     i = SystemInfo()
     _check(lib().fem_system_get_info(sys, C.byref(i)), "fem_system_get_info")
@@ -310,7 +339,9 @@ def amg_hier_get_info(h) -> dict:
     _check(lib().amg_hier_get_info(h, C.byref(i)), "amg_hier_get_info")
     L = i.levels
     return {"levels": L, "rows": list(i.rows[:L]), "nnz": list(i.nnz[:L]),
-            "lmax": list(i.lmax[:L]), "setup_ms": i.setup_ms}
+            "lmax": list(i.lmax[:L]), "setup_ms": i.setup_ms, "pnnz": list(i.pnnz[:L]),
+            "rnnz": list(i.rnnz[:L]), "finest_stencil": bool(i.finest_stencil),
+            "colours": list(i.colours[:L])}
 
 
 def amg_hier_export(h, level, which, rowptr=None, col=None, val=None, stream=None) -> int:

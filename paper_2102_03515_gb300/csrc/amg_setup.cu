@@ -77,6 +77,8 @@ __global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* bsum) {
   if (i == n - 1) out[n] = bsum[gridDim.x];
 }
 
+}  // namespace
+
 // out[0..n]: exclusive scan of in[0..n-1] and the total in out[n].  Returns the total.
 int64_t exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st) {
   if (n == 0) {
@@ -97,6 +99,8 @@ int64_t exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStream_t 
   return total;
 }
 
+namespace {
+
 __global__ void k_to_rowptr(const int64_t* in, int64_t n, int32_t* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i <= n) out[i] = (int32_t)in[i];
@@ -107,6 +111,8 @@ __global__ void k_pad4(const int64_t* cnt, int64_t n, int64_t* padded) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) padded[i] = (cnt[i] + 3) & ~(int64_t)3;
 }
+
+}  // namespace
 
 void rowptr_from_counts(const int64_t* cnt, int64_t n, Csr4& C, cudaStream_t st) {
   DevBuf<int64_t> padded(n, st), scan(n + 1, st);
@@ -120,6 +126,8 @@ void rowptr_from_counts(const int64_t* cnt, int64_t n, Csr4& C, cudaStream_t st)
   C.nnz = total;
   C.col.alloc(total);
 }
+
+namespace {
 
 // ------------------------------------------------------------------ small kernels
 

@@ -610,12 +610,296 @@ __global__ void k_recover(int n, const double* xyz, TargetDev T, double rho,
   if (p) p[r] = -rho * ur;
 }
 
+// ------------------------------------------------------------------ general meshes
+
+// Rows are built vertex by vertex from the vertex's incident tets, visited in increasing
+// tet order: the unknowns of those tets (sorted, unique) are the row's columns, and the
+// element contributions are added in that order.
+constexpr int kGmMaxInc = 64;    // tets per vertex
+constexpr int kGmMaxRow = 128;   // distinct unknowns per row
+
+__global__ void k_gm_dof(int64_t nv, const uint8_t* dir, const int64_t* scan, int32_t* vdof,
+                         int64_t* rvert) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  if (dir[v]) {
+    vdof[v] = -1;
+  } else {
+    vdof[v] = (int32_t)scan[v];
+    rvert[scan[v]] = v;
+  }
+}
+
+__global__ void k_gm_free_flags(int64_t nv, const uint8_t* dir, int64_t* flag) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) flag[v] = dir[v] ? 0 : 1;
+}
+
+__global__ void k_gm_inc_count(int64_t nt, const int32_t* tet, int64_t nv, int64_t* cnt,
+                               unsigned long long* bad) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  for (int a = 0; a < 4; a++) {
+    const int32_t v = tet[4 * t + a];
+    if (v < 0 || v >= nv) {
+      atomicAdd(bad, 1ull);
+      continue;
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(cnt) + v, 1ull);
+  }
+}
+
+__global__ void k_gm_inc_fill(int64_t nt, const int32_t* tet, const int64_t* vptr,
+                              unsigned long long* cursor, int32_t* vtet) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  for (int a = 0; a < 4; a++) {
+    const int32_t v = tet[4 * t + a];
+    vtet[vptr[v] + (int64_t)atomicAdd(cursor + v, 1ull)] = (int32_t)t;
+  }
+}
+
+// every tet must have a nonzero volume
+__global__ void k_gm_tet_check(int64_t nt, const int32_t* tet, const double* xyz,
+                               unsigned long long* bad) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double X[4][3], g[4][3];
+  for (int a = 0; a < 4; a++)
+    for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)tet[4 * t + a] + d];
+  const double det = tet_grads(X, g);
+  if (!(det != 0.0) || !isfinite(det)) atomicAdd(bad, 1ull);
+}
+
+// incident tets of each vertex in increasing order (lists are short: insertion sort)
+__global__ void k_gm_inc_sort(int64_t nv, const int64_t* vptr, int32_t* vtet,
+                              unsigned long long* over) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const int64_t a = vptr[v], b = vptr[v + 1];
+  if (b - a > kGmMaxInc) atomicAdd(over, 1ull);
+  for (int64_t i = a + 1; i < b; i++) {
+    const int32_t x = vtet[i];
+    int64_t j = i - 1;
+    while (j >= a && vtet[j] > x) {
+      vtet[j + 1] = vtet[j];
+      j--;
+    }
+    vtet[j + 1] = x;
+  }
+}
+
+// sorted unique unknowns of the tets around vertex v; -1 when the row is too long
+__device__ int gm_row_cols(int64_t v, const int64_t* vptr, const int32_t* vtet,
+                           const int32_t* tet, const int32_t* vdof, int32_t* buf) {
+  int cnt = 0;
+  for (int64_t e = vptr[v]; e < vptr[v + 1]; e++) {
+    const int64_t t = vtet[e];
+    for (int a = 0; a < 4; a++) {
+      const int32_t w = vdof[tet[4 * t + a]];
+      if (w < 0) continue;
+      int q = 0;
+      while (q < cnt && buf[q] < w) q++;
+      if (q < cnt && buf[q] == w) continue;
+      if (cnt == kGmMaxRow) return -1;
+      for (int z = cnt; z > q; z--) buf[z] = buf[z - 1];
+      buf[q] = w;
+      cnt++;
+    }
+  }
+  return cnt;
+}
+
+__global__ void k_gm_row_count(int64_t N, const int64_t* rvert, const int64_t* vptr,
+                               const int32_t* vtet, const int32_t* tet, const int32_t* vdof,
+                               int64_t* cnt, unsigned long long* over) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int32_t buf[kGmMaxRow];
+  const int c = gm_row_cols(rvert[r], vptr, vtet, tet, vdof, buf);
+  if (c < 0) {
+    atomicAdd(over, 1ull);
+    cnt[r] = 0;
+    return;
+  }
+  cnt[r] = c;
+}
+
+// the load contribution sum_q w_q ubar(x_q) lambda_loc(x_q) of one tet (times |tau|)
+__device__ __forceinline__ double gm_tet_load(const TargetDev& T, const double X[4][3], int loc,
+                                              const double* qb, const double* qw, int np) {
+  double acc = 0.0;
+  for (int q = 0; q < np; q++) {
+    double x[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int d = 0; d < 3; d++) x[d] += qb[4 * q + a] * X[a][d];
+    acc += qw[q] * target_eval(T, x[0], x[1], x[2]) * qb[4 * q + loc];
+  }
+  return acc;
+}
+
+// One row: columns, K, M, A = rho K + M and f.  With Aval null only f is written.
+__global__ void k_gm_row_fill(int64_t N, const int64_t* rvert, const int64_t* vptr,
+                              const int32_t* vtet, const int32_t* tet, const int32_t* vdof,
+                              const double* xyz, double rho, TargetDev T, const double* qb,
+                              const double* qw, int np, const int32_t* rowptr, int32_t* col,
+                              double* Aval, double* Kv, double* Mv, double* f,
+                              unsigned long long* bad) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int64_t v = rvert[r];
+  int32_t cols[kGmMaxRow];
+  double kacc[kGmMaxRow], macc[kGmMaxRow];
+  int nc = 0;
+  if (Aval) {
+    nc = gm_row_cols(v, vptr, vtet, tet, vdof, cols);
+    if (nc < 0) return;
+    for (int q = 0; q < nc; q++) kacc[q] = macc[q] = 0.0;
+  }
+  double fr = 0.0;
+  for (int64_t e = vptr[v]; e < vptr[v + 1]; e++) {
+    const int64_t t = vtet[e];
+    double X[4][3], g[4][3];
+    int loc = 0;
+    int32_t tv[4];
+    for (int a = 0; a < 4; a++) {
+      tv[a] = tet[4 * t + a];
+      if (tv[a] == v) loc = a;
+      for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)tv[a] + d];
+    }
+    const double det = tet_grads(X, g);
+    if (!(det != 0.0)) {
+      atomicAdd(bad, 1ull);
+      return;
+    }
+    const double vol = fabs(det) / 6.0;
+    if (Aval) {
+      for (int b = 0; b < 4; b++) {
+        const int32_t w = vdof[tv[b]];
+        if (w < 0) continue;
+        int lo = 0, hi = nc - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi) / 2;
+          if (cols[mid] < w) lo = mid + 1; else hi = mid;
+        }
+        kacc[lo] += vol * (g[loc][0] * g[b][0] + g[loc][1] * g[b][1] + g[loc][2] * g[b][2]);
+        macc[lo] += vol * (loc == b ? 2.0 : 1.0) / 20.0;
+      }
+    }
+    fr += vol * gm_tet_load(T, X, loc, qb, qw, np);
+  }
+  f[r] = fr;
+  if (!Aval) return;
+  const int64_t o0 = rowptr[r], o1 = rowptr[r + 1];
+  for (int q = 0; q < nc; q++) {
+    col[o0 + q] = cols[q];
+    Aval[o0 + q] = rho * kacc[q] + macc[q];
+    if (Kv) {
+      Kv[o0 + q] = kacc[q];
+      Mv[o0 + q] = macc[q];
+    }
+  }
+  for (int64_t o = o0 + nc; o < o1; o++) {
+    col[o] = -1;
+    Aval[o] = 0.0;
+    if (Kv) {
+      Kv[o] = 0.0;
+      Mv[o] = 0.0;
+    }
+  }
+}
+
+// errors over the tets of a general mesh (thread per tet, grid-stride, fixed grid)
+__global__ void k_gm_errors(int64_t nt, const int32_t* tet, const int32_t* vdof, const double* xyz,
+                            const double* __restrict__ u, TargetDev T, double scale, int grad,
+                            const double* __restrict__ qb, const double* __restrict__ qw, int np,
+                            double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double X[4][3], g[4][3], U[4];
+    for (int a = 0; a < 4; a++) {
+      const int32_t v = tet[4 * t + a];
+      const int32_t w = vdof[v];
+      U[a] = w >= 0 ? u[w] : 0.0;
+      for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)v + d];
+    }
+    const double vol = fabs(tet_grads(X, g)) / 6.0;
+    double guh[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; a++)
+      for (int d = 0; d < 3; d++) guh[d] += U[a] * g[a][d];
+    double e2 = 0.0, g2 = 0.0;
+    for (int q = 0; q < np; q++) {
+      double x[3] = {0.0, 0.0, 0.0}, uh = 0.0;
+      for (int a = 0; a < 4; a++) {
+        const double b = qb[4 * q + a];
+        for (int d = 0; d < 3; d++) x[d] += b * X[a][d];
+        uh += b * U[a];
+      }
+      const double diff = scale * target_eval(T, x[0], x[1], x[2]) - uh;
+      e2 += qw[q] * diff * diff;
+      if (grad) {
+        double ge[3];
+        target_grad(T, scale, x[0], x[1], x[2], ge);
+        const double d0 = ge[0] - guh[0], d1 = ge[1] - guh[1], d2 = ge[2] - guh[2];
+        g2 += qw[q] * (d0 * d0 + d1 * d1 + d2 * d2);
+      }
+    }
+    acc[0] += vol * e2;
+    acc[1] += vol * g2;
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc[0];
+    partials[gridDim.x + blockIdx.x] = acc[1];
+  }
+}
+
+__global__ void k_gm_recover(int64_t N, const int64_t* rvert, const double* xyz, TargetDev T,
+                             double rho, const double* __restrict__ u, double* z, double* p) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int64_t v = rvert[r];
+  const double ur = u[r];
+  if (z) z[r] = (target_eval(T, xyz[3 * v], xyz[3 * v + 1], xyz[3 * v + 2]) - ur) / rho;
+  if (p) p[r] = -rho * ur;
+}
+
+// 4-point Hammer-Stroud rule (level 0) for assembly
+void hs_rule(DevBuf<double>& qb, DevBuf<double>& qw, int level, cudaStream_t st) {
+  std::vector<double> bary, wt;
+  const double P[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+  bey_rule(P, level, 1.0, bary, wt);
+  qb.alloc_async(bary.size(), st);
+  qw.alloc_async(wt.size(), st);
+  FEM_CUDA(cudaMemcpyAsync(qb, bary.data(), 8 * bary.size(), cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(qw, wt.data(), 8 * wt.size(), cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
+void gm_load_vector(System& S, const TargetDev& T, double* f, cudaStream_t st) {
+  DevBuf<double> qb, qw;
+  hs_rule(qb, qw, 0, st);
+  DevBuf<unsigned long long> bad(1, st);
+  FEM_CUDA(cudaMemsetAsync(bad, 0, 8, st));
+  k_gm_row_fill<<<grid_for(S.N, 128), 128, 0, st>>>(
+      S.N, S.rvert, S.vptr, S.vtet, S.tet, S.vdof, S.xyz, S.rho, T, qb, qw, 4, nullptr, nullptr,
+      nullptr, nullptr, nullptr, f, bad);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
 }  // namespace
 
 void assemble_rhs(System& S, const fem_target& t, double* f, cudaStream_t st) {
   TargetHolder th;
   target_to_device(t, th, st);
-  load_vector(S, th.T, t, f, st);
+  if (S.general)
+    gm_load_vector(S, th.T, f, st);
+  else
+    load_vector(S, th.T, t, f, st);
   FEM_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -756,6 +1040,99 @@ static double* noalloc_scratch() {
   return addr[dev];
 }
 
+void assemble_mesh(System& S, const fem_mesh_desc& mesh, double rho, const fem_target& t,
+                   const fem_assemble_opts& o, cudaStream_t st) {
+  const int64_t nv = mesh.nv, nt = mesh.nt;
+  FEM_REQUIRE(nv >= 4 && nt >= 1 && nt < ((int64_t)1 << 31) && nv < ((int64_t)1 << 31),
+              FEM_EINVAL, "fem_assemble_mesh: bad sizes");
+  FEM_REQUIRE(mesh.xyz && mesh.tet && mesh.dirichlet, FEM_EINVAL,
+              "fem_assemble_mesh: null array");
+  FEM_REQUIRE(rho > 0.0 && std::isfinite(rho), FEM_EINVAL, "fem_assemble_mesh: rho must be > 0");
+  FEM_REQUIRE(o.format == FEM_FMT_AUTO || o.format == FEM_FMT_CSR, FEM_EINVAL,
+              "fem_assemble_mesh: a general mesh has no stencil format");
+  TargetHolder th;
+  target_to_device(t, th, st);
+  S.general = true;
+  S.uniform = false;
+  S.stencil = false;
+  S.pencil = o.keep_pencil != 0;
+  S.rho = rho;
+  S.n = 0;
+  S.nv = nv;
+  S.nt = nt;
+  Tracer tr(st);
+  S.xyz.alloc_async(3 * nv, st);
+  S.tet.alloc_async(4 * nt, st);
+  DevBuf<uint8_t> dir(nv, st);
+  FEM_CUDA(cudaMemcpyAsync(S.xyz, mesh.xyz, 24 * nv, cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(S.tet, mesh.tet, 16 * nt, cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(dir, mesh.dirichlet, nv, cudaMemcpyHostToDevice, st));
+  const unsigned gv = grid_for(nv, 256), gt = grid_for(nt, 256);
+  // unknowns
+  DevBuf<int64_t> flag(nv, st), scan(nv + 1, st);
+  k_gm_free_flags<<<gv, 256, 0, st>>>(nv, dir, flag);
+  FEM_CHECK_LAUNCH();
+  const int64_t N = exclusive_scan(flag, nv, scan, st);
+  FEM_REQUIRE(N >= 1, FEM_EINVAL, "fem_assemble_mesh: every vertex is a Dirichlet vertex");
+  S.N = N;
+  S.vdof.alloc(nv);
+  S.rvert.alloc(N);
+  k_gm_dof<<<gv, 256, 0, st>>>(nv, dir, scan, S.vdof, S.rvert);
+  FEM_CHECK_LAUNCH();
+  // vertex -> incident tets
+  DevBuf<int64_t> cnt(nv, st);
+  DevBuf<unsigned long long> flags(3, st);
+  FEM_CUDA(cudaMemsetAsync(cnt, 0, 8 * nv, st));
+  FEM_CUDA(cudaMemsetAsync(flags, 0, 24, st));
+  k_gm_inc_count<<<gt, 256, 0, st>>>(nt, S.tet, nv, cnt, flags);
+  FEM_CHECK_LAUNCH();
+  unsigned long long hf[3];
+  FEM_CUDA(cudaMemcpyAsync(hf, flags, 24, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(hf[0] == 0, FEM_EINVAL, "fem_assemble_mesh: a tet vertex index is out of range");
+  k_gm_tet_check<<<gt, 256, 0, st>>>(nt, S.tet, S.xyz, flags.p + 2);
+  FEM_CHECK_LAUNCH();
+  S.vptr.alloc(nv + 1);
+  const int64_t ninc = exclusive_scan(cnt, nv, S.vptr, st);
+  S.vtet.alloc(ninc);
+  FEM_CUDA(cudaMemsetAsync(cnt, 0, 8 * nv, st));
+  k_gm_inc_fill<<<gt, 256, 0, st>>>(nt, S.tet, S.vptr,
+                                    reinterpret_cast<unsigned long long*>(cnt.p), S.vtet);
+  FEM_CHECK_LAUNCH();
+  k_gm_inc_sort<<<gv, 256, 0, st>>>(nv, S.vptr, S.vtet, flags.p + 1);
+  FEM_CHECK_LAUNCH();
+  // pattern
+  DevBuf<int64_t> rc(N, st);
+  k_gm_row_count<<<grid_for(N, 128), 128, 0, st>>>(N, S.rvert, S.vptr, S.vtet, S.tet, S.vdof, rc,
+                                                   flags.p + 1);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaMemcpyAsync(hf, flags, 24, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(hf[1] == 0, FEM_EUNSUPPORTED,
+              "fem_assemble_mesh: more than 64 tets at a vertex or 128 neighbours in a row");
+  S.A.nrows = S.A.ncols = (int32_t)N;
+  rowptr_from_counts(rc, N, S.A, st);
+  S.A.val.alloc(S.A.nnz);
+  if (S.pencil) {
+    S.Kv.alloc(S.A.nnz);
+    S.Mv.alloc(S.A.nnz);
+  }
+  S.f.alloc(N);
+  DevBuf<double> qb, qw;
+  hs_rule(qb, qw, 0, st);
+  k_gm_row_fill<<<grid_for(N, 128), 128, 0, st>>>(
+      N, S.rvert, S.vptr, S.vtet, S.tet, S.vdof, S.xyz, rho, th.T, qb, qw, 4, S.A.rowptr, S.A.col,
+      S.A.val, S.pencil ? S.Kv.p : nullptr, S.pencil ? S.Mv.p : nullptr, S.f, flags.p + 2);
+  FEM_CHECK_LAUNCH();
+  tr.mark("assemble: general mesh");
+  S.dinv.alloc(N);
+  k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaMemcpyAsync(hf, flags, 24, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(hf[2] == 0, FEM_EINVAL, "fem_assemble_mesh: a tet has zero volume");
+}
+
 void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
                      double out[2], cudaStream_t st) {
   FEM_REQUIRE(qlevel >= 0 && qlevel <= 2, FEM_EINVAL, "fem_errors: qlevel in [0, 2]");
@@ -769,11 +1146,15 @@ void fem_error_norms(System& S, const double* u, const fem_target& t, double sca
   FEM_CUDA(cudaMemcpyAsync(qb, bary.data(), 8 * bary.size(), cudaMemcpyHostToDevice, st));
   FEM_CUDA(cudaMemcpyAsync(qw, wt.data(), 8 * wt.size(), cudaMemcpyHostToDevice, st));
   const int grad = (t.kind == FEM_TARGET_SINE || t.kind == FEM_TARGET_SINE_PLUS_ONE) ? 1 : 0;
-  const int64_t ncube = (int64_t)S.n * S.n * S.n;
+  const int64_t ncube = S.general ? S.nt : (int64_t)S.n * S.n * S.n;
   const unsigned g = persistent_grid(ncube, 128, 8);
   DevBuf<double> part(2 * (size_t)g, st), sums(2, st);
-  k_errors<<<g, 128, 0, st>>>(S.n, S.uniform ? nullptr : S.xyz.p, u, th.T, scale, grad, qb, qw,
-                              np, part);
+  if (S.general)
+    k_gm_errors<<<g, 128, 0, st>>>(S.nt, S.tet, S.vdof, S.xyz, u, th.T, scale, grad, qb, qw, np,
+                                   part);
+  else
+    k_errors<<<g, 128, 0, st>>>(S.n, S.uniform ? nullptr : S.xyz.p, u, th.T, scale, grad, qb, qw,
+                                np, part);
   FEM_CHECK_LAUNCH();
   finalize_sums(part, (int)g, 2, sums, st);
   FEM_CUDA(cudaMemcpyAsync(out, sums, 16, cudaMemcpyDeviceToHost, st));
@@ -785,13 +1166,18 @@ void fem_recovery(System& S, const double* u, const fem_target& t, double* z, do
                   cudaStream_t st) {
   TargetHolder th;
   target_to_device(t, th, st);
-  k_recover<<<grid_for(S.N, 256), 256, 0, st>>>(S.n, S.uniform ? nullptr : S.xyz.p, th.T, S.rho,
-                                                 u, z, p);
+  if (S.general)
+    k_gm_recover<<<grid_for(S.N, 256), 256, 0, st>>>(S.N, S.rvert, S.xyz, th.T, S.rho, u, z, p);
+  else
+    k_recover<<<grid_for(S.N, 256), 256, 0, st>>>(S.n, S.uniform ? nullptr : S.xyz.p, th.T,
+                                                   S.rho, u, z, p);
   FEM_CHECK_LAUNCH();
   FEM_CUDA(cudaStreamSynchronize(st));
 }
 
 void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_t st) {
+  FEM_REQUIRE(!S.general, FEM_EINVAL,
+              "fem_assemble_rhs_noalloc: Kuhn meshes only (no general meshes)");
   FEM_REQUIRE(S.n <= kNoAllocMaxN, FEM_EINVAL,
               "fem_assemble_rhs_noalloc: n = " + std::to_string(S.n) +
                   " exceeds the allocation-free limit of 64 cells per side");

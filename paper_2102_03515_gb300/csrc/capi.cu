@@ -129,6 +129,27 @@ fem_status fem_assemble(const fem_kuhn_desc* mesh, double rho, const fem_target*
   });
 }
 
+fem_status fem_assemble_mesh(const fem_mesh_desc* mesh, double rho, const fem_target* target,
+                             const fem_assemble_opts* opts, void* stream, fem_system* out) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(mesh && target && out, FEM_EINVAL, "fem_assemble_mesh: null argument");
+    *out = nullptr;
+    fem_assemble_opts o{FEM_FMT_AUTO, 0};
+    if (opts) o = *opts;
+    init_memory_pool();
+    auto* h = new fem_system_s();
+    try {
+      assemble_mesh(h->S, *mesh, rho, *target, o, as_stream(stream));
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return FEM_OK;
+  });
+}
+
 fem_status fem_system_get_info(fem_system sys, fem_system_info* info) {
   return guarded([&]() -> fem_status {
     FEM_REQUIRE(sys && info, FEM_EINVAL, "fem_system_get_info: null argument");
@@ -308,7 +329,11 @@ fem_status amg_hier_get_info(amg_hier h, amg_hier_info* info) {
       info->rows[l] = h->H.L[l]->N;
       info->nnz[l] = h->H.L[l]->A->nnz;
       info->lmax[l] = h->H.L[l]->lmax;
+      info->pnnz[l] = h->H.L[l]->coarsest ? 0 : h->H.L[l]->P.nnz;
+      info->rnnz[l] = h->H.L[l]->coarsest ? 0 : h->H.L[l]->R.nnz;
+      info->colours[l] = h->H.L[l]->coff.empty() ? 0 : (int32_t)h->H.L[l]->coff.size() - 1;
     }
+    info->finest_stencil = h->H.L.empty() ? 0 : (h->H.L[0]->stencil ? 1 : 0);
     info->setup_ms = h->H.setup_ms;
     return FEM_OK;
   });

@@ -32,7 +32,13 @@ struct System {
   DevBuf<double> Kv, Mv;  // pencil values on A's pattern
   DevBuf<double> f;       // load vector
   DevBuf<double> dinv;    // 1 / a_ii
-  DevBuf<double> xyz;     // vertex coordinates of a non-uniform grid
+  DevBuf<double> xyz;     // vertex coordinates of a non-uniform grid or a general mesh
+  // general tetrahedral mesh (fem_assemble_mesh): tets, unknown of each vertex (-1:
+  // Dirichlet), vertex of each unknown, vertex -> incident tets in increasing order
+  bool general = false;
+  int64_t nv = 0, nt = 0;
+  DevBuf<int32_t> tet, vdof, vtet;
+  DevBuf<int64_t> rvert, vptr;
 };
 
 struct Level {
@@ -80,6 +86,9 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
                      const fem_assemble_opts& o, cudaStream_t st);
 void assemble_rhs(System& S, const fem_target& t, double* f, cudaStream_t st);
 void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_t st);
+// general tetrahedral mesh: nv vertices (xyz host), nt tets (host), Dirichlet flags (host)
+void assemble_mesh(System& S, const fem_mesh_desc& mesh, double rho, const fem_target& t,
+                   const fem_assemble_opts& o, cudaStream_t st);
 // ||scale*t - u_h||^2 and ||grad(scale*t - u_h)||^2 (NaN without a gradient) by quadrature
 void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
                      double out[2], cudaStream_t st);
@@ -169,6 +178,12 @@ void autotune_pin(const char* kernel, int variant);
 // Tunes the launch shapes of a hierarchy's operators (ops.cu); runs on scratch vectors
 // after the set-up, before any solve uses the hierarchy.
 void tune_hierarchy(Hierarchy& H, System& S, cudaStream_t st);
+
+// ------------------------------------------------------------------ scans (amg_setup.cu)
+// out[i] = sum_{j < i} in[j] (out has n + 1 entries); returns the total
+int64_t exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st);
+// C.rowptr from per-row counts padded to multiples of 4; sets C.nnz and allocates C.col
+void rowptr_from_counts(const int64_t* cnt, int64_t n, Csr4& C, cudaStream_t st);
 
 // ------------------------------------------------------------------ utilities
 void finalize_sums(const double* partials, int nblocks, int nv, double* out, cudaStream_t st,
