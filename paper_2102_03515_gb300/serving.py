@@ -48,8 +48,8 @@ class Request:
 
 @dataclass
 class ServeConfig:
-    slots: int = 16               # slots per (n, bucket) session
-    steps_per_tick: int = 2       # CG iterations per session per tick
+    slots: int = 4                # slots per (n, bucket) session
+    steps_per_tick: int = 1       # CG iterations per session per tick
     hbm_budget: int = 160 << 30   # bytes the service may hold on the device
     precision: int = fa.AMG_PREC_FP32
     keep_solutions: bool = False  # keep each request's solution on the device
