@@ -274,6 +274,14 @@ fem_status amg_hier_export(amg_hier h, int32_t level, int32_t which, int32_t* ro
 /* z = V(r): one V-cycle with zero initial guess (eq. (amgpre) applied recursively). */
 fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stream);
 
+/* The same V-cycle applied `reps` times (reps >= 1) from one CUDA graph of a single
+ * application, for callers that apply the preconditioner many times (their own Krylov
+ * method, a timing of the V-cycle alone): z = V(r) after the call; *ms_out (may be null)
+ * receives the mean device time of one application, measured with CUDA events around the
+ * graph replays on `stream`.  Errors: FEM_EINVAL (null argument, reps < 1). */
+fem_status amg_vcycle_graph(amg_hier h, const double* r_dev, double* z_dev, int32_t reps,
+                            void* stream, double* ms_out);
+
 void amg_hier_destroy(amg_hier h);
 
 /* ------------------------------------------------------------------ PCG */

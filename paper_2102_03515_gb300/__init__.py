@@ -11,7 +11,8 @@ from ._binding import (  # noqa: F401
     AMG_COARSEN_RED_BLACK, AMG_COARSEN_SA, AMG_PREC_BF16, AMG_PREC_FP32, AMG_PREC_FP64,
     AMG_SMOOTHER_CHEBYSHEV, AMG_SMOOTHER_L1_JACOBI, AMG_SMOOTHER_SGS, FEM_FMT_AUTO, FEM_FMT_CSR,
     FEM_FMT_STENCIL, FemError, PCG_STOP_PRECONDITIONED, PCG_STOP_RESIDUAL, amg_default_opts,
-    amg_hier_destroy, amg_hier_export, amg_hier_get_info, amg_setup, amg_vcycle, fem_assemble,
+    amg_hier_destroy, amg_hier_export, amg_hier_get_info, amg_setup, amg_vcycle,
+    amg_vcycle_graph, fem_assemble,
     fem_assemble_mesh,
     fem_assemble_rhs, fem_assemble_rhs_noalloc, fem_autotune_clear, fem_autotune_pin,
     fem_autotune_report, fem_errors, fem_kernel_launches, fem_last_error, fem_recover, fem_spmv,

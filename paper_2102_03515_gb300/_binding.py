@@ -117,6 +117,7 @@ SIGNATURES = {
     "amg_hier_get_info": (C.c_int, [VP, P(HierInfo)]),
     "amg_hier_export": (C.c_int, [VP, C.c_int32, C.c_int32, VP, VP, VP, P(C.c_int64), VP]),
     "amg_vcycle": (C.c_int, [VP, VP, VP, VP]),
+    "amg_vcycle_graph": (C.c_int, [VP, VP, VP, C.c_int32, VP, P(C.c_double)]),
     "amg_hier_destroy": (None, [VP]),
     "pcg_default_opts": (None, [P(PcgOpts)]),
     "pcg_solve": (C.c_int, [VP, VP, VP, VP, C.c_int32, P(C.c_double), P(PcgOpts), VP,
@@ -342,6 +343,14 @@ def amg_hier_get_info(h) -> dict:
             "lmax": list(i.lmax[:L]), "setup_ms": i.setup_ms, "pnnz": list(i.pnnz[:L]),
             "rnnz": list(i.rnnz[:L]), "finest_stencil": bool(i.finest_stencil),
             "colours": list(i.colours[:L])}
+
+
+def amg_vcycle_graph(h, r, z, reps: int = 20, stream=None) -> float:
+    """z = V(r) applied `reps` times from a CUDA graph; returns ms per application."""
+    ms = C.c_double(0.0)
+    _check(lib().amg_vcycle_graph(h, _ptr(r), _ptr(z), int(reps), _stream(stream), C.byref(ms)),
+           "amg_vcycle_graph")
+    return ms.value
 
 
 def amg_hier_export(h, level, which, rowptr=None, col=None, val=None, stream=None) -> int:

@@ -171,6 +171,32 @@ __device__ __forceinline__ void mv_apply(const MvEpi<T>& e, int64_t i, int b,
   }
 }
 
+__device__ __forceinline__ void l2_prefetch(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// hint the L2 to fetch the epilogue operands of (i, b) (no registers, no wait)
+template <typename T, int MODE = -1>
+__device__ __forceinline__ void mv_prefetch(const MvEpi<T>& e, int64_t i, int b) {
+  const int64_t idx = i * e.B + b;
+  switch (MODE >= 0 ? (MODE == 5 ? 2 : MODE) : e.mode) {
+    case 1:
+    case 3:
+      l2_prefetch(e.b + idx);
+      break;
+    case 2:
+      l2_prefetch(e.r + idx);
+      l2_prefetch(e.x + idx);
+      if (MODE == 5) {
+        if (e.r1) l2_prefetch(e.r1 + idx);
+        if (e.r2) l2_prefetch(e.r2 + idx);
+      }
+      break;
+    default:
+      break;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void mv_epi(const MvEpi<T>& e, int64_t i, int b, typename Arith<T>::type av,
                                        double acc[2]) {
@@ -253,7 +279,7 @@ __global__ void __launch_bounds__(256) k_mv_stencil(const T* __restrict__ v, int
 // again one plane later (7 loads per point instead of 15) and issuing the loads of point
 // k + 1 before finishing point k.  grid: x over groups of 256 / B points along i, y strides
 // over j, z over plane ranges.
-template <typename T, int NV, int KZV, int MODE>
+template <typename T, int NV, int KZV, int MODE, int PF = 0>
 __global__ void __launch_bounds__(256) k_mv_stencil_col(const T* __restrict__ v, int m, MvEpi<T> e,
                                                         double* partials, int nblocks) {
   using AT = typename Arith<T>::type;
@@ -285,6 +311,10 @@ __global__ void __launch_bounds__(256) k_mv_stencil_col(const T* __restrict__ v,
       AT n_ip = ld(ip, k0 + 1, sB), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, sB + sj);
       Ops op = mv_load<T, MODE>(e, row0 + pk * k0, b);
       for (int k = k0; k < kend; k++) {
+        if (PF > 0 && k + PF < kend) {  // L2 prefetch of the streams PF planes ahead (in bounds)
+          if (k + PF + 1 < m) l2_prefetch(col + sk * (k + PF + 1));
+          mv_prefetch<T, MODE>(e, row0 + pk * (k + PF), b);
+        }
         const bool more = k + 1 < kend;
         const AT z2_im = ld(im && more, k + 1, -sB), z2_jm = ld(jm && more, k + 1, -sj),
                  z2_ijm = ld(im && jm && more, k + 1, -sB - sj);
@@ -906,10 +936,12 @@ dim3 mv_sgrid(int m, int B) {
 // ------------------------------------------------------------------ tuned launches
 
 // FP32 multivector stencil variants: 0 one thread per (point, slot) striding over planes,
-// 1..3 column marching over 16, 32, 64 planes per block.
-constexpr int kMvStencilVariants = 4;
+// 1..3 column marching over 16, 32, 64 planes per block, 4..5 column marching over 16, 32
+// planes with an L2 prefetch of the streams 4 planes ahead.
+constexpr int kMvStencilVariants = 6;
 const char* const kMvStencilNames[kMvStencilVariants] = {"point", "col_kz16", "col_kz32",
-                                                         "col_kz64"};
+                                                         "col_kz64", "col_kz16_pf4",
+                                                         "col_kz32_pf4"};
 // multivector CSR variants: 1, 2, 4 slots per thread
 constexpr int kMvCsrVariants = 3;
 const char* const kMvCsrNames[kMvCsrVariants] = {"vs1", "vs2", "vs4"};
@@ -928,22 +960,24 @@ dim3 mv_stencil_grid(int var, int m, int B) {
     case 1: return mv_colgrid(m, B, 16);
     case 2: return mv_colgrid(m, B, 32);
     case 3: return mv_colgrid(m, B, 64);
+    case 4: return mv_colgrid(m, B, 16);
+    case 5: return mv_colgrid(m, B, 32);
     default: return mv_sgrid(m, B);
   }
 }
 
-template <int NV, int KZV>
+template <int NV, int KZV, int PF = 0>
 void launch_mv_col(dim3 g, int nb, const float* v, int m, const MvEpi<float>& e, double* part,
                    cudaStream_t st) {
   switch (e.mode) {
-    case 0: k_mv_stencil_col<float, NV, KZV, 0><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
-    case 1: k_mv_stencil_col<float, NV, KZV, 1><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
-    case 3: k_mv_stencil_col<float, NV, KZV, 3><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 0: k_mv_stencil_col<float, NV, KZV, 0, PF><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 1: k_mv_stencil_col<float, NV, KZV, 1, PF><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
+    case 3: k_mv_stencil_col<float, NV, KZV, 3, PF><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
     default:
       if (e.z64)
-        k_mv_stencil_col<float, NV, KZV, 5><<<g, 256, 0, st>>>(v, m, e, part, nb);
+        k_mv_stencil_col<float, NV, KZV, 5, PF><<<g, 256, 0, st>>>(v, m, e, part, nb);
       else
-        k_mv_stencil_col<float, NV, KZV, 2><<<g, 256, 0, st>>>(v, m, e, part, nb);
+        k_mv_stencil_col<float, NV, KZV, 2, PF><<<g, 256, 0, st>>>(v, m, e, part, nb);
   }
 }
 
@@ -956,6 +990,8 @@ int launch_mv_stencil32(int var, const float* v, int m, const MvEpi<float>& e, d
     case 1: launch_mv_col<NV, 16>(g, nb, v, m, e, part, st); break;
     case 2: launch_mv_col<NV, 32>(g, nb, v, m, e, part, st); break;
     case 3: launch_mv_col<NV, 64>(g, nb, v, m, e, part, st); break;
+    case 4: launch_mv_col<NV, 16, 4>(g, nb, v, m, e, part, st); break;
+    case 5: launch_mv_col<NV, 32, 4>(g, nb, v, m, e, part, st); break;
     default: k_mv_stencil<float, NV><<<g, 256, 0, st>>>(v, m, e, part, nb); break;
   }
   FEM_CHECK_LAUNCH();

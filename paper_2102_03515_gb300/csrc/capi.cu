@@ -389,6 +389,59 @@ fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stre
   });
 }
 
+fem_status amg_vcycle_graph(amg_hier h, const double* r_dev, double* z_dev, int32_t reps,
+                            void* stream, double* ms_out) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(h && r_dev && z_dev && reps >= 1, FEM_EINVAL, "amg_vcycle_graph: bad argument");
+    cudaStream_t st = as_stream(stream);
+    // one application on the caller's stream first: it settles every launch shape and
+    // allocation, so the captured graph holds kernels only
+    vcycle(h->H, r_dev, z_dev, st, nullptr);
+    cudaStream_t cs;
+    FEM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    FEM_CUDA(cudaEventCreate(&e0));
+    FEM_CUDA(cudaEventCreate(&e1));
+    FEM_CUDA(cudaEventRecord(e0, st));
+    FEM_CUDA(cudaStreamWaitEvent(cs, e0, 0));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const long long c0 = launches_now();
+    FEM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+      vcycle(h->H, r_dev, z_dev, cs, nullptr);
+    } catch (...) {
+      cudaStreamEndCapture(cs, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cs);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    FEM_CUDA(cudaStreamEndCapture(cs, &graph));
+    const long long per = launches_now() - c0;
+    count_launches(-per);
+    FEM_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    FEM_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < reps; i++) {
+      FEM_CUDA(cudaGraphLaunch(exec, st));
+      count_launches(per);
+    }
+    FEM_CUDA(cudaEventRecord(e1, st));
+    FEM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_out) *ms_out = (double)ms / reps;
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return FEM_OK;
+  });
+}
+
 void amg_hier_destroy(amg_hier h) {
   if (!h) return;
   cudaDeviceSynchronize();

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-STENCIL_VARIANTS = 6
+STENCIL_VARIANTS = 8
 CSR_VARIANTS = 6
 
 
@@ -182,7 +182,7 @@ def test_every_multivector_variant_solves_to_the_oracle(fa, n, jit):
             refs.append(core.cholesky_solve(s.A(rhos[k]).toarray(), s.f))
         cases = [("mv_csr_f32", v) for v in range(3)]
         cases += [("mv_csr_f64", v) for v in range(3)] if jit else \
-            [("mv_stencil_f32", v) for v in range(4)]
+            [("mv_stencil_f32", v) for v in range(6)]
         for family, v in cases:
             fa.fem_autotune_pin(family, v)
             U = torch.zeros((N, nrhs), dtype=torch.float64, device="cuda")
@@ -220,4 +220,23 @@ def test_batched_session_tunes_its_shapes(fa):
         assert any(e["kernel"] == "mv_csr_f32" for e in mv), mv
     finally:
         fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+
+
+def test_graph_replayed_vcycle_equals_the_plain_one(fa):
+    n = 33
+    N = (n - 1) ** 3
+    sys_ = fa.fem_assemble(n, 1.0 / n ** 2, W.sine_target())
+    try:
+        for prec in (0, 1):
+            h = fa.amg_setup(sys_, precision=prec)
+            r = _dev(W.random_vector(N, 4))
+            z1 = torch.empty_like(r)
+            z2 = torch.full_like(r, float("nan"))
+            fa.amg_vcycle(h, r, z1)
+            ms = fa.amg_vcycle_graph(h, r, z2, reps=5)
+            fa.amg_hier_destroy(h)
+            assert ms > 0
+            assert torch.equal(z1, z2)
+    finally:
         fa.fem_system_destroy(sys_)
