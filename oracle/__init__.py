@@ -8,4 +8,6 @@ no code with the CUDA library ``paper_2102_03515_gb300`` and never imports it.
   Cholesky, error norms), loaded through ctypes.
 * :mod:`oracle.amg`   -- numpy/scipy smoothed-aggregation hierarchy, V-cycle and
   (flexible) PCG.
+* :mod:`oracle.refine` -- longest-edge bisection with conforming closure (the local
+  refinement of the adaptive runs, Sec. 4.2-4.3).
 """

@@ -345,6 +345,75 @@ def recover(system: System, rho: float, u: np.ndarray, target: dict):
     return z, p
 
 
+def tet_gradients(xyz: np.ndarray, tets: np.ndarray):
+    """(volume [nt], barycentric gradients [nt, 4, 3]) of every tet: with E the 3x3 matrix of
+    edge vectors x_a - x_0 (rows, a = 1..3), grad lambda_a are the columns of E^{-1} and
+    grad lambda_0 = -sum of the others."""
+    X = xyz[tets]
+    E = X[:, 1:, :] - X[:, :1, :]
+    det = np.linalg.det(E)
+    G = np.linalg.inv(E).transpose(0, 2, 1)          # row a-1 = grad lambda_a
+    g = np.concatenate([-G.sum(axis=1, keepdims=True), G], axis=1)
+    return np.abs(det) / 6.0, g
+
+
+def error_indicator(system: System, rho: float, u: np.ndarray, target: dict, qlevel: int = 1):
+    """Residual error indicator of the reaction-diffusion problem -rho Lap u + u = ubar
+    (the paper's adaptive runs, Sec. 4.2-4.3, use a residual indicator after Verfurth; this is
+    Verfurth's robust estimator for -eps Lap u + u = f with eps = rho), per tet:
+
+        eta_T^2 = a_T^2 ||ubar - u_h||^2_T + 1/2 sum_{interior faces F of T}
+                  rho^{-1/2} a_F |F| (rho [grad u_h . n_F])^2,   a_S = min(h_S / sqrt(rho), 1),
+
+    h_T, h_F the longest edge of T and F (Lap u_h = 0 on P1 elements; the jump of the
+    normal derivative is constant on a face).  The volume integral uses the rule of
+    :func:`qrule` of the given level.  Returns eta_T^2 [nt]."""
+    xyz, tets = system.xyz, np.asarray(system.tets, dtype=np.int64)
+    U = system.full_vector(u)
+    vol, g = tet_gradients(xyz, tets)
+    gu = np.einsum("ta,tad->td", U[tets], g)            # grad u_h per tet
+    X = xyz[tets]
+    edges = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    hT = np.max([np.linalg.norm(X[:, a] - X[:, b], axis=1) for a, b in edges], axis=0)
+    aT = np.minimum(hT / np.sqrt(rho), 1.0)
+    bary, wt = qrule(qlevel)
+    pts = np.einsum("qa,tad->tqd", bary, X)
+    ub = target_values(target, pts.reshape(-1, 3)).reshape(len(tets), -1)
+    uh = np.einsum("qa,ta->tq", bary, U[tets])
+    eta2 = aT ** 2 * vol * ((ub - uh) ** 2 @ wt)
+    # interior faces: the face opposite vertex a of each tet, matched by its vertex set
+    faces = np.stack([np.delete(tets, a, axis=1) for a in range(4)], axis=1)   # [nt, 4, 3]
+    keys = np.sort(faces, axis=2).reshape(-1, 3)
+    owner = np.repeat(np.arange(len(tets)), 4)
+    order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+    k, o = keys[order], owner[order]
+    same = np.all(k[1:] == k[:-1], axis=1)
+    i1 = np.flatnonzero(same)
+    t1, t2 = o[i1], o[i1 + 1]
+    F = xyz[k[i1]]                                      # [nf, 3, 3]
+    cr = np.cross(F[:, 1] - F[:, 0], F[:, 2] - F[:, 0])
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    n = cr / np.linalg.norm(cr, axis=1, keepdims=True)
+    jump = np.einsum("fd,fd->f", gu[t1] - gu[t2], n)
+    hF = np.max([np.linalg.norm(F[:, a] - F[:, b], axis=1) for a, b in ((0, 1), (0, 2), (1, 2))],
+                axis=0)
+    aF = np.minimum(hF / np.sqrt(rho), 1.0)
+    c = rho ** -0.5 * aF * area * (rho * jump) ** 2
+    np.add.at(eta2, t1, 0.5 * c)
+    np.add.at(eta2, t2, 0.5 * c)
+    return eta2
+
+
+def dorfler_mark(eta2: np.ndarray, theta: float = 0.5) -> np.ndarray:
+    """Bulk marking: the tets with eta_T^2 >= t for the largest t such that the marked tets
+    carry at least theta * sum eta^2 (ties at t are all marked)."""
+    order = np.sort(eta2)[::-1]
+    csum = np.cumsum(order)
+    k = int(np.searchsorted(csum, theta * csum[-1]))
+    t = order[min(k, len(order) - 1)]
+    return eta2 >= t
+
+
 def kuhn_rows(n: int, target: dict, rows, xyz: np.ndarray | None = None, qlevel: int = 0):
     """Rows (unknown indices) of K, M and f for selected unknowns, without assembling the mesh.
 
