@@ -198,6 +198,85 @@ fem_status fem_errors(fem_system sys, const double* u_dev, const fem_target* tar
 fem_status fem_recover(fem_system sys, const double* u_dev, const fem_target* target,
                        double* z_dev, double* p_dev, void* stream);
 
+/* ------------------------------------------------------------------ adaptive meshes */
+
+/* The adaptive runs of Sec. 4.2-4.3 refine the mesh where a residual error indicator is
+ * large.  These calls keep a general tetrahedral mesh on the device, compute the indicator
+ * of a solution on it, mark the tets with the largest indicators and refine them locally,
+ * so that solve -> estimate -> mark -> refine -> assemble runs without host copies of the
+ * mesh. */
+
+/* Residual error indicator of the reduced problem -rho Lap u + u = ubar (eq. (linsys) in
+ * strong form) for the P1 solution u_dev (length N, zero on Dirichlet vertices) on a system
+ * from fem_assemble_mesh / fem_assemble_on_mesh: per tet T, after Verfurth's robust
+ * estimator for reaction-diffusion problems,
+ *   eta_T^2 = a_T^2 ||ubar - u_h||^2_{L2(T)}
+ *           + 1/2 sum_{interior faces F of T} rho^{-1/2} a_F |F| (rho [grad u_h . n_F])^2,
+ *   a_S = min(h_S / sqrt(rho), 1),  h_S the longest edge of S,
+ * rho the system's.  The volume integral uses the rule of fem_errors of the given qlevel
+ * (0..2).  eta2_dev: device array of nt doubles (nt of the mesh, tets in the mesh's order);
+ * *total (may be null) receives sum_T eta_T^2 (fixed-order reduction).  Errors: FEM_EINVAL
+ * (null argument, Kuhn-mesh system, qlevel out of range, bad target, a face shared by more
+ * than two tets). */
+fem_status fem_error_indicator(fem_system sys, const double* u_dev, const fem_target* target,
+                               int32_t qlevel, double* eta2_dev, void* stream, double* total);
+
+/* Bulk marking: with S(t) = sum of the eta2_dev[i] >= t and t* the largest double with
+ * S(t*) >= theta * S(0), mark_dev[i] = (eta2_dev[i] >= t*) (ties at t* all marked; nothing is
+ * marked when every value is 0).  t* is found by bisection on the bits of non-negative
+ * doubles, each S by a fixed-order reduction.  eta2_dev: n finite values >= 0 (device);
+ * mark_dev: n bytes (device).  *threshold and *nmarked may be null.  Errors: FEM_EINVAL
+ * (n < 1, theta outside (0, 1], a negative or non-finite value). */
+fem_status fem_mark_bulk(const double* eta2_dev, int64_t n, double theta, uint8_t* mark_dev,
+                         void* stream, double* threshold, int64_t* nmarked);
+
+typedef struct fem_mesh_s* fem_mesh;
+
+/* Copy a conforming mesh (fem_mesh_desc, host arrays) to the device.  The mesh must be a
+ * manifold partition: every face in one or two tets (FEM_EINVAL otherwise, and for a zero
+ * volume or a vertex index out of range).  The Dirichlet flags must mark the vertices on the
+ * boundary: refinement flags its new boundary vertices the same way. */
+fem_status fem_mesh_create(const fem_mesh_desc* mesh, void* stream, fem_mesh* out);
+
+typedef struct {
+  int64_t nv;
+  int64_t nt;
+} fem_mesh_info;
+fem_status fem_mesh_get_info(fem_mesh m, fem_mesh_info* info);
+
+/* Copy the mesh to host arrays of nv * 3 doubles, nt * 4 int32 and nv bytes (any may be
+ * null). */
+fem_status fem_mesh_download(fem_mesh m, double* xyz, int32_t* tet, uint8_t* dirichlet,
+                             void* stream);
+
+/* Local refinement by longest-edge bisection (Rivara) with conforming closure: every tet
+ * with mark_dev[t] != 0 (device, nt bytes of the current mesh) is bisected on its longest
+ * edge, and every tet that then holds a bisected edge is bisected on its own longest edge,
+ * in passes, until the mesh is conforming again.  Deterministic:
+ *   - edge order: squared length (dx*dx + dy*dy) + dz*dz without fused multiply-add, ties
+ *     to the smaller vertex pair (min, max);
+ *   - a tet (v0..v3) with longest edge at local positions i < j and midpoint
+ *     m = 0.5 * (x_a + x_b) becomes, at its index, the tet with v_j replaced by m, and the
+ *     tet with v_i replaced by m is appended; appended tets follow their parents' order;
+ *   - the new vertices of a pass follow the order of the first tet that bisects their edge;
+ *   - a new vertex is a Dirichlet vertex when it lies on a boundary face.
+ * stats (may be null): passes, new vertices and new tets.  Errors: FEM_EINVAL (null
+ * argument), FEM_EUNSUPPORTED (2^31 tets or vertices). */
+typedef struct {
+  int32_t passes;
+  int64_t new_vertices;
+  int64_t new_tets;
+} fem_refine_stats;
+fem_status fem_mesh_refine(fem_mesh m, const uint8_t* mark_dev, void* stream,
+                           fem_refine_stats* stats);
+
+/* fem_assemble_mesh on a device mesh (the mesh is copied: it may be refined or destroyed
+ * afterwards). */
+fem_status fem_assemble_on_mesh(fem_mesh m, double rho, const fem_target* target,
+                                const fem_assemble_opts* opts, void* stream, fem_system* out);
+
+void fem_mesh_destroy(fem_mesh m);
+
 /* ------------------------------------------------------------------ AMG */
 
 /* Smoothers: Chebyshev of degree `degree` on D^{-1}A, one l1-Jacobi step, or symmetric

@@ -406,9 +406,11 @@ def error_indicator(system: System, rho: float, u: np.ndarray, target: dict, qle
 
 def dorfler_mark(eta2: np.ndarray, theta: float = 0.5) -> np.ndarray:
     """Bulk marking: the tets with eta_T^2 >= t for the largest t such that the marked tets
-    carry at least theta * sum eta^2 (ties at t are all marked)."""
+    carry at least theta * sum eta^2 (ties at t are all marked; none when every eta is 0)."""
     order = np.sort(eta2)[::-1]
     csum = np.cumsum(order)
+    if not csum[-1] > 0.0:
+        return np.zeros(len(eta2), dtype=bool)          # nothing to refine
     k = int(np.searchsorted(csum, theta * csum[-1]))
     t = order[min(k, len(order) - 1)]
     return eta2 >= t

@@ -99,6 +99,14 @@ class ErrorsResult(C.Structure):
     _fields_ = [("l2sq", C.c_double), ("h1sq", C.c_double)]
 
 
+class MeshInfo(C.Structure):
+    _fields_ = [("nv", C.c_int64), ("nt", C.c_int64)]
+
+
+class RefineStats(C.Structure):
+    _fields_ = [("passes", C.c_int32), ("new_vertices", C.c_int64), ("new_tets", C.c_int64)]
+
+
 SIGNATURES = {
     "fem_assemble": (C.c_int, [P(KuhnDesc), C.c_double, P(Target), P(AssembleOpts), VP, P(VP)]),
     "fem_system_get_info": (C.c_int, [VP, P(SystemInfo)]),
@@ -109,6 +117,15 @@ SIGNATURES = {
                                     P(VP)]),
     "fem_errors": (C.c_int, [VP, VP, P(Target), C.c_double, C.c_int32, VP, P(ErrorsResult)]),
     "fem_recover": (C.c_int, [VP, VP, P(Target), VP, VP, VP]),
+    "fem_error_indicator": (C.c_int, [VP, VP, P(Target), C.c_int32, VP, VP, P(C.c_double)]),
+    "fem_mark_bulk": (C.c_int, [VP, C.c_int64, C.c_double, VP, VP, P(C.c_double),
+                                P(C.c_int64)]),
+    "fem_mesh_create": (C.c_int, [P(MeshDesc), VP, P(VP)]),
+    "fem_mesh_get_info": (C.c_int, [VP, P(MeshInfo)]),
+    "fem_mesh_download": (C.c_int, [VP, VP, VP, VP, VP]),
+    "fem_mesh_refine": (C.c_int, [VP, VP, VP, P(RefineStats)]),
+    "fem_assemble_on_mesh": (C.c_int, [VP, C.c_double, P(Target), P(AssembleOpts), VP, P(VP)]),
+    "fem_mesh_destroy": (None, [VP]),
     "fem_system_export": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
     "fem_spmv": (C.c_int, [VP, VP, VP, VP]),
     "fem_system_destroy": (None, [VP]),
@@ -292,6 +309,83 @@ def fem_assemble_mesh(xyz, tets, dirichlet, rho: float, target: dict, keep_penci
     _check(lib().fem_assemble_mesh(C.byref(d), rho, C.byref(t), C.byref(o), _stream(stream),
                                    C.byref(h)), "fem_assemble_mesh")
     return h
+
+
+# ------------------------------------------------------------------ adaptive meshes
+
+def fem_error_indicator(sys, u, target: dict, eta2, qlevel: int = 1, stream=None) -> float:
+    """Residual indicator eta_T^2 of every tet into eta2 (device, nt doubles); returns the
+    sum."""
+    keep = []
+    t = _target(target, keep)
+    tot = C.c_double()
+    _check(lib().fem_error_indicator(sys, _ptr(u), C.byref(t), int(qlevel), _ptr(eta2),
+                                     _stream(stream), C.byref(tot)), "fem_error_indicator")
+    return tot.value
+
+
+def fem_mark_bulk(eta2, theta: float, mark, stream=None):
+    """Bulk marking of eta2 (device doubles) into mark (device uint8); returns
+    (threshold, number marked)."""
+    thr = C.c_double()
+    nm = C.c_int64()
+    _check(lib().fem_mark_bulk(_ptr(eta2), int(eta2.numel()), float(theta), _ptr(mark),
+                               _stream(stream), C.byref(thr), C.byref(nm)), "fem_mark_bulk")
+    return thr.value, nm.value
+
+
+def fem_mesh_create(xyz, tets, dirichlet, stream=None):
+    """Copy a conforming tetrahedral mesh (host arrays) to the device; returns the handle."""
+    xa = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    ta = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    da = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
+    assert len(da) == len(xa)
+    d = MeshDesc(len(xa), len(ta), _dp(xa), ta.ctypes.data_as(P(C.c_int32)),
+                 da.ctypes.data_as(P(C.c_uint8)))
+    h = VP()
+    _check(lib().fem_mesh_create(C.byref(d), _stream(stream), C.byref(h)), "fem_mesh_create")
+    return h
+
+
+def fem_mesh_get_info(mesh) -> dict:
+    i = MeshInfo()
+    _check(lib().fem_mesh_get_info(mesh, C.byref(i)), "fem_mesh_get_info")
+    return {"nv": i.nv, "nt": i.nt}
+
+
+def fem_mesh_download(mesh, stream=None):
+    """(xyz [nv, 3], tets [nt, 4] int32, dirichlet [nv] uint8) as numpy arrays."""
+    i = fem_mesh_get_info(mesh)
+    xyz = np.empty((i["nv"], 3), dtype=np.float64)
+    tets = np.empty((i["nt"], 4), dtype=np.int32)
+    d = np.empty(i["nv"], dtype=np.uint8)
+    _check(lib().fem_mesh_download(mesh, VP(xyz.ctypes.data), VP(tets.ctypes.data),
+                                   VP(d.ctypes.data), _stream(stream)), "fem_mesh_download")
+    return xyz, tets, d
+
+
+def fem_mesh_refine(mesh, mark, stream=None) -> dict:
+    """Longest-edge bisection of the tets with mark[t] != 0 (device uint8) and closure."""
+    r = RefineStats()
+    _check(lib().fem_mesh_refine(mesh, _ptr(mark), _stream(stream), C.byref(r)),
+           "fem_mesh_refine")
+    return {"passes": r.passes, "new_vertices": r.new_vertices, "new_tets": r.new_tets}
+
+
+def fem_assemble_on_mesh(mesh, rho: float, target: dict, keep_pencil: bool = False,
+                         stream=None):
+    """fem_assemble_mesh on a device mesh; returns the system handle."""
+    keep = []
+    t = _target(target, keep)
+    o = AssembleOpts(FEM_FMT_CSR, 1 if keep_pencil else 0)
+    h = VP()
+    _check(lib().fem_assemble_on_mesh(mesh, float(rho), C.byref(t), C.byref(o), _stream(stream),
+                                      C.byref(h)), "fem_assemble_on_mesh")
+    return h
+
+
+def fem_mesh_destroy(mesh) -> None:
+    lib().fem_mesh_destroy(mesh)
 
 
 def fem_system_get_info(sys) -> dict:

@@ -17,9 +17,10 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libfemamg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["assemble.cu", "ops.cu", "amg_setup.cu", "solve.cu", "batched.cu", "autotune.cu", "capi.cu"]
+SOURCES = ["assemble.cu", "ops.cu", "amg_setup.cu", "solve.cu", "batched.cu", "autotune.cu", "adapt.cu",
+           "capi.cu"]
 # element arithmetic is kept free of FMA contraction (plain IEEE products and sums)
-NO_FMAD = {"assemble.cu"}
+NO_FMAD = {"assemble.cu", "adapt.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

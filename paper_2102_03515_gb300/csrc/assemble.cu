@@ -857,6 +857,114 @@ __global__ void k_gm_errors(int64_t nt, const int32_t* tet, const int32_t* vdof,
   }
 }
 
+// The other tet of the face (b, c, d) of tet t: walks the tets around b (sorted, short) and
+// keeps those holding c and d.  -1 on the boundary, -2 when more than one tet has the face.
+__device__ __forceinline__ int64_t face_neighbour(int64_t t, int32_t b, int32_t c, int32_t d,
+                                                  const int64_t* vptr, const int32_t* vtet,
+                                                  const int32_t* tet) {
+  int64_t found = -1;
+  for (int64_t e = vptr[b]; e < vptr[b + 1]; e++) {
+    const int32_t s = vtet[e];
+    if (s == t) continue;
+    const int4 v = reinterpret_cast<const int4*>(tet)[s];
+    const bool hc = v.x == c || v.y == c || v.z == c || v.w == c;
+    const bool hd = v.x == d || v.y == d || v.z == d || v.w == d;
+    if (hc && hd) {
+      if (found >= 0) return -2;
+      found = s;
+    }
+  }
+  return found;
+}
+
+__device__ __forceinline__ double len2_rn(const double* a, const double* b) {
+  const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Residual error indicator of -rho Lap u + u = ubar on P1 elements (robust residual
+// estimator after Verfurth), one thread per tet, grid-stride over a fixed grid:
+//   eta_T^2 = a_T^2 ||ubar - u_h||^2_T
+//           + 1/2 sum_{interior faces F} rho^{-1/2} a_F |F| (rho [grad u_h . n_F])^2,
+// a_S = min(h_S / sqrt(rho), 1), h_S the longest edge of S; the volume integral by the
+// quadrature (qb, qw).  Writes eta2[t] and per-block partial sums of eta2.
+__global__ void k_gm_indicator(int64_t nt, const int32_t* __restrict__ tet,
+                               const int32_t* __restrict__ vdof, const double* __restrict__ xyz,
+                               const double* __restrict__ u, const int64_t* __restrict__ vptr,
+                               const int32_t* __restrict__ vtet, TargetDev T, double rho,
+                               const double* __restrict__ qb, const double* __restrict__ qw,
+                               int np, double* __restrict__ eta2, double* partials,
+                               unsigned long long* bad) {
+  const double srho = sqrt(rho), rho_m12 = 1.0 / srho;
+  double acc[1] = {0.0};
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 tv = reinterpret_cast<const int4*>(tet)[t];
+    const int32_t v[4] = {tv.x, tv.y, tv.z, tv.w};
+    double X[4][3], g[4][3], U[4];
+    for (int a = 0; a < 4; a++) {
+      const int32_t w = vdof[v[a]];
+      U[a] = w >= 0 ? u[w] : 0.0;
+      for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)v[a] + d];
+    }
+    const double vol = fabs(tet_grads(X, g)) / 6.0;
+    double gu[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; a++)
+      for (int d = 0; d < 3; d++) gu[d] += U[a] * g[a][d];
+    double h2 = 0.0;
+    for (int a = 0; a < 4; a++)
+      for (int b = a + 1; b < 4; b++) h2 = fmax(h2, len2_rn(X[a], X[b]));
+    const double aT = fmin(sqrt(h2) / srho, 1.0);
+    double e2 = 0.0;
+    for (int q = 0; q < np; q++) {
+      double x[3] = {0.0, 0.0, 0.0}, uh = 0.0;
+      for (int a = 0; a < 4; a++) {
+        const double bq = qb[4 * q + a];
+        for (int d = 0; d < 3; d++) x[d] += bq * X[a][d];
+        uh += bq * U[a];
+      }
+      const double diff = target_eval(T, x[0], x[1], x[2]) - uh;
+      e2 += qw[q] * diff * diff;
+    }
+    double eta = aT * aT * vol * e2;
+    for (int a = 0; a < 4; a++) {
+      const int i0 = (a + 1) & 3, i1 = (a + 2) & 3, i2 = (a + 3) & 3;
+      const int64_t s = face_neighbour(t, v[i0], v[i1], v[i2], vptr, vtet, tet);
+      if (s == -2) atomicAdd(bad, 1ull);
+      if (s < 0) continue;
+      const int4 sv = reinterpret_cast<const int4*>(tet)[s];
+      const int32_t w4[4] = {sv.x, sv.y, sv.z, sv.w};
+      double Y[4][3], gs[4][3], V[4];
+      for (int b = 0; b < 4; b++) {
+        const int32_t w = vdof[w4[b]];
+        V[b] = w >= 0 ? u[w] : 0.0;
+        for (int d = 0; d < 3; d++) Y[b][d] = xyz[3 * (int64_t)w4[b] + d];
+      }
+      tet_grads(Y, gs);
+      double jg[3] = {gu[0], gu[1], gu[2]};
+      for (int b = 0; b < 4; b++)
+        for (int d = 0; d < 3; d++) jg[d] -= V[b] * gs[b][d];
+      const double* P0 = X[i0];
+      const double* P1 = X[i1];
+      const double* P2 = X[i2];
+      const double e1[3] = {P1[0] - P0[0], P1[1] - P0[1], P1[2] - P0[2]};
+      const double e2v[3] = {P2[0] - P0[0], P2[1] - P0[1], P2[2] - P0[2]};
+      const double cr[3] = {e1[1] * e2v[2] - e1[2] * e2v[1], e1[2] * e2v[0] - e1[0] * e2v[2],
+                            e1[0] * e2v[1] - e1[1] * e2v[0]};
+      const double cn = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      const double jump = (jg[0] * cr[0] + jg[1] * cr[1] + jg[2] * cr[2]) / cn;
+      const double hF2 = fmax(fmax(len2_rn(P0, P1), len2_rn(P0, P2)), len2_rn(P1, P2));
+      const double aF = fmin(sqrt(hF2) / srho, 1.0);
+      const double rj = rho * jump;
+      eta += 0.5 * (rho_m12 * aF * (0.5 * cn) * (rj * rj));
+    }
+    eta2[t] = eta;
+    acc[0] += eta;
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
 __global__ void k_gm_recover(int64_t N, const int64_t* rvert, const double* xyz, TargetDev T,
                              double rho, const double* __restrict__ u, double* z, double* p) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1047,6 +1155,45 @@ void assemble_mesh(System& S, const fem_mesh_desc& mesh, double rho, const fem_t
               FEM_EINVAL, "fem_assemble_mesh: bad sizes");
   FEM_REQUIRE(mesh.xyz && mesh.tet && mesh.dirichlet, FEM_EINVAL,
               "fem_assemble_mesh: null array");
+  DevBuf<double> xyz(3 * nv, st);
+  DevBuf<int32_t> tet(4 * nt, st);
+  DevBuf<uint8_t> dir(nv, st);
+  FEM_CUDA(cudaMemcpyAsync(xyz, mesh.xyz, 24 * nv, cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(tet, mesh.tet, 16 * nt, cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(dir, mesh.dirichlet, nv, cudaMemcpyHostToDevice, st));
+  assemble_mesh_dev(S, nv, nt, xyz, tet, dir, rho, t, o, st);
+}
+
+void build_incidence(int64_t nv, int64_t nt, const int32_t* tet, DevBuf<int64_t>& vptr,
+                     DevBuf<int32_t>& vtet, cudaStream_t st) {
+  DevBuf<int64_t> cnt(nv, st);
+  DevBuf<unsigned long long> flags(2, st);
+  FEM_CUDA(cudaMemsetAsync(cnt, 0, 8 * nv, st));
+  FEM_CUDA(cudaMemsetAsync(flags, 0, 16, st));
+  const unsigned gt = grid_for(nt, 256);
+  k_gm_inc_count<<<gt, 256, 0, st>>>(nt, tet, nv, cnt, flags);
+  FEM_CHECK_LAUNCH();
+  unsigned long long hf = 0;
+  FEM_CUDA(cudaMemcpyAsync(&hf, flags, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(hf == 0, FEM_EINVAL, "mesh: a tet vertex index is out of range");
+  vptr.alloc(nv + 1);
+  const int64_t ninc = exclusive_scan(cnt, nv, vptr, st);
+  vtet.alloc(ninc);
+  FEM_CUDA(cudaMemsetAsync(cnt, 0, 8 * nv, st));
+  k_gm_inc_fill<<<gt, 256, 0, st>>>(nt, tet, vptr, reinterpret_cast<unsigned long long*>(cnt.p),
+                                    vtet);
+  FEM_CHECK_LAUNCH();
+  k_gm_inc_sort<<<grid_for(nv, 256), 256, 0, st>>>(nv, vptr, vtet, flags.p + 1);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
+void assemble_mesh_dev(System& S, int64_t nv, int64_t nt, const double* xyz_dev,
+                       const int32_t* tet_dev, const uint8_t* dir, double rho,
+                       const fem_target& t, const fem_assemble_opts& o, cudaStream_t st) {
+  FEM_REQUIRE(nv >= 4 && nt >= 1 && nt < ((int64_t)1 << 31) && nv < ((int64_t)1 << 31),
+              FEM_EINVAL, "fem_assemble_mesh: bad sizes");
   FEM_REQUIRE(rho > 0.0 && std::isfinite(rho), FEM_EINVAL, "fem_assemble_mesh: rho must be > 0");
   FEM_REQUIRE(o.format == FEM_FMT_AUTO || o.format == FEM_FMT_CSR, FEM_EINVAL,
               "fem_assemble_mesh: a general mesh has no stencil format");
@@ -1063,10 +1210,8 @@ void assemble_mesh(System& S, const fem_mesh_desc& mesh, double rho, const fem_t
   Tracer tr(st);
   S.xyz.alloc_async(3 * nv, st);
   S.tet.alloc_async(4 * nt, st);
-  DevBuf<uint8_t> dir(nv, st);
-  FEM_CUDA(cudaMemcpyAsync(S.xyz, mesh.xyz, 24 * nv, cudaMemcpyHostToDevice, st));
-  FEM_CUDA(cudaMemcpyAsync(S.tet, mesh.tet, 16 * nt, cudaMemcpyHostToDevice, st));
-  FEM_CUDA(cudaMemcpyAsync(dir, mesh.dirichlet, nv, cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(S.xyz, xyz_dev, 24 * nv, cudaMemcpyDeviceToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(S.tet, tet_dev, 16 * nt, cudaMemcpyDeviceToDevice, st));
   const unsigned gv = grid_for(nv, 256), gt = grid_for(nt, 256);
   // unknowns
   DevBuf<int64_t> flag(nv, st), scan(nv + 1, st);
@@ -1160,6 +1305,37 @@ void fem_error_norms(System& S, const double* u, const fem_target& t, double sca
   FEM_CUDA(cudaMemcpyAsync(out, sums, 16, cudaMemcpyDeviceToHost, st));
   FEM_CUDA(cudaStreamSynchronize(st));
   if (!grad) out[1] = std::nan("");
+}
+
+double error_indicator(System& S, const double* u, const fem_target& t, int qlevel,
+                       double* eta2, cudaStream_t st) {
+  FEM_REQUIRE(S.general, FEM_EINVAL,
+              "fem_error_indicator: general meshes only (assemble Kuhn meshes with "
+              "fem_assemble_mesh to use it)");
+  FEM_REQUIRE(qlevel >= 0 && qlevel <= 2, FEM_EINVAL, "fem_error_indicator: qlevel in [0, 2]");
+  TargetHolder th;
+  target_to_device(t, th, st);
+  std::vector<double> bary, wt;
+  const double P[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+  bey_rule(P, qlevel, 1.0, bary, wt);
+  DevBuf<double> qb(bary.size(), st), qw(wt.size(), st);
+  FEM_CUDA(cudaMemcpyAsync(qb, bary.data(), 8 * bary.size(), cudaMemcpyHostToDevice, st));
+  FEM_CUDA(cudaMemcpyAsync(qw, wt.data(), 8 * wt.size(), cudaMemcpyHostToDevice, st));
+  const unsigned g = persistent_grid(S.nt, 128, 8);
+  DevBuf<double> part(g, st), sum(1, st);
+  DevBuf<unsigned long long> bad(1, st);
+  FEM_CUDA(cudaMemsetAsync(bad, 0, 8, st));
+  k_gm_indicator<<<g, 128, 0, st>>>(S.nt, S.tet, S.vdof, S.xyz, u, S.vptr, S.vtet, th.T, S.rho,
+                                    qb, qw, (int)wt.size(), eta2, part, bad);
+  FEM_CHECK_LAUNCH();
+  finalize_sums(part, (int)g, 1, sum, st);
+  double out = 0.0;
+  unsigned long long hb = 0;
+  FEM_CUDA(cudaMemcpyAsync(&out, sum, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaMemcpyAsync(&hb, bad, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  FEM_REQUIRE(hb == 0, FEM_EINVAL, "fem_error_indicator: a face belongs to more than two tets");
+  return out;
 }
 
 void fem_recovery(System& S, const double* u, const fem_target& t, double* z, double* p,

@@ -91,6 +91,9 @@ struct amg_hier_s {
   fem::Hierarchy H;
   fem_system_s* sys = nullptr;
 };
+struct fem_mesh_s {
+  fem::Mesh M;
+};
 struct pcg_batch_s {
   fem::BatchSession* W = nullptr;
   fem_system_s* sys = nullptr;
@@ -206,6 +209,105 @@ fem_status fem_recover(fem_system sys, const double* u_dev, const fem_target* ta
     return FEM_OK;
   });
 }
+
+fem_status fem_error_indicator(fem_system sys, const double* u_dev, const fem_target* target,
+                               int32_t qlevel, double* eta2_dev, void* stream, double* total) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && u_dev && target && eta2_dev, FEM_EINVAL,
+                "fem_error_indicator: null argument");
+    StreamScope scope(as_stream(stream));
+    const double s = error_indicator(sys->S, u_dev, *target, qlevel, eta2_dev, as_stream(stream));
+    if (total) *total = s;
+    return FEM_OK;
+  });
+}
+
+fem_status fem_mark_bulk(const double* eta2_dev, int64_t n, double theta, uint8_t* mark_dev,
+                         void* stream, double* threshold, int64_t* nmarked) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(eta2_dev && mark_dev, FEM_EINVAL, "fem_mark_bulk: null argument");
+    StreamScope scope(as_stream(stream));
+    mark_bulk(eta2_dev, n, theta, mark_dev, as_stream(stream), threshold, nmarked);
+    return FEM_OK;
+  });
+}
+
+fem_status fem_mesh_create(const fem_mesh_desc* mesh, void* stream, fem_mesh* out) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(mesh && out, FEM_EINVAL, "fem_mesh_create: null argument");
+    *out = nullptr;
+    StreamScope scope(as_stream(stream));
+    init_memory_pool();
+    auto* h = new fem_mesh_s();
+    try {
+      mesh_create(h->M, *mesh, as_stream(stream));
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return FEM_OK;
+  });
+}
+
+fem_status fem_mesh_get_info(fem_mesh m, fem_mesh_info* info) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(m && info, FEM_EINVAL, "fem_mesh_get_info: null argument");
+    info->nv = m->M.nv;
+    info->nt = m->M.nt;
+    return FEM_OK;
+  });
+}
+
+fem_status fem_mesh_download(fem_mesh m, double* xyz, int32_t* tet, uint8_t* dirichlet,
+                             void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(m, FEM_EINVAL, "fem_mesh_download: null mesh");
+    cudaStream_t st = as_stream(stream);
+    const Mesh& M = m->M;
+    if (xyz) FEM_CUDA(cudaMemcpyAsync(xyz, M.xyz, 24 * M.nv, cudaMemcpyDeviceToHost, st));
+    if (tet) FEM_CUDA(cudaMemcpyAsync(tet, M.tet, 16 * M.nt, cudaMemcpyDeviceToHost, st));
+    if (dirichlet) FEM_CUDA(cudaMemcpyAsync(dirichlet, M.dir, M.nv, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    return FEM_OK;
+  });
+}
+
+fem_status fem_mesh_refine(fem_mesh m, const uint8_t* mark_dev, void* stream,
+                           fem_refine_stats* stats) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(m && mark_dev, FEM_EINVAL, "fem_mesh_refine: null argument");
+    StreamScope scope(as_stream(stream));
+    fem_refine_stats r{0, 0, 0};
+    mesh_refine(m->M, mark_dev, as_stream(stream), r);
+    if (stats) *stats = r;
+    return FEM_OK;
+  });
+}
+
+fem_status fem_assemble_on_mesh(fem_mesh m, double rho, const fem_target* target,
+                                const fem_assemble_opts* opts, void* stream, fem_system* out) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(m && target && out, FEM_EINVAL, "fem_assemble_on_mesh: null argument");
+    *out = nullptr;
+    StreamScope scope(as_stream(stream));
+    fem_assemble_opts o{FEM_FMT_AUTO, 0};
+    if (opts) o = *opts;
+    init_memory_pool();
+    auto* h = new fem_system_s();
+    try {
+      assemble_mesh_dev(h->S, m->M.nv, m->M.nt, m->M.xyz, m->M.tet, m->M.dir, rho, *target, o,
+                        as_stream(stream));
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return FEM_OK;
+  });
+}
+
+void fem_mesh_destroy(fem_mesh m) { delete m; }
 
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream) {
   return guarded([&]() -> fem_status {

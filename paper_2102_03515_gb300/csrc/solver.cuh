@@ -41,6 +41,16 @@ struct System {
   DevBuf<int64_t> rvert, vptr;
 };
 
+// A general tetrahedral mesh kept on the device for adaptive refinement: boundary-face mask
+// per tet (bit k: the face opposite local vertex k lies on the boundary); dir is padded to a
+// multiple of 4 bytes.
+struct Mesh {
+  int64_t nv = 0, nt = 0;
+  DevBuf<double> xyz;
+  DevBuf<int32_t> tet;
+  DevBuf<uint8_t> dir, bmask;
+};
+
 struct Level {
   int64_t N = 0;
   bool stencil = false;
@@ -89,12 +99,29 @@ void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_
 // general tetrahedral mesh: nv vertices (xyz host), nt tets (host), Dirichlet flags (host)
 void assemble_mesh(System& S, const fem_mesh_desc& mesh, double rho, const fem_target& t,
                    const fem_assemble_opts& o, cudaStream_t st);
+// the same from device arrays (copied: the caller keeps them)
+void assemble_mesh_dev(System& S, int64_t nv, int64_t nt, const double* xyz_dev,
+                       const int32_t* tet_dev, const uint8_t* dir_dev, double rho,
+                       const fem_target& t, const fem_assemble_opts& o, cudaStream_t st);
+// vertex -> incident tets (vptr[nv + 1], vtet sorted per vertex); FEM_EINVAL on an index
+// out of range
+void build_incidence(int64_t nv, int64_t nt, const int32_t* tet, DevBuf<int64_t>& vptr,
+                     DevBuf<int32_t>& vtet, cudaStream_t st);
 // ||scale*t - u_h||^2 and ||grad(scale*t - u_h)||^2 (NaN without a gradient) by quadrature
 void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
                      double out[2], cudaStream_t st);
+// residual error indicator eta_T^2 of every tet of a general mesh (eta2[nt]); returns the sum
+double error_indicator(System& S, const double* u, const fem_target& t, int qlevel,
+                       double* eta2, cudaStream_t st);
 // z = (ubar - u) / rho and p = -rho u at the unknowns (either output may be null)
 void fem_recovery(System& S, const double* u, const fem_target& t, double* z, double* p,
                   cudaStream_t st);
+
+// ------------------------------------------------------------------ adaptivity (adapt.cu)
+void mesh_create(Mesh& M, const fem_mesh_desc& d, cudaStream_t st);
+void mesh_refine(Mesh& M, const uint8_t* mark, cudaStream_t st, fem_refine_stats& out);
+void mark_bulk(const double* eta, int64_t n, double theta, uint8_t* mark, cudaStream_t st,
+               double* threshold, int64_t* nmarked);
 
 // ------------------------------------------------------------------ operators (ops.cu)
 // Chebyshev coefficients of one smoothing application of degree k on [lmax/ratio, lmax].
