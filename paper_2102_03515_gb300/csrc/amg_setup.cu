@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(SG_BLOCK)
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
   const int64_t r = (int64_t)blockIdx.x * (SG_BLOCK / G) + grp;
   if (r >= nrows) return;
+  if (Crp[r + 1] - Crp[r] > HT / 2) return;   // a long row: k_long_fill writes it
   const unsigned mask = group_mask<G>();
   char* base = smem + (size_t)grp * (14 * HT);
   int* keys = reinterpret_cast<int*>(base);
@@ -559,6 +560,178 @@ __global__ void k_max_i64(const int64_t* v, int64_t n, unsigned long long* out) 
     m = max(m, (unsigned long long)v[i]);
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// ---- long rows (more distinct product columns than a shared-memory table holds): one block
+// per row, the hash table in global memory, the sorted column list and the accumulators in
+// shared memory.  The sums run in the order of A's row like the short path.
+constexpr int kLongRowMax = 8192;
+constexpr int kLongBlock = 256;
+
+__global__ void k_long_flag(int64_t n, const int64_t* cnt, int64_t limit, int64_t* flag) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) flag[r] = cnt[r] > limit ? 1 : 0;
+}
+
+// list of the long rows and the size of each one's table (power of two >= 2 * bound)
+__global__ void k_long_list(int64_t n, const int64_t* flag, const int64_t* scan,
+                            const int64_t* ub, int64_t* list, int64_t* tsz) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n || !flag[r]) return;
+  const int64_t i = scan[r];
+  list[i] = r;
+  int64_t t = 1024;
+  while (t < 2 * ub[r]) t <<= 1;
+  tsz[i] = t;
+}
+
+__global__ void __launch_bounds__(kLongBlock)
+    k_long_count(const int64_t* list, const int64_t* off, const int64_t* tsz, const int32_t* Arp,
+                 const int32_t* Acol, const int32_t* Brp, const int32_t* Bcol, int32_t* gkeys,
+                 int64_t* cnt) {
+  __shared__ int count;
+  const int64_t r = list[blockIdx.x];
+  int32_t* keys = gkeys + off[blockIdx.x];
+  const int64_t T = tsz[blockIdx.x];
+  for (int64_t q = threadIdx.x; q < T; q += blockDim.x) keys[q] = -1;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int e = Arp[r] + threadIdx.x; e < Arp[r + 1]; e += blockDim.x) {
+    const int k = Acol[e];
+    if (k < 0) continue;
+    for (int f = Brp[k]; f < Brp[k + 1]; f++) {
+      const int j = Bcol[f];
+      if (j < 0) continue;
+      uint32_t h = hslot(j, (int)(T - 1));
+      for (int64_t probe = 0; probe < T; probe++) {
+        const int old = atomicCAS(keys + h, -1, j);
+        if (old == -1) {
+          mine++;
+          break;
+        }
+        if (old == j) break;
+        h = (h + 1) & (uint32_t)(T - 1);
+      }
+    }
+  }
+  atomicAdd(&count, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) cnt[r] = count;
+}
+
+// Ascending bitonic sort of n2 (a power of two) keys in shared memory, values alongside.
+__device__ void block_bitonic(int* key, double* val, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const int a = key[i], b = key[l];
+          if ((a > b) == up) {
+            key[i] = b;
+            key[l] = a;
+            if (val) {
+              const double t = val[i];
+              val[i] = val[l];
+              val[l] = t;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kLongBlock)
+    k_long_fill(const int64_t* list, const int64_t* off, const int64_t* tsz, const int64_t* cnt,
+                const int32_t* Arp, const int32_t* Acol, const double* Aval, const int32_t* Brp,
+                const int32_t* Bcol, const double* Bval, const int32_t* Crp, int32_t* Ccol,
+                double* Cval, const int32_t* gkeys) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int n;
+  const int64_t r = list[blockIdx.x];
+  const int32_t* keys = gkeys + off[blockIdx.x];
+  const int64_t T = tsz[blockIdx.x];
+  const int c = (int)cnt[r];
+  int n2 = 1;
+  while (n2 < c) n2 <<= 1;
+  double* acc = reinterpret_cast<double*>(smem);
+  int* skey = reinterpret_cast<int*>(smem + 8 * (size_t)kLongRowMax);
+  if (threadIdx.x == 0) n = 0;
+  __syncthreads();
+  for (int64_t q = threadIdx.x; q < T; q += blockDim.x) {
+    const int k = keys[q];
+    if (k >= 0) skey[atomicAdd(&n, 1)] = k;
+  }
+  __syncthreads();
+  for (int i = c + threadIdx.x; i < n2; i += blockDim.x) skey[i] = 0x7fffffff;
+  __syncthreads();
+  block_bitonic(skey, nullptr, n2);
+  const int64_t o0 = Crp[r], o1 = Crp[r + 1];
+  for (int i = threadIdx.x; i < c; i += blockDim.x) {
+    Ccol[o0 + i] = skey[i];
+    acc[i] = 0.0;
+  }
+  for (int64_t q = o0 + c + threadIdx.x; q < o1; q += blockDim.x) {
+    Ccol[q] = -1;
+    if (Cval) Cval[q] = 0.0;
+  }
+  __syncthreads();
+  if (!Cval) return;
+  for (int e = Arp[r]; e < Arp[r + 1]; e++) {
+    const int k = Acol[e];
+    if (k < 0) continue;
+    const double a = Aval[e];
+    for (int f = Brp[k] + threadIdx.x; f < Brp[k + 1]; f += blockDim.x) {
+      const int j = Bcol[f];
+      if (j < 0) continue;
+      int lo = 0, hi = c - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (skey[mid] < j) lo = mid + 1; else hi = mid;
+      }
+      acc[lo] = __dadd_rn(acc[lo], __dmul_rn(a, Bval[f]));
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < c; i += blockDim.x) Cval[o0 + i] = acc[i];
+}
+
+// rows of a transpose longer than the warp sort holds: block bitonic sort by column
+__global__ void __launch_bounds__(kLongBlock)
+    k_sort_long(int64_t nrows, const int32_t* rp, const int64_t* cnt, int limit, int32_t* col,
+                double* val, unsigned long long* err) {
+  extern __shared__ __align__(16) char smem[];
+  const int64_t r = blockIdx.x;
+  if (r >= nrows) return;
+  const int c = (int)cnt[r];
+  if (c <= limit) return;
+  if (c > kLongRowMax) {
+    if (threadIdx.x == 0) atomicAdd(err, 1ull);
+    return;
+  }
+  int n2 = 1;
+  while (n2 < c) n2 <<= 1;
+  double* sv = reinterpret_cast<double*>(smem);
+  int* sc = reinterpret_cast<int*>(smem + 8 * (size_t)kLongRowMax);
+  const int o = rp[r];
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    sc[i] = i < c ? col[o + i] : 0x7fffffff;
+    sv[i] = i < c ? val[o + i] : 0.0;
+  }
+  __syncthreads();
+  block_bitonic(sc, sv, n2);
+  for (int i = threadIdx.x; i < c; i += blockDim.x) {
+    col[o + i] = sc[i];
+    val[o + i] = sv[i];
+  }
+  for (int q = o + c + threadIdx.x; q < rp[r + 1]; q += blockDim.x) {
+    col[q] = -1;
+    val[q] = 0.0;
+  }
 }
 
 // Numeric product on a known output pattern (sorted real columns per row).
@@ -691,7 +864,7 @@ __global__ void k_sort_rows(int64_t nrows, const int32_t* rp, const int64_t* cnt
   const int c = (int)cnt[r];
   const int o = rp[r];
   if (c > TMAX) {
-    if (lane == 0) atomicAdd(err, 1ull);
+    if (lane == 0) atomicAdd(err, 1ull);   // counted: k_sort_long sorts these rows
     return;
   }
   for (int a = lane; a < c; a += 32) {
@@ -838,9 +1011,12 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
   C.ncols = B.ncols;
   DevBuf<int64_t> cnt(nr > 0 ? nr : 1, st);
   int G = 32, htc = 64;
+  int64_t nlong = 0;
+  DevBuf<int64_t> llist, loff, ltsz;
+  DevBuf<int32_t> lkeys;
+  DevBuf<int64_t> tmp(std::max<int64_t>(nr, B.nrows) + 1, st);
   if (nr > 0) {
     // group width from B's longest row, count-table size from the product bound
-    DevBuf<int64_t> tmp(std::max<int64_t>(nr, B.nrows) + 1, st);
     k_row_len<<<grid_for(B.nrows, 256), 256, 0, st>>>(B.nrows, B.rowptr, tmp);
     FEM_CHECK_LAUNCH();
     const int64_t maxb = max_of(tmp, B.nrows, st);
@@ -856,14 +1032,49 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
       case 16: sg_count_ht<16>(htc, nr, A, B, cnt, st); break;
       default: sg_count_ht<32>(htc, nr, A, B, cnt, st); break;
     }
+    if (maxub > kHTMax / 2) {
+      // rows whose count reached half a table (exact up to kHTMax, saturated beyond): count
+      // them again with a global table each
+      DevBuf<int64_t> flag(nr, st), scan(nr + 1, st);
+      k_long_flag<<<grid_for(nr, 256), 256, 0, st>>>(nr, cnt, kHTMax / 2, flag);
+      FEM_CHECK_LAUNCH();
+      nlong = exclusive_scan(flag, nr, scan, st);
+      if (nlong > 0) {
+        llist.alloc_async(nlong, st);
+        ltsz.alloc_async(nlong, st);
+        loff.alloc_async(nlong + 1, st);
+        k_long_list<<<grid_for(nr, 256), 256, 0, st>>>(nr, flag, scan, tmp, llist, ltsz);
+        FEM_CHECK_LAUNCH();
+        const int64_t total = exclusive_scan(ltsz, nlong, loff, st);
+        FEM_REQUIRE(total <= ((int64_t)1 << 31), FEM_EUNSUPPORTED,
+                    "spgemm: long product rows need more than 8 GB of hash tables");
+        lkeys.alloc_async(total, st);
+        k_long_count<<<(unsigned)nlong, kLongBlock, 0, st>>>(llist, loff, ltsz, A.rowptr, A.col,
+                                                             B.rowptr, B.col, lkeys, cnt);
+        FEM_CHECK_LAUNCH();
+      }
+    }
   }
   const int64_t maxc = nr > 0 ? max_of(cnt, nr, st) : 0;
-  FEM_REQUIRE(maxc <= kHTMax / 2, FEM_EUNSUPPORTED,
-              "spgemm: a product row has more than 512 distinct columns");
+  FEM_REQUIRE(maxc <= kLongRowMax, FEM_EUNSUPPORTED,
+              "spgemm: a product row has more than 8192 distinct columns");
   rowptr_from_counts(cnt, nr, C, st);
   if (values) C.val.alloc(C.nnz);
+  if (nlong > 0) {
+    const size_t smem = 12 * (size_t)kLongRowMax;
+    static bool attr = false;
+    if (!attr) {
+      FEM_CUDA(cudaFuncSetAttribute(k_long_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      attr = true;
+    }
+    k_long_fill<<<(unsigned)nlong, kLongBlock, smem, st>>>(
+        llist, loff, ltsz, cnt, A.rowptr, A.col, Aval, B.rowptr, B.col, Bval, C.rowptr, C.col,
+        values ? C.val.p : nullptr, lkeys);
+    FEM_CHECK_LAUNCH();
+  }
   if (nr > 0) {
-    const int htf = pow2_at_least(2 * maxc, 64);
+    const int htf = pow2_at_least(2 * std::min<int64_t>(maxc, kHTMax / 2), 64);
     double* cv = values ? C.val.p : nullptr;
     switch (group_for_smem(G, htf, 14)) {
       case 4: sg_fill_ht<4>(htf, nr, A, Aval, B, Bval, C, cv, st); break;
@@ -916,7 +1127,22 @@ void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st) {
   unsigned long long he = 0;
   FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
   FEM_CUDA(cudaStreamSynchronize(st));
-  FEM_REQUIRE(he == 0, FEM_EUNSUPPORTED, "transpose: a row has more than 1024 entries");
+  if (he) {
+    FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+    const size_t smem = 12 * (size_t)kLongRowMax;
+    static bool attr = false;
+    if (!attr) {
+      FEM_CUDA(cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      attr = true;
+    }
+    k_sort_long<<<(unsigned)ncols, kLongBlock, smem, st>>>(ncols, T.rowptr, c64, TMAX, T.col,
+                                                           T.val, err);
+    FEM_CHECK_LAUNCH();
+    FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    FEM_REQUIRE(he == 0, FEM_EUNSUPPORTED, "transpose: a row has more than 8192 entries");
+  }
 }
 
 static double rowabs_max(const Csr4& A, const double* val, const uint8_t* mask, const double* d,

@@ -199,3 +199,53 @@ def test_invalid_inputs_are_rejected(fa):
     flat[0] = [flat[0, 0], flat[0, 0], flat[0, 1], flat[0, 2]]
     with pytest.raises(fa.FemError):
         fa.fem_mesh_create(x, flat, d)
+
+
+def _graded_box_mesh(n0=6, fac=0.7, steps=12):
+    """Kuhn mesh refined by longest-edge bisection towards the faces of the box (0.25, 0.75)^3
+    (tets whose centroid lies within 0.2 fac^k of the box's surface at step k): a mesh
+    graded like the adaptive meshes of the discontinuous target."""
+    x, t, d = W.kuhn_mesh(n0)
+    for k in range(steps):
+        c = x[t].mean(axis=1)
+        inside = np.all((c > 0.25) & (c < 0.75), axis=1)
+        d_in = np.min(np.minimum(c - 0.25, 0.75 - c), axis=1)
+        d_out = np.linalg.norm(np.maximum(np.maximum(0.25 - c, c - 0.75), 0.0), axis=1)
+        x, t, d, _ = R.refine(x, t, d, np.where(inside, d_in, d_out) < 0.2 * fac ** k)
+    return x, t, d
+
+
+def test_graded_mesh_hierarchy_with_long_coarse_rows(fa):
+    # 44K unknowns; the first coarse operator has rows of about 700 entries, more than the
+    # shared-memory product tables hold, so its Galerkin product takes the long-row path
+    from oracle import amg
+    from tests import gpu_util as G
+    xyz, tets, d = _graded_box_mesh()
+    rho = 1e-6
+    s = core.assemble_mesh(xyz, tets, d, W.box_target())
+    A = s.A(rho).tocsr()
+    Ho = amg.build_hierarchy(A)
+    assert max(np.diff(L.A.indptr).max() for L in Ho) > 512
+    sys_ = fa.fem_assemble_mesh(xyz, tets, d, rho, W.box_target())
+    h = fa.amg_setup(sys_)
+    try:
+        info = fa.amg_hier_get_info(h)
+        assert info["levels"] == len(Ho)
+        for lev, Lo in enumerate(Ho):
+            n_l = Lo.A.shape[0]
+            Al = G.export_level(fa, h, lev, 0, n_l, n_l)
+            assert np.array_equal(Al.indptr, Lo.A.indptr), lev
+            assert np.array_equal(Al.indices, Lo.A.indices), lev
+            assert G.sparse_rel(Al, Lo.A) <= 1e-13, lev
+            if Lo.coarsest:
+                continue
+            assert np.array_equal(G.export_aggregates(fa, h, lev, n_l), Lo.agg), lev
+            Rl = G.export_level(fa, h, lev, 2, Lo.nagg, n_l)
+            assert G.sparse_rel(Rl, Lo.R) <= 1e-13, lev
+        r = W.random_vector(A.shape[0], 5)
+        z = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        fa.amg_vcycle(h, _dev(r), z)
+        assert G.rel(z.cpu().numpy(), amg.vcycle(Ho, r, {})) <= 1e-12
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
