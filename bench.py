@@ -36,7 +36,7 @@ BASELINE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of that kernel at 255^3, from the ncu capture
 # summarised in profiles/k_stencil_fp64_n256.md
-STENCIL64_TRAFFIC = 133.181440e6 + 89.830144e6
+STENCIL64_TRAFFIC = 133.248768e6 + 89.585152e6
 
 
 def _env_int(name, default):
@@ -571,6 +571,9 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     kms = k0.elapsed_time(k1) / reps
     fa.fem_system_destroy(sys_)
+    tuned = [e for e in fa.fem_autotune_report()["entries"]
+             if e["kernel"] == "stencil_f64" and e["a"] == n - 1]
+    k64_name = tuned[-1].get("pick_name", "?") if tuned else "default"
     # stored entries of the Kuhn stencil that are not padding: the centre plus, for each of
     # the 14 neighbour offsets, the points whose neighbour is interior
     m = n - 1
@@ -641,7 +644,7 @@ def run_ours(args, rank: int, world: int):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": STENCIL64_TRAFFIC,
-                     "kernel": "k_stencil<double> (q = A p, FP64 15-point stencil)",
+                     "kernel": "FP64 15-point stencil q = A p (launch shape %s)" % k64_name,
                      "kernel_ms": kms, "flops_per_launch": flops,
                      "peak_source": "FP64 unit counts x max SM clock (no FP64 entry in the "
                                     "measured peaks)"},
