@@ -454,11 +454,12 @@ __device__ int group_insert(const int32_t* Arp, const int32_t* Acol, const int32
 template <int G, int HT>
 __global__ void __launch_bounds__(SG_BLOCK)
     k_sg_count(int64_t nrows, const int32_t* Arp, const int32_t* Acol, const int32_t* Brp,
-               const int32_t* Bcol, int64_t* cnt) {
+               const int32_t* Bcol, const int64_t* rows, int64_t* cnt) {
   extern __shared__ __align__(16) char smem[];
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
-  const int64_t r = (int64_t)blockIdx.x * (SG_BLOCK / G) + grp;
-  if (r >= nrows) return;
+  const int64_t q = (int64_t)blockIdx.x * (SG_BLOCK / G) + grp;
+  if (q >= nrows) return;
+  const int64_t r = rows ? rows[q] : q;   // a listed subset of the rows, or all of them
   int* keys = reinterpret_cast<int*>(smem) + grp * HT;
   const int c = group_insert<G>(Arp, Acol, Brp, Bcol, r, keys, HT, lane, group_mask<G>());
   if (lane == 0) cnt[r] = c;
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(SG_BLOCK)
         uint32_t h = hslot(j, HT - 1);
         while (keys[h] != j) h = (h + 1) & (HT - 1);
         const int rk = rank[h];
-        acc[rk] = __dadd_rn(acc[rk], __dmul_rn(a, Bval[f]));
+        acc[rk] = fma(a, Bval[f], acc[rk]);
       }
       __syncwarp(mask);
     }
@@ -567,6 +568,24 @@ __global__ void k_max_i64(const int64_t* v, int64_t n, unsigned long long* out) 
 // shared memory.  The sums run in the order of A's row like the short path.
 constexpr int kLongRowMax = 8192;
 constexpr int kLongBlock = 256;
+
+constexpr int64_t kSgSample = 4096;
+
+// kSgSample evenly spaced rows of n (n > kSgSample)
+__global__ void k_sample_rows(int64_t n, int64_t ns, int64_t* rows) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < ns) rows[q] = q * (n / ns);
+}
+
+__global__ void k_gather_i64(int64_t n, const int64_t* idx, const int64_t* src, int64_t* dst) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) dst[q] = src[idx[q]];
+}
+
+__global__ void k_flag_list(int64_t n, const int64_t* flag, const int64_t* scan, int64_t* list) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n && flag[r]) list[scan[r]] = r;
+}
 
 __global__ void k_long_flag(int64_t n, const int64_t* cnt, int64_t limit, int64_t* flag) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -693,7 +712,7 @@ __global__ void __launch_bounds__(kLongBlock)
         const int mid = (lo + hi) >> 1;
         if (skey[mid] < j) lo = mid + 1; else hi = mid;
       }
-      acc[lo] = __dadd_rn(acc[lo], __dmul_rn(a, Bval[f]));
+      acc[lo] = fma(a, Bval[f], acc[lo]);
     }
     __syncthreads();
   }
@@ -760,7 +779,7 @@ __global__ void __launch_bounds__(32 * SG_WARPS)
         int mid = (lo + hi) >> 1;
         if (Ccol[mid] < j) lo = mid + 1; else hi = mid;
       }
-      Cval[lo] = __dadd_rn(Cval[lo], __dmul_rn(a, Bval[f]));
+      Cval[lo] = fma(a, Bval[f], Cval[lo]);
     }
     __syncwarp();
   }
@@ -950,8 +969,8 @@ static int pow2_at_least(int64_t v, int lo) {
 }
 
 template <int G, int HT>
-static void sg_count_launch(int64_t nr, const Csr4& A, const Csr4& B, int64_t* cnt,
-                            cudaStream_t st) {
+static void sg_count_launch(int64_t nr, const Csr4& A, const Csr4& B, const int64_t* rows,
+                            int64_t* cnt, cudaStream_t st) {
   const size_t smem = (size_t)(SG_BLOCK / G) * HT * 4;
   static bool attr = false;
   if (!attr) {
@@ -960,7 +979,7 @@ static void sg_count_launch(int64_t nr, const Csr4& A, const Csr4& B, int64_t* c
     attr = true;
   }
   unsigned g = (unsigned)((nr + SG_BLOCK / G - 1) / (SG_BLOCK / G));
-  k_sg_count<G, HT><<<g, SG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, B.rowptr, B.col, cnt);
+  k_sg_count<G, HT><<<g, SG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, B.rowptr, B.col, rows, cnt);
   FEM_CHECK_LAUNCH();
 }
 
@@ -981,14 +1000,25 @@ static void sg_fill_launch(int64_t nr, const Csr4& A, const double* Aval, const 
 }
 
 template <int G>
-static void sg_count_ht(int ht, int64_t nr, const Csr4& A, const Csr4& B, int64_t* cnt,
-                        cudaStream_t st) {
+static void sg_count_ht(int ht, int64_t nr, const Csr4& A, const Csr4& B, const int64_t* rows,
+                        int64_t* cnt, cudaStream_t st) {
   switch (ht) {
-    case 64: sg_count_launch<G, 64>(nr, A, B, cnt, st); break;
-    case 128: sg_count_launch<G, 128>(nr, A, B, cnt, st); break;
-    case 256: sg_count_launch<G, 256>(nr, A, B, cnt, st); break;
-    case 512: sg_count_launch<G, 512>(nr, A, B, cnt, st); break;
-    default: sg_count_launch<G, 1024>(nr, A, B, cnt, st); break;
+    case 64: sg_count_launch<G, 64>(nr, A, B, rows, cnt, st); break;
+    case 128: sg_count_launch<G, 128>(nr, A, B, rows, cnt, st); break;
+    case 256: sg_count_launch<G, 256>(nr, A, B, rows, cnt, st); break;
+    case 512: sg_count_launch<G, 512>(nr, A, B, rows, cnt, st); break;
+    default: sg_count_launch<G, 1024>(nr, A, B, rows, cnt, st); break;
+  }
+}
+
+// count pass over nr rows (or the listed ones) with hash tables of ht slots
+static void sg_count(int G, int ht, int64_t nr, const Csr4& A, const Csr4& B,
+                     const int64_t* rows, int64_t* cnt, cudaStream_t st) {
+  switch (group_for_smem(G, ht, 4)) {
+    case 4: sg_count_ht<4>(ht, nr, A, B, rows, cnt, st); break;
+    case 8: sg_count_ht<8>(ht, nr, A, B, rows, cnt, st); break;
+    case 16: sg_count_ht<16>(ht, nr, A, B, rows, cnt, st); break;
+    default: sg_count_ht<32>(ht, nr, A, B, rows, cnt, st); break;
   }
 }
 
@@ -1025,12 +1055,36 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
     const int64_t maxub = max_of(tmp, nr, st);
     G = maxb <= 4 ? 4 : (maxb <= 8 ? 8 : (maxb <= 16 ? 16 : 32));
     htc = pow2_at_least(std::min<int64_t>(2 * maxub, kHTMax), 64);
-    const int Gc = group_for_smem(G, htc, 4);
-    switch (Gc) {
-      case 4: sg_count_ht<4>(htc, nr, A, B, cnt, st); break;
-      case 8: sg_count_ht<8>(htc, nr, A, B, cnt, st); break;
-      case 16: sg_count_ht<16>(htc, nr, A, B, cnt, st); break;
-      default: sg_count_ht<32>(htc, nr, A, B, cnt, st); break;
+    if (htc > 64 && nr > 4 * kSgSample) {
+      // the bound overestimates the distinct columns several times over, and clearing and
+      // holding the tables is most of the count's work: size the tables from an exact count
+      // of evenly spaced sample rows, then count again (with full tables) the rows whose
+      // table filled up
+      DevBuf<int64_t> srow(kSgSample, st), sval(kSgSample, st);
+      k_sample_rows<<<grid_for(kSgSample, 256), 256, 0, st>>>(nr, kSgSample, srow);
+      FEM_CHECK_LAUNCH();
+      sg_count(G, htc, kSgSample, A, B, srow, cnt, st);   // counts land in cnt[sampled row]
+      k_gather_i64<<<grid_for(kSgSample, 256), 256, 0, st>>>(kSgSample, srow, cnt, sval);
+      FEM_CHECK_LAUNCH();
+      const int64_t smax = max_of(sval, kSgSample, st);
+      const int hts = pow2_at_least(std::min<int64_t>(4 * smax, htc), 64);
+      if (hts < htc) {
+        sg_count(G, hts, nr, A, B, nullptr, cnt, st);
+        DevBuf<int64_t> flag(nr, st), scan(nr + 1, st);
+        k_long_flag<<<grid_for(nr, 256), 256, 0, st>>>(nr, cnt, hts - 1, flag);
+        FEM_CHECK_LAUNCH();
+        const int64_t nfull = exclusive_scan(flag, nr, scan, st);
+        if (nfull > 0) {
+          DevBuf<int64_t> list(nfull, st);
+          k_flag_list<<<grid_for(nr, 256), 256, 0, st>>>(nr, flag, scan, list);
+          FEM_CHECK_LAUNCH();
+          sg_count(G, htc, nfull, A, B, list, cnt, st);
+        }
+      } else {
+        sg_count(G, htc, nr, A, B, nullptr, cnt, st);
+      }
+    } else {
+      sg_count(G, htc, nr, A, B, nullptr, cnt, st);
     }
     if (maxub > kHTMax / 2) {
       // rows whose count reached half a table (exact up to kHTMax, saturated beyond): count
