@@ -58,9 +58,10 @@ def _measured_hbm_gbs() -> float:
 def vcycle_bytes(info: dict, flexible_r2: bool = False) -> float:
     """Algorithmic bytes of one FP32 V-cycle (Chebyshev degree 2, matrix-free finest level,
     FP32 CSR4 values on coarser levels, every vector access counted once): finest level
-    24 (start from the FP64 residual) + 24 (Chebyshev step) + 12 (residual) + 16 (post start)
-    + 40 (last step: x, r, d, FP64 z and <z, r>; + 8 with <z, r_prev>) bytes per row; a CSR
-    level 104 bytes of vectors per row and four passes over its matrix (8 bytes per stored
+    16 (start from the FP64 residual: read it, write b and d) + 12 (the step after the start:
+    d, b -> x) + 12 (residual) + 16 (post start: b, x -> r, d) + 28 (last step: d, r, x,
+    FP64 z and <z, r>; + 8 with <z, r_prev>) bytes per row; a CSR level 64 bytes of vectors
+    per row (8 + 12 + 12 + 16 + 16) and four passes over its matrix (8 bytes per stored
     entry + 4 per row); R_l and P_l one pass each plus their vectors; the coarsest dense
     inverse N^2 x 8 bytes."""
     L = info["levels"]
@@ -73,9 +74,9 @@ def vcycle_bytes(info: dict, flexible_r2: bool = False) -> float:
             total += 8.0 * N * N + 12.0 * N
             continue
         if lev == 0 and info["finest_stencil"]:
-            total += (116.0 + (8.0 if flexible_r2 else 0.0)) * N
+            total += (84.0 + (8.0 if flexible_r2 else 0.0)) * N
         else:
-            total += 104.0 * N + 4 * (8.0 * nnz[lev] + 4.0 * N)
+            total += 64.0 * N + 4 * (8.0 * nnz[lev] + 4.0 * N)
         Nc = rows[lev + 1]
         total += 8.0 * rnnz[lev] + 4.0 * Nc + 4.0 * N + 4.0 * Nc      # restriction
         total += 8.0 * pnnz[lev] + 4.0 * N + 8.0 * N + 4.0 * Nc       # prolongation

@@ -36,7 +36,9 @@ ChebCoef cheb_coefficients(double lmax, double ratio, int degree) {
 
 namespace {
 
-enum EpiMode { E_STORE = 0, E_RESIDUAL = 1, E_CHEB_STEP = 2, E_CHEB_INIT = 3, E_ADD = 4 };
+enum EpiMode {
+  E_STORE = 0, E_RESIDUAL = 1, E_CHEB_STEP = 2, E_CHEB_INIT = 3, E_ADD = 4, E_CHEB_PRE1 = 6
+};
 // compile-time variants of E_CHEB_STEP for kernels specialised on the mode: without the
 // FP64 output (z64 null) and with it
 constexpr int E_CHEB_STEP_NOZ = 2, E_CHEB_STEP_Z = 5;
@@ -46,9 +48,15 @@ constexpr int E_CHEB_STEP_NOZ = 2, E_CHEB_STEP_Z = 5;
 //   E_ADD       y += Av
 //   E_RESIDUAL  y = b - Av
 //   E_CHEB_INIT r = s (b - Av); d_new = c2 r                       (v = x, x not written)
-//   E_CHEB_STEP r -= s Av; d_new = c1 d_old + c2 r; x += [d_old] + d_new   (v = d_old)
+//   E_CHEB_STEP r -= s Av; d_new = c1 d_old + c2 r; x += [d_old] + d_new   (v = d_old;
+//               with xonly, the last step of a smoothing, r and d_new are not written)
+//   E_CHEB_PRE1 the step above right after the start from x = 0, when it is the last of
+//               the pre-smoothing (degree 2): r = s b and x = d_old are implied by that
+//               start, and only the new x is used afterwards: x = d_old + c1 d_old
+//               + c2 (s b - s Av)                                         (v = d_old)
 // s is the smoother's diagonal inverse (scalar sinv_c when sinv is null).  When z64 is
-// set, the final x is also written in FP64 and <z, r1>, <z, r2> are accumulated.
+// set, the final x is written in FP64 only (the step is the V-cycle's last: its FP32 r,
+// d_new and x are not used again) and <z, r1>, <z, r2> are accumulated.
 //
 // The epilogue is split into load() (the row's operands, so that a kernel can issue these
 // loads early, together with its stencil loads) and apply(); "centre" is v[row], which
@@ -76,6 +84,7 @@ struct Epi {
   T sinv_c;
   T c1, c2;
   int add_prev;
+  int xonly;   // E_CHEB_STEP: the last smoothing step, only x is used afterwards
   const T* vin;
   int want_dot;
   double* z64;
@@ -100,6 +109,7 @@ struct Epi {
         o.a = (AT)b[row];
         break;
       case E_CHEB_INIT:
+      case E_CHEB_PRE1:
         o.a = (AT)b[row];
         o.s = sinv ? (AT)sinv[row] : (AT)sinv_c;
         break;
@@ -142,16 +152,26 @@ struct Epi {
         AT rr = o.a - o.s * av;
         AT dl = centre;
         AT dn = (AT)c1 * dl + (AT)c2 * rr;
-        r[row] = (T)rr;
-        dnew[row] = (T)dn;
         AT xv = o.x + (add_prev ? dl : (AT)0) + dn;
-        x[row] = (T)xv;
         if (zo) {
           double z = (double)xv;
           z64[row] = z;
           acc[0] += z * o.r1;
           if (r2) acc[1] += z * o.r2;
+        } else {
+          if (!xonly) {
+            r[row] = (T)rr;
+            dnew[row] = (T)dn;
+          }
+          x[row] = (T)xv;
         }
+      } break;
+      case E_CHEB_PRE1: {
+        AT r0 = o.s * o.a;
+        AT rr = r0 - o.s * av;
+        AT dl = centre;
+        AT dn = (AT)c1 * dl + (AT)c2 * rr;
+        x[row] = (T)(dl + dn);
       } break;
     }
   }
@@ -163,7 +183,7 @@ struct Epi {
     if (md == E_CHEB_STEP) {
       l2_prefetch(r + row);
       l2_prefetch(x + row);
-    } else if (md == E_RESIDUAL || md == E_CHEB_INIT) {
+    } else if (md == E_RESIDUAL || md == E_CHEB_INIT || md == E_CHEB_PRE1) {
       l2_prefetch(b + row);
     } else if (md == E_ADD) {
       l2_prefetch(y + row);
@@ -173,7 +193,7 @@ struct Epi {
   // centre value of a kernel that does not hold v[row]
   __device__ __forceinline__ AT centre_of(int64_t row) const {
     if (mode == E_STORE && want_dot) return (AT)vin[row];
-    if (mode == E_CHEB_STEP) return (AT)dold[row];
+    if (mode == E_CHEB_STEP || mode == E_CHEB_PRE1) return (AT)dold[row];
     return (AT)0;
   }
 
@@ -366,6 +386,9 @@ int launch_col(const Stencil& s, SC<T> c, const T* v, const Epi<T>& epi, double*
         break;
       case E_CHEB_INIT:
         k_stencil_col<T, TYV, KZV, E_CHEB_INIT, MINB, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+        break;
+      case E_CHEB_PRE1:
+        k_stencil_col<T, TYV, KZV, E_CHEB_PRE1, MINB, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
         break;
       default:
         k_stencil_col<T, TYV, KZV, E_ADD, MINB, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
@@ -588,6 +611,7 @@ Epi<T> epi_base(int mode) {
   e.sinv_c = (T)0;
   e.c1 = e.c2 = (T)0;
   e.add_prev = 0;
+  e.xonly = 0;
   e.vin = nullptr;
   e.want_dot = 0;
   e.z64 = nullptr;
@@ -606,6 +630,7 @@ const float* level_sinv<float>(const Level& Lv) { return Lv.scalar_sinv ? nullpt
 
 // Chebyshev start from x = 0: r = s b, d = r / theta, x = d.  With b64 given the FP64
 // right-hand side is converted into b as well (mixed precision, finest level).
+// r and x null: only d (and bout) are written (the next kernel is E_CHEB_PRE1).
 template <typename T>
 __global__ void k_cheb_zero(int64_t N, const T* __restrict__ b, const double* __restrict__ b64,
                             T* bout, const T* __restrict__ sinv, T sinv_c, T inv_theta, T* r,
@@ -624,9 +649,9 @@ __global__ void k_cheb_zero(int64_t N, const T* __restrict__ b, const double* __
     AT s = sinv ? (AT)sinv[i] : (AT)sinv_c;
     AT rr = s * bv;
     AT dd = (AT)inv_theta * rr;
-    r[i] = (T)rr;
+    if (r) r[i] = (T)rr;
     d[i] = (T)dd;
-    x[i] = (T)dd;
+    if (x) x[i] = (T)dd;
   }
 }
 
@@ -718,6 +743,25 @@ void smooth_pre_zero(const Level& Lv, int prec, const amg_opts& o, const ChebCoe
   const T* sinv = level_sinv<T>(Lv);
   T sinv_c = Lv.scalar_sinv ? (T)(1.0 / Lv.st.c0) : (T)0;
   unsigned g = persistent_grid(N, 256, 8);
+  if (cc.degree == 2) {
+    // start from x = 0 and the one step after it, which needs only d, b and writes x
+    k_cheb_zero<T><<<g, 256, 0, st>>>(N, b, b64, const_cast<T*>(b), sinv, sinv_c,
+                                      (T)cc.inv_theta, nullptr, d0, nullptr, Lv.done);
+    FEM_CHECK_LAUNCH();
+    Epi<T> e = epi_base<T>(E_CHEB_PRE1);
+    e.b = b;
+    e.dold = d0;
+    e.x = x;
+    e.sinv = sinv;
+    e.sinv_c = sinv_c;
+    e.c1 = (T)cc.c1[1];
+    e.c2 = (T)cc.c2[1];
+    launch_op<T>(Lv, prec, d0, e, nullptr, st, Lv.done);
+    (void)r;
+    (void)d1;
+    (void)o;
+    return;
+  }
   k_cheb_zero<T><<<g, 256, 0, st>>>(N, b, b64, const_cast<T*>(b), sinv, sinv_c,
                                     (T)cc.inv_theta, r, d0, x, Lv.done);
   FEM_CHECK_LAUNCH();
@@ -781,6 +825,7 @@ void smooth_post(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& c
     e.c1 = (T)cc.c1[i];
     e.c2 = (T)cc.c2[i];
     e.add_prev = (i == 1);
+    e.xonly = last ? 1 : 0;
     double* partials = nullptr;
     if (last && dot) {
       e.z64 = dot->z64;
