@@ -371,7 +371,10 @@ typedef struct {
   double tol;               /* default 1e-8                                           */
   int32_t max_iter;         /* default 1000                                           */
   int32_t stop;             /* PCG_STOP_RESIDUAL: ||r||/||f|| <= tol (default);
-                               PCG_STOP_PRECONDITIONED: sqrt(<r,z>/<r0,z0>) <= tol     */
+                               PCG_STOP_PRECONDITIONED: sqrt(<r,z>/<r0,z0>) <= tol;
+                               r is CG's updated residual: the true residual (relres
+                               below) can differ from it by about cond(A) x 1e-16, so
+                               near that level relres may end slightly above tol      */
   int32_t flexible;         /* -1 auto (on for FP32/BF16 V-cycles), 0 off, 1 on        */
   int32_t use_x0;           /* 1: u_dev holds the initial guess, 0: start from zero    */
   int32_t use_graph;        /* 1: replay iterations as a CUDA graph (default 1)       */
