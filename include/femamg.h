@@ -65,12 +65,23 @@ typedef struct {
 /* Targets of Sec. 4: FEM_TARGET_SINE (4.1), FEM_TARGET_BOX = 1 on (lo,hi)^3 (4.2),
  * FEM_TARGET_SINE_PLUS_ONE (4.3), and FEM_TARGET_BUMPS: sum_b a_b exp(-|x-c_b|^2/(2 w_b^2))
  * (synthetic batched/serving targets).  Arrays are host pointers of length nb (3*nb for
- * centres); nb <= 64. */
+ * centres); nb <= 64.
+ * FEM_TARGET_QUADVALS: any ubar in L2 (Sec. 2), given by its values at the quadrature points
+ * of the load vector: quadvals_dev (device, read during the call) holds 4 doubles per tet,
+ * [tet][q], the value at the point with barycentric weight (5 + 3 sqrt 5)/20 on the tet's
+ * local vertex q and (5 - sqrt 5)/20 on the other three.  Tets are numbered as the mesh
+ * gives them (fem_assemble_mesh, fem_mesh), and 6 c + p on the Kuhn mesh: cube
+ * c = i + n (j + n k), path p over the axis orders (x,y,z), (x,z,y), (y,x,z), (y,z,x),
+ * (z,x,y), (z,y,x), with local vertices corner, +e_a, +e_a+e_b, +(1,1,1).  Only the load
+ * vector uses it (fem_assemble*, fem_assemble_rhs); calls that evaluate ubar elsewhere
+ * (fem_errors, fem_recover, fem_error_indicator, fem_assemble_rhs_noalloc) return
+ * FEM_EINVAL for it. */
 typedef enum {
   FEM_TARGET_SINE = 0,
   FEM_TARGET_BOX = 1,
   FEM_TARGET_BUMPS = 2,
-  FEM_TARGET_SINE_PLUS_ONE = 3
+  FEM_TARGET_SINE_PLUS_ONE = 3,
+  FEM_TARGET_QUADVALS = 4
 } fem_target_kind;
 
 typedef struct {
@@ -80,6 +91,7 @@ typedef struct {
   const double* widths_host;
   const double* amps_host;
   double lo, hi;
+  const double* quadvals_dev;   /* FEM_TARGET_QUADVALS only (else ignored) */
 } fem_target;
 
 /* Operator storage for the finest level. */

@@ -25,9 +25,10 @@ _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-T_SINE, T_BOX, T_BUMPS, T_SINE_PLUS_ONE, T_SINE_SCALED = 0, 1, 2, 3, 4
+T_SINE, T_BOX, T_BUMPS, T_SINE_PLUS_ONE, T_SINE_SCALED, T_QUADVALS = 0, 1, 2, 3, 4, 5
 _KINDS = {"sine": T_SINE, "box": T_BOX, "bumps": T_BUMPS,
-          "sine_plus_one": T_SINE_PLUS_ONE, "sine_scaled": T_SINE_SCALED}
+          "sine_plus_one": T_SINE_PLUS_ONE, "sine_scaled": T_SINE_SCALED,
+          "quadvals": T_QUADVALS}
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +45,8 @@ def build(force: bool = False) -> str:
 class _Target(C.Structure):
     _fields_ = [("kind", C.c_int), ("nb", C.c_int), ("c", C.POINTER(C.c_double)),
                 ("w", C.POINTER(C.c_double)), ("a", C.POINTER(C.c_double)),
-                ("lo", C.c_double), ("hi", C.c_double), ("scale", C.c_double)]
+                ("lo", C.c_double), ("hi", C.c_double), ("scale", C.c_double),
+                ("qv", C.POINTER(C.c_double))]
 
 
 class _Sys(C.Structure):
@@ -156,6 +158,11 @@ def _target_struct(target: dict):
     t.lo = float(target.get("lo", 0.25))
     t.hi = float(target.get("hi", 0.75))
     t.scale = float(target.get("scale", 1.0))
+    if kind == T_QUADVALS:
+        # ubar at the 4 points of the degree-2 rule of every tet, [tet][point]
+        q = np.ascontiguousarray(target["values"], dtype=np.float64).reshape(-1)
+        keep.append(q)
+        t.qv = _dp(q)
     if kind == T_BUMPS:
         c = np.ascontiguousarray(target["centers"], dtype=np.float64).reshape(-1, 3)
         w = np.ascontiguousarray(target["widths"], dtype=np.float64).reshape(-1)
@@ -212,6 +219,8 @@ def assemble(n: int, target: dict, xyz: np.ndarray | None = None, qlevel: int = 
     try:
         if rc == -2:
             raise ValueError("oracle assembly: degenerate tetrahedron")
+        if rc == -3:
+            raise ValueError("oracle assembly: per-tet target values need the 4-point rule")
         nnz = s.nnz
         rowptr = np.ctypeslib.as_array(s.rowptr, (ndof + 1,)).copy()
         col = np.ctypeslib.as_array(s.col, (nnz,)).copy() if nnz else np.zeros(0, np.int32)
@@ -247,6 +256,8 @@ def assemble_mesh(xyz: np.ndarray, tets: np.ndarray, dirichlet: np.ndarray, targ
     try:
         if rc == -2:
             raise ValueError("oracle assembly: degenerate tetrahedron")
+        if rc == -3:
+            raise ValueError("oracle assembly: per-tet target values need the 4-point rule")
         nnz = s.nnz
         rowptr = np.ctypeslib.as_array(s.rowptr, (ndof + 1,)).copy()
         col = np.ctypeslib.as_array(s.col, (nnz,)).copy()

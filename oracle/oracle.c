@@ -122,7 +122,8 @@ double ora_element(const double *X12, double *Ke16, double *Me16) {
 
 /* ------------------------------------------------------------ targets */
 
-enum { T_SINE = 0, T_BOX = 1, T_BUMPS = 2, T_SINE_PLUS_ONE = 3, T_SINE_SCALED = 4 };
+enum { T_SINE = 0, T_BOX = 1, T_BUMPS = 2, T_SINE_PLUS_ONE = 3, T_SINE_SCALED = 4,
+       T_QUADVALS = 5 };
 
 typedef struct {
   int kind;
@@ -132,7 +133,10 @@ typedef struct {
   const double *a;  /* nb amplitudes */
   double lo, hi;    /* box (lo,hi)^3 for T_BOX */
   double scale;     /* factor for T_SINE_SCALED */
+  const double *qv; /* T_QUADVALS: ubar at the 4 points of the degree-2 rule of each tet,
+                       [tet][point], point q with barycentric weight A on local vertex q */
 } target_t;
+
 
 static const double PI = 3.14159265358979323846;
 
@@ -162,6 +166,12 @@ static double target_eval(const target_t *T, const double x[3]) {
     }
   }
   return 0.0;
+}
+
+/* ubar at point q of tet t for the load vector: the given values (T_QUADVALS, 4-point rule
+ * only) or the target at x. */
+static double target_at(const target_t *T, int64_t t, int q, const double x[3]) {
+  return T->kind == T_QUADVALS ? T->qv[4 * t + q] : target_eval(T, x);
 }
 
 /* Gradient of the smooth sine targets (for the H1-seminorm error, Table 2). */
@@ -282,6 +292,7 @@ int ora_assemble(int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
                  const int32_t *dof, int64_t ndof, const target_t *T, int qlevel,
                  ora_sys_t *out) {
   memset(out, 0, sizeof(*out));
+  if (T->kind == T_QUADVALS && qlevel != 0) return -3;   /* values given for 4 points */
   int64_t *inc_ptr = (int64_t *)calloc(nv + 1, sizeof(int64_t));
   if (!inc_ptr) return -1;
   for (int64_t t = 0; t < nt; t++)
@@ -374,7 +385,7 @@ int ora_assemble(int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
         double x[3] = {0, 0, 0};
         for (int a = 0; a < 4; a++)
           for (int d = 0; d < 3; d++) x[d] += Q.bary[4 * q + a] * X[3 * a + d];
-        acc += Q.wt[q] * target_eval(T, x) * Q.bary[4 * q + loc];
+        acc += Q.wt[q] * target_at(T, inc[e], q, x) * Q.bary[4 * q + loc];
       }
       f[r] += vol * acc;
     }
@@ -578,6 +589,7 @@ void ora_target_values(const target_t *T, int64_t npts, const double *xyz, doubl
  * f.  Returns 0, or -1 if a vertex is not interior. */
 int ora_kuhn_rows(int n, const double *xyz, const target_t *T, int qlevel, int64_t nsel,
                   const int64_t *vtx, int32_t *cols, double *Kout, double *Mout, double *fout) {
+  if (T->kind == T_QUADVALS && qlevel != 0) return -3;   /* values given for 4 points */
   qrule_t Q = qrule_make(qlevel);
   const int m = n - 1;
   const double h = 1.0 / n;
@@ -637,7 +649,8 @@ int ora_kuhn_rows(int n, const double *xyz, const target_t *T, int qlevel, int64
               double x[3] = {0, 0, 0};
               for (int a = 0; a < 4; a++)
                 for (int d = 0; d < 3; d++) x[d] += Q.bary[4 * q + a] * X[3 * a + d];
-              acc += Q.wt[q] * target_eval(T, x) * Q.bary[4 * q + loc];
+              const int64_t tid = 6 * (c[0] + (int64_t)n * (c[1] + (int64_t)n * c[2])) + p;
+              acc += Q.wt[q] * target_at(T, tid, q, x) * Q.bary[4 * q + loc];
             }
             fv += vol * acc;
           }

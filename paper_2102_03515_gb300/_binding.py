@@ -21,7 +21,7 @@ FEM_EBREAKDOWN, FEM_ECANCELLED, FEM_EDEVCHECK, FEM_EUNSUPPORTED = 5, 6, 7, 8
 STATUS_NAMES = {0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_ENOMEM", 3: "FEM_ECUDA", 4: "FEM_ENOCONV",
                 5: "FEM_EBREAKDOWN", 6: "FEM_ECANCELLED", 7: "FEM_EDEVCHECK",
                 8: "FEM_EUNSUPPORTED"}
-FEM_TARGET = {"sine": 0, "box": 1, "bumps": 2, "sine_plus_one": 3}
+FEM_TARGET = {"sine": 0, "box": 1, "bumps": 2, "sine_plus_one": 3, "quadvals": 4}
 FEM_FMT_AUTO, FEM_FMT_STENCIL, FEM_FMT_CSR = 0, 1, 2
 AMG_SMOOTHER_CHEBYSHEV, AMG_SMOOTHER_L1_JACOBI, AMG_SMOOTHER_SGS = 0, 1, 2
 AMG_COARSEN_SA, AMG_COARSEN_RED_BLACK = 0, 1
@@ -42,7 +42,7 @@ class KuhnDesc(C.Structure):
 class Target(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nb", C.c_int32), ("centers_host", C.POINTER(C.c_double)),
                 ("widths_host", C.POINTER(C.c_double)), ("amps_host", C.POINTER(C.c_double)),
-                ("lo", C.c_double), ("hi", C.c_double)]
+                ("lo", C.c_double), ("hi", C.c_double), ("quadvals_dev", C.c_void_p)]
 
 
 class AssembleOpts(C.Structure):
@@ -230,6 +230,14 @@ def _target(target: dict, keep: list) -> Target:
     t.kind = FEM_TARGET[target["kind"]]
     t.lo = float(target.get("lo", 0.25))
     t.hi = float(target.get("hi", 0.75))
+    if target["kind"] == "quadvals":
+        # ubar at the 4 load-vector points of every tet: a contiguous float64 device tensor
+        v = target["values"]
+        assert v.is_cuda and v.dtype.is_floating_point and v.element_size() == 8, \
+            "quadvals: a float64 CUDA tensor [nt, 4]"
+        v = v.contiguous()
+        keep.append(v)
+        t.quadvals_dev = v.data_ptr()
     if target["kind"] == "bumps":
         c = np.ascontiguousarray(target["centers"], dtype=np.float64)
         w = np.ascontiguousarray(target["widths"], dtype=np.float64)

@@ -214,6 +214,7 @@ struct TargetDev {
   const double* w;
   const double* a;
   double lo, hi;
+  const double* qv = nullptr;  // FEM_TARGET_QUADVALS: [tet][4] values at the load's points
 };
 
 __device__ double target_eval(const TargetDev& T, double x, double y, double z) {
@@ -340,7 +341,8 @@ __global__ void k_cube_load(int n, const double* xyz, TargetDev T, const double*
         for (int a = 0; a < 4; a++)
 #pragma unroll
           for (int d = 0; d < 3; d++) x[d] += mu[a] * Xc[lv[a]][d];
-        u = target_eval(T, x[0], x[1], x[2]);
+        u = T.kind == FEM_TARGET_QUADVALS ? T.qv[4 * (6 * c + p) + q]
+                                          : target_eval(T, x[0], x[1], x[2]);
       }
       uq[q] = u;
     }
@@ -437,7 +439,11 @@ void load_vector(System& S, const TargetDev& T, const fem_target& t, double* f, 
   const int64_t N = S.N;
   int64_t ncube = (int64_t)n * n * n;
   DevBuf<double> cf(8 * ncube, st);
-  if (S.uniform) {
+  if (t.kind == FEM_TARGET_QUADVALS) {
+    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, S.uniform ? nullptr : S.xyz.p, T,
+                                                             nullptr, nullptr, 0, cf);
+    FEM_CHECK_LAUNCH();
+  } else if (S.uniform) {
     int nterms = (t.kind == FEM_TARGET_BUMPS) ? t.nb : (t.kind == FEM_TARGET_SINE_PLUS_ONE ? 2 : 1);
     DevBuf<double> tab((size_t)nterms * 3 * n * 6, st), alpha(nterms, st);
     int total = nterms * 3 * n * 6;
@@ -459,11 +465,13 @@ struct TargetHolder {
 };
 
 void target_to_device(const fem_target& t, TargetHolder& h, cudaStream_t st) {
-  FEM_REQUIRE(t.kind >= 0 && t.kind <= 3, FEM_EINVAL, "unknown target kind");
+  FEM_REQUIRE(t.kind >= 0 && t.kind <= 4, FEM_EINVAL, "unknown target kind");
+  FEM_REQUIRE(t.kind != FEM_TARGET_QUADVALS || t.quadvals_dev, FEM_EINVAL,
+              "point-value target without values");
   FEM_REQUIRE(t.kind != FEM_TARGET_BUMPS || (t.nb >= 1 && t.nb <= 64 && t.centers_host &&
                                              t.widths_host && t.amps_host),
               FEM_EINVAL, "bumps need 1..64 centres/widths/amplitudes");
-  h.T = TargetDev{t.kind, 0, nullptr, nullptr, nullptr, t.lo, t.hi};
+  h.T = TargetDev{t.kind, 0, nullptr, nullptr, nullptr, t.lo, t.hi, t.quadvals_dev};
   if (t.kind == FEM_TARGET_BUMPS) {
     h.tc.alloc_async(3 * t.nb, st);
     h.tw.alloc_async(t.nb, st);
@@ -726,8 +734,9 @@ __global__ void k_gm_row_count(int64_t N, const int64_t* rvert, const int64_t* v
 }
 
 // the load contribution sum_q w_q ubar(x_q) lambda_loc(x_q) of one tet (times |tau|)
-__device__ __forceinline__ double gm_tet_load(const TargetDev& T, const double X[4][3], int loc,
-                                              const double* qb, const double* qw, int np) {
+__device__ __forceinline__ double gm_tet_load(const TargetDev& T, int64_t t, const double X[4][3],
+                                              int loc, const double* qb, const double* qw,
+                                              int np) {
   double acc = 0.0;
   for (int q = 0; q < np; q++) {
     double x[3] = {0.0, 0.0, 0.0};
@@ -735,7 +744,9 @@ __device__ __forceinline__ double gm_tet_load(const TargetDev& T, const double X
     for (int a = 0; a < 4; a++)
 #pragma unroll
       for (int d = 0; d < 3; d++) x[d] += qb[4 * q + a] * X[a][d];
-    acc += qw[q] * target_eval(T, x[0], x[1], x[2]) * qb[4 * q + loc];
+    const double u = T.kind == FEM_TARGET_QUADVALS ? T.qv[4 * t + q]
+                                                   : target_eval(T, x[0], x[1], x[2]);
+    acc += qw[q] * u * qb[4 * q + loc];
   }
   return acc;
 }
@@ -788,7 +799,7 @@ __global__ void k_gm_row_fill(int64_t N, const int64_t* rvert, const int64_t* vp
         macc[lo] += vol * (loc == b ? 2.0 : 1.0) / 20.0;
       }
     }
-    fr += vol * gm_tet_load(T, X, loc, qb, qw, np);
+    fr += vol * gm_tet_load(T, t, X, loc, qb, qw, np);
   }
   f[r] = fr;
   if (!Aval) return;
@@ -1016,7 +1027,7 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
   const int n = mesh.n;
   FEM_REQUIRE(n >= 2 && n <= 1290, FEM_EINVAL, "fem_assemble: n must be in [2, 1290]");
   FEM_REQUIRE(rho > 0.0 && std::isfinite(rho), FEM_EINVAL, "fem_assemble: rho must be > 0");
-  FEM_REQUIRE(t.kind >= 0 && t.kind <= 3, FEM_EINVAL, "fem_assemble: unknown target kind");
+  FEM_REQUIRE(t.kind >= 0 && t.kind <= 4, FEM_EINVAL, "fem_assemble: unknown target kind");
   FEM_REQUIRE(t.kind != FEM_TARGET_BUMPS || (t.nb >= 1 && t.nb <= 64 && t.centers_host &&
                                              t.widths_host && t.amps_host),
               FEM_EINVAL, "fem_assemble: bumps need 1..64 centres/widths/amplitudes");
@@ -1280,6 +1291,8 @@ void assemble_mesh_dev(System& S, int64_t nv, int64_t nt, const double* xyz_dev,
 
 void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
                      double out[2], cudaStream_t st) {
+  FEM_REQUIRE(t.kind != FEM_TARGET_QUADVALS, FEM_EINVAL,
+              "fem_errors: needs a target it can evaluate anywhere (not point values)");
   FEM_REQUIRE(qlevel >= 0 && qlevel <= 2, FEM_EINVAL, "fem_errors: qlevel in [0, 2]");
   TargetHolder th;
   target_to_device(t, th, st);
@@ -1309,6 +1322,8 @@ void fem_error_norms(System& S, const double* u, const fem_target& t, double sca
 
 double error_indicator(System& S, const double* u, const fem_target& t, int qlevel,
                        double* eta2, cudaStream_t st) {
+  FEM_REQUIRE(t.kind != FEM_TARGET_QUADVALS, FEM_EINVAL,
+              "fem_error_indicator: needs a target it can evaluate anywhere (not point values)");
   FEM_REQUIRE(S.general, FEM_EINVAL,
               "fem_error_indicator: general meshes only (assemble Kuhn meshes with "
               "fem_assemble_mesh to use it)");
@@ -1340,6 +1355,8 @@ double error_indicator(System& S, const double* u, const fem_target& t, int qlev
 
 void fem_recovery(System& S, const double* u, const fem_target& t, double* z, double* p,
                   cudaStream_t st) {
+  FEM_REQUIRE(t.kind != FEM_TARGET_QUADVALS, FEM_EINVAL,
+              "fem_recover: needs a target it can evaluate at the vertices (not point values)");
   TargetHolder th;
   target_to_device(t, th, st);
   if (S.general)
