@@ -173,6 +173,12 @@ fem_status fem_assemble_mesh(const fem_mesh_desc* mesh, double rho, const fem_ta
 /* Copy the assembled load vector f (length N) into f_dev. */
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream);
 
+/* The vertex of every unknown (the dof -> vertex map), vert_dev: device int64[N].  Kuhn mesh:
+ * vertex i + (n+1) (j + (n+1) k) of the interior point (i, j, k); general mesh: the index in
+ * the mesh's vertex array (unknowns follow increasing vertex order).  Lets a caller evaluate
+ * its own functions at the unknowns' vertices. */
+fem_status fem_system_dof_vertices(fem_system sys, int64_t* vert_dev, void* stream);
+
 /* Export A = rho K + M (which = 0), K (1) or M (2) in CSR4: rowptr_dev int32[N+1],
  * col_dev int32[nnz], val_dev double[nnz] with nnz from fem_system_get_info. */
 fem_status fem_system_export(fem_system sys, int32_t which, int32_t* rowptr_dev,

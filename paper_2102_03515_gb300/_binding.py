@@ -127,6 +127,7 @@ SIGNATURES = {
     "fem_assemble_on_mesh": (C.c_int, [VP, C.c_double, P(Target), P(AssembleOpts), VP, P(VP)]),
     "fem_mesh_destroy": (None, [VP]),
     "fem_system_export": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
+    "fem_system_dof_vertices": (C.c_int, [VP, VP, VP]),
     "fem_spmv": (C.c_int, [VP, VP, VP, VP]),
     "fem_system_destroy": (None, [VP]),
     "amg_setup": (C.c_int, [VP, P(AmgOpts), VP, P(VP)]),
@@ -394,6 +395,12 @@ def fem_assemble_on_mesh(mesh, rho: float, target: dict, keep_pencil: bool = Fal
 
 def fem_mesh_destroy(mesh) -> None:
     lib().fem_mesh_destroy(mesh)
+
+
+def fem_system_dof_vertices(sys, vert, stream=None):
+    """vert (device int64 tensor [N]) <- the vertex index of every unknown."""
+    _check(lib().fem_system_dof_vertices(sys, _ptr(vert), _stream(stream)),
+           "fem_system_dof_vertices")
 
 
 def fem_system_get_info(sys) -> dict:

@@ -1353,6 +1353,26 @@ double error_indicator(System& S, const double* u, const fem_target& t, int qlev
   return out;
 }
 
+namespace {
+__global__ void k_kuhn_dof_vertices(int n, int64_t N, int64_t* vert) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int64_t m = n - 1;
+  const int64_t i = r % m + 1, j = (r / m) % m + 1, k = r / (m * m) + 1;
+  vert[r] = i + (int64_t)(n + 1) * (j + (int64_t)(n + 1) * k);
+}
+}  // namespace
+
+void dof_vertices(System& S, int64_t* vert, cudaStream_t st) {
+  if (S.general) {
+    FEM_CUDA(cudaMemcpyAsync(vert, S.rvert, 8 * S.N, cudaMemcpyDeviceToDevice, st));
+  } else {
+    k_kuhn_dof_vertices<<<grid_for(S.N, 256), 256, 0, st>>>(S.n, S.N, vert);
+    FEM_CHECK_LAUNCH();
+  }
+  FEM_CUDA(cudaStreamSynchronize(st));
+}
+
 void fem_recovery(System& S, const double* u, const fem_target& t, double* z, double* p,
                   cudaStream_t st) {
   FEM_REQUIRE(t.kind != FEM_TARGET_QUADVALS, FEM_EINVAL,

@@ -309,6 +309,15 @@ fem_status fem_assemble_on_mesh(fem_mesh m, double rho, const fem_target* target
 
 void fem_mesh_destroy(fem_mesh m) { delete m; }
 
+fem_status fem_system_dof_vertices(fem_system sys, int64_t* vert_dev, void* stream) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && vert_dev, FEM_EINVAL, "fem_system_dof_vertices: null argument");
+    StreamScope scope(as_stream(stream));
+    dof_vertices(sys->S, vert_dev, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
 fem_status fem_system_get_rhs(fem_system sys, double* f_dev, void* stream) {
   return guarded([&]() -> fem_status {
     FEM_REQUIRE(sys && f_dev, FEM_EINVAL, "fem_system_get_rhs: null argument");

@@ -110,6 +110,8 @@ void build_incidence(int64_t nv, int64_t nt, const int32_t* tet, DevBuf<int64_t>
 // ||scale*t - u_h||^2 and ||grad(scale*t - u_h)||^2 (NaN without a gradient) by quadrature
 void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
                      double out[2], cudaStream_t st);
+// vertex of every unknown (device int64[N])
+void dof_vertices(System& S, int64_t* vert, cudaStream_t st);
 // residual error indicator eta_T^2 of every tet of a general mesh (eta2[nt]); returns the sum
 double error_indicator(System& S, const double* u, const fem_target& t, int qlevel,
                        double* eta2, cudaStream_t st);

@@ -174,3 +174,26 @@ def test_invalid_meshes_are_rejected(fa):
     flat[0] = [flat[0, 0], flat[0, 0], flat[0, 1], flat[0, 2]]   # zero volume
     with pytest.raises(fa.FemError):
         fa.fem_assemble_mesh(xyz, flat, d, 1.0, W.sine_target())
+
+
+def test_dof_vertex_map(fa):
+    n = 7
+    s = core.assemble(n, W.sine_target())
+    sys_ = fa.fem_assemble(n, 1.0, W.sine_target())
+    try:
+        v = torch.empty(s.K.shape[0], dtype=torch.int64, device="cuda")
+        fa.fem_system_dof_vertices(sys_, v)
+        dof = core.interior_dof_map(n)
+        expect = np.argsort(np.where(dof >= 0, dof, 10 ** 9))[: s.K.shape[0]]
+        assert np.array_equal(v.cpu().numpy(), expect)
+    finally:
+        fa.fem_system_destroy(sys_)
+    xyz, tets, d = MESHES["five_refined_relabelled"]()
+    sys_ = fa.fem_assemble_mesh(xyz, tets, d, 1.0, W.sine_target())
+    try:
+        N = fa.fem_system_get_info(sys_)["N"]
+        v = torch.empty(N, dtype=torch.int64, device="cuda")
+        fa.fem_system_dof_vertices(sys_, v)
+        assert np.array_equal(v.cpu().numpy(), np.flatnonzero(d == 0))
+    finally:
+        fa.fem_system_destroy(sys_)
