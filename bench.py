@@ -39,6 +39,26 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 STENCIL64_TRAFFIC = 133.248768e6 + 89.585152e6
 
 
+def reduce_over_ranks(x: float, op: str, world: int, device) -> float:
+    """Max or sum of a per-rank scalar over the process group (the value itself at world 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(units_local: float, ms_local: float, world: int, device):
+    """(whole-job units per second, the slowest rank's ms per step).  Replicas run their own
+    steps with nothing shared, so the job processes the units of all ranks in the time of
+    the slowest."""
+    ms = reduce_over_ranks(ms_local, "max", world, device)
+    units = reduce_over_ranks(units_local, "sum", world, device)
+    return units / (ms / 1e3), ms
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -364,6 +384,7 @@ def adaptive_sample(fa, torch, dev, max_dofs: int = 1_000_000, theta: float = 0.
             ph = {"assemble": 0.0, "setup": 0.0, "solve": 0.0, "estimate_mark": 0.0,
                   "refine": 0.0}
             its = []
+            dofs = []
             step = 0
             torch.cuda.synchronize()
             t_start = time.perf_counter()
@@ -381,6 +402,7 @@ def adaptive_sample(fa, torch, dev, max_dofs: int = 1_000_000, theta: float = 0.
                 torch.cuda.synchronize()
                 t3 = time.perf_counter()
                 its.append(res["iterations"])
+                dofs.append(info["N"])
                 ph["assemble"] += t1 - t0
                 ph["setup"] += t2 - t1
                 ph["solve"] += t3 - t2
@@ -410,7 +432,7 @@ def adaptive_sample(fa, torch, dev, max_dofs: int = 1_000_000, theta: float = 0.
                         "iterations_min": min(its), "iterations_max": max(its),
                         "iterations_last": its[-1], "l2sq": err["l2sq"], "paper_l2sq": pl2,
                         "ratio_to_paper": err["l2sq"] / pl2, "total_s": total,
-                        "phases_s": ph})
+                        "phases_s": ph, "dofs_per_step": dofs, "iterations_per_step": its})
     return {"workload": "adaptive loop from the Kuhn mesh n = %d to >= %d dofs, theta = %.2f, "
                         "longest-edge bisection, FP32 V-cycle in FP64 flexible CG to 1e-8"
                         % (n0, max_dofs, theta), "rows": out}
@@ -503,21 +525,16 @@ def run_ours(args, rank: int, world: int):
         return ms, results, fa.fem_kernel_launches() - l0
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", world, dev)
 
     u = torch.zeros(N, dtype=torch.float64, device=dev)
     # ---- headline: FP32 V-cycle inside FP64 flexible CG
     with Clocks(local) as clk:
         ms, results, launches = timed(fa.AMG_PREC_FP32, args.steps, args.warmup, u)
-    ms = max_over_ranks(ms)
     its = results[-1][0]["iterations"]
     relres = max(r[0]["relres"] for r in results)
     u_mixed = u.clone()
-    value = world * N * its / (ms / 1e3)
+    value, ms = replica_throughput(N * its, ms, world, dev)
     solve_ms = statistics.mean(r[0]["solve_ms"] for r in results)
     setup_ms = statistics.mean(r[1]["setup_ms"] for r in results)
 
@@ -525,9 +542,9 @@ def run_ours(args, rank: int, world: int):
     extra = {}
     for name, prec in (("fp64", fa.AMG_PREC_FP64), ("bf16", fa.AMG_PREC_BF16)):
         ms2, res2, _ = timed(prec, max(1, args.steps // 2), 1, u)
-        ms2 = max_over_ranks(ms2)
         it2 = res2[-1][0]["iterations"]
-        extra[name] = {"value": world * N * it2 / (ms2 / 1e3), "ms_per_step": ms2,
+        v2, ms2 = replica_throughput(N * it2, ms2, world, dev)
+        extra[name] = {"value": v2, "ms_per_step": ms2,
                        "iterations": it2, "relres": res2[-1][0]["relres"],
                        "solve_ms": res2[-1][0]["solve_ms"], "setup_ms": res2[-1][1]["setup_ms"]}
         if name == "fp64":
@@ -553,7 +570,8 @@ def run_ours(args, rank: int, world: int):
         step(fa.AMG_PREC_FP32, u)
         host_u.copy_(u, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps)
+    e2e_value, e2e_ms = replica_throughput(N * its, (time.perf_counter() - t0) * 1e3 / e2e_steps,
+                                           world, dev)
 
     # ---- dominant kernel: the FP64 stencil apply of every CG iteration, timed on the
     # stream it is launched on
@@ -639,7 +657,7 @@ def run_ours(args, rank: int, world: int):
         "fp64": extra["fp64"],
         "bf16": extra["bf16"],
         "err_vs_fp64_ref": errs,
-        "e2e": {"value": world * N * its / (e2e_ms / 1e3), "unit": "dof-iters/s",
+        "e2e": {"value": e2e_value, "unit": "dof-iters/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * N,
                 "ms_per_step": e2e_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
