@@ -19,8 +19,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["assemble.cu", "ops.cu", "amg_setup.cu", "solve.cu", "batched.cu", "autotune.cu", "adapt.cu",
            "capi.cu"]
-# element arithmetic is kept free of FMA contraction (plain IEEE products and sums)
-NO_FMAD = {"assemble.cu", "adapt.cu"}
+# the refinement's decisions (edge lengths, midpoints) are kept free of FMA contraction
+# (plain IEEE products and sums, as the oracle computes them); element arithmetic may contract
+NO_FMAD = {"adapt.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
