@@ -1561,10 +1561,96 @@ __global__ void k_st_mis_m2(int64_t N, int m, uint32_t strong, const uint64_t* m
       ns = ST_IN;
     else if ((best >> 62) == ST_IN)
       ns = ST_OUT;
-    else
-      *undecided = 1ull;  // any undecided node (a plain store: only "nonzero" is read)
   }
   state_out[r] = ns;
+  // count the nodes still undecided (one atomic per warp)
+  const unsigned am = __activemask();
+  const unsigned b = __ballot_sync(am, ns == ST_UND);
+  if ((threadIdx.x & 31) == __ffs(am) - 1 && b) atomicAdd(undecided, (unsigned long long)__popc(b));
+}
+
+// List rounds (once few nodes are undecided): m1 over the nodes within distance 1 of an
+// undecided node, then the decision for the undecided ones, written after the round.
+template <uint32_t MASK>
+__global__ void k_st_list_m1(int64_t nv, const int64_t* __restrict__ vlist, int m, uint32_t strong,
+                             const uint8_t* state, uint32_t s, uint64_t* m1) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv) return;
+  const int64_t r = vlist[t];
+  int i, j, k;
+  st_ijk(r, m, i, j, k);
+  uint64_t best = ((uint64_t)state[r] << 62) | prio_of(r, s);
+#pragma unroll
+  for (int d = 0; d < 27; d++) {
+    if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+    const int64_t q = r + st_off(d, m);
+    const uint64_t kq = ((uint64_t)state[q] << 62) | prio_of(q, s);
+    best = kq > best ? kq : best;
+  }
+  m1[r] = best;
+}
+
+template <uint32_t MASK>
+__global__ void k_st_list_m2(int64_t nu, const int64_t* __restrict__ ulist, int m, uint32_t strong,
+                             const uint64_t* m1, uint32_t s, const uint8_t* state,
+                             uint8_t* newst, unsigned long long* undecided) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nu) return;
+  const int64_t r = ulist[t];
+  const uint8_t st = state[r];
+  uint8_t ns = st;
+  if (st == ST_UND) {
+    int i, j, k;
+    st_ijk(r, m, i, j, k);
+    uint64_t best = m1[r];
+#pragma unroll
+    for (int d = 0; d < 27; d++) {
+      if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+      const uint64_t kq = m1[r + st_off(d, m)];
+      best = kq > best ? kq : best;
+    }
+    const uint64_t key = ((uint64_t)ST_UND << 62) | prio_of(r, s);
+    if (best == key)
+      ns = ST_IN;
+    else if ((best >> 62) == ST_IN)
+      ns = ST_OUT;
+    if (ns == ST_UND) atomicAdd(undecided, 1ull);
+  }
+  newst[t] = ns;
+}
+
+__global__ void k_st_list_apply(int64_t nu, const int64_t* __restrict__ ulist,
+                                const uint8_t* __restrict__ newst, uint8_t* state) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nu) state[ulist[t]] = newst[t];
+}
+
+__global__ void k_st_und_flag(int64_t N, const uint8_t* state, int64_t* flag) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N) flag[r] = state[r] == ST_UND ? 1 : 0;
+}
+
+__global__ void k_list_from_flags(int64_t N, const int64_t* flag, const int64_t* scan,
+                                  int64_t* list) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N && flag[r]) list[scan[r]] = r;
+}
+
+// flag every node within distance 1 (strong directions) of a listed node
+template <uint32_t MASK>
+__global__ void k_st_mark_ring(int64_t nu, const int64_t* __restrict__ ulist, int m,
+                               uint32_t strong, int64_t* flag) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nu) return;
+  const int64_t r = ulist[t];
+  int i, j, k;
+  st_ijk(r, m, i, j, k);
+  flag[r] = 1;
+#pragma unroll
+  for (int d = 0; d < 27; d++) {
+    if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+    flag[r + st_off(d, m)] = 1;
+  }
 }
 
 template <uint32_t MASK>
@@ -1760,9 +1846,10 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
   uint8_t* cur = s0;
   uint8_t* nxt = s1;
   bool finished = false;
-  for (int round = 0; round < 10000; round++) {
-    // two rounds per check of the undecided flag (a round after the last is a no-op)
-    FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+  unsigned long long hu = (unsigned long long)N;
+  int round = 0;
+  for (; round < 10000; round += 2) {
+    // two rounds per check of the undecided count (a round after the last is a no-op)
     for (int t = 0; t < 2; t++) {
       k_st_mis_m1<M><<<g, 256, 0, st>>>(N, S.m, S.strong, cur, seed_s, m1);
       FEM_CHECK_LAUNCH();
@@ -1771,12 +1858,48 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
       FEM_CHECK_LAUNCH();
       std::swap(cur, nxt);
     }
-    unsigned long long hu = 0;
     FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
     FEM_CUDA(cudaStreamSynchronize(st));
     if (hu == 0) {
       finished = true;
       break;
+    }
+    if ((int64_t)hu * 64 < N) break;   // few left: continue on lists
+  }
+  if (!finished && round < 10000) {
+    // the same rounds on the undecided nodes only (m1 on the nodes around them)
+    DevBuf<int64_t> flag(N, st), scan(N + 1, st);
+    k_st_und_flag<<<g, 256, 0, st>>>(N, cur, flag);
+    FEM_CHECK_LAUNCH();
+    const int64_t nu = exclusive_scan(flag, N, scan, st);
+    DevBuf<int64_t> ul(nu, st);
+    k_list_from_flags<<<g, 256, 0, st>>>(N, flag, scan, ul);
+    FEM_CHECK_LAUNCH();
+    FEM_CUDA(cudaMemsetAsync(flag, 0, 8 * N, st));
+    k_st_mark_ring<M><<<grid_for(nu, 256), 256, 0, st>>>(nu, ul, S.m, S.strong, flag);
+    FEM_CHECK_LAUNCH();
+    const int64_t nvr = exclusive_scan(flag, N, scan, st);
+    DevBuf<int64_t> vl(nvr, st);
+    k_list_from_flags<<<g, 256, 0, st>>>(N, flag, scan, vl);
+    FEM_CHECK_LAUNCH();
+    DevBuf<uint8_t> newst(nu, st);
+    const unsigned gu = grid_for(nu, 256), gv = grid_for(nvr, 256);
+    for (; round < 10000; round += 2) {
+      for (int t = 0; t < 2; t++) {
+        k_st_list_m1<M><<<gv, 256, 0, st>>>(nvr, vl, S.m, S.strong, cur, seed_s, m1);
+        FEM_CHECK_LAUNCH();
+        if (t == 1) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+        k_st_list_m2<M><<<gu, 256, 0, st>>>(nu, ul, S.m, S.strong, m1, seed_s, cur, newst, und);
+        FEM_CHECK_LAUNCH();
+        k_st_list_apply<<<gu, 256, 0, st>>>(nu, ul, newst, cur);
+        FEM_CHECK_LAUNCH();
+      }
+      FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
+      FEM_CUDA(cudaStreamSynchronize(st));
+      if (hu == 0) {
+        finished = true;
+        break;
+      }
     }
   }
   FEM_REQUIRE(finished, FEM_EDEVCHECK, "aggregation: MIS-2 did not terminate");
