@@ -733,31 +733,52 @@ __global__ void k_gm_row_count(int64_t N, const int64_t* rvert, const int64_t* v
   cnt[r] = c;
 }
 
-// the load contribution sum_q w_q ubar(x_q) lambda_loc(x_q) of one tet (times |tau|)
-__device__ __forceinline__ double gm_tet_load(const TargetDev& T, int64_t t, const double X[4][3],
-                                              int loc, const double* qb, const double* qw,
-                                              int np) {
-  double acc = 0.0;
+// Element quantities, once per tet: |tau| (in vol), the stiffness entries
+// |tau| grad(lambda_a).grad(lambda_b) for a <= b (ke, 10 per tet, index kGmPair[a][b]) and
+// the load integrals sum_q w_q ubar(x_q) lambda_a(x_q) (fe, 4 per tet, without |tau|),
+// with ubar evaluated once per point.  ke null: only vol and fe.
+__constant__ int8_t kGmPair[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+
+__global__ void k_gm_elements(int64_t nt, const int32_t* __restrict__ tet,
+                              const double* __restrict__ xyz, TargetDev T,
+                              const double* __restrict__ qb, const double* __restrict__ qw,
+                              int np, double* vol, double* ke, double* fe,
+                              unsigned long long* bad) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double X[4][3], g[4][3];
+  for (int a = 0; a < 4; a++) {
+    const int32_t v = tet[4 * t + a];
+    for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)v + d];
+  }
+  const double det = tet_grads(X, g);
+  if (!(det != 0.0)) atomicAdd(bad, 1ull);
+  const double V = fabs(det) / 6.0;
+  vol[t] = V;
+  if (ke)
+    for (int a = 0; a < 4; a++)
+      for (int b = a; b < 4; b++)
+        ke[10 * t + kGmPair[a][b]] = V * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int q = 0; q < np; q++) {
     double x[3] = {0.0, 0.0, 0.0};
-#pragma unroll
     for (int a = 0; a < 4; a++)
-#pragma unroll
       for (int d = 0; d < 3; d++) x[d] += qb[4 * q + a] * X[a][d];
     const double u = T.kind == FEM_TARGET_QUADVALS ? T.qv[4 * t + q]
                                                    : target_eval(T, x[0], x[1], x[2]);
-    acc += qw[q] * u * qb[4 * q + loc];
+    for (int a = 0; a < 4; a++) acc[a] += qw[q] * u * qb[4 * q + a];
   }
-  return acc;
+  for (int a = 0; a < 4; a++) fe[4 * t + a] = acc[a];
 }
 
-// One row: columns, K, M, A = rho K + M and f.  With Aval null only f is written.
+// One row: columns, K, M, A = rho K + M and f from the element quantities, summed over the
+// row's tets in increasing tet order.  With Aval null only f is written.
 __global__ void k_gm_row_fill(int64_t N, const int64_t* rvert, const int64_t* vptr,
                               const int32_t* vtet, const int32_t* tet, const int32_t* vdof,
-                              const double* xyz, double rho, TargetDev T, const double* qb,
-                              const double* qw, int np, const int32_t* rowptr, int32_t* col,
-                              double* Aval, double* Kv, double* Mv, double* f,
-                              unsigned long long* bad) {
+                              double rho, const double* __restrict__ vol,
+                              const double* __restrict__ ke, const double* __restrict__ fe,
+                              const int32_t* rowptr, int32_t* col, double* Aval, double* Kv,
+                              double* Mv, double* f) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   const int64_t v = rvert[r];
@@ -772,20 +793,12 @@ __global__ void k_gm_row_fill(int64_t N, const int64_t* rvert, const int64_t* vp
   double fr = 0.0;
   for (int64_t e = vptr[v]; e < vptr[v + 1]; e++) {
     const int64_t t = vtet[e];
-    double X[4][3], g[4][3];
+    const int4 tv4 = reinterpret_cast<const int4*>(tet)[t];
+    const int32_t tv[4] = {tv4.x, tv4.y, tv4.z, tv4.w};
     int loc = 0;
-    int32_t tv[4];
-    for (int a = 0; a < 4; a++) {
-      tv[a] = tet[4 * t + a];
+    for (int a = 0; a < 4; a++)
       if (tv[a] == v) loc = a;
-      for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)tv[a] + d];
-    }
-    const double det = tet_grads(X, g);
-    if (!(det != 0.0)) {
-      atomicAdd(bad, 1ull);
-      return;
-    }
-    const double vol = fabs(det) / 6.0;
+    const double V = vol[t];
     if (Aval) {
       for (int b = 0; b < 4; b++) {
         const int32_t w = vdof[tv[b]];
@@ -795,11 +808,11 @@ __global__ void k_gm_row_fill(int64_t N, const int64_t* rvert, const int64_t* vp
           const int mid = (lo + hi) / 2;
           if (cols[mid] < w) lo = mid + 1; else hi = mid;
         }
-        kacc[lo] += vol * (g[loc][0] * g[b][0] + g[loc][1] * g[b][1] + g[loc][2] * g[b][2]);
-        macc[lo] += vol * (loc == b ? 2.0 : 1.0) / 20.0;
+        kacc[lo] += ke[10 * t + kGmPair[loc][b]];
+        macc[lo] += V * (loc == b ? 2.0 : 1.0) / 20.0;
       }
     }
-    fr += vol * gm_tet_load(T, t, X, loc, qb, qw, np);
+    fr += V * fe[4 * t + loc];
   }
   f[r] = fr;
   if (!Aval) return;
@@ -1003,9 +1016,13 @@ void gm_load_vector(System& S, const TargetDev& T, double* f, cudaStream_t st) {
   hs_rule(qb, qw, 0, st);
   DevBuf<unsigned long long> bad(1, st);
   FEM_CUDA(cudaMemsetAsync(bad, 0, 8, st));
+  DevBuf<double> vol(S.nt, st), fe(4 * S.nt, st);
+  k_gm_elements<<<grid_for(S.nt, 128), 128, 0, st>>>(S.nt, S.tet, S.xyz, T, qb, qw, 4, vol,
+                                                     nullptr, fe, bad);
+  FEM_CHECK_LAUNCH();
   k_gm_row_fill<<<grid_for(S.N, 128), 128, 0, st>>>(
-      S.N, S.rvert, S.vptr, S.vtet, S.tet, S.vdof, S.xyz, S.rho, T, qb, qw, 4, nullptr, nullptr,
-      nullptr, nullptr, nullptr, f, bad);
+      S.N, S.rvert, S.vptr, S.vtet, S.tet, S.vdof, S.rho, vol, nullptr, fe, nullptr, nullptr,
+      nullptr, nullptr, nullptr, f);
   FEM_CHECK_LAUNCH();
   FEM_CUDA(cudaStreamSynchronize(st));
 }
@@ -1276,10 +1293,16 @@ void assemble_mesh_dev(System& S, int64_t nv, int64_t nt, const double* xyz_dev,
   S.f.alloc(N);
   DevBuf<double> qb, qw;
   hs_rule(qb, qw, 0, st);
-  k_gm_row_fill<<<grid_for(N, 128), 128, 0, st>>>(
-      N, S.rvert, S.vptr, S.vtet, S.tet, S.vdof, S.xyz, rho, th.T, qb, qw, 4, S.A.rowptr, S.A.col,
-      S.A.val, S.pencil ? S.Kv.p : nullptr, S.pencil ? S.Mv.p : nullptr, S.f, flags.p + 2);
-  FEM_CHECK_LAUNCH();
+  {
+    DevBuf<double> vol(nt, st), ke(10 * nt, st), fe(4 * nt, st);
+    k_gm_elements<<<grid_for(nt, 128), 128, 0, st>>>(nt, S.tet, S.xyz, th.T, qb, qw, 4, vol, ke,
+                                                     fe, flags.p + 2);
+    FEM_CHECK_LAUNCH();
+    k_gm_row_fill<<<grid_for(N, 128), 128, 0, st>>>(
+        N, S.rvert, S.vptr, S.vtet, S.tet, S.vdof, rho, vol, ke, fe, S.A.rowptr, S.A.col, S.A.val,
+        S.pencil ? S.Kv.p : nullptr, S.pencil ? S.Mv.p : nullptr, S.f);
+    FEM_CHECK_LAUNCH();
+  }
   tr.mark("assemble: general mesh");
   S.dinv.alloc(N);
   k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);
