@@ -912,9 +912,31 @@ __device__ __forceinline__ double len2_rn(const double* a, const double* b) {
 //           + 1/2 sum_{interior faces F} rho^{-1/2} a_F |F| (rho [grad u_h . n_F])^2,
 // a_S = min(h_S / sqrt(rho), 1), h_S the longest edge of S; the volume integral by the
 // quadrature (qb, qw).  Writes eta2[t] and per-block partial sums of eta2.
+// grad u_h on every tet (gu[3 t .. 3 t + 2]) and |tau| (vol[t])
+__global__ void k_gm_grad_uh(int64_t nt, const int32_t* __restrict__ tet,
+                             const int32_t* __restrict__ vdof, const double* __restrict__ xyz,
+                             const double* __restrict__ u, double* gu, double* vol) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int4 tv = reinterpret_cast<const int4*>(tet)[t];
+  const int32_t v[4] = {tv.x, tv.y, tv.z, tv.w};
+  double X[4][3], g[4][3], U[4];
+  for (int a = 0; a < 4; a++) {
+    const int32_t w = vdof[v[a]];
+    U[a] = w >= 0 ? u[w] : 0.0;
+    for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)v[a] + d];
+  }
+  vol[t] = fabs(tet_grads(X, g)) / 6.0;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < 4; a++)
+    for (int d = 0; d < 3; d++) s[d] += U[a] * g[a][d];
+  for (int d = 0; d < 3; d++) gu[3 * t + d] = s[d];
+}
+
 __global__ void k_gm_indicator(int64_t nt, const int32_t* __restrict__ tet,
                                const int32_t* __restrict__ vdof, const double* __restrict__ xyz,
-                               const double* __restrict__ u, const int64_t* __restrict__ vptr,
+                               const double* __restrict__ u, const double* __restrict__ guh,
+                               const double* __restrict__ tvol, const int64_t* __restrict__ vptr,
                                const int32_t* __restrict__ vtet, TargetDev T, double rho,
                                const double* __restrict__ qb, const double* __restrict__ qw,
                                int np, double* __restrict__ eta2, double* partials,
@@ -925,16 +947,14 @@ __global__ void k_gm_indicator(int64_t nt, const int32_t* __restrict__ tet,
        t += (int64_t)gridDim.x * blockDim.x) {
     const int4 tv = reinterpret_cast<const int4*>(tet)[t];
     const int32_t v[4] = {tv.x, tv.y, tv.z, tv.w};
-    double X[4][3], g[4][3], U[4];
+    double X[4][3], U[4];
     for (int a = 0; a < 4; a++) {
       const int32_t w = vdof[v[a]];
       U[a] = w >= 0 ? u[w] : 0.0;
       for (int d = 0; d < 3; d++) X[a][d] = xyz[3 * (int64_t)v[a] + d];
     }
-    const double vol = fabs(tet_grads(X, g)) / 6.0;
-    double gu[3] = {0.0, 0.0, 0.0};
-    for (int a = 0; a < 4; a++)
-      for (int d = 0; d < 3; d++) gu[d] += U[a] * g[a][d];
+    const double vol = tvol[t];
+    const double gu[3] = {guh[3 * t], guh[3 * t + 1], guh[3 * t + 2]};
     double h2 = 0.0;
     for (int a = 0; a < 4; a++)
       for (int b = a + 1; b < 4; b++) h2 = fmax(h2, len2_rn(X[a], X[b]));
@@ -956,18 +976,7 @@ __global__ void k_gm_indicator(int64_t nt, const int32_t* __restrict__ tet,
       const int64_t s = face_neighbour(t, v[i0], v[i1], v[i2], vptr, vtet, tet);
       if (s == -2) atomicAdd(bad, 1ull);
       if (s < 0) continue;
-      const int4 sv = reinterpret_cast<const int4*>(tet)[s];
-      const int32_t w4[4] = {sv.x, sv.y, sv.z, sv.w};
-      double Y[4][3], gs[4][3], V[4];
-      for (int b = 0; b < 4; b++) {
-        const int32_t w = vdof[w4[b]];
-        V[b] = w >= 0 ? u[w] : 0.0;
-        for (int d = 0; d < 3; d++) Y[b][d] = xyz[3 * (int64_t)w4[b] + d];
-      }
-      tet_grads(Y, gs);
-      double jg[3] = {gu[0], gu[1], gu[2]};
-      for (int b = 0; b < 4; b++)
-        for (int d = 0; d < 3; d++) jg[d] -= V[b] * gs[b][d];
+      const double jg[3] = {gu[0] - guh[3 * s], gu[1] - guh[3 * s + 1], gu[2] - guh[3 * s + 2]};
       const double* P0 = X[i0];
       const double* P1 = X[i1];
       const double* P2 = X[i2];
@@ -1360,11 +1369,13 @@ double error_indicator(System& S, const double* u, const fem_target& t, int qlev
   FEM_CUDA(cudaMemcpyAsync(qb, bary.data(), 8 * bary.size(), cudaMemcpyHostToDevice, st));
   FEM_CUDA(cudaMemcpyAsync(qw, wt.data(), 8 * wt.size(), cudaMemcpyHostToDevice, st));
   const unsigned g = persistent_grid(S.nt, 128, 8);
-  DevBuf<double> part(g, st), sum(1, st);
+  DevBuf<double> part(g, st), sum(1, st), gu(3 * S.nt, st), vol(S.nt, st);
   DevBuf<unsigned long long> bad(1, st);
   FEM_CUDA(cudaMemsetAsync(bad, 0, 8, st));
-  k_gm_indicator<<<g, 128, 0, st>>>(S.nt, S.tet, S.vdof, S.xyz, u, S.vptr, S.vtet, th.T, S.rho,
-                                    qb, qw, (int)wt.size(), eta2, part, bad);
+  k_gm_grad_uh<<<grid_for(S.nt, 128), 128, 0, st>>>(S.nt, S.tet, S.vdof, S.xyz, u, gu, vol);
+  FEM_CHECK_LAUNCH();
+  k_gm_indicator<<<g, 128, 0, st>>>(S.nt, S.tet, S.vdof, S.xyz, u, gu, vol, S.vptr, S.vtet, th.T,
+                                    S.rho, qb, qw, (int)wt.size(), eta2, part, bad);
   FEM_CHECK_LAUNCH();
   finalize_sums(part, (int)g, 1, sum, st);
   double out = 0.0;
