@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(SG_BLOCK)
         uint32_t h = hslot(j, HT - 1);
         while (keys[h] != j) h = (h + 1) & (HT - 1);
         const int rk = rank[h];
-        acc[rk] = fma(a, Bval[f], acc[rk]);
+        acc[rk] = __dadd_rn(acc[rk], __dmul_rn(a, Bval[f]));
       }
       __syncwarp(mask);
     }
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(kLongBlock)
         const int mid = (lo + hi) >> 1;
         if (skey[mid] < j) lo = mid + 1; else hi = mid;
       }
-      acc[lo] = fma(a, Bval[f], acc[lo]);
+      acc[lo] = __dadd_rn(acc[lo], __dmul_rn(a, Bval[f]));
     }
     __syncthreads();
   }
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(32 * SG_WARPS)
         int mid = (lo + hi) >> 1;
         if (Ccol[mid] < j) lo = mid + 1; else hi = mid;
       }
-      Cval[lo] = fma(a, Bval[f], Cval[lo]);
+      Cval[lo] = __dadd_rn(Cval[lo], __dmul_rn(a, Bval[f]));
     }
     __syncwarp();
   }
