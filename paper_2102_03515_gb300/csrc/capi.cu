@@ -415,6 +415,7 @@ fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hie
       build_hierarchy(h->H, sys->S, o, st);
       alloc_level_vectors(h->H);
       tune_hierarchy(h->H, sys->S, st);
+      reset_ghost_vectors(h->H, st);
       FEM_CUDA(cudaEventRecord(e1, st));
       FEM_CUDA(cudaEventSynchronize(e1));
       float ms = 0;

@@ -90,10 +90,16 @@ struct Epi {
   double* z64;
   const double* r1;
   const double* r2;
+  // gm > 0: the level vectors (y, b, r, d_old, d_new, x, vin) live in the ghost layout of the
+  // gm^3 grid: (gm + 2)^3 entries, interior (i, j, k) at (i+1) + G ((j+1) + G (k+1)),
+  // G = gm + 2, zero faces.  z64, r1, r2 are always dense; ydense: y too (the residual
+  // handed to the restriction).
+  int gm;
+  int ydense;
 
   // MODE >= 0: the mode fixed at compile time (the switch folds away); -1: run time.
   template <int MODE = -1>
-  __device__ __forceinline__ Ops load(int64_t row) const {
+  __device__ __forceinline__ Ops load(int64_t row, int64_t drow) const {
     Ops o;
     o.a = (AT)0;
     o.x = (AT)0;
@@ -118,8 +124,8 @@ struct Epi {
         o.s = sinv ? (AT)sinv[row] : (AT)sinv_c;
         o.x = (AT)x[row];
         if (zo) {
-          o.r1 = r1[row];
-          if (r2) o.r2 = r2[row];
+          o.r1 = r1[drow];
+          if (r2) o.r2 = r2[drow];
         }
         break;
       default:
@@ -129,8 +135,8 @@ struct Epi {
   }
 
   template <int MODE = -1>
-  __device__ __forceinline__ void apply(int64_t row, AT av, AT centre, const Ops& o,
-                                        double acc[2]) const {
+  __device__ __forceinline__ void apply(int64_t row, int64_t drow, AT av, AT centre,
+                                        const Ops& o, double acc[2]) const {
     const bool zo = MODE == E_CHEB_STEP_Z || (MODE < 0 && z64 != nullptr);
     switch (MODE >= 0 ? (MODE == E_CHEB_STEP_Z ? E_CHEB_STEP : MODE) : mode) {
       case E_STORE:
@@ -141,7 +147,7 @@ struct Epi {
         y[row] = (T)(o.a + av);
         break;
       case E_RESIDUAL:
-        y[row] = (T)(o.a - av);
+        y[ydense ? drow : row] = (T)(o.a - av);
         break;
       case E_CHEB_INIT: {
         AT rr = o.s * (o.a - av);
@@ -155,7 +161,7 @@ struct Epi {
         AT xv = o.x + (add_prev ? dl : (AT)0) + dn;
         if (zo) {
           double z = (double)xv;
-          z64[row] = z;
+          z64[drow] = z;
           acc[0] += z * o.r1;
           if (r2) acc[1] += z * o.r2;
         } else {
@@ -197,8 +203,15 @@ struct Epi {
     return (AT)0;
   }
 
+  // row: the dense row (CSR and shared-memory stencil kernels)
   __device__ __forceinline__ void operator()(int64_t row, AT av, double acc[2]) const {
-    apply(row, av, centre_of(row), load(row), acc);
+    int64_t g = row;
+    if (gm) {
+      const uint32_t r32 = (uint32_t)row, um = (uint32_t)gm, q1 = r32 / um;
+      const int64_t G = gm + 2;
+      g = (int64_t)(r32 - q1 * um) + 1 + G * ((int64_t)(q1 % um) + 1 + G * ((int64_t)(q1 / um) + 1));
+    }
+    apply(g, row, av, centre_of(g), load(g, row), acc);
   }
 };
 
@@ -306,7 +319,7 @@ __global__ void __launch_bounds__(TX* TYV, MINB) k_stencil_col(const T* __restri
     AT z_im = ld(im, k0, -1), z_jm = ld(jm, k0, -sj), z_ijm = ld(im && jm, k0, -1 - sj);
     AT cp = ld(true, k0 + 1, 0);
     AT n_ip = ld(ip, k0 + 1, 1), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, 1 + sj);
-    Ops op = epi.template load<MODE>(row0 + sk * k0);
+    Ops op = epi.template load<MODE>(row0 + sk * k0, row0 + sk * k0);
     const AT a0 = (AT)c.c0, aa = (AT)c.ca, af = (AT)c.cf, ab = (AT)c.cb;
     for (int k = k0; k < kend; k++) {
       if (PF > 0 && k + PF < kend) {  // L2 prefetch of the streams PF planes ahead (in bounds)
@@ -321,12 +334,12 @@ __global__ void __launch_bounds__(TX* TYV, MINB) k_stencil_col(const T* __restri
       const AT n2_ip = ld(ip && more, k + 2, 1), n2_jp = ld(jp && more, k + 2, sj),
                n2_ijp = ld(ip && jp && more, k + 2, 1 + sj);
       Ops op2;
-      if (more) op2 = epi.template load<MODE>(row0 + sk * (k + 1));
+      if (more) op2 = epi.template load<MODE>(row0 + sk * (k + 1), row0 + sk * (k + 1));
       const AT axis = z_im + p_ip + z_jm + p_jp + cm + cp;
       const AT face = p_ijp + z_ijm + n_ip + m_im + n_jp + m_jm;
       const AT body = n_ijp + m_ijm;
       const AT av = a0 * c0v + aa * axis + af * face + ab * body;
-      epi.template apply<MODE>(row0 + sk * k, av, c0v, op, acc);
+      epi.template apply<MODE>(row0 + sk * k, row0 + sk * k, av, c0v, op, acc);
       // shift: plane k becomes k-1, plane k+1 becomes k
       cm = c0v;
       m_im = z_im;
@@ -347,6 +360,115 @@ __global__ void __launch_bounds__(TX* TYV, MINB) k_stencil_col(const T* __restri
     }
   }
   write_partials<T>(acc, partials, partials != nullptr, nblocks);
+}
+
+// The column march on the ghost layout (Epi::gm): every neighbour load hits either the grid
+// or a zero face, so no load needs a bounds check; only the plane two ahead of the last point
+// would leave the array and is not loaded.  Same loads, sums and epilogue as k_stencil_col.
+template <typename T, int TYV, int KZV, int MODE, int PF>
+__global__ void __launch_bounds__(TX* TYV) k_stencil_gh(const T* __restrict__ v, int m, SC<T> c,
+                                                        Epi<T> epi, double* partials,
+                                                        int nblocks, const int* done) {
+  using AT = typename Arith<T>::type;
+  using Ops = typename Epi<T>::Ops;
+  if (done && *done) return;
+  const int i = blockIdx.x * TX + (threadIdx.x & (TX - 1));
+  const int j = blockIdx.y * TYV + threadIdx.x / TX;
+  const int k0 = blockIdx.z * KZV;
+  const int kend = min(k0 + KZV, m);
+  double acc[2] = {0.0, 0.0};
+  if (i < m && j < m) {
+    const int64_t G = m + 2, sj = G, sk = G * G;
+    const int64_t g0 = (int64_t)(i + 1) + sj * (j + 1) + sk * (k0 + 1);   // (i, j, k0)
+    const int64_t dsk = (int64_t)m * m;
+    const int64_t d0 = (int64_t)i + (int64_t)m * j + dsk * k0;
+    const T* pc = v + g0;
+    AT cm = (AT)__ldg(pc - sk), m_im = (AT)__ldg(pc - sk - 1), m_jm = (AT)__ldg(pc - sk - sj),
+       m_ijm = (AT)__ldg(pc - sk - 1 - sj);
+    AT c0v = (AT)__ldg(pc), p_ip = (AT)__ldg(pc + 1), p_jp = (AT)__ldg(pc + sj),
+       p_ijp = (AT)__ldg(pc + 1 + sj);
+    AT z_im = (AT)__ldg(pc - 1), z_jm = (AT)__ldg(pc - sj), z_ijm = (AT)__ldg(pc - 1 - sj);
+    AT cp = (AT)__ldg(pc + sk), n_ip = (AT)__ldg(pc + sk + 1), n_jp = (AT)__ldg(pc + sk + sj),
+       n_ijp = (AT)__ldg(pc + sk + 1 + sj);
+    Ops op = epi.template load<MODE>(g0, d0);
+    const AT a0 = (AT)c.c0, aa = (AT)c.ca, af = (AT)c.cf, ab = (AT)c.cb;
+    int64_t g = g0, d = d0;
+    for (int k = k0; k < kend; k++) {
+      if (PF > 0 && k + PF < kend) {
+        l2_prefetch(pc + (PF + 1) * sk);
+        epi.template prefetch<MODE>(g + PF * sk);
+      }
+      const bool more = k + 1 < kend;
+      // next point: plane k + 1 minus set (in the array), plane k + 2 centre and plus set
+      // (plane m, the zero face, at the last interior plane; beyond it not loaded)
+      const bool two = k + 1 < m;
+      const AT z2_im = (AT)__ldg(pc + sk - 1), z2_jm = (AT)__ldg(pc + sk - sj),
+               z2_ijm = (AT)__ldg(pc + sk - 1 - sj);
+      const AT cp2 = two ? (AT)__ldg(pc + 2 * sk) : (AT)0;
+      const AT n2_ip = two ? (AT)__ldg(pc + 2 * sk + 1) : (AT)0,
+               n2_jp = two ? (AT)__ldg(pc + 2 * sk + sj) : (AT)0,
+               n2_ijp = two ? (AT)__ldg(pc + 2 * sk + 1 + sj) : (AT)0;
+      Ops op2;
+      if (more) op2 = epi.template load<MODE>(g + sk, d + dsk);
+      const AT axis = z_im + p_ip + z_jm + p_jp + cm + cp;
+      const AT face = p_ijp + z_ijm + n_ip + m_im + n_jp + m_jm;
+      const AT body = n_ijp + m_ijm;
+      const AT av = a0 * c0v + aa * axis + af * face + ab * body;
+      epi.template apply<MODE>(g, d, av, c0v, op, acc);
+      cm = c0v;
+      m_im = z_im;
+      m_jm = z_jm;
+      m_ijm = z_ijm;
+      c0v = cp;
+      p_ip = n_ip;
+      p_jp = n_jp;
+      p_ijp = n_ijp;
+      z_im = z2_im;
+      z_jm = z2_jm;
+      z_ijm = z2_ijm;
+      cp = cp2;
+      n_ip = n2_ip;
+      n_jp = n2_jp;
+      n_ijp = n2_ijp;
+      if (more) op = op2;
+      pc += sk;
+      g += sk;
+      d += dsk;
+    }
+  }
+  write_partials<T>(acc, partials, partials != nullptr, nblocks);
+}
+
+template <typename T>
+int launch_stencil_ghost(const Stencil& s, const T* v, const Epi<T>& epi, double* partials,
+                         cudaStream_t st, const int* done) {
+  constexpr int TYV = 8, KZV = 16, PF = 4;
+  SC<T> c{(T)s.c0, (T)s.ca, (T)s.cf, (T)s.cb};
+  const int m = s.m;
+  dim3 grid((m + TX - 1) / TX, (m + TYV - 1) / TYV, (m + KZV - 1) / KZV);
+  int nb = grid.x * grid.y * grid.z;
+  FEM_REQUIRE(!partials || nb <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "stencil grid too large");
+  switch (epi.mode) {
+    case E_RESIDUAL:
+      k_stencil_gh<T, TYV, KZV, E_RESIDUAL, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+      break;
+    case E_CHEB_STEP:
+      if (epi.z64)
+        k_stencil_gh<T, TYV, KZV, E_CHEB_STEP_Z, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+      else
+        k_stencil_gh<T, TYV, KZV, E_CHEB_STEP_NOZ, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+      break;
+    case E_CHEB_INIT:
+      k_stencil_gh<T, TYV, KZV, E_CHEB_INIT, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+      break;
+    case E_CHEB_PRE1:
+      k_stencil_gh<T, TYV, KZV, E_CHEB_PRE1, PF><<<grid, TX * TYV, 0, st>>>(v, m, c, epi, partials, nb, done);
+      break;
+    default:
+      FEM_REQUIRE(false, FEM_EUNSUPPORTED, "ghost-layout stencil: unsupported epilogue");
+  }
+  FEM_CHECK_LAUNCH();
+  return nb;
 }
 
 // Variants of the stencil launch (chosen per (precision, m) by the autotuner):
@@ -427,6 +549,7 @@ const char* stencil_key() { return sizeof(T) == 8 ? "stencil_f64" : "stencil_f32
 template <typename T>
 int launch_stencil(const Stencil& s, const T* v, const Epi<T>& epi, double* partials,
                    cudaStream_t st, const int* done = nullptr) {
+  if (epi.gm) return launch_stencil_ghost<T>(s, v, epi, partials, st, done);
   // untuned default: FP64 is ALU-bound (shared-memory planes), FP32 bandwidth-bound
   const int def = sizeof(T) == 8 ? 0 : 6;
   const int var = tuned_variant(stencil_key<T>(), s.m, 0, 0, def, kStencilVariants);
@@ -613,6 +736,8 @@ Epi<T> epi_base(int mode) {
   e.add_prev = 0;
   e.xonly = 0;
   e.vin = nullptr;
+  e.gm = 0;
+  e.ydense = 0;
   e.want_dot = 0;
   e.z64 = nullptr;
   e.r1 = e.r2 = nullptr;
@@ -630,28 +755,35 @@ const float* level_sinv<float>(const Level& Lv) { return Lv.scalar_sinv ? nullpt
 
 // Chebyshev start from x = 0: r = s b, d = r / theta, x = d.  With b64 given the FP64
 // right-hand side is converted into b as well (mixed precision, finest level).
-// r and x null: only d (and bout) are written (the next kernel is E_CHEB_PRE1).
+// r and x null: only d (and bout) are written (the next kernel is E_CHEB_PRE1).  gm > 0:
+// b, bout, r, d, x in the ghost layout of the gm^3 grid (b64 stays dense).
 template <typename T>
 __global__ void k_cheb_zero(int64_t N, const T* __restrict__ b, const double* __restrict__ b64,
                             T* bout, const T* __restrict__ sinv, T sinv_c, T inv_theta, T* r,
-                            T* d, T* x, const int* done) {
+                            T* d, T* x, const int* done, int gm) {
   using AT = typename Arith<T>::type;
   if (done && *done) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t g = i;
+    if (gm) {
+      const uint32_t r32 = (uint32_t)i, um = (uint32_t)gm, q1 = r32 / um;
+      const int64_t G = gm + 2;
+      g = (int64_t)(r32 - q1 * um) + 1 + G * ((int64_t)(q1 % um) + 1 + G * ((int64_t)(q1 / um) + 1));
+    }
     AT bv;
     if (b64) {
       bv = (AT)b64[i];
-      bout[i] = (T)bv;
+      bout[g] = (T)bv;
     } else {
-      bv = (AT)b[i];
+      bv = (AT)b[g];
     }
     AT s = sinv ? (AT)sinv[i] : (AT)sinv_c;
     AT rr = s * bv;
     AT dd = (AT)inv_theta * rr;
-    if (r) r[i] = (T)rr;
-    d[i] = (T)dd;
-    if (x) x[i] = (T)dd;
+    if (r) r[g] = (T)rr;
+    d[g] = (T)dd;
+    if (x) x[g] = (T)dd;
   }
 }
 
@@ -713,22 +845,28 @@ void op_residual(const Level& Lv, int prec, const T* b, const T* x, T* r, cudaSt
   Epi<T> e = epi_base<T>(E_RESIDUAL);
   e.y = r;
   e.b = b;
+  if (Lv.ghost) {
+    e.gm = Lv.st.m;
+    e.ydense = 1;
+  }
   launch_op<T>(Lv, prec, x, e, nullptr, st, Lv.done);
 }
 
 template <>
 void csr_spmv<double>(const Csr4& M, int prec, const double* x, double* y, bool accumulate,
-                      cudaStream_t st, const int* done) {
+                      cudaStream_t st, const int* done, int ghost_m) {
   (void)prec;
   Epi<double> e = epi_base<double>(accumulate ? E_ADD : E_STORE);
   e.y = y;
+  e.gm = ghost_m;
   launch_csr<double, double>(M, M.val.p, x, e, nullptr, st, done);
 }
 template <>
 void csr_spmv<float>(const Csr4& M, int prec, const float* x, float* y, bool accumulate,
-                     cudaStream_t st, const int* done) {
+                     cudaStream_t st, const int* done, int ghost_m) {
   Epi<float> e = epi_base<float>(accumulate ? E_ADD : E_STORE);
   e.y = y;
+  e.gm = ghost_m;
   if (prec == AMG_PREC_BF16 && M.val16.p)
     launch_csr<__nv_bfloat16, float>(M, M.val16.p, x, e, nullptr, st, done);
   else
@@ -746,9 +884,11 @@ void smooth_pre_zero(const Level& Lv, int prec, const amg_opts& o, const ChebCoe
   if (cc.degree == 2) {
     // start from x = 0 and the one step after it, which needs only d, b and writes x
     k_cheb_zero<T><<<g, 256, 0, st>>>(N, b, b64, const_cast<T*>(b), sinv, sinv_c,
-                                      (T)cc.inv_theta, nullptr, d0, nullptr, Lv.done);
+                                      (T)cc.inv_theta, nullptr, d0, nullptr, Lv.done,
+                                      Lv.ghost ? Lv.st.m : 0);
     FEM_CHECK_LAUNCH();
     Epi<T> e = epi_base<T>(E_CHEB_PRE1);
+    e.gm = Lv.ghost ? Lv.st.m : 0;
     e.b = b;
     e.dold = d0;
     e.x = x;
@@ -763,12 +903,13 @@ void smooth_pre_zero(const Level& Lv, int prec, const amg_opts& o, const ChebCoe
     return;
   }
   k_cheb_zero<T><<<g, 256, 0, st>>>(N, b, b64, const_cast<T*>(b), sinv, sinv_c,
-                                    (T)cc.inv_theta, r, d0, x, Lv.done);
+                                    (T)cc.inv_theta, r, d0, x, Lv.done, Lv.ghost ? Lv.st.m : 0);
   FEM_CHECK_LAUNCH();
   T* dold = d0;
   T* dnew = d1;
   for (int i = 1; i < cc.degree; i++) {
     Epi<T> e = epi_base<T>(E_CHEB_STEP);
+    e.gm = Lv.ghost ? Lv.st.m : 0;
     e.r = r;
     e.dold = dold;
     e.dnew = dnew;
@@ -794,6 +935,7 @@ void smooth_post(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& c
   const int* done = Lv.done;
   {
     Epi<T> e = epi_base<T>(E_CHEB_INIT);
+    e.gm = Lv.ghost ? Lv.st.m : 0;
     e.b = b;
     e.r = r;
     e.dnew = d0;
@@ -816,6 +958,7 @@ void smooth_post(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& c
   for (int i = 1; i < cc.degree; i++) {
     const bool last = (i == cc.degree - 1);
     Epi<T> e = epi_base<T>(E_CHEB_STEP);
+    e.gm = Lv.ghost ? Lv.st.m : 0;
     e.r = r;
     e.dold = dold;
     e.dnew = dnew;
@@ -1018,6 +1161,15 @@ double* vec_d(Level& L, int k) {
   return v[k]->p;
 }
 }  // namespace
+
+void reset_ghost_vectors(Hierarchy& H, cudaStream_t st) {
+  for (auto& Lp : H.L) {
+    Level& L = *Lp;
+    if (!L.ghost) continue;
+    for (DevBuf<float>* v : {&L.xf, &L.bf, &L.rf, &L.d0f, &L.d1f})
+      FEM_CUDA(cudaMemsetAsync(v->p, 0, sizeof(float) * v->n, st));
+  }
+}
 
 void tune_hierarchy(Hierarchy& H, System& S, cudaStream_t st) {
   if (H.o.precision == AMG_PREC_FP64)

@@ -170,11 +170,13 @@ void vc(Hierarchy& H, int lev, const T* b, T* x, const double* b64, const DotOut
   T* d0 = Bufs<T>::d0(L);
   T* d1 = Bufs<T>::d1(L);
   smooth_pre_zero<T>(L, prec, o, cc, b, x, r, d0, d1, st, b64);
-  op_residual<T>(L, prec, b, x, r, st);
+  // the residual for the restriction is dense (on a ghost-layout level in a buffer of its own)
+  T* rres = L.ghost ? reinterpret_cast<T*>(L.rdf.p) : r;
+  op_residual<T>(L, prec, b, x, rres, st);
   Level& C = *H.L[lev + 1];
-  csr_spmv<T>(L.R, prec, r, Bufs<T>::b(C), false, st, L.done);
+  csr_spmv<T>(L.R, prec, rres, Bufs<T>::b(C), false, st, L.done);
   vc<T>(H, lev + 1, Bufs<T>::b(C), Bufs<T>::x(C), nullptr, nullptr, st);
-  csr_spmv<T>(L.P, prec, Bufs<T>::x(C), x, true, st, L.done);
+  csr_spmv<T>(L.P, prec, Bufs<T>::x(C), x, true, st, L.done, L.ghost ? L.st.m : 0);
   smooth_post<T>(L, prec, o, cc, b, x, r, d0, d1, st, dot);
 }
 
@@ -182,15 +184,25 @@ void vc(Hierarchy& H, int lev, const T* b, T* x, const double* b64, const DotOut
 
 void alloc_level_vectors(Hierarchy& H) {
   const bool lowp = H.o.precision != AMG_PREC_FP64;
-  for (auto& Lp : H.L) {
-    Level& L = *Lp;
+  for (size_t lev = 0; lev < H.L.size(); lev++) {
+    Level& L = *H.L[lev];
     const int64_t N = L.N;
+    // the matrix-free finest level of a Chebyshev V-cycle keeps its FP32 vectors with zero
+    // ghost faces, so that its stencil kernels need no bounds checks
+    L.ghost = lowp && lev == 0 && L.stencil && L.scalar_sinv && !L.coarsest &&
+              H.o.smoother == AMG_SMOOTHER_CHEBYSHEV && H.o.degree >= 2;
     if (lowp) {
-      L.xf.alloc(N);
-      L.bf.alloc(N);
-      L.rf.alloc(N);
-      L.d0f.alloc(N);
-      L.d1f.alloc(N);
+      const int64_t NV = L.ghost ? (int64_t)(L.st.m + 2) * (L.st.m + 2) * (L.st.m + 2) : N;
+      L.xf.alloc(NV);
+      L.bf.alloc(NV);
+      L.rf.alloc(NV);
+      L.d0f.alloc(NV);
+      L.d1f.alloc(NV);
+      if (L.ghost) {
+        L.rdf.alloc(N);
+        for (DevBuf<float>* v : {&L.xf, &L.bf, &L.rf, &L.d0f, &L.d1f})
+          FEM_CUDA(cudaMemset(v->p, 0, sizeof(float) * NV));
+      }
     } else {
       L.x.alloc(N);
       L.b.alloc(N);

@@ -77,6 +77,10 @@ struct Level {
   // single-vector work space (FP64 or FP32 according to the hierarchy precision)
   DevBuf<double> x, b, r, d0, d1;
   DevBuf<float> xf, bf, rf, d0f, d1f;
+  // ghost: the FP32 vectors xf, bf, rf, d0f, d1f of a matrix-free finest level use the
+  // layout with zero ghost faces ((m+2)^3 entries); rdf is its dense residual (restriction)
+  bool ghost = false;
+  DevBuf<float> rdf;
 };
 
 struct Hierarchy {
@@ -141,13 +145,15 @@ void op_apply_d_done(const Level& Lv, const double* x, double* y, double* partia
                      int* nblocks, cudaStream_t st, const int* done);
 // Non-owning finest-level view of a system's operator.
 void system_level(System& S, Level& Lv);
-// r = b - A x
+// r = b - A x (r dense when the level is in the ghost layout)
 template <typename T>
 void op_residual(const Level& Lv, int prec, const T* b, const T* x, T* r, cudaStream_t st);
+// zero the ghost-layout vectors of a hierarchy (after anything wrote them densely)
+void reset_ghost_vectors(Hierarchy& H, cudaStream_t st);
 // y (+)= M x for a CSR4 matrix M (restriction / prolongation).
 template <typename T>
 void csr_spmv(const Csr4& M, int prec, const T* x, T* y, bool accumulate, cudaStream_t st,
-              const int* done = nullptr);
+              const int* done = nullptr, int ghost_m = 0);
 
 // One Gauss-Seidel sweep over the colour classes (increasing order when forward):
 // x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii.
