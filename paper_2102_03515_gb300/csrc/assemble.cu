@@ -173,6 +173,78 @@ __global__ void k_csr_uniform(int m, Stencil sa, Stencil sk, Stencil sm, int32_t
   if (mval) mval[e] = cl >= 0 ? mt[t] : 0.0;
 }
 
+// The same rows, one thread per row with 16-byte stores: interior rows (all 15 neighbours on
+// the grid) take their columns from fixed offsets, rows next to the boundary list their
+// existing neighbours in slot order and pad.
+__global__ void k_csr_uniform_rows(int m, Stencil sa, Stencil sk, Stencil sm, int32_t* rowptr,
+                                   int32_t* col, double* aval, double* kval, double* mval) {
+  const int64_t N = (int64_t)m * m * m;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > N) return;
+  rowptr[r] = (int32_t)(16 * r);
+  if (r == N) return;
+  const uint32_t r32 = (uint32_t)r, um = (uint32_t)m, q1 = r32 / um;
+  const int i = (int)(r32 - q1 * um), j = (int)(q1 % um), k = (int)(q1 / um);
+  const int64_t o = 16 * r;
+  if (i > 0 && j > 0 && k > 0 && i < m - 1 && j < m - 1 && k < m - 1) {
+    // the slot tables above, as compile-time constants
+    constexpr int off[15][3] = {{-1, -1, -1}, {0, -1, -1}, {-1, 0, -1}, {0, 0, -1}, {-1, -1, 0},
+                                {0, -1, 0},   {-1, 0, 0},  {0, 0, 0},   {1, 0, 0},  {0, 1, 0},
+                                {1, 1, 0},    {0, 0, 1},   {1, 0, 1},   {0, 1, 1},  {1, 1, 1}};
+    constexpr int type[15] = {3, 2, 2, 1, 2, 1, 1, 0, 1, 1, 2, 1, 2, 2, 3};
+    int32_t cl[16];
+    double av[16], kv[16], mv[16];
+#pragma unroll
+    for (int s = 0; s < 15; s++) {
+      cl[s] = (int32_t)(r + off[s][0] + (int64_t)m * (off[s][1] + (int64_t)m * off[s][2]));
+      av[s] = type[s] == 0 ? sa.c0 : type[s] == 1 ? sa.ca : type[s] == 2 ? sa.cf : sa.cb;
+      kv[s] = type[s] == 0 ? sk.c0 : type[s] == 1 ? sk.ca : type[s] == 2 ? sk.cf : sk.cb;
+      mv[s] = type[s] == 0 ? sm.c0 : type[s] == 1 ? sm.ca : type[s] == 2 ? sm.cf : sm.cb;
+    }
+    cl[15] = -1;
+    av[15] = kv[15] = mv[15] = 0.0;
+    int4* c4 = reinterpret_cast<int4*>(col + o);
+#pragma unroll
+    for (int q = 0; q < 4; q++) c4[q] = make_int4(cl[4 * q], cl[4 * q + 1], cl[4 * q + 2], cl[4 * q + 3]);
+    double2* a2 = reinterpret_cast<double2*>(aval + o);
+#pragma unroll
+    for (int q = 0; q < 8; q++) a2[q] = make_double2(av[2 * q], av[2 * q + 1]);
+    if (kval) {
+      double2* k2 = reinterpret_cast<double2*>(kval + o);
+      double2* m2 = reinterpret_cast<double2*>(mval + o);
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        k2[q] = make_double2(kv[2 * q], kv[2 * q + 1]);
+        m2[q] = make_double2(mv[2 * q], mv[2 * q + 1]);
+      }
+    }
+    return;
+  }
+  const double at[4] = {sa.c0, sa.ca, sa.cf, sa.cb}, kt[4] = {sk.c0, sk.ca, sk.cf, sk.cb},
+               mt[4] = {sm.c0, sm.ca, sm.cf, sm.cb};
+  int cnt = 0;
+  for (int s = 0; s < 15; s++) {
+    const int ii = i + kSlotOff[s][0], jj = j + kSlotOff[s][1], kk = k + kSlotOff[s][2];
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= m || jj >= m || kk >= m) continue;
+    const int t = kSlotType[s];
+    col[o + cnt] = (int32_t)(ii + (int64_t)m * (jj + (int64_t)m * kk));
+    aval[o + cnt] = at[t];
+    if (kval) {
+      kval[o + cnt] = kt[t];
+      mval[o + cnt] = mt[t];
+    }
+    cnt++;
+  }
+  for (int p = cnt; p < 16; p++) {
+    col[o + p] = -1;
+    aval[o + p] = 0.0;
+    if (kval) {
+      kval[o + p] = 0.0;
+      mval[o + p] = 0.0;
+    }
+  }
+}
+
 // CSR4 rows on a general (jittered) vertex grid with Kuhn connectivity.
 __global__ void k_csr_general(int n, const double* xyz, double rho, int32_t* rowptr,
                               int32_t* col, double* aval, double* kval, double* mval) {
@@ -420,6 +492,11 @@ __global__ void k_gather_load(int n, const double* cf, double* f) {
     s += cf[8 * c + dd];
   }
   f[r] = s;
+}
+
+__global__ void k_fill_value(int64_t N, double value, double* out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N) out[r] = value;
 }
 
 __global__ void k_diag_inv(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
@@ -1120,7 +1197,7 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
     S.stK = mk(0);
     S.stM = mk(1);
     S.stA = mk(2);
-    k_csr_uniform<<<grid_for(16 * N + 1, 256), 256, 0, st>>>(m, S.stA, S.stK, S.stM, S.A.rowptr,
+    k_csr_uniform_rows<<<grid_for(N + 1, 128), 128, 0, st>>>(m, S.stA, S.stK, S.stM, S.A.rowptr,
                                                               S.A.col, S.A.val, S.Kv.p, S.Mv.p);
     FEM_CHECK_LAUNCH();
   } else {
@@ -1137,7 +1214,10 @@ void assemble_system(System& S, const fem_kuhn_desc& mesh, double rho, const fem
   load_vector(S, T, t, S.f, st);
   tr.mark("assemble: load vector");
   S.dinv.alloc(N);
-  k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);
+  if (S.uniform)   // every row of the uniform grid has the centre coefficient on its diagonal
+    k_fill_value<<<grid_for(N, 256), 256, 0, st>>>(N, 1.0 / S.stA.c0, S.dinv);
+  else
+    k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.A.val, S.dinv);
   FEM_CHECK_LAUNCH();
   // temporaries are freed stream-ordered; make sure the caller's data is complete
   FEM_CUDA(cudaStreamSynchronize(st));
