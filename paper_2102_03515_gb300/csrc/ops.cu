@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(TX* TYV) k_stencil_gh(const T* __restrict__ v,
     Ops op = epi.template load<MODE>(g0, d0);
     const AT a0 = (AT)c.c0, aa = (AT)c.ca, af = (AT)c.cf, ab = (AT)c.cb;
     int64_t g = g0, d = d0;
+#pragma unroll 2
     for (int k = k0; k < kend; k++) {
       if (PF > 0 && k + PF < kend) {
         l2_prefetch(pc + (PF + 1) * sk);
