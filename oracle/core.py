@@ -17,6 +17,7 @@ import threading
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
@@ -332,6 +333,23 @@ def errors(system: System, u: np.ndarray, exact: dict, qlevel: int = 1):
     _load().ora_errors(len(U), _dp(system.xyz), len(tets), _ip(tets), _dp(U), C.byref(t),
                        qlevel, C.byref(l2), C.byref(h1))
     return l2.value, h1.value
+
+
+def error_hm1(system: System, u: np.ndarray, scale: float = 1.0) -> float:
+    """Discrete H^-1 error of w - u_h, w = scale * ubar, ubar the target the system was
+    assembled with (the H^-1 column of Tables 3, 6 and 8; the paper does not state its
+    discrete form, this is the dual norm on the P1 space with zero boundary values):
+
+        ||w - u_h||_{-1,h}^2 = sup_v (w - u_h, v)^2 / ||grad v||^2 = r^T K^-1 r,
+        r_i = (w - u_h, phi_i)_L2 = scale * f_i - (M u)_i,
+
+    with f the system's load vector (its quadrature for the w part) and M, K its mass and
+    stiffness matrices; K^-1 r by a sparse direct solve."""
+    r = scale * system.f - system.M @ u
+    if not np.any(r):
+        return 0.0
+    y = spla.spsolve(system.K.tocsc(), r)
+    return float(r @ y)
 
 
 def target_values(target: dict, pts: np.ndarray) -> np.ndarray:
