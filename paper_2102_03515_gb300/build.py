@@ -20,7 +20,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["assemble.cu", "ops.cu", "amg_setup.cu", "solve.cu", "batched.cu", "autotune.cu", "adapt.cu",
            "capi.cu"]
 # the refinement's decisions (edge lengths, midpoints) are kept free of FMA contraction
-# (plain IEEE products and sums, as the oracle computes them); element arithmetic may contract
+# (each product and sum rounded on its own, the same on every machine); element arithmetic
+# may contract
 NO_FMAD = {"adapt.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
