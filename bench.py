@@ -280,6 +280,43 @@ def paper_tables_sample(fa, torch, dev, n: int):
     return out
 
 
+# Table 3 of the paper (Sec. 4.1): ||ubar - u_h||^2 in H^-1 and in L2 for ubar = sin sin sin at
+# h = rho^(1/2); its L2 column is the continuous (1/8) (3 rho pi^2 / (3 rho pi^2 + 1))^2, its
+# H^-1 column 0.030341 times that (the continuous dual norm gives 1 / (3 pi^2) = 0.033774 times)
+PAPER_TABLE3 = {1.0: (3.54886e-3, 1.16966e-1), 1e-1: (2.11939e-3, 6.98529e-2),
+                1e-2: (1.97952e-4, 6.52427e-3), 1e-3: (3.13686e-6, 1.03388e-4),
+                1e-4: (3.30578e-8, 1.08962e-6)}
+
+
+def table3_sample(fa, torch, dev, n: int):
+    """||ubar - u_h||^2 in the discrete H^-1 norm (fem_error_hm1: r^T K^-1 r) and in L2
+    (fem_errors) from GPU solves on one mesh (h = 1/n, FP64 V-cycle, tol 1e-10), next to the
+    continuous values and the paper's Table 3 (its meshes follow h = rho^(1/2): context)."""
+    import math
+    import fem_workloads as W
+    rows = []
+    N = (n - 1) ** 3
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    for rho, (phm1, pl2) in PAPER_TABLE3.items():
+        sys_ = fa.fem_assemble(n, rho, W.sine_target())
+        h = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP64)
+        res = fa.pcg_solve(sys_, h, None, u, tol=1e-10)[0]
+        fa.amg_hier_destroy(h)
+        l2sq = fa.fem_errors(sys_, u, W.sine_target(), qlevel=0)["l2sq"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hm = fa.fem_error_hm1(sys_, u, W.sine_target(), tol=1e-10)
+        thm = time.perf_counter() - t0
+        a = 3.0 * rho * math.pi ** 2 / (3.0 * rho * math.pi ** 2 + 1.0)
+        l2c = a * a / 8.0
+        rows.append({"rho": rho, "iterations": res["iterations"], "hm1sq": hm["hm1sq"],
+                     "l2sq": l2sq, "continuous_hm1sq": l2c / (3.0 * math.pi ** 2),
+                     "continuous_l2sq": l2c, "paper_hm1sq": phm1, "paper_l2sq": pl2,
+                     "hm1_ms": thm * 1e3, "hm1_stiffness_iterations": hm["solve"]["iterations"]})
+        fa.fem_system_destroy(sys_)
+    return {"h": 1.0 / n, "rows": rows}
+
+
 # Table 4 of the paper (Sec. 4.1): AMG-PCG iterations and total coarsening + solving time at
 # h = 1/256 on MACH-2 (cores not stated), stopped at a preconditioned relative residual 1e-8
 PAPER_TABLE4_H256 = {1.0: (20, 1420.73), 1e-2: (15, 910.77), 1e-4: (8, 646.14), 1e-6: (4, 499.10)}
@@ -617,9 +654,10 @@ def run_ours(args, rank: int, world: int):
                    "kernel": "one FP32 V-cycle (all levels, replayed from a CUDA graph)",
                    "ms": vms, "algorithmic_bytes": vbytes, "peak_source": "measured copy rate"}
 
-    batched = serving = tables = table4 = general = adaptive = None
+    batched = serving = tables = table3 = table4 = general = adaptive = None
     if not args.no_extras:
         tables = paper_tables_sample(fa, torch, dev, n)
+        table3 = table3_sample(fa, torch, dev, n)
         table4 = table4_sample(fa, torch, dev, n)
         general = general_mesh_sample(fa, torch, dev)
         adaptive = adaptive_sample(fa, torch, dev)
@@ -673,6 +711,8 @@ def run_ours(args, rank: int, world: int):
     }
     if tables is not None:
         line["paper_tables"] = tables
+    if table3 is not None:
+        line["paper_table3"] = table3
     if table4 is not None:
         line["paper_table4"] = table4
     if general is not None:

@@ -419,6 +419,27 @@ fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double*
                      int32_t nrhs, const double* rho_k_host, const pcg_opts* opts,
                      void* stream, pcg_result* res);
 
+/* Discrete H^-1 error of a solution (Tables 3, 6 and 8 report ||ubar - u_h||^2 in H^-1
+ * without stating its discrete form): with w = scale * target,
+ *   hm1sq = r^T K^-1 r,   r_i = (w - u_h, phi_i)_{L2} = scale * f_i(target) - (M u)_i,
+ * the square of sup_v (w - u_h, v) / ||grad v|| over the P1 functions v with zero boundary
+ * values.  f(target) is the load vector fem_assemble builds for that target (the same
+ * quadrature), M and K the system's mass and stiffness matrices, u_h the P1 function with
+ * the nodal values u_dev (length N, interior unknowns).  K^-1 r comes from CG preconditioned
+ * by an FP64 smoothed-aggregation V-cycle built on K (default amg_opts), started from zero,
+ * to ||r_k|| <= tol ||r||; hm1sq is then accurate to about tol^2 cond(K) relative (CG's
+ * iterate y_k has r^T y_k = y_k^T K y_k, short of r^T K^-1 r by the squared energy norm of
+ * its error).  A uniform Kuhn mesh rebuilds K and M from its stencils; any other system needs
+ * keep_pencil at assembly.  The call allocates the stiffness system and its hierarchy and
+ * frees them before it returns; it synchronises the stream.  *hm1sq_out receives the value
+ * (0 when r = 0), *res (may be null) the stiffness solve's result.  Errors: FEM_EINVAL (null
+ * sys / u_dev / target / hm1sq_out, tol outside (0, 1), bad target, a non-uniform system
+ * without its pencil), or the stiffness solve's status (FEM_ENOCONV, ...), with the value of
+ * the last iterate still written. */
+fem_status fem_error_hm1(fem_system sys, const double* u_dev, const fem_target* target,
+                         double scale, double tol, void* stream, double* hm1sq_out,
+                         pcg_result* res);
+
 /* ------------------------------------------------------------------ batched sessions */
 
 /* A batch session holds up to `slots` independent solves on one system/hierarchy, each

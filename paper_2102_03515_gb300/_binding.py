@@ -117,6 +117,8 @@ SIGNATURES = {
                                     P(VP)]),
     "fem_errors": (C.c_int, [VP, VP, P(Target), C.c_double, C.c_int32, VP, P(ErrorsResult)]),
     "fem_recover": (C.c_int, [VP, VP, P(Target), VP, VP, VP]),
+    "fem_error_hm1": (C.c_int, [VP, VP, P(Target), C.c_double, C.c_double, VP, P(C.c_double),
+                                P(PcgResult)]),
     "fem_error_indicator": (C.c_int, [VP, VP, P(Target), C.c_int32, VP, VP, P(C.c_double)]),
     "fem_mark_bulk": (C.c_int, [VP, C.c_int64, C.c_double, VP, VP, P(C.c_double),
                                 P(C.c_int64)]),
@@ -263,6 +265,19 @@ def fem_errors(sys, u, target: dict, scale: float = 1.0, qlevel: int = 1, stream
     _check(lib().fem_errors(sys, _ptr(u), C.byref(t), float(scale), int(qlevel), _stream(stream),
                             C.byref(r)), "fem_errors")
     return {"l2sq": r.l2sq, "h1sq": r.h1sq}
+
+
+def fem_error_hm1(sys, u, target: dict, scale: float = 1.0, tol: float = 1e-10,
+                  stream=None) -> dict:
+    """{"hm1sq": r^T K^-1 r with r = scale * f(target) - M u, "solve": the stiffness solve's
+    result} (the discrete H^-1 error of w - u_h, w = scale * target)."""
+    keep = []
+    t = _target(target, keep)
+    v = C.c_double(0.0)
+    r = PcgResult()
+    _check(lib().fem_error_hm1(sys, _ptr(u), C.byref(t), float(scale), float(tol),
+                               _stream(stream), C.byref(v), C.byref(r)), "fem_error_hm1")
+    return {"hm1sq": v.value, "solve": r.as_dict()}
 
 
 def fem_recover(sys, u, target: dict, z=None, p=None, stream=None):

@@ -1432,6 +1432,80 @@ void fem_error_norms(System& S, const double* u, const fem_target& t, double sca
   if (!grad) out[1] = std::nan("");
 }
 
+// ------------------------------------------------------------------ mass and stiffness alone
+
+namespace {
+// y = V x for values V on a CSR4 pattern (padding columns are -1), FP64
+__global__ void k_csr_values_apply(int64_t N, const int32_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ col, const double* __restrict__ v,
+                                   const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double s = 0.0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+    const int j = col[e];
+    if (j >= 0) s = fma(v[e], x[j], s);
+  }
+  y[r] = s;
+}
+}  // namespace
+
+void mass_apply(const System& S, const double* x, double* y, cudaStream_t st) {
+  const int64_t N = S.N;
+  if (N == 0) return;
+  FEM_REQUIRE(S.pencil || (S.uniform && !S.general), FEM_EINVAL,
+              "mass matrix: a system on a non-uniform mesh needs keep_pencil");
+  if (S.pencil) {
+    k_csr_values_apply<<<grid_for(N, 256), 256, 0, st>>>(N, S.A.rowptr, S.A.col, S.Mv, x, y);
+    FEM_CHECK_LAUNCH();
+    return;
+  }
+  // the uniform grid's mass rows from its stencil
+  DevBuf<int32_t> rp(N + 1, st), cl(16 * N, st);
+  DevBuf<double> mv(16 * N, st);
+  k_csr_uniform_rows<<<grid_for(N + 1, 128), 128, 0, st>>>(S.n - 1, S.stM, S.stK, S.stM, rp, cl,
+                                                            mv, nullptr, nullptr);
+  FEM_CHECK_LAUNCH();
+  k_csr_values_apply<<<grid_for(N, 256), 256, 0, st>>>(N, rp, cl, mv, x, y);
+  FEM_CHECK_LAUNCH();
+}
+
+void stiffness_system(const System& S, System& SK, cudaStream_t st) {
+  FEM_REQUIRE(S.pencil || (S.uniform && !S.general), FEM_EINVAL,
+              "stiffness matrix: a system on a non-uniform mesh needs keep_pencil");
+  const int64_t N = S.N;
+  SK.n = S.n;
+  SK.N = N;
+  SK.h = S.h;
+  SK.rho = 1.0;
+  SK.uniform = S.uniform;
+  SK.stencil = S.stencil;
+  SK.pencil = false;
+  SK.general = false;
+  SK.stA = S.stK;
+  SK.stK = S.stK;
+  SK.A.nrows = SK.A.ncols = S.A.nrows;
+  SK.A.nnz = S.A.nnz;
+  SK.A.rowptr.alloc(N + 1);
+  SK.A.col.alloc(S.A.nnz);
+  SK.A.val.alloc(S.A.nnz);
+  if (S.pencil) {
+    FEM_CUDA(cudaMemcpyAsync(SK.A.rowptr, S.A.rowptr, 4 * (N + 1), cudaMemcpyDeviceToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(SK.A.col, S.A.col, 4 * S.A.nnz, cudaMemcpyDeviceToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(SK.A.val, S.Kv, 8 * S.A.nnz, cudaMemcpyDeviceToDevice, st));
+  } else {
+    k_csr_uniform_rows<<<grid_for(N + 1, 128), 128, 0, st>>>(S.n - 1, S.stK, S.stK, S.stM,
+                                                              SK.A.rowptr, SK.A.col, SK.A.val,
+                                                              nullptr, nullptr);
+    FEM_CHECK_LAUNCH();
+  }
+  SK.dinv.alloc(N);
+  if (N > 0) {
+    k_diag_inv<<<grid_for(N, 256), 256, 0, st>>>(N, SK.A.rowptr, SK.A.col, SK.A.val, SK.dinv);
+    FEM_CHECK_LAUNCH();
+  }
+}
+
 double error_indicator(System& S, const double* u, const fem_target& t, int qlevel,
                        double* eta2, cudaStream_t st) {
   FEM_REQUIRE(t.kind != FEM_TARGET_QUADVALS, FEM_EINVAL,

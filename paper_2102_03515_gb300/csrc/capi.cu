@@ -593,6 +593,19 @@ fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double*
   });
 }
 
+fem_status fem_error_hm1(fem_system sys, const double* u_dev, const fem_target* target,
+                         double scale, double tol, void* stream, double* hm1sq_out,
+                         pcg_result* res) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(sys && u_dev && target && hm1sq_out, FEM_EINVAL, "fem_error_hm1: null argument");
+    StreamScope scope(as_stream(stream));
+    pcg_result r{};
+    *hm1sq_out = error_hm1(sys->S, u_dev, *target, scale, tol, as_stream(stream), r);
+    if (res) *res = r;
+    return (fem_status)r.status;
+  });
+}
+
 fem_status pcg_batch_create(fem_system sys, amg_hier hier, int32_t slots, const pcg_opts* opts,
                             void* stream, pcg_batch* out) {
   return guarded([&]() -> fem_status {

@@ -18,6 +18,7 @@
 // one iteration) and check convergence only every few iterations.
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 #include "solver.cuh"
 
@@ -595,6 +596,71 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
   res.relres = hs2[1] > 0 ? std::sqrt(hs2[0] / hs2[1]) : 0.0;
   res.prec_relres = hs.rz0 > 0 ? std::sqrt(std::fabs(hs.rz / hs.rz0)) : 0.0;
   res.solve_ms = ms;
+}
+
+// ------------------------------------------------------------------ discrete H^-1 error
+
+namespace {
+__global__ void k_hm1_residual(int64_t N, double scale, const double* fw, const double* mu,
+                               double* r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) r[i] = scale * fw[i] - mu[i];
+}
+
+// per-block partial sums of <a, b> (fixed order: deterministic)
+__global__ void k_dot_partials(int64_t N, const double* a, const double* b, double* part) {
+  double v[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[0] = fma(a[i], b[i], v[0]);
+  block_sum<1>(v);
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+double device_dot(int64_t N, const double* a, const double* b, cudaStream_t st) {
+  const unsigned g = persistent_grid(N, 256, 4);
+  DevBuf<double> part(g, st), sum(1, st);
+  k_dot_partials<<<g, 256, 0, st>>>(N, a, b, part);
+  FEM_CHECK_LAUNCH();
+  finalize_sums(part, (int)g, 1, sum, st);
+  double out = 0.0;
+  FEM_CUDA(cudaMemcpyAsync(&out, sum, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  return out;
+}
+}  // namespace
+
+// ||w - u_h||^2 in the dual norm of the P1 space with zero boundary values, w = scale * t:
+// r_i = (w - u_h, phi_i) = scale * f_i(t) - (M u)_i, value r^T K^-1 r.  The stiffness solve
+// is CG with an FP64 smoothed-aggregation V-cycle built on K, started from zero; CG's
+// iterate y_k satisfies r^T y_k = y_k^T K y_k, so r^T K^-1 r - r^T y_k is the squared energy
+// norm of its error and the value is accurate to about tol^2 cond(K) relative.
+double error_hm1(System& S, const double* u, const fem_target& t, double scale, double tol,
+                 cudaStream_t st, pcg_result& res) {
+  FEM_REQUIRE(tol > 0.0 && tol < 1.0, FEM_EINVAL, "fem_error_hm1: tol in (0, 1)");
+  std::memset(&res, 0, sizeof(res));
+  res.status = FEM_OK;
+  const int64_t N = S.N;
+  if (N == 0) return 0.0;
+  System SK;
+  stiffness_system(S, SK, st);   // checks that K and M are available first
+  DevBuf<double> r(N, st), mu(N, st), y(N, st);
+  assemble_rhs(S, t, r, st);     // load vector of t: the rule of the system's f
+  mass_apply(S, u, mu, st);
+  k_hm1_residual<<<grid_for(N, 256), 256, 0, st>>>(N, scale, r, mu, r);
+  FEM_CHECK_LAUNCH();
+  if (device_dot(N, r, r, st) == 0.0) return 0.0;
+  Hierarchy HK;
+  amg_opts ao;
+  amg_default_opts(&ao);
+  build_hierarchy(HK, SK, ao, st);
+  alloc_level_vectors(HK);
+  pcg_opts po;
+  pcg_default_opts(&po);
+  po.tol = tol;
+  FEM_CUDA(cudaMemsetAsync(y, 0, 8 * N, st));
+  pcg_single(SK, &HK, r, y, po, st, res);
+  return device_dot(N, r, y, st);
 }
 
 }  // namespace fem

@@ -114,6 +114,13 @@ void build_incidence(int64_t nv, int64_t nt, const int32_t* tet, DevBuf<int64_t>
 // ||scale*t - u_h||^2 and ||grad(scale*t - u_h)||^2 (NaN without a gradient) by quadrature
 void fem_error_norms(System& S, const double* u, const fem_target& t, double scale, int qlevel,
                      double out[2], cudaStream_t st);
+// y = M x with the system's mass matrix (from the pencil, or the uniform grid's stencil)
+void mass_apply(const System& S, const double* x, double* y, cudaStream_t st);
+// SK = the system's stiffness matrix K as a system of its own (rho = 1, no mass term)
+void stiffness_system(const System& S, System& SK, cudaStream_t st);
+// discrete H^-1 error r^T K^-1 r, r = scale * f(t) - M u, K^-1 r by AMG-PCG to tol
+double error_hm1(System& S, const double* u, const fem_target& t, double scale, double tol,
+                 cudaStream_t st, pcg_result& res);
 // vertex of every unknown (device int64[N])
 void dof_vertices(System& S, int64_t* vert, cudaStream_t st);
 // residual error indicator eta_T^2 of every tet of a general mesh (eta2[nt]); returns the sum
