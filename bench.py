@@ -402,6 +402,11 @@ PAPER_TABLE6_L2SQ = {1e0: 1.2018e-1, 1e-1: 9.0747e-2, 1e-2: 3.6563e-2, 1e-3: 1.1
                      1e-4: 3.8028e-3, 1e-5: 1.2075e-3, 1e-6: 3.7988e-4}
 PAPER_TABLE8_L2SQ = {1e0: 1.5613e0, 1e-1: 1.0842e0, 1e-2: 3.2593e-1, 1e-3: 9.5243e-2,
                      1e-4: 3.0292e-2, 1e-5: 9.6709e-3}
+# and the H^-1 columns of the same tables (the paper's discrete H^-1 norm is not stated)
+PAPER_TABLE6_HM1SQ = {1e0: 2.1308e-3, 1e-1: 1.3401e-3, 1e-2: 1.9101e-4, 1e-3: 9.0010e-6,
+                      1e-4: 3.1821e-7, 1e-5: 1.0474e-8, 1e-6: 3.3491e-10}
+PAPER_TABLE8_HM1SQ = {1e0: 3.5241e-2, 1e-1: 2.1590e-2, 1e-2: 2.5430e-3, 1e-3: 8.8234e-5,
+                      1e-4: 2.7302e-6, 1e-5: 8.5525e-8}
 
 
 def adaptive_sample(fa, torch, dev, max_dofs: int = 1_000_000, theta: float = 0.5, n0: int = 8,
@@ -409,13 +414,15 @@ def adaptive_sample(fa, torch, dev, max_dofs: int = 1_000_000, theta: float = 0.
     """The adaptive runs of Sec. 4.2-4.3 with the mesh on the device: from the Kuhn mesh with
     n0^3 cubes, solve (FP32 V-cycle in FP64 flexible CG to 1e-8) -> residual indicator ->
     bulk marking (theta) -> longest-edge bisection, until the mesh has max_dofs unknowns;
-    then ||ubar - u_h||^2 against the paper's Tables 6 and 8 (its meshes come from another
-    refinement rule and stop at 1.3-3.7M dofs)."""
+    then ||ubar - u_h||^2 in L2 and in the discrete H^-1 norm (fem_error_hm1 on the final
+    mesh, outside the timed phases) against the paper's Tables 6 and 8 (its meshes come from
+    another refinement rule and stop at 1.3-3.7M dofs)."""
     import fem_workloads as W
-    cases = [("box (Table 6)", W.box_target(), PAPER_TABLE6_L2SQ),
-             ("1 + sin sin sin (Table 8)", W.sine_plus_one_target(), PAPER_TABLE8_L2SQ)]
+    cases = [("box (Table 6)", W.box_target(), PAPER_TABLE6_L2SQ, PAPER_TABLE6_HM1SQ),
+             ("1 + sin sin sin (Table 8)", W.sine_plus_one_target(), PAPER_TABLE8_L2SQ,
+              PAPER_TABLE8_HM1SQ)]
     out = []
-    for name, target, paper in cases:
+    for name, target, paper, paper_hm1 in cases:
         for rho, pl2 in paper.items():
             m = fa.fem_mesh_create(*W.kuhn_mesh(n0))
             ph = {"assemble": 0.0, "setup": 0.0, "solve": 0.0, "estimate_mark": 0.0,
@@ -464,11 +471,17 @@ def adaptive_sample(fa, torch, dev, max_dofs: int = 1_000_000, theta: float = 0.
                 ph["refine"] += t5 - t4
                 step += 1
             total = time.perf_counter() - t_start
+            sys_p = fa.fem_assemble_on_mesh(m, rho, target, keep_pencil=True)
+            hm = fa.fem_error_hm1(sys_p, u, target, tol=1e-10)
+            fa.fem_system_destroy(sys_p)
             fa.fem_mesh_destroy(m)
             out.append({"target": name, "rho": rho, "steps": step, "dofs": info["N"], "tets": nt,
                         "iterations_min": min(its), "iterations_max": max(its),
                         "iterations_last": its[-1], "l2sq": err["l2sq"], "paper_l2sq": pl2,
-                        "ratio_to_paper": err["l2sq"] / pl2, "total_s": total,
+                        "ratio_to_paper": err["l2sq"] / pl2, "hm1sq": hm["hm1sq"],
+                        "paper_hm1sq": paper_hm1[rho], "hm1_ratio_to_paper":
+                            hm["hm1sq"] / paper_hm1[rho],
+                        "hm1_stiffness_iterations": hm["solve"]["iterations"], "total_s": total,
                         "phases_s": ph, "dofs_per_step": dofs, "iterations_per_step": its})
     return {"workload": "adaptive loop from the Kuhn mesh n = %d to >= %d dofs, theta = %.2f, "
                         "longest-edge bisection, FP32 V-cycle in FP64 flexible CG to 1e-8"

@@ -1035,7 +1035,7 @@ static void sg_fill_ht(int ht, int64_t nr, const Csr4& A, const double* Aval, co
 }
 
 void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
-            cudaStream_t st, bool values) {
+            cudaStream_t st, bool values, bool* too_long) {
   const int64_t nr = A.nrows;
   C.nrows = A.nrows;
   C.ncols = B.ncols;
@@ -1100,6 +1100,10 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
         k_long_list<<<grid_for(nr, 256), 256, 0, st>>>(nr, flag, scan, tmp, llist, ltsz);
         FEM_CHECK_LAUNCH();
         const int64_t total = exclusive_scan(ltsz, nlong, loff, st);
+        if (total > ((int64_t)1 << 31) && too_long) {
+          *too_long = true;
+          return;
+        }
         FEM_REQUIRE(total <= ((int64_t)1 << 31), FEM_EUNSUPPORTED,
                     "spgemm: long product rows need more than 8 GB of hash tables");
         lkeys.alloc_async(total, st);
@@ -1110,6 +1114,10 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
     }
   }
   const int64_t maxc = nr > 0 ? max_of(cnt, nr, st) : 0;
+  if (maxc > kLongRowMax && too_long) {
+    *too_long = true;
+    return;
+  }
   FEM_REQUIRE(maxc <= kLongRowMax, FEM_EUNSUPPORTED,
               "spgemm: a product row has more than 8192 distinct columns");
   rowptr_from_counts(cnt, nr, C, st);
@@ -1150,7 +1158,7 @@ void spgemm_numeric(const Csr4& A, const double* Aval, const Csr4& B, const doub
   FEM_CHECK_LAUNCH();
 }
 
-void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st) {
+void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long) {
   T.nrows = (int32_t)ncols;
   T.ncols = A.nrows;
   DevBuf<unsigned long long> cnt(ncols, st), fill(ncols, st);
@@ -1195,6 +1203,10 @@ void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st) {
     FEM_CHECK_LAUNCH();
     FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
     FEM_CUDA(cudaStreamSynchronize(st));
+    if (he && too_long) {
+      *too_long = true;
+      return;
+    }
     FEM_REQUIRE(he == 0, FEM_EUNSUPPORTED, "transpose: a row has more than 8192 entries");
   }
 }
@@ -2248,7 +2260,11 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       FEM_CHECK_LAUNCH();
     }
     tr.mark("level: P = (I - w D^-1 A_F) P_t");
-    transpose(Lv.P, Lv.R, ag.nagg, st);
+    // a level whose restriction or coarse operator would have rows longer than the products
+    // handle (graded meshes make the coarse levels of the Laplacian dense) becomes the
+    // coarsest level instead
+    bool too_long = false;
+    transpose(Lv.P, Lv.R, ag.nagg, st, &too_long);
     tr.mark("level: R = P^T");
     if (lowp) {
       make_lowp(Lv.P, AMG_PREC_FP32, st);
@@ -2260,11 +2276,20 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     }
     // Galerkin coarse operator A_c = R (A P)  (Sec. 3.1)
     Csr4 AP;
-    spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true);
+    if (!too_long) spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long);
     tr.mark("level: A P (spgemm)");
     auto nxt = std::make_unique<Level>();
-    spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true);
+    if (!too_long) spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true, &too_long);
     tr.mark("level: R (A P) (spgemm)");
+    if (too_long) {
+      Lv.P = Csr4();
+      Lv.R = Csr4();
+      Lv.coarsest = true;
+      if (N <= o.coarse_max) dense_inverse(*Acur, Acur->val, Lv.Ainv, st);
+      tr.mark("coarsest (dense coarse rows): dense inverse");
+      H.L.push_back(std::move(cur));
+      break;
+    }
     nxt->Aown.ncols = (int32_t)ag.nagg;
     nxt->A = &nxt->Aown;
     if (S.pencil) {
