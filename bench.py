@@ -109,15 +109,37 @@ def oracle_sample(n: int) -> dict:
     import fem_workloads as W
     from oracle import amg, core
     t0 = time.perf_counter()
+    c0 = time.process_time()
     s = core.assemble(n, W.sine_target())
     rho = 1.0 / n ** 2
     A = s.A(rho)
     H = amg.build_hierarchy(A)
     x, it, rr, _ = amg.pcg(A, s.f, lambda r: amg.vcycle(H, r), tol=TOL)
     dt = time.perf_counter() - t0
+    cpu = time.process_time() - c0
     N = A.shape[0]
     return {"n": n, "N": N, "iterations": it, "seconds": dt, "relres": rr,
-            "value": N * it / dt}
+            "value": N * it / dt, "cores_used": cpu / dt if dt > 0 else 1.0}
+
+
+def host_cpu() -> dict:
+    """Cores this process may run on and the CPU model (from /proc/cpuinfo when present)."""
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        ncores = os.cpu_count() or 0
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "processor name") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    return {"host_cores": ncores, "cpu_model": model}
 
 
 def oracle_subprocess(n: int, timeout: float = 600.0) -> dict:
@@ -738,8 +760,9 @@ def run_ours(args, rank: int, world: int):
         line["serving"] = serving
     if cpu is not None:
         if "value" in cpu:
-            line["cpu_baseline"] = {"value": cpu["value"], "unit": "dof-iters/s", "cores": 1,
-                                    "kind": "oracle",
+            line["cpu_baseline"] = {"value": cpu["value"], "unit": "dof-iters/s",
+                                    "cores": round(cpu.get("cores_used", 1.0), 2),
+                                    "kind": "oracle", **host_cpu(),
                                     "sample": "oracle assemble + SA hierarchy + AMG-PCG to 1e-8 "
                                               "on the %d^3 mesh (%d dofs, %d iterations, %.1f s)"
                                               % (cpu["n"], cpu["N"], cpu["iterations"],
@@ -782,7 +805,9 @@ def run_reference(args, rank: int):
                                "CG, tol 1e-8; each step a bounded sample on the %d^3 mesh "
                                "(%d dofs)" % (ORACLE_N, samples[0]["N"] if samples else 0),
                    "n": ORACLE_N},
-        "cpu_baseline": {"value": value, "unit": "dof-iters/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "dof-iters/s",
+                         "cores": round(statistics.mean(s["cores_used"] for s in samples), 2)
+                         if samples else 1.0, "kind": "oracle", **host_cpu(),
                          "sample": "oracle full path on the %d^3 mesh per step" % ORACLE_N},
         "e2e": {"value": value, "unit": "dof-iters/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
