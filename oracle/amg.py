@@ -41,7 +41,8 @@ import scipy.sparse as sp
 
 UNDECIDED, IN, OUT = 1, 2, 0
 DEFAULTS = dict(theta=0.05, smoother="chebyshev", degree=2, cheb_ratio=6.0,
-                coarse_max=256, max_levels=16, seed=0, min_ratio=0.9, coarsening="sa")
+                coarse_max=256, max_levels=16, seed=0, min_ratio=0.9, coarsening="sa",
+                max_row=8192)
 
 
 # ------------------------------------------------------------- utilities
@@ -364,6 +365,11 @@ class Level:
     pass
 
 
+def _longest_row(B) -> int:
+    """Most stored entries in a row of a CSR matrix (0 for no rows)."""
+    return int(np.diff(B.indptr).max()) if B.shape[0] else 0
+
+
 def build_hierarchy(A, opts: dict | None = None, K=None, M=None):
     """Smoothed-aggregation hierarchy of A.  With K and M given (A = rho K + M),
     the coarse pencils K_l = P^T K P and M_l = P^T M P are kept as well."""
@@ -412,7 +418,21 @@ def build_hierarchy(A, opts: dict | None = None, K=None, M=None):
             L.P, L.omega = smoothed_prolongator(Al, smask, agg, nagg)
         L.R = sp.csr_matrix(L.P.T)
         L.R.sort_indices()
-        Al = spgemm(L.R, spgemm(Al, L.P))
+        AP = spgemm(Al, L.P)
+        Ac = spgemm(L.R, AP)
+        if max(_longest_row(L.R), _longest_row(AP), _longest_row(Ac)) > o["max_row"]:
+            # the restriction or a Galerkin product would have a row longer than max_row
+            # (dense coarse levels): this level is the coarsest instead
+            L.coarsest = True
+            L.P = L.R = None
+            if n <= o["coarse_max"]:
+                Lc = np.linalg.cholesky(Al.toarray())
+                Li = np.linalg.inv(Lc)
+                L.Ainv = Li.T @ Li
+            else:
+                L.Ainv = None
+            return levels
+        Al = Ac
         if K is not None:
             Kl = spgemm(L.R, spgemm(Kl, L.P))
             Ml = spgemm(L.R, spgemm(Ml, L.P))

@@ -188,3 +188,31 @@ def test_pencil_hierarchy_matches_direct_galerkin():
     for L in H[1:]:
         np.testing.assert_allclose(L.A.toarray(), (rho * L.K + L.M).toarray(), rtol=1e-12,
                                    atol=1e-13 * abs(L.A).max())
+
+
+def test_row_limit_stops_coarsening():
+    # a level whose restriction or Galerkin products would have a row longer than max_row is
+    # the coarsest: at or above every level's longest product row the hierarchy is the
+    # default one; below level 0's, it is level 0 alone, and the V-cycle is then one
+    # Chebyshev smoothing from zero
+    s = core.assemble(20, W.sine_target())
+    A = s.A(1e-2).tocsr()
+    H = amg.build_hierarchy(A)
+    assert len(H) >= 3
+
+    def longest(L):
+        AP = amg.spgemm(L.A, L.P)
+        return max(int(np.diff(B.indptr).max()) for B in (L.R, AP, amg.spgemm(L.R, AP)))
+
+    top = max(longest(L) for L in H if not L.coarsest)
+    Hs = amg.build_hierarchy(A, {"max_row": top})
+    assert len(Hs) == len(H)
+    for L, Ls in zip(H, Hs):
+        assert (L.A != Ls.A).nnz == 0
+    H1 = amg.build_hierarchy(A, {"max_row": longest(H[0]) - 1})
+    assert len(H1) == 1 and H1[0].coarsest and H1[0].Ainv is None
+    b = W.random_vector(A.shape[0], 3)
+    L0 = H1[0]
+    ref = amg.chebyshev(A, L0.dinv, b, None, L0.lmax, amg.DEFAULTS["cheb_ratio"],
+                        amg.DEFAULTS["degree"])
+    assert np.array_equal(amg.vcycle(H1, b), ref)
