@@ -135,6 +135,8 @@ def host_cpu() -> dict:
                 key = line.split(":")[0].strip().lower()
                 if key in ("model name", "cpu part", "processor name") and ":" in line:
                     model = line.split(":", 1)[1].strip()
+                    if key == "cpu part":   # Arm: the part number (0xd4f: Neoverse V2)
+                        model = "CPU part " + model
                     if key == "model name":
                         break
     except OSError:

@@ -335,6 +335,11 @@ typedef struct {
                             pencil; the finest operator of solves is unchanged);
                             default 0 = the system's rho                        */
   int32_t coarsening;    /* amg_coarsening, default smoothed aggregation         */
+  int32_t max_row;       /* a level whose restriction R, product A P or coarse
+                            operator R A P would have a row with more than max_row
+                            entries becomes the coarsest level (dense inverse if it
+                            has <= coarse_max unknowns, else the smoother alone);
+                            1..8192, default (and 0) 8192, the products' limit      */
 } amg_opts;
 
 typedef struct amg_hier_s* amg_hier;

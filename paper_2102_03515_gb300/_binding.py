@@ -58,7 +58,7 @@ class AmgOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("smoother", C.c_int32), ("degree", C.c_int32),
                 ("cheb_ratio", C.c_double), ("coarse_max", C.c_int32),
                 ("max_levels", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint32),
-                ("rho_setup", C.c_double), ("coarsening", C.c_int32)]
+                ("rho_setup", C.c_double), ("coarsening", C.c_int32), ("max_row", C.c_int32)]
 
 
 class HierInfo(C.Structure):

@@ -1035,7 +1035,7 @@ static void sg_fill_ht(int ht, int64_t nr, const Csr4& A, const double* Aval, co
 }
 
 void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
-            cudaStream_t st, bool values, bool* too_long) {
+            cudaStream_t st, bool values, bool* too_long, int64_t limit) {
   const int64_t nr = A.nrows;
   C.nrows = A.nrows;
   C.ncols = B.ncols;
@@ -1114,7 +1114,7 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
     }
   }
   const int64_t maxc = nr > 0 ? max_of(cnt, nr, st) : 0;
-  if (maxc > kLongRowMax && too_long) {
+  if (too_long && maxc > std::min<int64_t>(limit, kLongRowMax)) {
     *too_long = true;
     return;
   }
@@ -1158,7 +1158,8 @@ void spgemm_numeric(const Csr4& A, const double* Aval, const Csr4& B, const doub
   FEM_CHECK_LAUNCH();
 }
 
-void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long) {
+void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long,
+               int64_t limit) {
   T.nrows = (int32_t)ncols;
   T.ncols = A.nrows;
   DevBuf<unsigned long long> cnt(ncols, st), fill(ncols, st);
@@ -1172,6 +1173,10 @@ void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too
   if (ncols > 0) {
     k_u64_to_i64<<<grid_for(ncols, 256), 256, 0, st>>>(ncols, cnt, c64);
     FEM_CHECK_LAUNCH();
+  }
+  if (too_long && ncols > 0 && max_of(c64, ncols, st) > std::min<int64_t>(limit, kLongRowMax)) {
+    *too_long = true;
+    return;
   }
   rowptr_from_counts(c64, ncols, T, st);
   T.val.alloc(T.nnz);
@@ -2260,11 +2265,12 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       FEM_CHECK_LAUNCH();
     }
     tr.mark("level: P = (I - w D^-1 A_F) P_t");
-    // a level whose restriction or coarse operator would have rows longer than the products
-    // handle (graded meshes make the coarse levels of the Laplacian dense) becomes the
-    // coarsest level instead
+    // a level whose restriction or Galerkin products would have a row longer than max_row
+    // (at most the products' limit; graded meshes make the coarse levels of the Laplacian
+    // that dense) becomes the coarsest level instead
     bool too_long = false;
-    transpose(Lv.P, Lv.R, ag.nagg, st, &too_long);
+    const int64_t row_limit = o.max_row > 0 ? o.max_row : kLongRowMax;
+    transpose(Lv.P, Lv.R, ag.nagg, st, &too_long, row_limit);
     tr.mark("level: R = P^T");
     if (lowp) {
       make_lowp(Lv.P, AMG_PREC_FP32, st);
@@ -2276,10 +2282,11 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     }
     // Galerkin coarse operator A_c = R (A P)  (Sec. 3.1)
     Csr4 AP;
-    if (!too_long) spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long);
+    if (!too_long) spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long, row_limit);
     tr.mark("level: A P (spgemm)");
     auto nxt = std::make_unique<Level>();
-    if (!too_long) spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true, &too_long);
+    if (!too_long)
+      spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true, &too_long, row_limit);
     tr.mark("level: R (A P) (spgemm)");
     if (too_long) {
       Lv.P = Csr4();

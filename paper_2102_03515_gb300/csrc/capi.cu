@@ -379,6 +379,7 @@ void amg_default_opts(amg_opts* o) {
   o->seed = 0;
   o->rho_setup = 0.0;
   o->coarsening = AMG_COARSEN_SA;
+  o->max_row = 8192;
 }
 
 fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hier* out) {
@@ -390,6 +391,7 @@ fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hie
     amg_default_opts(&o);
     if (opts) o = *opts;
     FEM_REQUIRE(o.theta >= 0.0 && o.theta < 1.0, FEM_EINVAL, "amg_setup: theta in [0, 1)");
+    FEM_REQUIRE(o.max_row >= 0 && o.max_row <= 8192, FEM_EINVAL, "amg_setup: max_row in [0, 8192]");
     FEM_REQUIRE(o.degree >= 1 && o.degree <= 15, FEM_EINVAL, "amg_setup: degree in [1, 15]");
     FEM_REQUIRE(o.cheb_ratio > 1.0, FEM_EINVAL, "amg_setup: cheb_ratio > 1");
     FEM_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= 4096, FEM_EINVAL,

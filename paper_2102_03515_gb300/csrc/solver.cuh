@@ -187,11 +187,14 @@ void smooth_post(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& c
 // ------------------------------------------------------------------ setup (amg_setup.cu)
 void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st);
 void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
-            cudaStream_t st, bool values = true, bool* too_long = nullptr);
+            cudaStream_t st, bool values = true, bool* too_long = nullptr,
+            int64_t limit = 8192);
 // T = A^T.  A product row beyond the products' limits (8192 distinct columns, 8 GB of
 // long-row hash tables) or a transposed row beyond 8192 entries throws FEM_EUNSUPPORTED, or,
-// when too_long is given, sets *too_long and returns with the output unset.
-void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long = nullptr);
+// when too_long is given, sets *too_long and returns with the output unset; with too_long
+// given, a row longer than limit (<= 8192) counts as too long as well.
+void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long = nullptr,
+               int64_t limit = 8192);
 double gershgorin(const Csr4& A, const double* val, cudaStream_t st);
 void dense_inverse(const Csr4& A, const double* val, DevBuf<double>& Ainv, cudaStream_t st);
 

@@ -249,3 +249,32 @@ def test_graded_mesh_hierarchy_with_long_coarse_rows(fa):
     finally:
         fa.amg_hier_destroy(h)
         fa.fem_system_destroy(sys_)
+
+
+@pytest.mark.parametrize("max_row", [500, 300])
+def test_row_limit_makes_the_dense_level_the_coarsest(fa, max_row):
+    # on the graded mesh the first coarse operator has rows of about 700 entries and the
+    # restriction rows of about 360: a limit of 500 stops at the Galerkin product, 300 at the
+    # restriction; either way level 0 is the coarsest and the V-cycle is its smoother alone
+    from oracle import amg
+    from tests import gpu_util as G
+    xyz, tets, d = _graded_box_mesh()
+    rho = 1e-6
+    s = core.assemble_mesh(xyz, tets, d, W.box_target())
+    A = s.A(rho).tocsr()
+    Ho = amg.build_hierarchy(A, {"max_row": max_row})
+    assert len(Ho) == 1 and Ho[0].coarsest and Ho[0].Ainv is None
+    sys_ = fa.fem_assemble_mesh(xyz, tets, d, rho, W.box_target())
+    h = fa.amg_setup(sys_, max_row=max_row)
+    try:
+        assert fa.amg_hier_get_info(h)["levels"] == 1
+        r = W.random_vector(A.shape[0], 6)
+        z = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        fa.amg_vcycle(h, _dev(r), z)
+        assert G.rel(z.cpu().numpy(), amg.vcycle(Ho, r, {})) <= 1e-12
+        u = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        res = fa.pcg_solve(sys_, h, None, u, tol=1e-8)[0]
+        assert res["status"] == "FEM_OK"
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
