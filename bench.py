@@ -683,6 +683,8 @@ def run_ours(args, rank: int, world: int):
     real_nnz = m ** 3 + 6 * m * m * (m - 1) + 6 * m * (m - 1) ** 2 + 2 * (m - 1) ** 3
     flops = 2.0 * real_nnz
     achieved = flops / (kms * 1e-3) / 1e12
+    # the FP64 ceiling measured on this GPU (independent FMA chains), beside the derived peak
+    fp64_measured = fa.fem_measure_fp64_rate(10)
 
     # ---- the V-cycle as a whole against the HBM roofline (FP32 hierarchy, warm, in situ)
     sys_ = fa.fem_assemble(n, rho, target)
@@ -747,6 +749,8 @@ def run_ours(args, rank: int, world: int):
                 "ms_per_step": e2e_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_measured_fma": fp64_measured,
+                     "frac_of_measured_fma": achieved / fp64_measured if fp64_measured else None,
                      "traffic": STENCIL64_TRAFFIC,
                      "kernel": "FP64 15-point stencil q = A p (launch shape %s)" % k64_name,
                      "kernel_ms": kms, "flops_per_launch": flops,

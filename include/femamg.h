@@ -503,6 +503,13 @@ const char* fem_autotune_report(void);
 void fem_autotune_clear(void);
 fem_status fem_autotune_pin(const char* kernel, int32_t variant);
 
+/* Measured FP64 fused multiply-add throughput of the current GPU in TFLOP/s (2 flops per
+ * FMA): `reps` timed launches (CUDA events on the stream, after one untimed launch) of a
+ * kernel with 8 independent FMA chains per thread and 8 blocks of 256 threads per SM.  The
+ * ceiling of the FP64 kernels, which this GPU's FP64 rate makes ALU-bound rather than
+ * HBM-bound.  Synchronises the stream.  Errors: FEM_EINVAL (null tflops_out, reps < 1). */
+fem_status fem_measure_fp64_rate(int32_t reps, void* stream, double* tflops_out);
+
 /* Library version string. */
 const char* fem_version(void);
 

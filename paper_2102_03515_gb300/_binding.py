@@ -117,6 +117,7 @@ SIGNATURES = {
                                     P(VP)]),
     "fem_errors": (C.c_int, [VP, VP, P(Target), C.c_double, C.c_int32, VP, P(ErrorsResult)]),
     "fem_recover": (C.c_int, [VP, VP, P(Target), VP, VP, VP]),
+    "fem_measure_fp64_rate": (C.c_int, [C.c_int32, VP, P(C.c_double)]),
     "fem_error_hm1": (C.c_int, [VP, VP, P(Target), C.c_double, C.c_double, VP, P(C.c_double),
                                 P(PcgResult)]),
     "fem_error_indicator": (C.c_int, [VP, VP, P(Target), C.c_int32, VP, VP, P(C.c_double)]),
@@ -205,6 +206,14 @@ def fem_last_error() -> str:
 
 def fem_version() -> str:
     return lib().fem_version().decode()
+
+
+def fem_measure_fp64_rate(reps: int = 10, stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU, TFLOP/s."""
+    v = C.c_double(0.0)
+    _check(lib().fem_measure_fp64_rate(int(reps), _stream(stream), C.byref(v)),
+           "fem_measure_fp64_rate")
+    return v.value
 
 
 def fem_kernel_launches() -> int:

@@ -109,6 +109,15 @@ const char* fem_last_error(void) { return g_last_error.c_str(); }
 
 const char* fem_version(void) { return "femamg 0.1 (sm_103a)"; }
 
+fem_status fem_measure_fp64_rate(int32_t reps, void* stream, double* tflops_out) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(tflops_out && reps >= 1, FEM_EINVAL, "fem_measure_fp64_rate: bad argument");
+    StreamScope scope(as_stream(stream));
+    *tflops_out = fp64_fma_rate(reps, as_stream(stream));
+    return FEM_OK;
+  });
+}
+
 int64_t fem_kernel_launches(void) { return (int64_t)launches_now(); }
 
 fem_status fem_assemble(const fem_kuhn_desc* mesh, double rho, const fem_target* target,

@@ -1210,4 +1210,52 @@ void finalize_sums(const double* partials, int nblocks, int nv, double* out, cud
   FEM_CHECK_LAUNCH();
 }
 
+// ------------------------------------------------------------------ FP64 throughput probe
+
+namespace {
+// 8 independent chains of fused multiply-adds per thread, so that the FP64 pipe's throughput
+// and not its latency bounds the kernel; the chains converge to c / (1 - m) (no overflow or
+// subnormal values), and the final test keeps them live
+__global__ void __launch_bounds__(256) k_fp64_fma_probe(int iters, double m, double c,
+                                                        double* out) {
+  double a[8];
+  const double s = 1.0 + 1e-9 * (double)(blockIdx.x * blockDim.x + threadIdx.x);
+#pragma unroll
+  for (int k = 0; k < 8; k++) a[k] = s + k;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = fma(a[k], m, c);
+  }
+  const double t = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  if (t == -1.0) out[0] = t;
+}
+}  // namespace
+
+double fp64_fma_rate(int reps, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  FEM_CUDA(cudaGetDevice(&dev));
+  FEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned blocks = 8u * (unsigned)sms;
+  const int iters = 4096;
+  DevBuf<double> out(1, st);
+  k_fp64_fma_probe<<<blocks, 256, 0, st>>>(iters, 0.9999999, 1e-7, out);
+  FEM_CHECK_LAUNCH();
+  cudaEvent_t e0, e1;
+  FEM_CUDA(cudaEventCreate(&e0));
+  FEM_CUDA(cudaEventCreate(&e1));
+  FEM_CUDA(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps; r++) {
+    k_fp64_fma_probe<<<blocks, 256, 0, st>>>(iters, 0.9999999, 1e-7, out);
+    FEM_CHECK_LAUNCH();
+  }
+  FEM_CUDA(cudaEventRecord(e1, st));
+  FEM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  FEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * 256.0 * reps;
+  return flops / (ms * 1e-3) / 1e12;
+}
+
 }  // namespace fem

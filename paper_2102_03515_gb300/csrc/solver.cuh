@@ -233,6 +233,9 @@ int64_t exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStream_t 
 // C.rowptr from per-row counts padded to multiples of 4; sets C.nnz and allocates C.col
 void rowptr_from_counts(const int64_t* cnt, int64_t n, Csr4& C, cudaStream_t st);
 
+// measured FP64 FMA throughput (TFLOP/s) over reps timed launches of a probe kernel (ops.cu)
+double fp64_fma_rate(int reps, cudaStream_t st);
+
 // ------------------------------------------------------------------ utilities
 void finalize_sums(const double* partials, int nblocks, int nv, double* out, cudaStream_t st,
                    const int* done = nullptr);

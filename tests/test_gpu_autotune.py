@@ -240,3 +240,9 @@ def test_graph_replayed_vcycle_equals_the_plain_one(fa):
             assert torch.equal(z1, z2)
     finally:
         fa.fem_system_destroy(sys_)
+
+
+def test_measured_fp64_rate_is_plausible(fa):
+    # FMA throughput of the FP64 pipe: positive and of the order of the nominal 1.25 TFLOP/s
+    rate = fa.fem_measure_fp64_rate(3)
+    assert 0.05 < rate < 5.0, rate
