@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 N_CELLS = 256
 TOL = 1e-8
 ORACLE_N = 48          # reference-arm step: the same workload on a 48^3 mesh
-BASELINE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
+CPU_SAMPLE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
 # dominant kernel: the FP64 15-point stencil A p of every CG iteration; 2 flops per stored
 # stencil entry, FP64 peak from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -554,7 +554,7 @@ def run_ours(args, rank: int, world: int):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # oracle first: no process is forked after the GPU is initialised
         try:
-            cpu = oracle_subprocess(BASELINE_N)
+            cpu = oracle_subprocess(CPU_SAMPLE_N)
         except Exception as e:  # the GPU number stands on its own
             cpu = {"error": str(e)[:300]}
 
