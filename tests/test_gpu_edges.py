@@ -1,0 +1,98 @@
+"""Edge cases of the path against the oracle: the smallest meshes (1, 8 and 27 unknowns: the
+finest level is the coarsest, solved by its dense inverse), a zero right-hand side (u = 0 is
+exact, no iteration), rho far on either side of h^2 (mass- and stiffness-dominated systems),
+and arguments outside what the library accepts (refused with FEM_EINVAL)."""
+import numpy as np
+import pytest
+
+import fem_workloads as W
+from oracle import core
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fa():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2102_03515_gb300 import build as b
+    b.build()
+    import paper_2102_03515_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_smallest_meshes_solve_like_the_oracle(fa, n, fp32):
+    rho = 1e-2
+    s = core.assemble(n, W.sine_target())
+    x = core.cholesky_solve(s.A(rho).toarray(), s.f)
+    sys_ = fa.fem_assemble(n, rho, W.sine_target())
+    h = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32 if fp32 else fa.AMG_PREC_FP64)
+    try:
+        assert fa.amg_hier_get_info(h)["levels"] == 1
+        u = torch.zeros(len(s.f), dtype=torch.float64, device="cuda")
+        res = fa.pcg_solve(sys_, h, None, u, tol=1e-13)[0]
+        assert res["status"] == "FEM_OK" and res["iterations"] <= 2
+        assert _rel(u.cpu().numpy(), x) <= 1e-12
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+
+
+def test_zero_right_hand_side_gives_zero_without_iterating(fa):
+    n = 9
+    sys_ = fa.fem_assemble(n, 1e-2, W.sine_target())
+    h = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32)
+    try:
+        N = (n - 1) ** 3
+        f = torch.zeros(N, dtype=torch.float64, device="cuda")
+        u = torch.full((N,), 7.0, dtype=torch.float64, device="cuda")
+        res = fa.pcg_solve(sys_, h, f, u, tol=1e-8)[0]
+        assert res["status"] == "FEM_OK" and res["iterations"] == 0
+        assert torch.count_nonzero(u).item() == 0
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+
+
+@pytest.mark.parametrize("rho", [1e-12, 1e6])
+def test_extreme_rho_solves_like_the_oracle(fa, rho):
+    n = 12
+    s = core.assemble(n, W.box_target(0.3, 0.7))
+    x = core.cholesky_solve(s.A(rho).toarray(), s.f)
+    sys_ = fa.fem_assemble(n, rho, W.box_target(0.3, 0.7))
+    h = fa.amg_setup(sys_)
+    try:
+        u = torch.zeros(len(s.f), dtype=torch.float64, device="cuda")
+        res = fa.pcg_solve(sys_, h, None, u, tol=1e-13)[0]
+        assert res["status"] == "FEM_OK"
+        assert _rel(u.cpu().numpy(), x) <= 1e-10
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+
+
+def test_arguments_outside_the_accepted_range_are_refused(fa):
+    for n in (1, 1291):
+        with pytest.raises(fa.FemError):
+            fa.fem_assemble(n, 1.0, W.sine_target())
+    for rho in (0.0, -1.0, float("inf")):
+        with pytest.raises(fa.FemError):
+            fa.fem_assemble(8, rho, W.sine_target())
+    sys_ = fa.fem_assemble(8, 1.0, W.sine_target())
+    try:
+        with pytest.raises(fa.FemError):
+            fa.amg_setup(sys_, max_row=9000)
+        with pytest.raises(fa.FemError):
+            fa.amg_setup(sys_, coarse_max=0)
+        u = torch.zeros(7 ** 3, dtype=torch.float64, device="cuda")
+        with pytest.raises(fa.FemError):
+            fa.pcg_solve(sys_, None, None, u, tol=0.0)
+    finally:
+        fa.fem_system_destroy(sys_)
