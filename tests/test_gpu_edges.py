@@ -1,7 +1,8 @@
 """Edge cases of the path against the oracle: the smallest meshes (1, 8 and 27 unknowns: the
 finest level is the coarsest, solved by its dense inverse), a zero right-hand side (u = 0 is
 exact, no iteration), rho far on either side of h^2 (mass- and stiffness-dominated systems),
-and arguments outside what the library accepts (refused with FEM_EINVAL)."""
+arguments outside what the library accepts (refused with FEM_EINVAL), and a general mesh
+without unknowns (refused) or with a single one."""
 import numpy as np
 import pytest
 
@@ -94,5 +95,24 @@ def test_arguments_outside_the_accepted_range_are_refused(fa):
         u = torch.zeros(7 ** 3, dtype=torch.float64, device="cuda")
         with pytest.raises(fa.FemError):
             fa.pcg_solve(sys_, None, None, u, tol=0.0)
+    finally:
+        fa.fem_system_destroy(sys_)
+
+
+def test_a_mesh_without_unknowns_is_refused(fa):
+    # one tet whose four vertices all carry the Dirichlet condition: no unknown to solve for
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    with pytest.raises(fa.FemError):
+        fa.fem_assemble_mesh(xyz, tets, np.ones(4, np.uint8), 1.0, W.sine_target())
+    # the same tet with one free vertex is a system of one unknown
+    d = np.array([1, 1, 1, 0], np.uint8)
+    s = core.assemble_mesh(xyz, tets, d, W.sine_target())
+    sys_ = fa.fem_assemble_mesh(xyz, tets, d, 1.0, W.sine_target())
+    try:
+        assert fa.fem_system_get_info(sys_)["N"] == 1
+        f = torch.empty(1, dtype=torch.float64, device="cuda")
+        fa.fem_system_get_rhs(sys_, f)
+        assert abs(f.item() - s.f[0]) <= 1e-13 * abs(s.f[0])
     finally:
         fa.fem_system_destroy(sys_)
