@@ -284,8 +284,10 @@ def fem_error_hm1(sys, u, target: dict, scale: float = 1.0, tol: float = 1e-10,
     t = _target(target, keep)
     v = C.c_double(0.0)
     r = PcgResult()
-    _check(lib().fem_error_hm1(sys, _ptr(u), C.byref(t), float(scale), float(tol),
-                               _stream(stream), C.byref(v), C.byref(r)), "fem_error_hm1")
+    st = lib().fem_error_hm1(sys, _ptr(u), C.byref(t), float(scale), float(tol),
+                             _stream(stream), C.byref(v), C.byref(r))
+    if st not in (FEM_OK, FEM_ENOCONV):   # FEM_ENOCONV: the value of the last iterate
+        raise FemError(st, fem_last_error() or "fem_error_hm1")
     return {"hm1sq": v.value, "solve": r.as_dict()}
 
 
