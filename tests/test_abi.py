@@ -54,3 +54,22 @@ def test_version_and_error_strings_without_gpu(lib):
     import paper_2102_03515_gb300 as fa
     assert "sm_103a" in fa.fem_version()
     assert isinstance(fa.fem_last_error(), str)
+
+
+def test_autotuner_pins_and_clears_without_a_gpu(lib):
+    # the tuner's table is host state: pinning, unpinning, clearing and the JSON report need
+    # no device
+    import paper_2102_03515_gb300 as fa
+    fa.fem_autotune_clear()
+    rep = fa.fem_autotune_report()
+    assert rep["entries"] == [] and rep["pins"] == {}
+    fa.fem_autotune_pin("csr_f64", 3)
+    fa.fem_autotune_pin("stencil_f32", 1)
+    fa.fem_autotune_pin("csr_f64", 2)   # a second pin of a family replaces the first
+    assert fa.fem_autotune_report()["pins"] == {"stencil_f32": 1, "csr_f64": 2}
+    fa.fem_autotune_pin("stencil_f32", -1)
+    assert fa.fem_autotune_report()["pins"] == {"csr_f64": 2}
+    fa.fem_autotune_clear()
+    assert fa.fem_autotune_report()["pins"] == {}
+    from paper_2102_03515_gb300 import _binding as B
+    assert lib.fem_autotune_pin(None, 0) == B.FEM_EINVAL
