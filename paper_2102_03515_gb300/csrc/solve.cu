@@ -564,7 +564,7 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
       FEM_CUDA(cudaEventSynchronize(W.ev[(k - 1) & 1]));
       const PcgState& hs = W.hstate[(k - 1) & 1];
       if (hs.done) finished = true;
-      if (o.cancel_host && *o.cancel_host) {
+      if (!finished && o.cancel_host && *o.cancel_host) {   // a finished solve stands
         status = FEM_ECANCELLED;
         finished = true;
       }

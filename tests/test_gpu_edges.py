@@ -116,3 +116,34 @@ def test_a_mesh_without_unknowns_is_refused(fa):
         assert abs(f.item() - s.f[0]) <= 1e-13 * abs(s.f[0])
     finally:
         fa.fem_system_destroy(sys_)
+
+
+def test_iteration_cap_and_cancellation(fa):
+    # max_iter reached: FEM_ENOCONV with the iterate of the last iteration written; a raised
+    # host cancel flag: FEM_ECANCELLED within two chunks of two iterations; a solve that
+    # finishes is never reported cancelled
+    import ctypes
+    n = 24
+    sys_ = fa.fem_assemble(n, 1.0, W.sine_target())
+    h = fa.amg_setup(sys_)
+    try:
+        N = (n - 1) ** 3
+        u = torch.zeros(N, dtype=torch.float64, device="cuda")
+        res = fa.pcg_solve(sys_, h, None, u, tol=1e-14, max_iter=3)[0]
+        assert res["status"] == "FEM_ENOCONV" and res["iterations"] == 3
+        assert 1e-14 < res["relres"] < 1.0 and torch.count_nonzero(u).item() == N
+        flag = ctypes.c_int32(1)
+        with pytest.raises(fa.FemError) as ei:
+            fa.pcg_solve(sys_, h, None, u, tol=1e-14, cancel_host=ctypes.pointer(flag))
+        assert ei.value.status == 6   # FEM_ECANCELLED
+        sys2 = fa.fem_assemble(2, 1.0, W.sine_target())   # one unknown: exact after one step
+        try:
+            u2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+            res = fa.pcg_solve(sys2, None, None, u2, tol=1e-8,
+                               cancel_host=ctypes.pointer(flag))[0]
+            assert res["status"] == "FEM_OK"
+        finally:
+            fa.fem_system_destroy(sys2)
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
