@@ -4,6 +4,19 @@ This package is a thin ctypes binding of the CUDA library ``_lib/libfemamg.so`` 
 ``include/femamg.h``).  Every step of the solver runs in the library's kernels; this
 module only marshals arguments (torch tensors as device buffers, torch streams).  If the
 library is missing the import of any entry point raises: there is no fallback.
+
+A solve at h = 1/n with rho = h^2 and the smooth target of Sec. 4.1::
+
+    import torch, paper_2102_03515_gb300 as fa
+    n = 128
+    sys_ = fa.fem_assemble(n, 1.0 / n ** 2, {"kind": "sine"})
+    h = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32)      # FP32 V-cycle
+    u = torch.zeros((n - 1) ** 3, dtype=torch.float64, device="cuda")
+    res = fa.pcg_solve(sys_, h, None, u, tol=1e-8)[0]         # flexible CG, FP64
+    err = fa.fem_errors(sys_, u, {"kind": "sine"})            # ||ubar - u_h||^2 in L2, H1
+    hm1 = fa.fem_error_hm1(sys_, u, {"kind": "sine"})         # ... in the discrete H^-1
+    fa.amg_hier_destroy(h)
+    fa.fem_system_destroy(sys_)
 """
 from __future__ import annotations
 
