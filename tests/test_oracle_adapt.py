@@ -263,3 +263,26 @@ def test_bulk_marking_brute_force(seed, theta):
             best = t
     assert np.array_equal(got, eta >= best)
     assert eta[got].sum() >= goal * (1 - 1e-15)
+
+
+def test_tet_gradients_reproduce_the_barycentric_coordinates():
+    # lambda_a is the affine function with lambda_a(x_b) = delta_ab: its gradient dotted with
+    # x_b - x_0 is delta_ab - delta_a0, the four gradients sum to zero, and the volume is the
+    # tet's (a unit reference tet, scaled and sheared copies, and a jittered Kuhn mesh)
+    ref = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    A = np.array([[2.0, 0.3, 0.0], [0.0, 0.5, 0.1], [0.2, 0.0, 1.5]])
+    xyz = np.concatenate([ref, ref @ A.T + 3.0])
+    tets = np.array([[0, 1, 2, 3], [4, 5, 6, 7]])
+    vol, g = core.tet_gradients(xyz, tets)
+    assert np.allclose(vol, [1.0 / 6.0, abs(np.linalg.det(A)) / 6.0], rtol=1e-14)
+    assert np.allclose(g[0], np.array([[-1, -1, -1], [1, 0, 0], [0, 1, 0], [0, 0, 1]]),
+                       atol=1e-15)
+    x2, t2, _ = W.kuhn_mesh(4, W.jittered_xyz(4, 0.2, seed=2))
+    for X, T in ((xyz, tets), (x2, t2)):
+        vol, g = core.tet_gradients(X, T)
+        P = X[T]
+        lam = np.einsum("tad,tbd->tab", g, P - P[:, :1, :])   # grad lambda_a . (x_b - x_0)
+        want = np.eye(4)[None] - np.eye(4)[None, :, :1]
+        assert np.allclose(lam, want, atol=1e-12)
+        assert np.allclose(g.sum(axis=1), 0.0, atol=1e-12)
+        assert np.allclose(vol, np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6.0, rtol=1e-13)
