@@ -216,3 +216,44 @@ def test_row_limit_stops_coarsening():
     ref = amg.chebyshev(A, L0.dinv, b, None, L0.lmax, amg.DEFAULTS["cheb_ratio"],
                         amg.DEFAULTS["degree"])
     assert np.array_equal(amg.vcycle(H1, b), ref)
+
+
+def test_strength_gershgorin_and_l1_jacobi_against_independent_facts():
+    # strength: a brute-force loop over the stored entries of a random symmetric matrix with a
+    # positive diagonal (stored zeros are never strong); Gershgorin: the bound lies above the
+    # largest eigenvalue of D^-1 A and is 1 for a diagonal matrix; l1-Jacobi: exact in one
+    # step for a positive diagonal matrix, and for SPD A its error propagator I - D_l1^-1 A
+    # has spectral radius below 1 (the l1 row sums dominate the diagonal part of A)
+    rng = np.random.default_rng(8)
+    n = 30
+    R = sp.random(n, n, density=0.2, random_state=3, format="csr")
+    S = (R + R.T).tocsr()
+    S.setdiag(np.abs(S).sum(axis=1).A1 * 0.5 + rng.uniform(0.5, 1.5, n))
+    S = S.tocsr()
+    off = np.flatnonzero(np.repeat(np.arange(n), np.diff(S.indptr)) != S.indices)
+    S.data[off[::7]] = 0.0                  # a few stored zeros off the diagonal
+    theta = 0.1
+    mask = amg.strength(S, theta)
+    d = S.diagonal()
+    rows = np.repeat(np.arange(n), np.diff(S.indptr))
+    for e, (i, j, v) in enumerate(zip(rows, S.indices, S.data)):
+        want = i != j and v != 0.0 and abs(v) >= theta * np.sqrt(d[i] * d[j])
+        assert bool(mask[e]) == want
+    A = core.assemble(6, W.sine_target()).A(1e-2).tocsr()
+    Dinv = np.diag(1.0 / A.diagonal())
+    lam = np.max(np.linalg.eigvals(Dinv @ A.toarray()).real)
+    assert amg.gershgorin(A) >= lam * (1 - 1e-12)
+    Dg = sp.diags(rng.uniform(1.0, 2.0, 10)).tocsr()
+    assert amg.gershgorin(Dg) == 1.0
+    b = rng.standard_normal(10)
+    assert np.allclose(amg.l1_jacobi(Dg, Dg.diagonal(), b, None), b / Dg.diagonal(), rtol=0,
+                       atol=0)
+    l1 = np.abs(A).sum(axis=1).A1
+    Ad = A.toarray()
+    E = np.eye(len(l1)) - Ad / l1[:, None]
+    assert np.max(np.abs(np.linalg.eigvals(E))) < 1.0
+    x = rng.standard_normal(len(l1))
+    bb = Ad @ rng.standard_normal(len(l1))
+    xs = np.linalg.solve(Ad, bb)
+    e0, e1 = x - xs, amg.l1_jacobi(A, l1, bb, x) - xs
+    assert e1 @ Ad @ e1 < e0 @ Ad @ e0
