@@ -73,3 +73,17 @@ def test_autotuner_pins_and_clears_without_a_gpu(lib):
     assert fa.fem_autotune_report()["pins"] == {}
     from paper_2102_03515_gb300 import _binding as B
     assert lib.fem_autotune_pin(None, 0) == B.FEM_EINVAL
+
+
+def test_build_targets_sm_103a_only_and_keeps_refinement_unfused():
+    # every translation unit is compiled for sm_103a alone with line info; the refinement's
+    # decisions are kept free of FMA contraction; every .cu file of the library is built
+    from paper_2102_03515_gb300 import build as b
+    srcs = sorted(f for f in os.listdir(b.SRC) if f.endswith(".cu"))
+    assert sorted(b.SOURCES) == srcs
+    for s in srcs:
+        f = b._flags(s)
+        gencodes = [f[i + 1] for i, t in enumerate(f) if t == "-gencode"]
+        assert gencodes == ["arch=compute_103a,code=sm_103a"] and "-lineinfo" in f
+        assert ("-fmad=false" in f) == (s in b.NO_FMAD)
+    assert b.NO_FMAD == {"adapt.cu"}
