@@ -401,7 +401,10 @@ typedef struct {
   int32_t flexible;         /* -1 auto (on for FP32/BF16 V-cycles), 0 off, 1 on        */
   int32_t use_x0;           /* 1: u_dev holds the initial guess, 0: start from zero    */
   int32_t use_graph;        /* 1: replay iterations as a CUDA graph (default 1)       */
-  const volatile int32_t* cancel_host; /* optional host flag; nonzero cancels          */
+  const volatile int32_t* cancel_host; /* optional host flag; nonzero cancels: read
+                               every two iterations, the solve then returns
+                               FEM_ECANCELLED with its iterate so far, unless it
+                               had already converged or stopped                       */
 } pcg_opts;
 
 typedef struct {
