@@ -152,11 +152,13 @@ fem_status fem_assemble_rhs(fem_system sys, const fem_target* target, double* f_
  * a fixed pre-reserved budget, latency-critical loops that must not pay for an allocation
  * and its implicit synchronisation -- get the same f_dev as fem_assemble_rhs, computed in a
  * fixed 17 MB scratch array that the library holds on every GPU it is loaded on until the
- * process exits.  Limits: n <= 64 cells per side and at most 64 bumps; larger inputs return
- * FEM_EINVAL with a message.  The first call on each device looks up the array's device
- * address and must not be made during a stream capture.  All calls share the array: calls
- * that overlap on the GPU (different streams without ordering) race and must not be issued.
- * Returns after the work is complete. */
+ * process exits.  Limits: Kuhn meshes with n <= 64 cells per side, at most 64 bumps, and
+ * targets given by formula (FEM_TARGET_QUADVALS is not taken); other inputs return
+ * FEM_EINVAL with a message naming the limit.  The first call on each device looks up the
+ * array's device address.  Every call synchronises its stream before it returns (the bump
+ * parameters are copied from the caller's host arrays), so no call may be made during a
+ * stream capture.  All calls share the array: calls that overlap on the GPU (different
+ * streams without ordering) race and must not be issued. */
 fem_status fem_assemble_rhs_noalloc(fem_system sys, const fem_target* target, double* f_dev,
                                     void* stream);
 
@@ -402,9 +404,11 @@ typedef struct {
   int32_t use_x0;           /* 1: u_dev holds the initial guess, 0: start from zero    */
   int32_t use_graph;        /* 1: replay iterations as a CUDA graph (default 1)       */
   const volatile int32_t* cancel_host; /* optional host flag; nonzero cancels: read
-                               every two iterations, the solve then returns
-                               FEM_ECANCELLED with its iterate so far, unless it
-                               had already converged or stopped                       */
+                               on the host after every chunk of two iterations,
+                               while the next chunk is already queued; the solve
+                               then returns FEM_ECANCELLED with its iterate so far,
+                               unless it converged or stopped by the end of the
+                               chunks it ran (then its own status is returned)      */
 } pcg_opts;
 
 typedef struct {

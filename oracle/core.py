@@ -33,12 +33,16 @@ _KINDS = {"sine": T_SINE, "box": T_BOX, "bumps": T_BUMPS,
 
 
 def build(force: bool = False) -> str:
-    """Compile the C core with gcc (no FMA contraction: same results on x86 and Arm)."""
+    """Compile the C core with gcc (no FMA contraction: same results on x86 and Arm), with
+    OpenMP where gcc has it (row loops only; the results do not depend on the threads)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -62,6 +66,9 @@ def _load():
         if _lib is None:
             lib = C.CDLL(build())
             P = C.POINTER
+            lib.ora_set_threads.argtypes = [C.c_int]
+            lib.ora_set_threads.restype = C.c_int
+            lib.ora_set_threads(1)
             lib.ora_uniform_xyz.argtypes = [C.c_int, P(C.c_double)]
             lib.ora_kuhn_tets.argtypes = [C.c_int, P(C.c_int32)]
             lib.ora_element.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double)]
@@ -92,6 +99,12 @@ def _load():
                                        P(C.c_double)]
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the C core's row loops (assembly, A x); 1 (serial) unless set.  Returns
+    the count in effect (1 when the core was built without OpenMP)."""
+    return int(_load().ora_set_threads(int(n)))
 
 
 def _dp(a):

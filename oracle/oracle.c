@@ -19,12 +19,31 @@
  *   - L2 and H1-seminorm errors by quadrature (Sec. 4.1, Tables 1-2).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so x86 and
- * aarch64 hosts give identical results).
+ * aarch64 hosts give identical results), with -fopenmp where the compiler has it: the
+ * independent rows of assembly and of A x are then shared out among threads (the thread
+ * count is set by ora_set_threads, 1 by default) without changing any result.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the row loops of assembly and of A x (1 = serial; without OpenMP always 1).
+ * Returns the count in effect. */
+int ora_set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+  omp_set_num_threads(nthreads);
+  return nthreads;
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ mesh */
 
@@ -317,21 +336,33 @@ int ora_assemble(int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
     int64_t d = inc_ptr[v + 1] - inc_ptr[v];
     if (d > maxdeg) maxdeg = (int)d;
   }
-  int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (4 * (size_t)maxdeg + 1));
-  for (int64_t r = 0; r < ndof; r++) {
-    int64_t v = row_vertex[r];
-    int cnt = 0;
-    for (int64_t e = inc_ptr[v]; e < inc_ptr[v + 1]; e++)
-      for (int a = 0; a < 4; a++) {
-        int32_t w = dof[tets[4 * inc[e] + a]];
-        if (w >= 0) buf[cnt++] = w;
-      }
-    qsort(buf, cnt, sizeof(int32_t), cmp_i32);
-    int u = 0;
-    for (int q = 0; q < cnt; q++)
-      if (u == 0 || buf[q] != buf[u - 1]) buf[u++] = buf[q];
-    rowptr[r + 1] = rowptr[r] + u;
+  /* rows are independent: with OpenMP they are shared out among threads (each with its
+   * own scratch list); every row is computed the same way whatever the thread count */
+  int alloc_fail = 0;
+#pragma omp parallel reduction(| : alloc_fail)
+  {
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (4 * (size_t)maxdeg + 1));
+    if (!buf) alloc_fail = 1;
+#pragma omp for schedule(static, 1024)
+    for (int64_t r = 0; r < ndof; r++) {
+      if (!buf) continue;
+      int64_t v = row_vertex[r];
+      int cnt = 0;
+      for (int64_t e = inc_ptr[v]; e < inc_ptr[v + 1]; e++)
+        for (int a = 0; a < 4; a++) {
+          int32_t w = dof[tets[4 * inc[e] + a]];
+          if (w >= 0) buf[cnt++] = w;
+        }
+      qsort(buf, cnt, sizeof(int32_t), cmp_i32);
+      int u = 0;
+      for (int q = 0; q < cnt; q++)
+        if (u == 0 || buf[q] != buf[u - 1]) buf[u++] = buf[q];
+      rowptr[r + 1] = u;   /* row length; the prefix sum follows */
+    }
+    free(buf);
   }
+  if (alloc_fail) return -1;
+  for (int64_t r = 0; r < ndof; r++) rowptr[r + 1] += rowptr[r];
   int64_t nnz = rowptr[ndof];
   int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1));
   double *K = (double *)calloc(nnz > 0 ? nnz : 1, sizeof(double));
@@ -341,7 +372,13 @@ int ora_assemble(int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
 
   qrule_t Q = qrule_make(qlevel);
   int bad = 0;
+#pragma omp parallel reduction(| : bad, alloc_fail)
+  {
+  int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (4 * (size_t)maxdeg + 1));
+  if (!buf) alloc_fail = 1;
+#pragma omp for schedule(static, 1024)
   for (int64_t r = 0; r < ndof; r++) {
+    if (!buf) continue;
     int64_t v = row_vertex[r];
     int cnt = 0;
     for (int64_t e = inc_ptr[v]; e < inc_ptr[v + 1]; e++)
@@ -390,11 +427,13 @@ int ora_assemble(int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
       f[r] += vol * acc;
     }
   }
-  qrule_free(&Q);
   free(buf);
+  }
+  qrule_free(&Q);
   free(inc);
   free(inc_ptr);
   free(row_vertex);
+  if (alloc_fail) return -1;
   out->nrows = ndof;
   out->nnz = nnz;
   out->rowptr = rowptr;
@@ -427,8 +466,10 @@ void ora_tet_dets(int64_t nt, const int32_t *tets, const double *xyz, double *de
 
 /* ------------------------------------------------------------ solvers */
 
-/* y = (rho K + M) x, summing each row in column order. */
+/* y = (rho K + M) x, summing each row in column order (rows shared out among OpenMP
+ * threads when built with it; each row's sum is the same whatever the thread count). */
 void ora_apply(const ora_sys_t *s, double rho, const double *x, double *y) {
+#pragma omp parallel for schedule(static, 4096)
   for (int64_t r = 0; r < s->nrows; r++) {
     double acc = 0.0;
     for (int64_t e = s->rowptr[r]; e < s->rowptr[r + 1]; e++)

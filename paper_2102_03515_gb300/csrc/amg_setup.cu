@@ -938,6 +938,145 @@ __global__ void k_gj_step(int64_t N, int64_t k, const double* __restrict__ D, do
   }
 }
 
+// ------------------------------------------------------------------ merge SpGEMM
+
+// C = A B when every row of B holds sorted, distinct columns (CSR4 rows, whose (-1, 0)
+// padding ends a row).  G lanes per row of C; lane l holds the B rows named by the entries
+// t = l + G s (s < K) of the A row, each as a cursor and its current column (the head).
+//  * keys: each step the group takes the smallest head over all its lists (a lane's own
+//    minimum, then a shuffle reduction), records it and advances every list whose head it
+//    is: the distinct columns of the product row come out in increasing order, with no
+//    hash table and no sort;
+//  * values (fill pass): the A row is walked in its stored order; for each entry the lanes
+//    split the B row, find each column's position in the sorted key list by binary search
+//    and add the product there.  A B row's columns are distinct, so one step adds at most
+//    once to an output entry, and every entry is summed in the order of A's row whatever G.
+// The count pass runs the key merge alone and writes the row lengths.
+constexpr int MG_BLOCK = 256;
+constexpr int MG_INF = 0x7fffffff;
+
+template <int G>
+__device__ __forceinline__ int group_min(int v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(mask, v, o, G));
+  return v;
+}
+
+// Load the lane's lists of A row [ea, e1) (padding and entries beyond the row: empty).
+template <int G, int K>
+__device__ __forceinline__ void mg_open(const int32_t* __restrict__ Acol, int ea, int e1,
+                                        const int32_t* __restrict__ Brp,
+                                        const int32_t* __restrict__ Bcol, int lane, int* cur,
+                                        int* end, int* head) {
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    const int e = ea + lane + G * s;
+    const int k = e < e1 ? Acol[e] : -1;
+    cur[s] = k >= 0 ? Brp[k] : 0;
+    end[s] = k >= 0 ? Brp[k + 1] : 0;
+    int h = cur[s] < end[s] ? Bcol[cur[s]] : MG_INF;
+    head[s] = h < 0 ? MG_INF : h;
+  }
+}
+
+// One merge step: the next distinct column of the product row (MG_INF when done); the
+// lists whose head it is move on.
+template <int G, int K>
+__device__ __forceinline__ int mg_next(const int32_t* __restrict__ Bcol, int* cur, const int* end,
+                                       int* head, unsigned mask) {
+  int lm = head[0];
+#pragma unroll
+  for (int s = 1; s < K; s++) lm = min(lm, head[s]);
+  const int m = group_min<G>(lm, mask);
+  if (m != MG_INF) {
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+      if (head[s] == m) {
+        const int c = ++cur[s];
+        const int h = c < end[s] ? Bcol[c] : MG_INF;
+        head[s] = h < 0 ? MG_INF : h;
+      }
+    }
+  }
+  return m;
+}
+
+template <int G, int K>
+__global__ void __launch_bounds__(MG_BLOCK)
+    k_mg_count(int64_t nrows, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Acol,
+               const int32_t* __restrict__ Brp, const int32_t* __restrict__ Bcol, int64_t* cnt) {
+  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
+  const int64_t r = (int64_t)blockIdx.x * (MG_BLOCK / G) + grp;
+  if (r >= nrows) return;
+  const unsigned mask = group_mask<G>();
+  int cur[K], end[K], head[K];
+  mg_open<G, K>(Acol, Arp[r], Arp[r + 1], Brp, Bcol, lane, cur, end, head);
+  int64_t c = 0;
+  while (mg_next<G, K>(Bcol, cur, end, head, mask) != MG_INF) c++;
+  if (lane == 0) cnt[r] = c;
+}
+
+template <int G, int K>
+__global__ void __launch_bounds__(MG_BLOCK)
+    k_mg_fill(int64_t nrows, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Acol,
+              const double* __restrict__ Aval, const int32_t* __restrict__ Brp,
+              const int32_t* __restrict__ Bcol, const double* __restrict__ Bval,
+              const int32_t* __restrict__ Crp, int32_t* __restrict__ Ccol,
+              double* __restrict__ Cval, int kc) {
+  extern __shared__ __align__(16) char smem[];
+  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
+  const int64_t r = (int64_t)blockIdx.x * (MG_BLOCK / G) + grp;
+  if (r >= nrows) return;
+  const unsigned mask = group_mask<G>();
+  double* acc = reinterpret_cast<double*>(smem) + (size_t)grp * kc;
+  int* keys = reinterpret_cast<int*>(reinterpret_cast<double*>(smem) + (size_t)(MG_BLOCK / G) * kc) +
+              (size_t)grp * kc;
+  const int ea = Arp[r], e1 = Arp[r + 1];
+  int cur[K], end[K], head[K];
+  mg_open<G, K>(Acol, ea, e1, Brp, Bcol, lane, cur, end, head);
+  int c = 0;
+  for (;;) {
+    const int m = mg_next<G, K>(Bcol, cur, end, head, mask);
+    if (m == MG_INF) break;
+    if (lane == (c % G)) {   // the lanes take turns: the key and a zero sum per entry
+      keys[c] = m;
+      acc[c] = 0.0;
+    }
+    c++;
+  }
+  __syncwarp(mask);
+  for (int e0 = ea; e0 < e1; e0 += G) {
+    const int e = e0 + lane;
+    const int k = e < e1 ? Acol[e] : -1;
+    const int fb = k >= 0 ? Brp[k] : 0, fe = k >= 0 ? Brp[k + 1] : 0;
+    const double av = k >= 0 ? Aval[e] : 0.0;
+    const int nt = min(G, e1 - e0);
+    for (int t = 0; t < nt; t++) {
+      const int b0 = __shfl_sync(mask, fb, t, G), b1 = __shfl_sync(mask, fe, t, G);
+      const double a = __shfl_sync(mask, av, t, G);
+      for (int f = b0 + lane; f < b1; f += G) {
+        const int j = Bcol[f];
+        if (j < 0) continue;
+        int lo = 0, hi = c;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (keys[mid] < j)
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        acc[lo] = fma(a, Bval[f], acc[lo]);
+      }
+      __syncwarp(mask);
+    }
+  }
+  const int64_t o0 = Crp[r], o1 = Crp[r + 1];
+  for (int q = lane; q < o1 - o0; q += G) {
+    Ccol[o0 + q] = q < c ? keys[q] : -1;
+    Cval[o0 + q] = q < c ? acc[q] : 0.0;
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host wrappers
@@ -1156,6 +1295,84 @@ void spgemm_numeric(const Csr4& A, const double* Aval, const Csr4& B, const doub
   k_spgemm_numeric<<<g, 32 * SG_WARPS, 0, st>>>(nr, A.rowptr, A.col, Aval, B.rowptr, B.col,
                                                 Bval, C.rowptr, C.col, Cval);
   FEM_CHECK_LAUNCH();
+}
+
+template <int G, int K>
+static void mg_launch(bool fill, int64_t nr, const Csr4& A, const double* Aval, const Csr4& B,
+                      const double* Bval, Csr4& C, int64_t* cnt, int kc, cudaStream_t st) {
+  const unsigned g = (unsigned)((nr + MG_BLOCK / G - 1) / (MG_BLOCK / G));
+  if (!fill) {
+    k_mg_count<G, K><<<g, MG_BLOCK, 0, st>>>(nr, A.rowptr, A.col, B.rowptr, B.col, cnt);
+  } else {
+    const size_t smem = (size_t)(MG_BLOCK / G) * kc * 12;
+    static size_t attr = 48 * 1024;
+    if (smem > attr) {
+      FEM_CUDA(cudaFuncSetAttribute(k_mg_fill<G, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      attr = smem;
+    }
+    k_mg_fill<G, K><<<g, MG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, Aval, B.rowptr, B.col, Bval,
+                                               C.rowptr, C.col, C.val, kc);
+  }
+  FEM_CHECK_LAUNCH();
+}
+
+template <int G>
+static void mg_launch_k(int K, bool fill, int64_t nr, const Csr4& A, const double* Aval,
+                        const Csr4& B, const double* Bval, Csr4& C, int64_t* cnt, int kc,
+                        cudaStream_t st) {
+  switch (K) {
+    case 2: mg_launch<G, 2>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+    case 4: mg_launch<G, 4>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+    case 8: mg_launch<G, 8>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+    default: mg_launch<G, 16>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+  }
+}
+
+static void mg_dispatch(int G, int K, bool fill, int64_t nr, const Csr4& A, const double* Aval,
+                        const Csr4& B, const double* Bval, Csr4& C, int64_t* cnt, int kc,
+                        cudaStream_t st) {
+  switch (G) {
+    case 4: mg_launch_k<4>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+    case 8: mg_launch_k<8>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+    case 16: mg_launch_k<16>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+    default: mg_launch_k<32>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+  }
+}
+
+bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
+                  cudaStream_t st, bool* too_long, int64_t limit) {
+  const int64_t nr = A.nrows;
+  if (nr == 0 || B.nrows == 0) return false;
+  // lanes per row from B's mean row (the lanes split B rows in the fill pass; the padding
+  // of CSR4 adds 1.5 stored entries per row on average), wide enough that K <= 16 lists
+  // per lane cover the longest A row
+  DevBuf<int64_t> len(nr, st);
+  k_row_len<<<grid_for(nr, 256), 256, 0, st>>>(nr, A.rowptr, len);
+  FEM_CHECK_LAUNCH();
+  const int64_t maxa = max_of(len, nr, st);
+  const double meanb = (double)B.nnz / (double)B.nrows - 1.5;
+  int G = 4;
+  while (G < 32 && (G < meanb || (int64_t)G * 16 < maxa)) G <<= 1;
+  if ((int64_t)G * 16 < maxa) return false;
+  int K = 2;
+  while ((int64_t)G * K < maxa) K <<= 1;
+  DevBuf<int64_t> cnt(nr, st);
+  mg_dispatch(G, K, false, nr, A, Aval, B, Bval, C, cnt, 0, st);
+  const int64_t maxc = max_of(cnt, nr, st);
+  if (too_long && maxc > std::min<int64_t>(limit, kLongRowMax)) {
+    *too_long = true;
+    return true;
+  }
+  int kc = 32;
+  while (kc < maxc) kc <<= 1;
+  if ((size_t)(MG_BLOCK / G) * kc * 12 > 200 * 1024) return false;   // the hash path's long rows
+  C.nrows = A.nrows;
+  C.ncols = B.ncols;
+  rowptr_from_counts(cnt, nr, C, st);
+  C.val.alloc(C.nnz);
+  mg_dispatch(G, K, true, nr, A, Aval, B, Bval, C, nullptr, kc, st);
+  return true;
 }
 
 void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long,
@@ -2282,10 +2499,11 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     }
     // Galerkin coarse operator A_c = R (A P)  (Sec. 3.1)
     Csr4 AP;
-    if (!too_long) spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long, row_limit);
+    if (!too_long && !spgemm_merge(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, &too_long, row_limit))
+      spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long, row_limit);
     tr.mark("level: A P (spgemm)");
     auto nxt = std::make_unique<Level>();
-    if (!too_long)
+    if (!too_long && !spgemm_merge(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, &too_long, row_limit))
       spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true, &too_long, row_limit);
     tr.mark("level: R (A P) (spgemm)");
     if (too_long) {

@@ -1582,6 +1582,9 @@ void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_
   FEM_REQUIRE(S.n <= kNoAllocMaxN, FEM_EINVAL,
               "fem_assemble_rhs_noalloc: n = " + std::to_string(S.n) +
                   " exceeds the allocation-free limit of 64 cells per side");
+  FEM_REQUIRE(t.kind != FEM_TARGET_QUADVALS, FEM_EINVAL,
+              "fem_assemble_rhs_noalloc: targets given at quadrature points are not taken "
+              "(formula targets only: sine, box, bumps, 1 + sine)");
   FEM_REQUIRE(t.kind >= 0 && t.kind <= 3, FEM_EINVAL, "fem_assemble_rhs_noalloc: unknown target");
   FEM_REQUIRE(t.kind != FEM_TARGET_BUMPS || (t.nb >= 1 && t.nb <= kNoAllocMaxTerms &&
                                              t.centers_host && t.widths_host && t.amps_host),

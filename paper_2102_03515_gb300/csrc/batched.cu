@@ -719,6 +719,7 @@ __global__ void k_slot_admit(SlotState* S, const int32_t* slots, const double* s
     s.maxit = maxit;
     s.status = FEM_OK;
     s.done = (v[0] > 0.0) ? 0 : 1;
+    if (!isfinite(v[0])) s.status = FEM_EBREAKDOWN;   // a non-finite right-hand side
   }
 }
 
@@ -1664,7 +1665,11 @@ fem_status pcg_multi(System& S, Hierarchy& H, const double* f, double* u, int nr
     res[k].solve_ms = ms;
     if (res[k].status != FEM_OK && all == FEM_OK) all = (fem_status)res[k].status;
   }
-  if (o.cancel_host && *o.cancel_host) all = FEM_ECANCELLED;
+  bool unfinished = false;
+  for (int k = 0; k < nrhs; k++)
+    if (st[k] == 0) unfinished = true;
+  // a cancel raised after every slot had finished leaves the results standing
+  if (o.cancel_host && *o.cancel_host && unfinished) all = FEM_ECANCELLED;
   FEM_CUDA(cudaStreamSynchronize(user));
   return all;
 }

@@ -260,7 +260,10 @@ __global__ void k_pcg_start(PcgState* S, const double* sums_bb, const double* su
   S->flexible = flexible;
   S->alpha = S->beta = S->pq = 0.0;
   int done = 0;
-  if (!(S->bb > 0.0)) done = 1;  // f = 0: u = 0 is exact
+  if (!isfinite(S->bb) || !isfinite(S->rr)) {   // a non-finite right-hand side or start
+    done = 1;
+    S->status = FEM_EBREAKDOWN;
+  } else if (!(S->bb > 0.0)) done = 1;  // f = 0: u = 0 is exact
   else if (stop == PCG_STOP_RESIDUAL && S->rr <= S->tol2_res) done = 1;
   else if (!(S->rz > 0.0) || !isfinite(S->rz)) {
     done = 1;
@@ -576,6 +579,9 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
   FEM_CUDA(cudaMemcpyAsync(&W.hstate[0], W.state, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
   FEM_CUDA(cudaStreamSynchronize(st));
   const PcgState hs = W.hstate[0];
+  // the flag was read while the last chunk was still queued: a solve that finished in that
+  // chunk stands
+  if (status == FEM_ECANCELLED && hs.done) status = FEM_OK;
   float ms = 0.f;
   FEM_CUDA(cudaEventElapsedTime(&ms, W.t0, W.t1));
   // true residual

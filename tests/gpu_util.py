@@ -54,3 +54,16 @@ def sparse_rel(A, B):
     d = np.sqrt((D.multiply(D)).sum()) if D.nnz else 0.0
     nb = np.sqrt((B.multiply(B)).sum())
     return d / nb
+
+
+def entrywise_rel(A, B):
+    """Largest |a_ij - b_ij| over entries of the same pattern, each divided by the largest
+    |b_ik| of its row."""
+    A = A.tocsr()
+    B = B.tocsr()
+    D = abs(A - B).tocsr()
+    if D.nnz == 0:
+        return 0.0
+    rmax = abs(B).max(axis=1).toarray().ravel()
+    rows = np.repeat(np.arange(D.shape[0]), np.diff(D.indptr))
+    return float(np.max(D.data / np.where(rmax[rows] > 0, rmax[rows], 1.0)))

@@ -147,3 +147,95 @@ def test_iteration_cap_and_cancellation(fa):
     finally:
         fa.amg_hier_destroy(h)
         fa.fem_system_destroy(sys_)
+
+
+def test_non_finite_right_hand_side_is_a_breakdown(fa):
+    # a NaN in f (host-made failure, no GPU fault): the solve stops before its first
+    # iteration with FEM_EBREAKDOWN and the iterate it started from (zero) written
+    n = 12
+    sys_ = fa.fem_assemble(n, 1e-2, W.sine_target())
+    h = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32)
+    try:
+        N = (n - 1) ** 3
+        f = torch.ones(N, dtype=torch.float64, device="cuda")
+        f[N // 2] = float("nan")
+        u = torch.full((N,), 3.0, dtype=torch.float64, device="cuda")
+        with pytest.raises(fa.FemError) as ei:
+            fa.pcg_solve(sys_, h, f, u, tol=1e-8)
+        assert ei.value.status == 5   # FEM_EBREAKDOWN
+        assert torch.count_nonzero(u).item() == 0
+        f[N // 2] = float("inf")
+        with pytest.raises(fa.FemError) as ei:
+            fa.pcg_solve(sys_, h, f, u, tol=1e-8)
+        assert ei.value.status == 5
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+
+
+def test_non_finite_slot_breaks_down_alone_in_a_batch(fa):
+    # one slot of a batched session gets a NaN right-hand side: that slot reports a
+    # breakdown, the other slot converges to the same result as alone
+    n = 12
+    rho = 1e-2
+    sys_ = fa.fem_assemble(n, rho, W.sine_target(), keep_pencil=True)
+    h = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32)
+    b = fa.pcg_batch_create(sys_, h, 2, tol=1e-10)
+    try:
+        N = (n - 1) ** 3
+        fgood = torch.empty(N, dtype=torch.float64, device="cuda")
+        fa.fem_system_get_rhs(sys_, fgood)
+        fbad = fgood.clone()
+        fbad[3] = float("nan")
+        s_bad = fa.pcg_batch_admit(b, fbad, rho)
+        s_good = fa.pcg_batch_admit(b, fgood, rho)
+        for _ in range(200):
+            fa.pcg_batch_step(b, 2)
+            st, it, rr = fa.pcg_batch_poll(b, 2)
+            if st[s_good] != 0 and st[s_bad] != 0:
+                break
+        assert st[s_bad] == 2 and st[s_good] == 1
+        u = torch.zeros(N, dtype=torch.float64, device="cuda")
+        fa.pcg_batch_retire(b, s_good, u)
+        s = core.assemble(n, W.sine_target())
+        x = core.cholesky_solve(s.A(rho).toarray(), s.f)
+        assert _rel(u.cpu().numpy(), x) <= 1e-8
+    finally:
+        fa.pcg_batch_destroy(b)
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+
+
+def test_cancel_raised_by_a_host_thread_during_a_solve(fa):
+    # a long Jacobi-preconditioned solve (rho = 1 on the 96^3 mesh converges slowly, and a
+    # tolerance of 1e-300 is met only once the recursive residual underflows, some 10^4
+    # iterations later) runs until another host thread raises the cancel flag 0.1 s after
+    # the call: FEM_ECANCELLED, with the iterations done so far in the written iterate
+    import ctypes
+    import threading
+    import time
+    n = 96
+    sys_ = fa.fem_assemble(n, 1.0, W.sine_target())
+    try:
+        N = (n - 1) ** 3
+        u = torch.zeros(N, dtype=torch.float64, device="cuda")
+        flag = ctypes.c_int32(0)
+        timer = threading.Timer(0.1, lambda: setattr(flag, "value", 1))
+        t0 = time.time()
+        timer.start()
+        with pytest.raises(fa.FemError) as ei:
+            fa.pcg_solve(sys_, None, None, u, tol=1e-300, max_iter=10000000,
+                         cancel_host=ctypes.pointer(flag))
+        timer.join()
+        assert ei.value.status == 6   # FEM_ECANCELLED
+        assert time.time() - t0 < 30.0
+        un = u.cpu().numpy()
+        assert np.all(np.isfinite(un)) and np.count_nonzero(un) == N
+        # the iterate is a CG iterate: its residual is below that of the start (u = 0)
+        r = torch.empty_like(u)
+        fa.fem_spmv(sys_, u, r)
+        f = torch.empty_like(u)
+        fa.fem_system_get_rhs(sys_, f)
+        assert torch.linalg.norm(f - r).item() < 1e-3 * torch.linalg.norm(f).item()
+    finally:
+        fa.fem_system_destroy(sys_)

@@ -1,9 +1,10 @@
 """Parity at the benchmark's full size: 256^3 cells (16,581,375 unknowns), rho = h^2.
 
-The oracle cannot assemble or solve this mesh in seconds, so it computes sampled rows one
-by one (from each vertex's incident tets) and the checks use properties that hold at any
-size: sampled load-vector entries and operator rows, the residual of the solution on the
-sampled rows, and agreement of the mixed-precision solve with an FP64 solve.
+Two kinds of checks.  The oracle computes sampled rows one by one (from each vertex's
+incident tets): sampled load-vector entries and operator rows, and the residual of the
+solution on the sampled rows.  And the oracle assembles and solves the whole system itself
+(Jacobi-PCG, its row loops on all host cores, about a minute): the GPU's solutions in every
+V-cycle precision are compared with that reference vector.
 """
 import numpy as np
 import pytest
@@ -80,5 +81,50 @@ def test_full_size_rows_operator_and_solution(fa):
         assert res64["status"] == "FEM_OK" and res64["relres"] <= 1e-12
         rel = (torch.linalg.norm(u - u64) / torch.linalg.norm(u64)).item()
         assert rel <= 1e-8, rel
+    finally:
+        fa.fem_system_destroy(sys_)
+
+
+def test_full_size_solutions_match_the_oracle_reference(fa):
+    # The oracle's own solution of the full system: its assembly and Jacobi-PCG to a
+    # relative residual of 1e-13 (cond(D^-1 A) <= 12.2 at rho = h^2, so a few dozen
+    # iterations), with the independent rows of assembly and of A x spread over the host's
+    # cores.  The GPU's FP64, FP32 and BF16 V-cycle solves to 1e-13 must agree with it to
+    # 1e-10; stopped at 1e-8 (the benchmark's tolerance), within cond(A) times both
+    # tolerances.
+    import os
+    n = 256
+    N = (n - 1) ** 3
+    rho = 1.0 / n ** 2
+    t = W.sine_target()
+    core.set_threads(max(1, len(os.sched_getaffinity(0))))
+    try:
+        s = core.assemble(n, t)
+        x_ref, it, rr = core.jacobi_pcg(s, rho, s.f, tol=1e-13)
+    finally:
+        core.set_threads(1)
+    f_or = s.f
+    del s
+    assert rr <= 1e-13 and it < 200
+    x_ref_d = torch.as_tensor(x_ref, device="cuda")
+    nref = torch.linalg.norm(x_ref_d).item()
+    sys_ = fa.fem_assemble(n, rho, t)
+    try:
+        f = torch.empty(N, dtype=torch.float64, device="cuda")
+        fa.fem_system_get_rhs(sys_, f)
+        assert np.max(np.abs(f.cpu().numpy() - f_or)) <= 1e-13 * np.max(np.abs(f_or))
+        for prec in (fa.AMG_PREC_FP64, fa.AMG_PREC_FP32, fa.AMG_PREC_BF16):
+            h = fa.amg_setup(sys_, precision=prec)
+            try:
+                for tol, bar in ((1e-13, 1e-10), (1e-8, 12.2 * 2e-8)):
+                    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+                    res = fa.pcg_solve(sys_, h, None, u, tol=tol)[0]
+                    assert res["status"] == "FEM_OK", res
+                    err = (torch.linalg.norm(u - x_ref_d) / nref).item()
+                    print("precision %d tol %.0e: %d iterations, |u - u_oracle| / |u_oracle| = %.3e"
+                          % (prec, tol, res["iterations"], err))
+                    assert err <= bar, (prec, tol, err)
+            finally:
+                fa.amg_hier_destroy(h)
     finally:
         fa.fem_system_destroy(sys_)

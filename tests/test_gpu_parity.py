@@ -91,8 +91,12 @@ def test_operator_matches_oracle(fa, n, jit, fmt):
         fa.fem_system_destroy(sys_)
 
 
+# n = 48 and 64 (103,823 and 250,047 rows) run the Galerkin products on several thousand
+# thread blocks with ragged last blocks, level 0 through the stencil's strength graph
+# (uniform) or through A's CSR (jittered, format CSR)
 HIER_CASES = [(16, 1.0 / 256, False, 0), (16, 1.0, False, 0), (12, 1e-6, False, 2),
-              (13, 1.0 / 169, True, 0)]
+              (13, 1.0 / 169, True, 0), (48, 1.0 / 48 ** 2, False, 0), (48, 1.0, True, 0),
+              (64, 1.0 / 64 ** 2, False, 0), (64, 1e-6, True, 0), (48, 1e-2, False, 2)]
 
 
 @pytest.mark.parametrize("n,rho,jit,fmt", HIER_CASES)
@@ -100,9 +104,10 @@ def test_hierarchy_matches_oracle(fa, n, rho, jit, fmt):
     xyz = W.jittered_xyz(n, 0.2, seed=2) if jit else None
     s = core.assemble(n, W.sine_target(), xyz=xyz)
     A = s.A(rho)
-    Ho = amg.build_hierarchy(A, dict(coarse_max=40))
+    cmax = 40 if n <= 16 else 256
+    Ho = amg.build_hierarchy(A, dict(coarse_max=cmax))
     sys_ = fa.fem_assemble(n, rho, W.sine_target(), xyz=xyz, fmt=fmt)
-    h = fa.amg_setup(sys_, coarse_max=40)
+    h = fa.amg_setup(sys_, coarse_max=cmax)
     try:
         info = fa.amg_hier_get_info(h)
         assert info["levels"] == len(Ho)
@@ -113,6 +118,8 @@ def test_hierarchy_matches_oracle(fa, n, rho, jit, fmt):
             assert np.array_equal(Al.indptr, Lo.A.indptr)
             assert np.array_equal(Al.indices, Lo.A.indices)
             assert G.sparse_rel(Al, Lo.A) <= 1e-13
+            # entry by entry, against the size of the row's largest entry
+            assert G.entrywise_rel(Al, Lo.A) <= 1e-13
             assert info["lmax"][lev] == pytest.approx(Lo.lmax, rel=1e-13)
             if Lo.coarsest:
                 continue

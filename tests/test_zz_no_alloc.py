@@ -55,3 +55,18 @@ def test_noalloc_rhs_rejects_meshes_beyond_its_scratch(fa):
         assert "64" in str(ei.value)
     finally:
         fa.fem_system_destroy(sys_)
+
+
+def test_noalloc_rhs_rejects_point_value_targets(fa):
+    n = 8
+    sys_ = fa.fem_assemble(n, 1.0 / n ** 2, W.sine_target())
+    try:
+        N = (n - 1) ** 3
+        vals = torch.ones(6 * n ** 3 * 4, dtype=torch.float64, device="cuda")
+        f = torch.empty(N, dtype=torch.float64, device="cuda")
+        with pytest.raises(fa.FemError) as ei:
+            fa.fem_assemble_rhs_noalloc(sys_, {"kind": "quadvals", "values": vals}, f)
+        assert ei.value.status == 1  # FEM_EINVAL
+        assert "quadrature points" in str(ei.value)
+    finally:
+        fa.fem_system_destroy(sys_)
