@@ -19,6 +19,8 @@
 // Everything is deterministic: integer atomics only, fixed summation orders.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "solver.cuh"
@@ -402,9 +404,12 @@ __device__ __forceinline__ uint32_t hslot(int key, int mask) {
 
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
-  if (G == 32) return 0xffffffffu;
-  const int lw = threadIdx.x & 31;
-  return ((1u << G) - 1u) << (lw & ~(G - 1));
+  if constexpr (G == 32) {
+    return 0xffffffffu;
+  } else {
+    const int lw = threadIdx.x & 31;
+    return ((1u << G) - 1u) << (lw & ~(G - 1));
+  }
 }
 
 template <int G>
@@ -940,20 +945,34 @@ __global__ void k_gj_step(int64_t N, int64_t k, const double* __restrict__ D, do
 
 // ------------------------------------------------------------------ merge SpGEMM
 
-// C = A B when every row of B holds sorted, distinct columns (CSR4 rows, whose (-1, 0)
-// padding ends a row).  G lanes per row of C; lane l holds the B rows named by the entries
-// t = l + G s (s < K) of the A row, each as a cursor and its current column (the head).
+// C = A B when every row of B holds sorted, distinct columns: CSR4 rows, whose (-1, 0)
+// padding ends a row, or rows at a fixed stride with their lengths (an earlier product).
+// G lanes per row of C; lane l holds the B rows named by the entries t = l + G s (s < K) of
+// the A row, each as a cursor and its current column (the head).
 //  * keys: each step the group takes the smallest head over all its lists (a lane's own
-//    minimum, then a shuffle reduction), records it and advances every list whose head it
-//    is: the distinct columns of the product row come out in increasing order, with no
-//    hash table and no sort;
-//  * values (fill pass): the A row is walked in its stored order; for each entry the lanes
-//    split the B row, find each column's position in the sorted key list by binary search
-//    and add the product there.  A B row's columns are distinct, so one step adds at most
-//    once to an output entry, and every entry is summed in the order of A's row whatever G.
-// The count pass runs the key merge alone and writes the row lengths.
+//    minimum, then a shuffle reduction), writes it as the next column of the row and
+//    advances every list whose head it is, noting in shared memory the output position of
+//    the B entry it passed: the distinct columns come out in increasing order, with no hash
+//    table and no sort;
+//  * values: the A row is walked in its stored order; for each entry the lanes split the B
+//    row and add each product at the noted position.  A B row's columns are distinct, so
+//    one step adds at most once to an output entry, and every entry is summed in the order
+//    of A's row whatever G.
+// C is written at a fixed stride W with its row lengths.  A row with more than W columns
+// writes only its length and raises the overflow flag (the caller repeats the product
+// with a wider stride).
 constexpr int MG_BLOCK = 256;
 constexpr int MG_INF = 0x7fffffff;
+
+struct MgRows {
+  const int32_t* rp;    // CSR4 row pointer, or null: rows at a fixed stride
+  const int64_t* len;   // row lengths at the fixed stride
+  int32_t stride;
+  __device__ __forceinline__ int beg(int k) const { return rp ? rp[k] : k * stride; }
+  __device__ __forceinline__ int end(int k) const {
+    return rp ? rp[k + 1] : k * stride + (int)len[k];
+  }
+};
 
 template <int G>
 __device__ __forceinline__ int group_min(int v, unsigned mask) {
@@ -962,118 +981,102 @@ __device__ __forceinline__ int group_min(int v, unsigned mask) {
   return v;
 }
 
-// Load the lane's lists of A row [ea, e1) (padding and entries beyond the row: empty).
-template <int G, int K>
-__device__ __forceinline__ void mg_open(const int32_t* __restrict__ Acol, int ea, int e1,
-                                        const int32_t* __restrict__ Brp,
-                                        const int32_t* __restrict__ Bcol, int lane, int* cur,
-                                        int* end, int* head) {
-#pragma unroll
-  for (int s = 0; s < K; s++) {
-    const int e = ea + lane + G * s;
-    const int k = e < e1 ? Acol[e] : -1;
-    cur[s] = k >= 0 ? Brp[k] : 0;
-    end[s] = k >= 0 ? Brp[k + 1] : 0;
-    int h = cur[s] < end[s] ? Bcol[cur[s]] : MG_INF;
-    head[s] = h < 0 ? MG_INF : h;
-  }
-}
-
-// One merge step: the next distinct column of the product row (MG_INF when done); the
-// lists whose head it is move on.
-template <int G, int K>
-__device__ __forceinline__ int mg_next(const int32_t* __restrict__ Bcol, int* cur, const int* end,
-                                       int* head, unsigned mask) {
-  int lm = head[0];
-#pragma unroll
-  for (int s = 1; s < K; s++) lm = min(lm, head[s]);
-  const int m = group_min<G>(lm, mask);
-  if (m != MG_INF) {
-#pragma unroll
-    for (int s = 0; s < K; s++) {
-      if (head[s] == m) {
-        const int c = ++cur[s];
-        const int h = c < end[s] ? Bcol[c] : MG_INF;
-        head[s] = h < 0 ? MG_INF : h;
-      }
-    }
-  }
-  return m;
-}
-
 template <int G, int K>
 __global__ void __launch_bounds__(MG_BLOCK)
-    k_mg_count(int64_t nrows, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Acol,
-               const int32_t* __restrict__ Brp, const int32_t* __restrict__ Bcol, int64_t* cnt) {
-  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
-  const int64_t r = (int64_t)blockIdx.x * (MG_BLOCK / G) + grp;
-  if (r >= nrows) return;
-  const unsigned mask = group_mask<G>();
-  int cur[K], end[K], head[K];
-  mg_open<G, K>(Acol, Arp[r], Arp[r + 1], Brp, Bcol, lane, cur, end, head);
-  int64_t c = 0;
-  while (mg_next<G, K>(Bcol, cur, end, head, mask) != MG_INF) c++;
-  if (lane == 0) cnt[r] = c;
-}
-
-template <int G, int K>
-__global__ void __launch_bounds__(MG_BLOCK)
-    k_mg_fill(int64_t nrows, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Acol,
-              const double* __restrict__ Aval, const int32_t* __restrict__ Brp,
-              const int32_t* __restrict__ Bcol, const double* __restrict__ Bval,
-              const int32_t* __restrict__ Crp, int32_t* __restrict__ Ccol,
-              double* __restrict__ Cval, int kc) {
+    k_mg(int64_t nrows, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Acol,
+         const double* __restrict__ Aval, MgRows B, const int32_t* __restrict__ Bcol,
+         const double* __restrict__ Bval, int W, int lmax, int32_t* __restrict__ Ccol,
+         double* __restrict__ Cval, int64_t* __restrict__ Clen, unsigned int* overflow) {
   extern __shared__ __align__(16) char smem[];
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
   const int64_t r = (int64_t)blockIdx.x * (MG_BLOCK / G) + grp;
   if (r >= nrows) return;
   const unsigned mask = group_mask<G>();
-  double* acc = reinterpret_cast<double*>(smem) + (size_t)grp * kc;
-  int* keys = reinterpret_cast<int*>(reinterpret_cast<double*>(smem) + (size_t)(MG_BLOCK / G) * kc) +
-              (size_t)grp * kc;
+  // per group: W + 1 sums, then the output position of every entry of every list (G K lists
+  // of at most lmax entries) and 4 bytes (the odd strides start the groups in different
+  // shared-memory banks)
+  constexpr int NG = MG_BLOCK / G;
+  double* acc = reinterpret_cast<double*>(smem) + (size_t)grp * (W + 1);
+  uint8_t* pos = reinterpret_cast<uint8_t*>(reinterpret_cast<double*>(smem) + (size_t)NG * (W + 1)) +
+                 (size_t)grp * (G * K * lmax + 4);
   const int ea = Arp[r], e1 = Arp[r + 1];
-  int cur[K], end[K], head[K];
-  mg_open<G, K>(Acol, ea, e1, Brp, Bcol, lane, cur, end, head);
+  int cur[K], end[K], head[K], base[K];   // base + cursor: the entry's position slot
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    const int e = ea + lane + G * s;
+    const int k = e < e1 ? Acol[e] : -1;
+    cur[s] = k >= 0 ? B.beg(k) : 0;
+    end[s] = k >= 0 ? B.end(k) : 0;
+    base[s] = (lane + G * s) * lmax - cur[s];
+    const int h = cur[s] < end[s] ? Bcol[cur[s]] : MG_INF;
+    head[s] = h < 0 ? MG_INF : h;
+  }
+  int32_t* crow = Ccol + r * W;
   int c = 0;
   for (;;) {
-    const int m = mg_next<G, K>(Bcol, cur, end, head, mask);
+    int lm = head[0];
+#pragma unroll
+    for (int s = 1; s < K; s++) lm = min(lm, head[s]);
+    const int m = group_min<G>(lm, mask);
     if (m == MG_INF) break;
-    if (lane == (c % G)) {   // the lanes take turns: the key and a zero sum per entry
-      keys[c] = m;
-      acc[c] = 0.0;
+    const bool keep = c < W;
+    if (keep && lane == (c & (G - 1))) crow[c] = m;
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+      if (head[s] == m) {
+        if (keep) pos[base[s] + cur[s]] = (uint8_t)c;
+        const int q = ++cur[s];
+        const int h = q < end[s] ? Bcol[q] : MG_INF;
+        head[s] = h < 0 ? MG_INF : h;
+      }
     }
     c++;
   }
+  if (c > W) {   // the row does not fit: its length only
+    if (lane == 0) {
+      Clen[r] = c;
+      atomicOr(overflow, 1u);
+    }
+    return;
+  }
+  for (int q = lane; q < c; q += G) acc[q] = 0.0;
   __syncwarp(mask);
   for (int e0 = ea; e0 < e1; e0 += G) {
     const int e = e0 + lane;
     const int k = e < e1 ? Acol[e] : -1;
-    const int fb = k >= 0 ? Brp[k] : 0, fe = k >= 0 ? Brp[k + 1] : 0;
+    const int fb = k >= 0 ? B.beg(k) : 0, fe = k >= 0 ? B.end(k) : 0;
     const double av = k >= 0 ? Aval[e] : 0.0;
     const int nt = min(G, e1 - e0);
     for (int t = 0; t < nt; t++) {
       const int b0 = __shfl_sync(mask, fb, t, G), b1 = __shfl_sync(mask, fe, t, G);
       const double a = __shfl_sync(mask, av, t, G);
+      const uint8_t* pt = pos + (e0 - ea + t) * lmax - b0;
       for (int f = b0 + lane; f < b1; f += G) {
-        const int j = Bcol[f];
-        if (j < 0) continue;
-        int lo = 0, hi = c;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (keys[mid] < j)
-            lo = mid + 1;
-          else
-            hi = mid;
-        }
-        acc[lo] = fma(a, Bval[f], acc[lo]);
+        if (Bcol[f] < 0) continue;
+        const int q = pt[f];
+        acc[q] = fma(a, Bval[f], acc[q]);
       }
       __syncwarp(mask);
     }
   }
-  const int64_t o0 = Crp[r], o1 = Crp[r + 1];
-  for (int q = lane; q < o1 - o0; q += G) {
-    Ccol[o0 + q] = q < c ? keys[q] : -1;
-    Cval[o0 + q] = q < c ? acc[q] : 0.0;
+  double* vrow = Cval + r * W;
+  for (int q = lane; q < c; q += G) vrow[q] = acc[q];
+  if (lane == 0) Clen[r] = c;
+}
+
+// CSR4 from rows at a fixed stride (a warp per row; padding appended)
+__global__ void k_mg_compact(int64_t nrows, int W, const int32_t* __restrict__ Scol,
+                             const double* __restrict__ Sval, const int64_t* __restrict__ len,
+                             const int32_t* __restrict__ Crp, int32_t* __restrict__ Ccol,
+                             double* __restrict__ Cval) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  const int c = (int)len[r];
+  const int o0 = Crp[r], o1 = Crp[r + 1];
+  for (int q = lane; q < o1 - o0; q += 32) {
+    Ccol[o0 + q] = q < c ? Scol[r * W + q] : -1;
+    Cval[o0 + q] = q < c ? Sval[r * W + q] : 0.0;
   }
 }
 
@@ -1297,81 +1300,161 @@ void spgemm_numeric(const Csr4& A, const double* Aval, const Csr4& B, const doub
   FEM_CHECK_LAUNCH();
 }
 
+// A product at a fixed stride: column indices, values and row lengths.
+struct Strided {
+  int64_t nrows = 0;
+  int32_t ncols = 0, W = 0;
+  int64_t maxlen = 0;
+  DevBuf<int32_t> col;
+  DevBuf<double> val;
+  DevBuf<int64_t> len;
+};
+
+static size_t mg_smem(int G, int K, int W, int lmax) {
+  return (size_t)(MG_BLOCK / G) * ((size_t)(W + 1) * 8 + (size_t)G * K * lmax + 4);
+}
+
 template <int G, int K>
-static void mg_launch(bool fill, int64_t nr, const Csr4& A, const double* Aval, const Csr4& B,
-                      const double* Bval, Csr4& C, int64_t* cnt, int kc, cudaStream_t st) {
+static void mg_launch(int64_t nr, const Csr4& A, const double* Aval, MgRows Brows,
+                      const int32_t* Bcol, const double* Bval, int lmax, Strided& C,
+                      unsigned int* ovf, cudaStream_t st) {
   const unsigned g = (unsigned)((nr + MG_BLOCK / G - 1) / (MG_BLOCK / G));
-  if (!fill) {
-    k_mg_count<G, K><<<g, MG_BLOCK, 0, st>>>(nr, A.rowptr, A.col, B.rowptr, B.col, cnt);
-  } else {
-    const size_t smem = (size_t)(MG_BLOCK / G) * kc * 12;
-    static size_t attr = 48 * 1024;
-    if (smem > attr) {
-      FEM_CUDA(cudaFuncSetAttribute(k_mg_fill<G, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-      attr = smem;
-    }
-    k_mg_fill<G, K><<<g, MG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, Aval, B.rowptr, B.col, Bval,
-                                               C.rowptr, C.col, C.val, kc);
+  const size_t smem = mg_smem(G, K, C.W, lmax);
+  static size_t attr = 48 * 1024;
+  if (smem > attr) {
+    FEM_CUDA(cudaFuncSetAttribute(k_mg<G, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    attr = smem;
   }
+  k_mg<G, K><<<g, MG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, Aval, Brows, Bcol, Bval, C.W, lmax,
+                                        C.col, C.val, C.len, ovf);
   FEM_CHECK_LAUNCH();
 }
 
 template <int G>
-static void mg_launch_k(int K, bool fill, int64_t nr, const Csr4& A, const double* Aval,
-                        const Csr4& B, const double* Bval, Csr4& C, int64_t* cnt, int kc,
-                        cudaStream_t st) {
+static void mg_launch_k(int K, int64_t nr, const Csr4& A, const double* Aval, MgRows Brows,
+                        const int32_t* Bcol, const double* Bval, int lmax, Strided& C,
+                        unsigned int* ovf, cudaStream_t st) {
   switch (K) {
-    case 2: mg_launch<G, 2>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
-    case 4: mg_launch<G, 4>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
-    case 8: mg_launch<G, 8>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
-    default: mg_launch<G, 16>(fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+    case 2: mg_launch<G, 2>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    case 4: mg_launch<G, 4>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    case 8: mg_launch<G, 8>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    default: mg_launch<G, 16>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
   }
 }
 
-static void mg_dispatch(int G, int K, bool fill, int64_t nr, const Csr4& A, const double* Aval,
-                        const Csr4& B, const double* Bval, Csr4& C, int64_t* cnt, int kc,
-                        cudaStream_t st) {
-  switch (G) {
-    case 4: mg_launch_k<4>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
-    case 8: mg_launch_k<8>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
-    case 16: mg_launch_k<16>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
-    default: mg_launch_k<32>(K, fill, nr, A, Aval, B, Bval, C, cnt, kc, st); break;
+// stride last used for a product of this shape (the next set-up of the same system starts
+// from it); 32 for a new shape
+static int mg_stride_guess(uint64_t key, int set) {
+  static std::mutex mu;
+  static std::unordered_map<uint64_t, int> seen;
+  std::lock_guard<std::mutex> lk(mu);
+  if (set > 0) {
+    seen[key] = set;
+    return set;
   }
+  auto it = seen.find(key);
+  return it == seen.end() ? 32 : it->second;
 }
 
-bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval, Csr4& C,
-                  cudaStream_t st, bool* too_long, int64_t limit) {
+// C = A B by the merge kernel, C at a fixed stride.  B's rows: CSR4 (Bs null) or the
+// strided product Bs.  Returns false when the kernel cannot take the product (an A row
+// beyond 16 x 32 entries, B rows beyond 255 entries, or tables beyond the shared memory):
+// the caller takes the hash path.
+static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, const double* Bval,
+                         const Strided* Bs, Strided& C, cudaStream_t st) {
   const int64_t nr = A.nrows;
-  if (nr == 0 || B.nrows == 0) return false;
-  // lanes per row from B's mean row (the lanes split B rows in the fill pass; the padding
-  // of CSR4 adds 1.5 stored entries per row on average), wide enough that K <= 16 lists
-  // per lane cover the longest A row
+  const int64_t nb = Bc ? Bc->nrows : Bs->nrows;
+  if (nr == 0 || nb == 0) return false;
   DevBuf<int64_t> len(nr, st);
   k_row_len<<<grid_for(nr, 256), 256, 0, st>>>(nr, A.rowptr, len);
   FEM_CHECK_LAUNCH();
   const int64_t maxa = max_of(len, nr, st);
-  const double meanb = (double)B.nnz / (double)B.nrows - 1.5;
+  int64_t lmax;
+  MgRows R{};
+  if (Bc) {
+    DevBuf<int64_t> blen(nb, st);
+    k_row_len<<<grid_for(nb, 256), 256, 0, st>>>(nb, Bc->rowptr, blen);
+    FEM_CHECK_LAUNCH();
+    lmax = max_of(blen, nb, st);
+    R.rp = Bc->rowptr;
+  } else {
+    lmax = Bs->maxlen;
+    R.len = Bs->len;
+    R.stride = Bs->W;
+  }
+  if (lmax > 255 || lmax < 1) return false;
+  lmax = (lmax + 3) & ~(int64_t)3;
+  // lanes per row from B's mean row (the lanes split B rows; CSR4 padding adds 1.5 stored
+  // entries per row on average), wide enough that K <= 16 lists per lane cover the longest
+  // A row
+  const double meanb = Bc ? (double)Bc->nnz / (double)nb - 1.5 : 0.6 * (double)Bs->maxlen;
   int G = 4;
   while (G < 32 && (G < meanb || (int64_t)G * 16 < maxa)) G <<= 1;
   if ((int64_t)G * 16 < maxa) return false;
   int K = 2;
   while ((int64_t)G * K < maxa) K <<= 1;
-  DevBuf<int64_t> cnt(nr, st);
-  mg_dispatch(G, K, false, nr, A, Aval, B, Bval, C, cnt, 0, st);
-  const int64_t maxc = max_of(cnt, nr, st);
-  if (too_long && maxc > std::min<int64_t>(limit, kLongRowMax)) {
+  const int64_t bcols = Bc ? Bc->ncols : Bs->ncols;
+  const uint64_t key = (uint64_t)nr * 0x9E3779B97F4A7C15ull ^ (uint64_t)A.nnz * 0xC2B2AE3D27D4EB4Full ^
+                       (uint64_t)nb * 0x165667B19E3779F9ull ^ (uint64_t)bcols;
+  int W = mg_stride_guess(key, 0);
+  DevBuf<unsigned int> ovf(1, st);
+  for (int attempt = 0; attempt < 2; attempt++) {
+    if (mg_smem(G, K, W, (int)lmax) > 200 * 1024 || nr * (int64_t)W >= ((int64_t)1 << 31) ||
+        W > 255)
+      return false;
+    C.nrows = nr;
+    C.ncols = (int32_t)bcols;
+    C.W = W;
+    C.col.alloc_async((size_t)nr * W, st);
+    C.val.alloc_async((size_t)nr * W, st);
+    C.len.alloc_async(nr, st);
+    FEM_CUDA(cudaMemsetAsync(ovf, 0, 4, st));
+    const int32_t* bcol = Bc ? Bc->col.p : Bs->col.p;
+    switch (G) {
+      case 4: mg_launch_k<4>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+      case 8: mg_launch_k<8>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+      case 16: mg_launch_k<16>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+      default: mg_launch_k<32>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+    }
+    C.maxlen = max_of(C.len, nr, st);
+    unsigned int hov = 0;
+    FEM_CUDA(cudaMemcpyAsync(&hov, ovf, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    if (!hov) {
+      mg_stride_guess(key, W);
+      return true;
+    }
+    W = 4;
+    while (W < C.maxlen) W <<= 1;
+  }
+  return false;
+}
+
+// Galerkin product A_c = R (A P) by the merge kernel (A P at a fixed stride, A_c compacted
+// to CSR4).  Returns false when the kernel cannot take it (the hash path then runs); sets
+// *too_long when A P or A_c has a row longer than limit.
+bool galerkin_merge(const Csr4& A, const Csr4& P, const Csr4& R, Csr4& Ac, cudaStream_t st,
+                    bool* too_long, int64_t limit) {
+  Strided AP, RAP;
+  if (!spgemm_merge(A, A.val, &P, P.val, nullptr, AP, st)) return false;
+  if (AP.maxlen > limit) {
     *too_long = true;
     return true;
   }
-  int kc = 32;
-  while (kc < maxc) kc <<= 1;
-  if ((size_t)(MG_BLOCK / G) * kc * 12 > 200 * 1024) return false;   // the hash path's long rows
-  C.nrows = A.nrows;
-  C.ncols = B.ncols;
-  rowptr_from_counts(cnt, nr, C, st);
-  C.val.alloc(C.nnz);
-  mg_dispatch(G, K, true, nr, A, Aval, B, Bval, C, nullptr, kc, st);
+  if (!spgemm_merge(R, R.val, nullptr, AP.val, &AP, RAP, st)) return false;
+  if (RAP.maxlen > limit) {
+    *too_long = true;
+    return true;
+  }
+  AP = Strided();
+  Ac.nrows = (int32_t)R.nrows;
+  Ac.ncols = P.ncols;
+  rowptr_from_counts(RAP.len, RAP.nrows, Ac, st);
+  Ac.val.alloc(Ac.nnz);
+  k_mg_compact<<<grid_for(RAP.nrows * 32, 256), 256, 0, st>>>(RAP.nrows, RAP.W, RAP.col, RAP.val,
+                                                              RAP.len, Ac.rowptr, Ac.col, Ac.val);
+  FEM_CHECK_LAUNCH();
   return true;
 }
 
@@ -2498,12 +2581,16 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       }
     }
     // Galerkin coarse operator A_c = R (A P)  (Sec. 3.1)
+    // (the merge kernels when they take the product; the pencil keeps A P for its parts)
     Csr4 AP;
-    if (!too_long && !spgemm_merge(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, &too_long, row_limit))
+    auto nxt = std::make_unique<Level>();
+    bool merged = false;
+    if (!too_long && !S.pencil)
+      merged = galerkin_merge(*Acur, Lv.P, Lv.R, nxt->Aown, st, &too_long, row_limit);
+    if (!merged && !too_long)
       spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long, row_limit);
     tr.mark("level: A P (spgemm)");
-    auto nxt = std::make_unique<Level>();
-    if (!too_long && !spgemm_merge(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, &too_long, row_limit))
+    if (!merged && !too_long)
       spgemm(Lv.R, Lv.R.val, AP, AP.val, nxt->Aown, st, true, &too_long, row_limit);
     tr.mark("level: R (A P) (spgemm)");
     if (too_long) {
