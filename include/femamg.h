@@ -186,8 +186,23 @@ fem_status fem_system_dof_vertices(fem_system sys, int64_t* vert_dev, void* stre
 fem_status fem_system_export(fem_system sys, int32_t which, int32_t* rowptr_dev,
                              int32_t* col_dev, double* val_dev, void* stream);
 
-/* y = A x for the system's operator, FP64 (the operator of eq. (linsys)). */
+/* y = A x for the system's operator (the operator of eq. (linsys)) in FP64.  x_dev, y_dev:
+ * device FP64 [N], distinct.  Synchronises the stream. */
 fem_status fem_spmv(fem_system sys, const double* x_dev, double* y_dev, void* stream);
+
+/* y = A x as CG's iterations apply it, reps times after one untimed application; ms_out
+ * receives the mean device time of one operator launch (CUDA events on `stream`).  CSR4
+ * systems (jittered and general meshes): the FP64 product of fem_spmv.  The matrix-free
+ * operator of the uniform grid: double-float arithmetic on the FP32 pipe -- x rounded to 48
+ * significant bits and split into two FP32 numbers (once, before the timed launches), the
+ * four stencil coefficients held exactly as three FP32 numbers each, the sums of each
+ * coefficient class and the products carried by error-free transformations -- so that each
+ * y_i is within 2^-44 sum_j |a_ij x_j| of the exact product (FP64: a few 2^-53); when some
+ * x_i != 0 lies outside 2^-74 <= |x_i| < 2^101 the product is FP64 instead.  pcg_solve
+ * recomputes the residual with the FP64 operator at the end and continues from its iterate
+ * when that residual is above the tolerance.  Errors: FEM_EINVAL (null argument, reps < 1). */
+fem_status fem_spmv_timed(fem_system sys, const double* x_dev, double* y_dev, int32_t reps,
+                          void* stream, double* ms_out);
 
 void fem_system_destroy(fem_system sys);
 

@@ -30,7 +30,7 @@ from ._binding import (  # noqa: F401
     fem_mesh_create, fem_mesh_destroy, fem_mesh_download, fem_mesh_get_info, fem_mesh_refine,
     fem_assemble_rhs, fem_assemble_rhs_noalloc, fem_autotune_clear, fem_autotune_pin,
     fem_autotune_report, fem_error_hm1, fem_errors, fem_kernel_launches, fem_last_error,
-    fem_measure_fp64_rate, fem_recover, fem_spmv,
+    fem_measure_fp64_rate, fem_recover, fem_spmv, fem_spmv_timed,
     fem_system_destroy, fem_system_dof_vertices, fem_system_export, fem_system_get_info,
     fem_system_get_rhs, fem_version,
     lib, pcg_batch_admit, pcg_batch_create, pcg_batch_destroy, pcg_batch_footprint,

@@ -139,6 +139,7 @@ SIGNATURES = {
     "amg_hier_export": (C.c_int, [VP, C.c_int32, C.c_int32, VP, VP, VP, P(C.c_int64), VP]),
     "amg_vcycle": (C.c_int, [VP, VP, VP, VP]),
     "amg_vcycle_graph": (C.c_int, [VP, VP, VP, C.c_int32, VP, P(C.c_double)]),
+    "fem_spmv_timed": (C.c_int, [VP, VP, VP, C.c_int32, VP, P(C.c_double)]),
     "amg_hier_destroy": (None, [VP]),
     "pcg_default_opts": (None, [P(PcgOpts)]),
     "pcg_solve": (C.c_int, [VP, VP, VP, VP, C.c_int32, P(C.c_double), P(PcgOpts), VP,
@@ -447,6 +448,14 @@ def fem_system_export(sys, which, rowptr, col, val, stream=None):
 
 def fem_spmv(sys, x, y, stream=None):
     _check(lib().fem_spmv(sys, _ptr(x), _ptr(y), _stream(stream)), "fem_spmv")
+
+
+def fem_spmv_timed(sys, x, y, reps: int = 20, stream=None) -> float:
+    """y = A x applied `reps` times; returns the mean ms of one operator launch."""
+    ms = C.c_double(0.0)
+    _check(lib().fem_spmv_timed(sys, _ptr(x), _ptr(y), int(reps), _stream(stream), C.byref(ms)),
+           "fem_spmv_timed")
+    return ms.value
 
 
 def fem_system_destroy(sys):

@@ -364,8 +364,51 @@ fem_status fem_spmv(fem_system sys, const double* x_dev, double* y_dev, void* st
     FEM_REQUIRE(sys && x_dev && y_dev, FEM_EINVAL, "fem_spmv: null argument");
     Level L;
     system_level(sys->S, L);
-    op_apply_d(L, x_dev, y_dev, nullptr, nullptr, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    op_apply_d(L, x_dev, y_dev, nullptr, nullptr, st);
     FEM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    return FEM_OK;
+  });
+}
+
+fem_status fem_spmv_timed(fem_system sys, const double* x_dev, double* y_dev, int32_t reps,
+                          void* stream, double* ms_out) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(sys && x_dev && y_dev && reps >= 1, FEM_EINVAL, "fem_spmv_timed: bad argument");
+    Level L;
+    system_level(sys->S, L);
+    cudaStream_t st = as_stream(stream);
+    const int64_t N = sys->S.N;
+    DevBuf<float2> x2;
+    DevBuf<int> rflag;
+    DfOperator D;
+    if (L.stencil) {
+      x2.alloc_async(N > 0 ? N : 1, st);
+      rflag.alloc_async(1, st);
+      FEM_CUDA(cudaMemsetAsync(rflag, 0, sizeof(int), st));
+      df_split_vec(N, x_dev, nullptr, x2, rflag, st);
+      D = df_operator(L.st);
+    }
+    auto once = [&]() {
+      if (L.stencil)
+        op_apply_df(L, D, x2, x_dev, y_dev, nullptr, st, nullptr, rflag);
+      else
+        op_apply_d(L, x_dev, y_dev, nullptr, nullptr, st);
+    };
+    once();
+    cudaEvent_t e0, e1;
+    FEM_CUDA(cudaEventCreate(&e0));
+    FEM_CUDA(cudaEventCreate(&e1));
+    FEM_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < reps; i++) once();
+    FEM_CUDA(cudaEventRecord(e1, st));
+    FEM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms_out) *ms_out = (double)ms / reps;
     return FEM_OK;
   });
 }

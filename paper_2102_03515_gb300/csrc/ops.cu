@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "solver.cuh"
 
 namespace fem {
@@ -557,6 +558,151 @@ int launch_stencil(const Stencil& s, const T* v, const Epi<T>& epi, double* part
   return launch_stencil_variant<T>(var, s, v, epi, partials, st, done);
 }
 
+// ------------------------------------------------------------------ double-float stencil
+
+// q = A p for CG's FP64 vectors without the FP64 pipe: p arrives split into FP32 pairs
+// (hi, lo) with p = hi + lo exactly (the split rounds p to 48 bits when CG forms it), the
+// four stencil coefficients, scaled by 2^s to about 1, as three FP32 numbers each (exact),
+// and the sums of each coefficient class (axis, face, body neighbours) are carried in
+// double-float arithmetic: TwoSum on the high parts, the low parts and the rounding errors
+// collected in FP32.  The four products and their sum follow the same way; only the final
+// hi + lo (one FP64 addition) and <p, q> (one FP64 fused multiply-add) touch the FP64 pipe,
+// against 15 FP64 operations per row in FP64.  When any entry of p lies outside the split's
+// range (rflag set by the split), the kernel computes the rows in FP64 instead.
+// Thread (i, j) marches its column in k like k_stencil_col: 7 pair loads per point, the
+// next point's loads issued before the current point is finished.
+struct DfCoef {
+  float C[4][3];     // c0, ca, cf, cb times 2^s, each as C1 + C2 + C3
+  int s;
+  double c64[4];     // the FP64 coefficients (fallback)
+};
+
+template <int TYV, int KZV>
+__global__ void __launch_bounds__(TX* TYV) k_stencil_df(const float2* __restrict__ v,
+                                                       const double* __restrict__ v64, int m,
+                                                       DfCoef cf, double* __restrict__ y,
+                                                       double* partials, int nblocks,
+                                                       const int* done, const int* rflag) {
+  if (done && *done) return;
+  const int i = blockIdx.x * TX + (threadIdx.x & (TX - 1));
+  const int j = blockIdx.y * TYV + threadIdx.x / TX;
+  const int k0 = blockIdx.z * KZV;
+  const int kend = min(k0 + KZV, m);
+  double acc[2] = {0.0, 0.0};
+  const bool fp64 = *rflag != 0;
+  if (i < m && j < m) {
+    const int64_t sj = m, sk = (int64_t)m * m;
+    const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1;
+    const int64_t row0 = (int64_t)i + sj * j;
+    if (fp64) {
+      const double* col = v64 + row0;
+      auto ld = [&](bool ok, int k, int64_t off) -> double {
+        return (ok && k >= 0 && k < m) ? __ldg(col + sk * k + off) : 0.0;
+      };
+      for (int k = k0; k < kend; k++) {
+        const double axis = ld(im, k, -1) + ld(ip, k, 1) + ld(jm, k, -sj) + ld(jp, k, sj) +
+                            ld(true, k - 1, 0) + ld(true, k + 1, 0);
+        const double face = ld(ip && jp, k, 1 + sj) + ld(im && jm, k, -1 - sj) +
+                            ld(ip, k + 1, 1) + ld(im, k - 1, -1) + ld(jp, k + 1, sj) +
+                            ld(jm, k - 1, -sj);
+        const double body = ld(ip && jp, k + 1, 1 + sj) + ld(im && jm, k - 1, -1 - sj);
+        const double c0v = ld(true, k, 0);
+        const double av = cf.c64[0] * c0v + cf.c64[1] * axis + cf.c64[2] * face + cf.c64[3] * body;
+        y[row0 + sk * k] = av;
+        acc[0] = fma(c0v, av, acc[0]);
+      }
+    } else {
+      const float2* col = v + row0;
+      const float2 Z = make_float2(0.0f, 0.0f);
+      auto ld = [&](bool ok, int k, int64_t off) -> float2 {
+        return (ok && k >= 0 && k < m) ? __ldg(col + sk * k + off) : Z;
+      };
+      float2 cm = ld(true, k0 - 1, 0);
+      float2 m_im = ld(im, k0 - 1, -1), m_jm = ld(jm, k0 - 1, -sj), m_ijm = ld(im && jm, k0 - 1, -1 - sj);
+      float2 c0v = ld(true, k0, 0);
+      float2 p_ip = ld(ip, k0, 1), p_jp = ld(jp, k0, sj), p_ijp = ld(ip && jp, k0, 1 + sj);
+      float2 z_im = ld(im, k0, -1), z_jm = ld(jm, k0, -sj), z_ijm = ld(im && jm, k0, -1 - sj);
+      float2 cp = ld(true, k0 + 1, 0);
+      float2 n_ip = ld(ip, k0 + 1, 1), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, 1 + sj);
+      double pc = v64 ? __ldg(v64 + row0 + sk * k0) : 0.0;
+      for (int k = k0; k < kend; k++) {
+        const bool more = k + 1 < kend;
+        const float2 z2_im = ld(im && more, k + 1, -1), z2_jm = ld(jm && more, k + 1, -sj),
+                     z2_ijm = ld(im && jm && more, k + 1, -1 - sj);
+        const float2 cp2 = ld(more, k + 2, 0);
+        const float2 n2_ip = ld(ip && more, k + 2, 1), n2_jp = ld(jp && more, k + 2, sj),
+                     n2_ijp = ld(ip && jp && more, k + 2, 1 + sj);
+        const double pc2 = (v64 && more) ? __ldg(v64 + row0 + sk * (k + 1)) : 0.0;
+        // class sums: s exact part, c collected low parts and errors
+        float as = z_im.x, ac = z_im.y;
+        df_acc(as, ac, p_ip.x, p_ip.y);
+        df_acc(as, ac, z_jm.x, z_jm.y);
+        df_acc(as, ac, p_jp.x, p_jp.y);
+        df_acc(as, ac, cm.x, cm.y);
+        df_acc(as, ac, cp.x, cp.y);
+        float fs = p_ijp.x, fc = p_ijp.y;
+        df_acc(fs, fc, z_ijm.x, z_ijm.y);
+        df_acc(fs, fc, n_ip.x, n_ip.y);
+        df_acc(fs, fc, m_im.x, m_im.y);
+        df_acc(fs, fc, n_jp.x, n_jp.y);
+        df_acc(fs, fc, m_jm.x, m_jm.y);
+        float bs = n_ijp.x, bc = n_ijp.y;
+        df_acc(bs, bc, m_ijm.x, m_ijm.y);
+        float p0, l0, p1, l1, p2, l2, p3, l3;
+        df_mul(cf.C[0][0], cf.C[0][1], cf.C[0][2], c0v.x, c0v.y, p0, l0);
+        df_mul(cf.C[1][0], cf.C[1][1], cf.C[1][2], as, ac, p1, l1);
+        df_mul(cf.C[2][0], cf.C[2][1], cf.C[2][2], fs, fc, p2, l2);
+        df_mul(cf.C[3][0], cf.C[3][1], cf.C[3][2], bs, bc, p3, l3);
+        float ys = p0, yc = l0;
+        df_acc(ys, yc, p1, l1);
+        df_acc(ys, yc, p2, l2);
+        df_acc(ys, yc, p3, l3);
+        const float yh = ys + yc;                 // FastTwoSum: |yc| small against ys
+        const float yl = yc - (yh - ys);
+        const double av = df_to_double(yh, cf.s) + df_to_double(yl, cf.s);
+        y[row0 + sk * k] = av;
+        acc[0] = fma(pc, av, acc[0]);
+        cm = c0v;
+        m_im = z_im;
+        m_jm = z_jm;
+        m_ijm = z_ijm;
+        c0v = cp;
+        p_ip = n_ip;
+        p_jp = n_jp;
+        p_ijp = n_ijp;
+        z_im = z2_im;
+        z_jm = z2_jm;
+        z_ijm = z2_ijm;
+        cp = cp2;
+        n_ip = n2_ip;
+        n_jp = n2_jp;
+        n_ijp = n2_ijp;
+        pc = pc2;
+      }
+    }
+  }
+  write_partials<double>(acc, partials, partials != nullptr, nblocks);
+}
+
+// split of an FP64 vector into FP32 pairs (x_out = hi + lo, the 48-bit value; x_out may be
+// x), rflag raised when an entry lies outside the split's range
+__global__ void k_df_split_vec(int64_t N, const double* x, double* x_out, float2* p2, int* rflag) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float hi, lo;
+    double xs;
+    if (df_split(x[i], hi, lo, xs)) {
+      p2[i] = make_float2(hi, lo);
+      if (x_out) x_out[i] = xs;
+    } else {
+      bad = true;
+      if (x_out) x_out[i] = x[i];
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(rflag, 1);
+}
+
 // ------------------------------------------------------------------ CSR4
 
 template <typename VT>
@@ -839,6 +985,49 @@ void op_apply_d_done(const Level& Lv, const double* x, double* y, double* partia
   e.want_dot = partials != nullptr;
   int nb = launch_op<double>(Lv, AMG_PREC_FP64, x, e, partials, st, done);
   if (nblocks) *nblocks = nb;
+}
+
+DfOperator df_operator(const Stencil& st) {
+  DfOperator D;
+  const double c[4] = {st.c0, st.ca, st.cf, st.cb};
+  double mx = 0.0;
+  for (double v : c) mx = std::max(mx, std::fabs(v));
+  D.s = mx > 0.0 ? -std::ilogb(mx) : 0;
+  for (int k = 0; k < 4; k++) {
+    const double cs = std::ldexp(c[k], D.s);
+    const float c1 = (float)cs;
+    const float c2 = (float)(cs - (double)c1);
+    const float c3 = (float)(cs - (double)c1 - (double)c2);
+    D.C[k][0] = c1;
+    D.C[k][1] = c2;
+    D.C[k][2] = c3;
+    D.c64[k] = c[k];
+  }
+  return D;
+}
+
+int op_apply_df(const Level& Lv, const DfOperator& D, const float2* p2, const double* p64,
+                double* y, double* partials, cudaStream_t st, const int* done, const int* rflag) {
+  constexpr int TYV = 8, KZV = 32;
+  DfCoef c;
+  for (int k = 0; k < 4; k++) {
+    for (int t = 0; t < 3; t++) c.C[k][t] = D.C[k][t];
+    c.c64[k] = D.c64[k];
+  }
+  c.s = D.s;
+  const int m = Lv.st.m;
+  dim3 grid((m + TX - 1) / TX, (m + TYV - 1) / TYV, (m + KZV - 1) / KZV);
+  const int nb = grid.x * grid.y * grid.z;
+  FEM_REQUIRE(!partials || nb <= kMaxPartialBlocks, FEM_EUNSUPPORTED, "stencil grid too large");
+  k_stencil_df<TYV, KZV><<<grid, TX * TYV, 0, st>>>(p2, p64, m, c, y, partials, nb, done, rflag);
+  FEM_CHECK_LAUNCH();
+  return nb;
+}
+
+void df_split_vec(int64_t N, const double* x, double* x_out, float2* p2, int* rflag,
+                  cudaStream_t st) {
+  k_df_split_vec<<<persistent_grid(N, 256, 8), 256, 0, st>>>(N, x, x_out, p2, rflag);
+  FEM_CHECK_LAUNCH();
 }
 
 template <typename T>

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "dfloat.cuh"
 #include "solver.cuh"
 
 namespace fem {
@@ -330,8 +331,9 @@ __global__ void k_fin_rr(const double* partials, int nb, PcgState* S) {
   }
 }
 
-__global__ void k_fin_rz(const double* partials, int nb, PcgState* S) {
+__global__ void k_fin_rz(const double* partials, int nb, PcgState* S, int* rflag) {
   if (S->done) return;
+  if (rflag && threadIdx.x == 0) *rflag = 0;   // the p update that follows raises it again
   double v[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     v[0] += partials[i];
@@ -353,12 +355,31 @@ __global__ void k_fin_rz(const double* partials, int nb, PcgState* S) {
   }
 }
 
-__global__ void k_update_p(int64_t N, const double* z, double* p, const PcgState* S) {
+// p = z + beta p; with p2 given, p is rounded to 48 bits and kept as FP32 pairs as well (the
+// input of the double-float operator), rflag raised for entries outside the pairs' range
+__global__ void k_update_p(int64_t N, const double* z, double* p, const PcgState* S, float2* p2,
+                           int* rflag) {
   if (S->done) return;
   const double beta = S->beta;
+  bool bad = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = z[i] + beta * p[i];
+    if (p2) {
+      float hi, lo;
+      double vs;
+      if (df_split(v, hi, lo, vs)) {
+        p2[i] = make_float2(hi, lo);
+        p[i] = vs;
+      } else {
+        p[i] = v;
+        bad = true;
+      }
+    } else {
+      p[i] = v;
+    }
+  }
+  if (p2 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(rflag, 1);
 }
 
 __global__ void k_jacobi_prec(int64_t N, const double* dinv, const double* r, const double* rprev,
@@ -411,6 +432,8 @@ __global__ void k_copy(int64_t N, const double* a, double* b) {
 struct PcgWork {
   int64_t N = 0;
   DevBuf<double> r, rprev, p, q, z, partials, sums;
+  DevBuf<float2> p2;     // p as FP32 pairs (double-float operator on the uniform grid)
+  DevBuf<int> rflag;     // p has entries outside the pairs' range: FP64 operator
   DevBuf<PcgState> state;
   PcgState* hstate = nullptr;  // pinned, 2 slots
   cudaStream_t s = nullptr;
@@ -463,8 +486,16 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
         for (auto& Lp : H->L) Lp->done = nullptr;
     }
   } done_reset{H};
-  // CG's operator is always the system's (a hierarchy may be set up from another rho)
+  // CG's operator is always the system's (a hierarchy may be set up from another rho); on
+  // the uniform grid it runs in double-float arithmetic on p split into FP32 pairs
   Level& L0 = sysL;
+  const bool dfop = L0.stencil;
+  DfOperator dfo;
+  if (dfop) {
+    W.p2.alloc(N);
+    W.rflag.alloc(1);
+    dfo = df_operator(L0.st);
+  }
   const int* done = &W.state.p->done;
   const unsigned gv = persistent_grid(N, 256, 8);
   if (!f) f = S.f.p;
@@ -491,7 +522,10 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
   // one iteration, all kernels gated by the device flag
   auto iteration = [&]() {
     int nb_pq = 0;
-    op_apply_d_done(L0, W.p, W.q, W.partials, &nb_pq, st, done);
+    if (dfop)
+      nb_pq = op_apply_df(L0, dfo, W.p2, W.p, W.q, W.partials, st, done, W.rflag);
+    else
+      op_apply_d_done(L0, W.p, W.q, W.partials, &nb_pq, st, done);
     k_fin_pq<<<1, 1024, 0, st>>>(W.partials, nb_pq, W.state);
     FEM_CHECK_LAUNCH();
     k_update_xr<<<gv, 256, 0, st>>>(N, u, W.p, W.r, W.q, flexible ? W.rprev.p : nullptr, W.state,
@@ -500,9 +534,10 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
     k_fin_rr<<<1, 1024, 0, st>>>(W.partials, gv, W.state);
     FEM_CHECK_LAUNCH();
     precondition(done);
-    k_fin_rz<<<1, 1024, 0, st>>>(W.partials, nb_rz, W.state);
+    k_fin_rz<<<1, 1024, 0, st>>>(W.partials, nb_rz, W.state, dfop ? W.rflag.p : nullptr);
     FEM_CHECK_LAUNCH();
-    k_update_p<<<gv, 256, 0, st>>>(N, W.z, W.p, W.state);
+    k_update_p<<<gv, 256, 0, st>>>(N, W.z, W.p, W.state, dfop ? W.p2.p : nullptr,
+                                   dfop ? W.rflag.p : nullptr);
     FEM_CHECK_LAUNCH();
   };
 
@@ -525,79 +560,99 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
     count_launches(-per_iter);
   }
   FEM_CUDA(cudaEventRecord(W.t0, st));
-  // r = f - A x0  (or f)
-  if (o.use_x0) {
-    op_apply_d(L0, u, W.r, nullptr, nullptr, st);
-    k_sub<<<gv, 256, 0, st>>>(N, f, W.r);
+  // With the double-float operator CG's recursive residual can run ahead of the FP64 one by
+  // about 2^-44 cond(A): when the FP64 residual recomputed at the end is above the
+  // tolerance, CG starts again from its iterate (at most twice).
+  bool from_u = o.use_x0 != 0;
+  int status = FEM_OK, iters = 0;
+  PcgState hs{};
+  double hs2[2] = {0.0, 0.0};
+  for (int pass = 0;; pass++) {
+    // r = f - A x0  (or f)
+    if (from_u) {
+      op_apply_d(L0, u, W.r, nullptr, nullptr, st);
+      k_sub<<<gv, 256, 0, st>>>(N, f, W.r);
+      FEM_CHECK_LAUNCH();
+    } else {
+      FEM_CUDA(cudaMemsetAsync(u, 0, 8 * N, st));
+      k_copy<<<gv, 256, 0, st>>>(N, f, W.r);
+      FEM_CHECK_LAUNCH();
+    }
+    if (flexible) FEM_CUDA(cudaMemsetAsync(W.rprev, 0, 8 * N, st));
+    // bb = <f,f>, rr = <r,r>
+    k_dot_self<<<gv, 256, 0, st>>>(N, f, W.r, W.partials);
     FEM_CHECK_LAUNCH();
-  } else {
-    FEM_CUDA(cudaMemsetAsync(u, 0, 8 * N, st));
-    k_copy<<<gv, 256, 0, st>>>(N, f, W.r);
-  }
-  FEM_CHECK_LAUNCH();
-  if (flexible) FEM_CUDA(cudaMemsetAsync(W.rprev, 0, 8 * N, st));
-  // bb = <f,f>, rr = <r,r>
-  k_dot_self<<<gv, 256, 0, st>>>(N, f, W.r, W.partials);
-  FEM_CHECK_LAUNCH();
-  finalize_sums(W.partials, gv, 2, W.sums, st);
-  precondition(nullptr);
-  finalize_sums(W.partials, nb_rz, 1, W.sums.p + 4, st);
-  k_pcg_start<<<1, 1, 0, st>>>(W.state, W.sums, W.sums.p + 4, o.tol, o.max_iter, o.stop, flexible);
-  FEM_CHECK_LAUNCH();
-  k_copy<<<gv, 256, 0, st>>>(N, W.z, W.p);
-  FEM_CHECK_LAUNCH();
+    finalize_sums(W.partials, gv, 2, W.sums, st);
+    precondition(nullptr);
+    finalize_sums(W.partials, nb_rz, 1, W.sums.p + 4, st);
+    k_pcg_start<<<1, 1, 0, st>>>(W.state, W.sums, W.sums.p + 4, o.tol, o.max_iter - iters, o.stop,
+                                 flexible);
+    FEM_CHECK_LAUNCH();
+    if (dfop) {
+      FEM_CUDA(cudaMemsetAsync(W.rflag, 0, sizeof(int), st));
+      df_split_vec(N, W.z, W.p, W.p2, W.rflag, st);
+    } else {
+      k_copy<<<gv, 256, 0, st>>>(N, W.z, W.p);
+      FEM_CHECK_LAUNCH();
+    }
 
-  const int chunk = 2;
-  int k = 0;
-  int status = FEM_OK;
-  int launched = 0;
-  bool finished = false;
-  while (!finished) {
-    for (int c = 0; c < chunk; c++) {
-      if (use_graph) {
-        FEM_CUDA(cudaGraphLaunch(W.exec, st));
-        count_launches(per_iter);
-      } else
-        iteration();
-      launched++;
-    }
-    FEM_CUDA(cudaMemcpyAsync(&W.hstate[k & 1], W.state, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
-    FEM_CUDA(cudaEventRecord(W.ev[k & 1], st));
-    if (k > 0) {
-      FEM_CUDA(cudaEventSynchronize(W.ev[(k - 1) & 1]));
-      const PcgState& hs = W.hstate[(k - 1) & 1];
-      if (hs.done) finished = true;
-      if (!finished && o.cancel_host && *o.cancel_host) {   // a finished solve stands
-        status = FEM_ECANCELLED;
-        finished = true;
+    const int chunk = 2;
+    int k = 0;
+    int launched = 0;
+    bool finished = false;
+    while (!finished) {
+      for (int c = 0; c < chunk; c++) {
+        if (use_graph) {
+          FEM_CUDA(cudaGraphLaunch(W.exec, st));
+          count_launches(per_iter);
+        } else
+          iteration();
+        launched++;
       }
+      FEM_CUDA(cudaMemcpyAsync(&W.hstate[k & 1], W.state, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
+      FEM_CUDA(cudaEventRecord(W.ev[k & 1], st));
+      if (k > 0) {
+        FEM_CUDA(cudaEventSynchronize(W.ev[(k - 1) & 1]));
+        const PcgState& h1 = W.hstate[(k - 1) & 1];
+        if (h1.done) finished = true;
+        if (!finished && o.cancel_host && *o.cancel_host) {   // a finished solve stands
+          status = FEM_ECANCELLED;
+          finished = true;
+        }
+      }
+      if (launched > o.max_iter + 4 * chunk) finished = true;  // safety: flag never set
+      k++;
     }
-    if (launched > o.max_iter + 4 * chunk) finished = true;  // safety: flag never set
-    k++;
+    FEM_CUDA(cudaMemcpyAsync(&W.hstate[0], W.state, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    hs = W.hstate[0];
+    // the flag was read while the last chunk was still queued: a solve that finished in
+    // that chunk stands
+    if (status == FEM_ECANCELLED && hs.done) status = FEM_OK;
+    iters += hs.iter;
+    // true residual
+    op_apply_d(L0, u, W.q, nullptr, nullptr, st);
+    k_sub<<<gv, 256, 0, st>>>(N, f, W.q);
+    FEM_CHECK_LAUNCH();
+    k_dot_self<<<gv, 256, 0, st>>>(N, W.q, f, W.partials);
+    FEM_CHECK_LAUNCH();
+    finalize_sums(W.partials, gv, 2, W.sums, st);
+    FEM_CUDA(cudaMemcpyAsync(hs2, W.sums, 16, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    const bool again = dfop && status == FEM_OK && hs.done && hs.status == FEM_OK &&
+                       o.stop == PCG_STOP_RESIDUAL && hs2[1] > 0 &&
+                       hs2[0] > o.tol * o.tol * hs2[1] && pass < 2 && iters < o.max_iter;
+    if (!again) break;
+    from_u = true;
   }
   FEM_CUDA(cudaEventRecord(W.t1, st));
-  FEM_CUDA(cudaMemcpyAsync(&W.hstate[0], W.state, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
-  FEM_CUDA(cudaStreamSynchronize(st));
-  const PcgState hs = W.hstate[0];
-  // the flag was read while the last chunk was still queued: a solve that finished in that
-  // chunk stands
-  if (status == FEM_ECANCELLED && hs.done) status = FEM_OK;
+  FEM_CUDA(cudaEventSynchronize(W.t1));
   float ms = 0.f;
   FEM_CUDA(cudaEventElapsedTime(&ms, W.t0, W.t1));
-  // true residual
-  op_apply_d(L0, u, W.q, nullptr, nullptr, st);
-  k_sub<<<gv, 256, 0, st>>>(N, f, W.q);
-  FEM_CHECK_LAUNCH();
-  k_dot_self<<<gv, 256, 0, st>>>(N, W.q, f, W.partials);
-  FEM_CHECK_LAUNCH();
-  finalize_sums(W.partials, gv, 2, W.sums, st);
-  double hs2[2];
-  FEM_CUDA(cudaMemcpyAsync(hs2, W.sums, 16, cudaMemcpyDeviceToHost, st));
-  FEM_CUDA(cudaStreamSynchronize(st));
   // the caller's stream continues after the solve
   FEM_CUDA(cudaEventRecord(W.ev[0], st));
   FEM_CUDA(cudaStreamWaitEvent(user, W.ev[0], 0));
-  res.iterations = hs.iter;
+  res.iterations = iters;
   res.status = status != FEM_OK ? status : (hs.done ? hs.status : FEM_ENOCONV);
   res.relres = hs2[1] > 0 ? std::sqrt(hs2[0] / hs2[1]) : 0.0;
   res.prec_relres = hs.rz0 > 0 ? std::sqrt(std::fabs(hs.rz / hs.rz0)) : 0.0;

@@ -152,6 +152,18 @@ void op_apply_d_done(const Level& Lv, const double* x, double* y, double* partia
                      int* nblocks, cudaStream_t st, const int* done);
 // Non-owning finest-level view of a system's operator.
 void system_level(System& S, Level& Lv);
+// CG's operator on the uniform grid in double-float arithmetic (ops.cu): coefficients
+// prepared once per system; p split into FP32 pairs by df_split_vec (or by CG's p update)
+struct DfOperator {
+  float C[4][3];
+  int s = 0;
+  double c64[4];
+};
+DfOperator df_operator(const Stencil& st);
+int op_apply_df(const Level& Lv, const DfOperator& D, const float2* p2, const double* p64,
+                double* y, double* partials, cudaStream_t st, const int* done, const int* rflag);
+void df_split_vec(int64_t N, const double* x, double* x_out, float2* p2, int* rflag,
+                  cudaStream_t st);
 // r = b - A x (r dense when the level is in the ghost layout)
 template <typename T>
 void op_residual(const Level& Lv, int prec, const T* b, const T* x, T* r, cudaStream_t st);

@@ -94,6 +94,37 @@ def test_operator_matches_oracle(fa, n, jit, fmt):
 # n = 48 and 64 (103,823 and 250,047 rows) run the Galerkin products on several thousand
 # thread blocks with ragged last blocks, level 0 through the stencil's strength graph
 # (uniform) or through A's CSR (jittered, format CSR)
+@pytest.mark.parametrize("n,wide", [(16, False), (48, False), (33, True)])
+def test_cg_operator_matches_oracle(fa, n, wide):
+    # CG's operator on the uniform grid runs in double-float arithmetic (fem_spmv_timed
+    # applies it as CG does).  Bound: x is rounded to 48 bits (2^-49 sum |a x|), and about a
+    # dozen FP32 roundings of quantities at most 2^-23 of the row's terms stay below
+    # 2^-44 sum |a_ij x_j| together.  wide: entries spread over 17 decades.
+    rho = 1.0 / n ** 2
+    s = core.assemble(n, W.sine_target())
+    sys_ = fa.fem_assemble(n, rho, W.sine_target())
+    try:
+        N = (n - 1) ** 3
+        x = W.random_vector(N, 17)
+        if wide:
+            x = x * np.exp(np.random.default_rng(5).uniform(-20.0, 20.0, N))
+        y = torch.empty(N, dtype=torch.float64, device="cuda")
+        ms = fa.fem_spmv_timed(sys_, _dev(x), y, 2)
+        assert ms > 0.0
+        yo = core.apply(s, rho, x)
+        scale = np.abs(s.A(rho)).dot(np.abs(x))
+        err = np.max(np.abs(y.cpu().numpy() - yo) / scale)
+        assert err <= 2.0 ** -44, err
+        # entries beyond the split's range: the product falls back to FP64
+        x[N // 2] = 1e-30
+        fa.fem_spmv_timed(sys_, _dev(x), y, 1)
+        yo = core.apply(s, rho, x)
+        scale = np.abs(s.A(rho)).dot(np.abs(x))
+        assert np.max(np.abs(y.cpu().numpy() - yo) / scale) <= 1e-14
+    finally:
+        fa.fem_system_destroy(sys_)
+
+
 HIER_CASES = [(16, 1.0 / 256, False, 0), (16, 1.0, False, 0), (12, 1e-6, False, 2),
               (13, 1.0 / 169, True, 0), (48, 1.0 / 48 ** 2, False, 0), (48, 1.0, True, 0),
               (64, 1.0 / 64 ** 2, False, 0), (64, 1e-6, True, 0), (48, 1e-2, False, 2)]
