@@ -401,6 +401,16 @@ fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stre
 fem_status amg_vcycle_graph(amg_hier h, const double* r_dev, double* z_dev, int32_t reps,
                             void* stream, double* ms_out);
 
+/* The Galerkin product A_{l+1} = R_l (A_l P_l) of level `level` (Sec. 3.1: the coarse
+ * operator P^T A P), computed again from the hierarchy's A_l, P_l, R_l reps times after one
+ * untimed product, into scratch storage (the hierarchy is not changed).  ms_out receives the
+ * mean device time of one product (CUDA events on `stream`: both SpGEMM launches and the
+ * compaction), ap_entries_out the entries of A_l P_l.  Errors: FEM_EINVAL (null hierarchy,
+ * reps < 1, a level without a coarse operator, or a finest level kept without its FP64
+ * matrix). */
+fem_status amg_galerkin_timed(amg_hier h, int32_t level, int32_t reps, void* stream,
+                              double* ms_out, int64_t* ap_entries_out);
+
 void amg_hier_destroy(amg_hier h);
 
 /* ------------------------------------------------------------------ PCG */

@@ -140,6 +140,8 @@ SIGNATURES = {
     "amg_vcycle": (C.c_int, [VP, VP, VP, VP]),
     "amg_vcycle_graph": (C.c_int, [VP, VP, VP, C.c_int32, VP, P(C.c_double)]),
     "fem_spmv_timed": (C.c_int, [VP, VP, VP, C.c_int32, VP, P(C.c_double)]),
+    "amg_galerkin_timed": (C.c_int, [VP, C.c_int32, C.c_int32, VP, P(C.c_double),
+                                     P(C.c_int64)]),
     "amg_hier_destroy": (None, [VP]),
     "pcg_default_opts": (None, [P(PcgOpts)]),
     "pcg_solve": (C.c_int, [VP, VP, VP, VP, C.c_int32, P(C.c_double), P(PcgOpts), VP,
@@ -495,6 +497,16 @@ def amg_vcycle_graph(h, r, z, reps: int = 20, stream=None) -> float:
     _check(lib().amg_vcycle_graph(h, _ptr(r), _ptr(z), int(reps), _stream(stream), C.byref(ms)),
            "amg_vcycle_graph")
     return ms.value
+
+
+def amg_galerkin_timed(h, level: int = 0, reps: int = 5, stream=None):
+    """Level `level`'s Galerkin product recomputed `reps` times: (ms per product, entries of
+    A P)."""
+    ms = C.c_double(0.0)
+    ape = C.c_int64(0)
+    _check(lib().amg_galerkin_timed(h, int(level), int(reps), _stream(stream), C.byref(ms),
+                                    C.byref(ape)), "amg_galerkin_timed")
+    return ms.value, int(ape.value)
 
 
 def amg_hier_export(h, level, which, rowptr=None, col=None, val=None, stream=None) -> int:

@@ -1300,6 +1300,11 @@ void spgemm_numeric(const Csr4& A, const double* Aval, const Csr4& B, const doub
   FEM_CHECK_LAUNCH();
 }
 
+static int64_t row_sum(const int64_t* len, int64_t n, cudaStream_t st) {
+  DevBuf<int64_t> scan(n + 1, st);
+  return exclusive_scan(len, n, scan, st);
+}
+
 // A product at a fixed stride: column indices, values and row lengths.
 struct Strided {
   int64_t nrows = 0;
@@ -1433,11 +1438,13 @@ static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, cons
 
 // Galerkin product A_c = R (A P) by the merge kernel (A P at a fixed stride, A_c compacted
 // to CSR4).  Returns false when the kernel cannot take it (the hash path then runs); sets
-// *too_long when A P or A_c has a row longer than limit.
+// *too_long when A P or A_c has a row longer than limit; *ap_entries (if given) receives the
+// entries of A P.
 bool galerkin_merge(const Csr4& A, const Csr4& P, const Csr4& R, Csr4& Ac, cudaStream_t st,
-                    bool* too_long, int64_t limit) {
+                    bool* too_long, int64_t limit, int64_t* ap_entries) {
   Strided AP, RAP;
   if (!spgemm_merge(A, A.val, &P, P.val, nullptr, AP, st)) return false;
+  if (ap_entries) *ap_entries = row_sum(AP.len, AP.nrows, st);
   if (AP.maxlen > limit) {
     *too_long = true;
     return true;
@@ -1456,6 +1463,41 @@ bool galerkin_merge(const Csr4& A, const Csr4& P, const Csr4& R, Csr4& Ac, cudaS
                                                               RAP.len, Ac.rowptr, Ac.col, Ac.val);
   FEM_CHECK_LAUNCH();
   return true;
+}
+
+double galerkin_timed(const Hierarchy& H, int lev, int reps, cudaStream_t st,
+                      int64_t* ap_entries) {
+  FEM_REQUIRE(lev >= 0 && lev < (int)H.L.size() && !H.L[lev]->coarsest, FEM_EINVAL,
+              "amg_galerkin_timed: level without a coarse operator");
+  const Level& L = *H.L[lev];
+  FEM_REQUIRE(L.A && L.A->val.p && L.A->nnz > 0, FEM_EINVAL,
+              "amg_galerkin_timed: the level keeps no FP64 matrix");
+  cudaEvent_t e0, e1;
+  FEM_CUDA(cudaEventCreate(&e0));
+  FEM_CUDA(cudaEventCreate(&e1));
+  double ms_sum = 0.0;
+  for (int rep = -1; rep < reps; rep++) {   // one untimed product first
+    Csr4 Ac;
+    bool too_long = false;
+    FEM_CUDA(cudaEventRecord(e0, st));
+    int64_t ape = 0;
+    const bool merged = galerkin_merge(*L.A, L.P, L.R, Ac, st, &too_long, kLongRowMax, &ape);
+    if (!merged && !too_long) {
+      Csr4 AP;
+      spgemm(*L.A, L.A->val, L.P, L.P.val, AP, st, true);
+      spgemm(L.R, L.R.val, AP, AP.val, Ac, st, true);
+      ape = AP.nnz;
+    }
+    FEM_CUDA(cudaEventRecord(e1, st));
+    FEM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep >= 0) ms_sum += ms;
+    if (ap_entries) *ap_entries = ape;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms_sum / reps;
 }
 
 void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long,
@@ -2586,7 +2628,7 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     auto nxt = std::make_unique<Level>();
     bool merged = false;
     if (!too_long && !S.pencil)
-      merged = galerkin_merge(*Acur, Lv.P, Lv.R, nxt->Aown, st, &too_long, row_limit);
+      merged = galerkin_merge(*Acur, Lv.P, Lv.R, nxt->Aown, st, &too_long, row_limit, nullptr);
     if (!merged && !too_long)
       spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long, row_limit);
     tr.mark("level: A P (spgemm)");

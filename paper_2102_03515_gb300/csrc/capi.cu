@@ -555,6 +555,19 @@ fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stre
   });
 }
 
+fem_status amg_galerkin_timed(amg_hier h, int32_t level, int32_t reps, void* stream,
+                              double* ms_out, int64_t* ap_entries_out) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(h && reps >= 1, FEM_EINVAL, "amg_galerkin_timed: bad argument");
+    int64_t ape = 0;
+    const double ms = galerkin_timed(h->H, level, reps, as_stream(stream), &ape);
+    if (ms_out) *ms_out = ms;
+    if (ap_entries_out) *ap_entries_out = ape;
+    return FEM_OK;
+  });
+}
+
 fem_status amg_vcycle_graph(amg_hier h, const double* r_dev, double* z_dev, int32_t reps,
                             void* stream, double* ms_out) {
   return guarded([&]() -> fem_status {

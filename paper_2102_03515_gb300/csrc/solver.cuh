@@ -208,6 +208,9 @@ void spgemm(const Csr4& A, const double* Aval, const Csr4& B, const double* Bval
 void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long = nullptr,
                int64_t limit = 8192);
 double gershgorin(const Csr4& A, const double* val, cudaStream_t st);
+// level lev's Galerkin product R (A P) repeated reps times (after one untimed product), mean
+// ms by CUDA events on st; the stored entries of A P in *ap_entries
+double galerkin_timed(const Hierarchy& H, int lev, int reps, cudaStream_t st, int64_t* ap_entries);
 void dense_inverse(const Csr4& A, const double* val, DevBuf<double>& Ainv, cudaStream_t st);
 
 // ------------------------------------------------------------------ V-cycle (vcycle.cu)
