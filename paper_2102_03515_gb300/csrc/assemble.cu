@@ -679,6 +679,95 @@ __global__ void k_errors(int n, const double* xyz, const double* __restrict__ u,
   }
 }
 
+// The same norms on the uniform grid for the sine targets (ubar = sin sin sin, or 1 + it),
+// whose values factor by axis: a quadrature point (p, q) of Kuhn tet p in cube (i, j, k)
+// sits at h (i + xi_pq, j + eta_pq, k + zeta_pq), so sin(pi x) = Sx[pq][i] with
+// Sx[pq][i] = sin(pi h (i + xi_pq)) from a table (and cos for the gradient), instead of
+// three FP64 sine evaluations per point.  Each Kuhn tet has volume h^3 / 6 and fixed
+// barycentric gradients gref[p] / h.
+__global__ void k_err_tables(int n, int npq, const double* __restrict__ xi, double* tabs,
+                             double* tabc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)npq * n;
+  if (t >= 3 * per) return;
+  const int d = (int)(t / per), pq = (int)((t % per) / n), i = (int)(t % n);
+  double sv, cv;
+  sincospi((i + xi[3 * pq + d]) / n, &sv, &cv);
+  tabs[t] = sv;
+  if (tabc) tabc[t] = cv;
+}
+
+__global__ void k_errors_sep(int n, const double* __restrict__ u, double scale, double add,
+                             int grad, int np, const double* __restrict__ tabs,
+                             const double* __restrict__ tabc, const double* __restrict__ bary,
+                             const double* __restrict__ qw, const double* __restrict__ gref,
+                             double* partials) {
+  constexpr int PP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int64_t nc = (int64_t)n * n * n;
+  const int m = n - 1;
+  const int npq = 6 * np;
+  const int64_t per = (int64_t)npq * n;
+  const double vol = 1.0 / (6.0 * (double)n * n * n), hinv = (double)n;
+  const double spi = scale * 3.14159265358979323846;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(c % n), cj = (int)((c / n) % n), ck = (int)(c / ((int64_t)n * n));
+    double Uc[8];
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+      const int vi = ci + (a & 1), vj = cj + ((a >> 1) & 1), vk = ck + ((a >> 2) & 1);
+      const bool in = vi >= 1 && vj >= 1 && vk >= 1 && vi <= m && vj <= m && vk <= m;
+      Uc[a] = in ? u[(int64_t)(vi - 1) + (int64_t)m * ((vj - 1) + (int64_t)m * (vk - 1))] : 0.0;
+    }
+    const double* sx = tabs + ci;
+    const double* sy = tabs + per + cj;
+    const double* sz = tabs + 2 * per + ck;
+    const double* cx = tabc + ci;
+    const double* cy = tabc + per + cj;
+    const double* cz = tabc + 2 * per + ck;
+#pragma unroll
+    for (int p = 0; p < 6; p++) {
+      int lv[4];
+      lv[0] = 0;
+#pragma unroll
+      for (int s2 = 0; s2 < 3; s2++) lv[s2 + 1] = lv[s2] | (1 << PP[p][s2]);
+      double U[4];
+#pragma unroll
+      for (int a = 0; a < 4; a++) U[a] = Uc[lv[a]];
+      double guh[3] = {0.0, 0.0, 0.0};
+      if (grad) {
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+          for (int d = 0; d < 3; d++) guh[d] += U[a] * (gref[(p * 4 + a) * 3 + d] * hinv);
+      }
+      double e2 = 0.0, g2 = 0.0;
+      for (int q = 0; q < np; q++) {
+        const int64_t o = (int64_t)(p * np + q) * n;
+        const double* b = bary + 4 * (p * np + q);
+        const double uh = b[0] * U[0] + b[1] * U[1] + b[2] * U[2] + b[3] * U[3];
+        const double vx = sx[o], vy = sy[o], vz = sz[o];
+        const double diff = scale * (add + vx * vy * vz) - uh;
+        e2 += qw[q] * diff * diff;
+        if (grad) {
+          const double d0 = spi * cx[o] * vy * vz - guh[0];
+          const double d1 = spi * vx * cy[o] * vz - guh[1];
+          const double d2 = spi * vx * vy * cz[o] - guh[2];
+          g2 += qw[q] * (d0 * d0 + d1 * d1 + d2 * d2);
+        }
+      }
+      acc[0] += vol * e2;
+      acc[1] += vol * g2;
+    }
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc[0];
+    partials[gridDim.x + blockIdx.x] = acc[1];
+  }
+}
+
 // Control and adjoint at the unknowns' vertices: z = (ubar - u) / rho, p = -rho u.
 __global__ void k_recover(int n, const double* xyz, TargetDev T, double rho,
                           const double* __restrict__ u, double* z, double* p) {
@@ -1419,6 +1508,65 @@ void fem_error_norms(System& S, const double* u, const fem_target& t, double sca
   const int64_t ncube = S.general ? S.nt : (int64_t)S.n * S.n * S.n;
   const unsigned g = persistent_grid(ncube, 128, 8);
   DevBuf<double> part(2 * (size_t)g, st), sums(2, st);
+  if (!S.general && S.uniform && grad) {
+    // separable sine targets on the uniform grid: per-axis tables of the point coordinates'
+    // sines and cosines
+    static const int PP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int n = S.n;
+    const int npq = 6 * np;
+    std::vector<double> xi(3 * (size_t)npq), bq(4 * (size_t)npq), gref(6 * 4 * 3);
+    for (int p = 0; p < 6; p++) {
+      int lv[4] = {0, 0, 0, 0};
+      for (int s2 = 0; s2 < 3; s2++) lv[s2 + 1] = lv[s2] | (1 << PP[p][s2]);
+      double X[4][3];
+      for (int a = 0; a < 4; a++)
+        for (int d = 0; d < 3; d++) X[a][d] = (double)((lv[a] >> d) & 1);
+      for (int q = 0; q < np; q++) {
+        const int pq = p * np + q;
+        for (int d = 0; d < 3; d++) {
+          double v = 0.0;
+          for (int a = 0; a < 4; a++) v += bary[4 * q + a] * X[a][d];
+          xi[3 * pq + d] = v;
+        }
+        for (int a = 0; a < 4; a++) bq[4 * pq + a] = bary[4 * q + a];
+      }
+      // barycentric gradients of the unit-cube tet: rows of the inverse of [x_a - x_0]
+      double J[3][3], Ji[3][3];
+      for (int r = 0; r < 3; r++)
+        for (int d = 0; d < 3; d++) J[r][d] = X[r + 1][d] - X[0][d];
+      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      for (int r = 0; r < 3; r++)
+        for (int d = 0; d < 3; d++) {
+          const int r1 = (d + 1) % 3, r2 = (d + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+          Ji[r][d] = (J[r1][c1] * J[r2][c2] - J[r1][c2] * J[r2][c1]) / det;   // (J^-1)_{r d}
+        }
+      // grad lambda_a = column a-1 of J^-T for a >= 1, lambda_0 = -(sum of the others)
+      for (int d = 0; d < 3; d++) {
+        double s0 = 0.0;
+        for (int a = 1; a < 4; a++) {
+          gref[(p * 4 + a) * 3 + d] = Ji[d][a - 1];
+          s0 += Ji[d][a - 1];
+        }
+        gref[(p * 4 + 0) * 3 + d] = -s0;
+      }
+    }
+    DevBuf<double> dxi(xi.size(), st), dbq(bq.size(), st), dg(gref.size(), st);
+    DevBuf<double> tabs(3 * (size_t)npq * n, st), tabc(3 * (size_t)npq * n, st);
+    FEM_CUDA(cudaMemcpyAsync(dxi, xi.data(), 8 * xi.size(), cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(dbq, bq.data(), 8 * bq.size(), cudaMemcpyHostToDevice, st));
+    FEM_CUDA(cudaMemcpyAsync(dg, gref.data(), 8 * gref.size(), cudaMemcpyHostToDevice, st));
+    k_err_tables<<<grid_for(3 * (int64_t)npq * n, 256), 256, 0, st>>>(n, npq, dxi, tabs, tabc);
+    FEM_CHECK_LAUNCH();
+    k_errors_sep<<<g, 128, 0, st>>>(n, u, scale, t.kind == FEM_TARGET_SINE_PLUS_ONE ? 1.0 : 0.0,
+                                    grad, np, tabs, tabc, dbq, qw, dg, part);
+    FEM_CHECK_LAUNCH();
+    finalize_sums(part, (int)g, 2, sums, st);
+    FEM_CUDA(cudaMemcpyAsync(out, sums, 16, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    return;
+  }
   if (S.general)
     k_gm_errors<<<g, 128, 0, st>>>(S.nt, S.tet, S.vdof, S.xyz, u, th.T, scale, grad, qb, qw, np,
                                    part);
