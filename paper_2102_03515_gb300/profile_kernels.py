@@ -4,6 +4,8 @@
     python -m paper_2102_03515_gb300.profile_kernels vcycle32 256  # one FP32 V-cycle
     python -m paper_2102_03515_gb300.profile_kernels step 256      # one assemble+setup+solve
     python -m paper_2102_03515_gb300.profile_kernels batched 128   # 64-slot batched solve
+    python -m paper_2102_03515_gb300.profile_kernels galerkin 128  # finest Galerkin product
+    python -m paper_2102_03515_gb300.profile_kernels cgop 256      # CG's q = A p
 
 Each mode runs its work three times; the last pass is inside the NVTX range "profiled",
 so that `ncu --nvtx --nvtx-include "profiled/"` sees only the steady state (the first
@@ -68,6 +70,24 @@ def main(argv):
                 fa.pcg_solve(s, h, None, u, tol=1e-8, use_graph=0)
                 fa.amg_hier_destroy(h)
                 fa.fem_system_destroy(s)
+    elif mode == "galerkin":
+        # the finest level's Galerkin product, recomputed from an FP32 hierarchy
+        s = fa.fem_assemble(n, rho, sine)
+        h = fa.amg_setup(s, precision=fa.AMG_PREC_FP32)
+        for it in range(reps):
+            with _range(it == reps - 1):
+                fa.amg_galerkin_timed(h, 0, 1)
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(s)
+    elif mode == "cgop":
+        # CG's operator (double-float on the uniform grid), one timed launch per pass
+        s = fa.fem_assemble(n, rho, sine)
+        x = torch.randn(N, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        for it in range(reps):
+            with _range(it == reps - 1):
+                fa.fem_spmv_timed(s, x, y, 1)
+        fa.fem_system_destroy(s)
     elif mode == "batched":
         import numpy as np
         import fem_workloads as W
