@@ -456,6 +456,52 @@ fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double*
                      int32_t nrhs, const double* rho_k_host, const pcg_opts* opts,
                      void* stream, pcg_result* res);
 
+/* ------------------------------------------------------------------ BDDC (Sec. 3.2)
+ *
+ * CG on the interface Schur complement S_C u_C = g preconditioned by the two-level BDDC
+ * preconditioner P^-1 = R_D^T (T_sub + T_0) R_D of Sec. 3.2, on the uniform Kuhn mesh split
+ * into `slabs` slabs of whole cube layers along z (slab s: layers [floor(s n / slabs),
+ * floor((s+1) n / slabs))).  Interface: the slabs - 1 vertex planes between slabs; primal
+ * constraints: the average over each plane; scaling D = 1/2 (every interface unknown lies in
+ * two slabs).  Each slab assembles its own Neumann and internal systems from its tets (the
+ * P1 element matrices of the global system) and solves them with FP64 AMG-PCG to inner_tol.
+ * A process may set up a range of the slabs [slab_begin, slab_end): the sums over slabs then
+ * go through `reduce` (every rank passes the same sequence of calls; interface and coarse
+ * vectors are replicated); with all slabs in one process, reduce may be null.  The stopping
+ * test of bddc_solve is ||r_C|| <= tol ||g|| on the interface system; res->relres is the
+ * global ||f - A u|| / ||f|| in FP64, res->iterations the CG iterations. */
+typedef struct bddc_s* bddc_solver;
+typedef void (*fem_allreduce_fn)(double* buf, int64_t count, int32_t on_device, void* ctx);
+typedef struct {
+  int32_t slabs;        /* 2 <= slabs <= n/2                                         */
+  int32_t slab_begin;   /* slabs owned by this process: [slab_begin, slab_end)        */
+  int32_t slab_end;     /* 0: up to slabs                                             */
+  double inner_tol;     /* relative residual of the subdomain AMG-PCG solves, < 1e-6 */
+} bddc_opts;
+
+/* The slab layers (host only, no GPU needed): layer_begin[0..slabs] (nullable) and the
+ * interface unknowns (slabs - 1) (n - 1)^2.  FEM_EINVAL for n < 4 or slabs out of range. */
+fem_status fem_bddc_partition(int32_t n, int32_t slabs, int32_t* layer_begin,
+                              int64_t* interface_unknowns);
+
+/* Set up the owned slabs' systems, hierarchies, constraint solves and the coarse matrix of
+ * a Kuhn-mesh system (uniform grid).  Errors: FEM_EINVAL (null argument, a general or
+ * jittered mesh, slabs out of range, inner_tol outside (0, 1e-6)), FEM_ENOCONV (a
+ * constraint solve did not converge), FEM_ENOMEM. */
+fem_status bddc_setup(fem_system sys, const bddc_opts* opts, fem_allreduce_fn reduce, void* ctx,
+                      void* stream, bddc_solver* out);
+
+/* Solve A u = f (f_dev: device [N], null for the assembled load vector) into u_dev (device
+ * [N]; on every rank the whole solution after the final all-reduce).  Statuses as
+ * pcg_solve (FEM_ENOCONV after opts->max_iter interface iterations). */
+fem_status bddc_solve(bddc_solver b, const double* f_dev, double* u_dev, const pcg_opts* opts,
+                      fem_allreduce_fn reduce, void* ctx, void* stream, pcg_result* res);
+
+/* Wall time of bddc_setup in ms. */
+double bddc_get_setup_ms(bddc_solver b);
+
+void bddc_destroy(bddc_solver b);
+
 /* Discrete H^-1 error of a solution (Tables 3, 6 and 8 report ||ubar - u_h||^2 in H^-1
  * without stating its discrete form): with w = scale * target,
  *   hm1sq = r^T K^-1 r,   r_i = (w - u_h, phi_i)_{L2} = scale * f_i(target) - (M u)_i,

@@ -25,7 +25,8 @@ from ._binding import (  # noqa: F401
     AMG_SMOOTHER_CHEBYSHEV, AMG_SMOOTHER_L1_JACOBI, AMG_SMOOTHER_SGS, FEM_FMT_AUTO, FEM_FMT_CSR,
     FEM_FMT_STENCIL, FemError, PCG_STOP_PRECONDITIONED, PCG_STOP_RESIDUAL, amg_default_opts,
     amg_hier_destroy, amg_hier_export, amg_hier_get_info, amg_setup, amg_vcycle,
-    amg_galerkin_timed, amg_vcycle_graph, fem_assemble,
+    amg_galerkin_timed, amg_vcycle_graph, bddc_destroy, bddc_get_setup_ms, bddc_setup,
+    bddc_solve, fem_assemble, fem_bddc_partition, make_allreduce,
     fem_assemble_mesh, fem_assemble_on_mesh, fem_error_indicator, fem_mark_bulk,
     fem_mesh_create, fem_mesh_destroy, fem_mesh_download, fem_mesh_get_info, fem_mesh_refine,
     fem_assemble_rhs, fem_assemble_rhs_noalloc, fem_autotune_clear, fem_autotune_pin,

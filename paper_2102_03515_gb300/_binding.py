@@ -95,6 +95,15 @@ class MeshDesc(C.Structure):
                 ("tet", P(C.c_int32)), ("dirichlet", P(C.c_uint8))]
 
 
+class BddcOpts(C.Structure):
+    _fields_ = [("slabs", C.c_int32), ("slab_begin", C.c_int32), ("slab_end", C.c_int32),
+                ("inner_tol", C.c_double)]
+
+
+# void (*)(double* buf, int64_t count, int32_t on_device, void* ctx)
+ALLREDUCE_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_int64, C.c_int32, C.c_void_p)
+
+
 class ErrorsResult(C.Structure):
     _fields_ = [("l2sq", C.c_double), ("h1sq", C.c_double)]
 
@@ -140,6 +149,11 @@ SIGNATURES = {
     "amg_vcycle": (C.c_int, [VP, VP, VP, VP]),
     "amg_vcycle_graph": (C.c_int, [VP, VP, VP, C.c_int32, VP, P(C.c_double)]),
     "fem_spmv_timed": (C.c_int, [VP, VP, VP, C.c_int32, VP, P(C.c_double)]),
+    "fem_bddc_partition": (C.c_int, [C.c_int32, C.c_int32, P(C.c_int32), P(C.c_int64)]),
+    "bddc_setup": (C.c_int, [VP, P(BddcOpts), ALLREDUCE_FN, VP, VP, P(VP)]),
+    "bddc_solve": (C.c_int, [VP, VP, VP, P(PcgOpts), ALLREDUCE_FN, VP, VP, P(PcgResult)]),
+    "bddc_get_setup_ms": (C.c_double, [VP]),
+    "bddc_destroy": (None, [VP]),
     "amg_galerkin_timed": (C.c_int, [VP, C.c_int32, C.c_int32, VP, P(C.c_double),
                                      P(C.c_int64)]),
     "amg_hier_destroy": (None, [VP]),
@@ -591,3 +605,75 @@ def pcg_batch_footprint(sys, hier, slots: int) -> int:
 
 def pcg_batch_destroy(b):
     lib().pcg_batch_destroy(b)
+
+
+# ------------------------------------------------------------------ BDDC (Sec. 3.2)
+
+def fem_bddc_partition(n: int, slabs: int):
+    """(layer_begin[0..slabs], interface unknowns) of the slab split; host only."""
+    lb = (C.c_int32 * (slabs + 1))()
+    ni = C.c_int64(0)
+    _check(lib().fem_bddc_partition(int(n), int(slabs), lb, C.byref(ni)), "fem_bddc_partition")
+    return [int(v) for v in lb], int(ni.value)
+
+
+class _DevView:
+    """A device buffer given by pointer and length, seen by torch without a copy."""
+
+    def __init__(self, ptr: int, count: int):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def make_allreduce(group=None):
+    """The sum over the ranks of a torch.distributed group, as the library's all-reduce
+    callback: device buffers are summed in place through the group's backend (NCCL on
+    GPUs), host buffers through a CPU tensor.  Keep the returned object alive while the
+    library may call it."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    def fn(buf, count, on_device, ctx):
+        if count <= 0:
+            return
+        addr = C.cast(buf, C.c_void_p).value
+        if on_device:
+            t = torch.as_tensor(_DevView(addr, count), device="cuda")
+            dist.all_reduce(t, group=group)
+        else:
+            a = np.ctypeslib.as_array(buf, shape=(int(count),))
+            t = torch.from_numpy(a.copy())
+            dist.all_reduce(t, group=group)
+            a[:] = t.numpy()
+
+    return ALLREDUCE_FN(fn)
+
+
+def bddc_setup(sys, slabs: int, slab_begin: int = 0, slab_end: int = 0, inner_tol: float = 1e-13,
+               allreduce=None, stream=None):
+    o = BddcOpts(int(slabs), int(slab_begin), int(slab_end), float(inner_tol))
+    h = VP()
+    cb = allreduce if allreduce is not None else ALLREDUCE_FN()
+    _check(lib().bddc_setup(sys, C.byref(o), cb, None, _stream(stream), C.byref(h)), "bddc_setup")
+    return h
+
+
+def bddc_solve(b, f, u, allreduce=None, stream=None, **kw):
+    """Solve with the BDDC-preconditioned interface CG; returns the result dict."""
+    o = pcg_default_opts(**kw)
+    r = PcgResult()
+    cb = allreduce if allreduce is not None else ALLREDUCE_FN()
+    st = lib().bddc_solve(b, _ptr(f), _ptr(u), C.byref(o), cb, None, _stream(stream), C.byref(r))
+    out = r.as_dict()
+    if st not in (FEM_OK, FEM_ENOCONV):
+        raise FemError(st, fem_last_error())
+    return out
+
+
+def bddc_get_setup_ms(b) -> float:
+    return float(lib().bddc_get_setup_ms(b))
+
+
+def bddc_destroy(b):
+    lib().bddc_destroy(b)

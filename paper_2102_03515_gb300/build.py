@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "libfemamg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["assemble.cu", "ops.cu", "amg_setup.cu", "solve.cu", "batched.cu", "autotune.cu", "adapt.cu",
-           "capi.cu"]
+           "bddc.cu", "capi.cu"]
 # the refinement's decisions (edge lengths, midpoints) are kept free of FMA contraction
 # (each product and sum rounded on its own, the same on every machine); element arithmetic
 # may contract

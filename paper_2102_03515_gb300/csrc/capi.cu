@@ -555,6 +555,73 @@ fem_status amg_vcycle(amg_hier h, const double* r_dev, double* z_dev, void* stre
   });
 }
 
+struct bddc_s {
+  fem::Bddc* B = nullptr;
+  fem_system_s* sys = nullptr;
+  ~bddc_s() { fem::bddc_free(B); }
+};
+
+fem_status fem_bddc_partition(int32_t n, int32_t slabs, int32_t* layer_begin,
+                              int64_t* interface_unknowns) {
+  return guarded([&]() -> fem_status {
+    FEM_REQUIRE(n >= 4 && slabs >= 2 && slabs <= n / 2, FEM_EINVAL,
+                "fem_bddc_partition: n >= 4 and 2 <= slabs <= n/2");
+    if (layer_begin)
+      for (int s = 0; s <= slabs; s++) layer_begin[s] = slab_layer(n, slabs, s);
+    if (interface_unknowns) *interface_unknowns = (int64_t)(slabs - 1) * (n - 1) * (n - 1);
+    return FEM_OK;
+  });
+}
+
+fem_status bddc_setup(fem_system sys, const bddc_opts* opts, fem_allreduce_fn reduce, void* ctx,
+                      void* stream, bddc_solver* out) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(sys && opts && out, FEM_EINVAL, "bddc_setup: null argument");
+    *out = nullptr;
+    const int p = opts->slabs;
+    const int s0 = opts->slab_begin, s1 = opts->slab_end > 0 ? opts->slab_end : p;
+    FEM_REQUIRE(opts->inner_tol > 0.0 && opts->inner_tol < 1e-6, FEM_EINVAL,
+                "bddc_setup: inner_tol in (0, 1e-6)");
+    amg_opts ao;
+    amg_default_opts(&ao);
+    auto* b = new bddc_s();
+    try {
+      b->B = bddc_create(sys->S, p, s0, s1, ao, opts->inner_tol, reduce, ctx, as_stream(stream));
+    } catch (...) {
+      delete b;
+      throw;
+    }
+    b->sys = sys;
+    *out = b;
+    return FEM_OK;
+  });
+}
+
+fem_status bddc_solve(bddc_solver b, const double* f_dev, double* u_dev, const pcg_opts* opts,
+                      fem_allreduce_fn reduce, void* ctx, void* stream, pcg_result* res) {
+  return guarded([&]() -> fem_status {
+    StreamScope scope(as_stream(stream));
+    FEM_REQUIRE(b && u_dev && res, FEM_EINVAL, "bddc_solve: null argument");
+    pcg_opts o;
+    pcg_default_opts(&o);
+    if (opts) o = *opts;
+    FEM_REQUIRE(o.tol > 0.0 && o.max_iter >= 0, FEM_EINVAL, "bddc_solve: tol > 0, max_iter >= 0");
+    *res = pcg_result{};
+    bddc_run(*b->B, f_dev, u_dev, o, reduce, ctx, as_stream(stream), *res);
+    res->solve_ms += 0.0;
+    return (fem_status)res->status;
+  });
+}
+
+double bddc_get_setup_ms(bddc_solver b) { return b ? bddc_setup_ms(*b->B) : 0.0; }
+
+void bddc_destroy(bddc_solver b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  delete b;
+}
+
 fem_status amg_galerkin_timed(amg_hier h, int32_t level, int32_t reps, void* stream,
                               double* ms_out, int64_t* ap_entries_out) {
   return guarded([&]() -> fem_status {

@@ -251,6 +251,19 @@ void rowptr_from_counts(const int64_t* cnt, int64_t n, Csr4& C, cudaStream_t st)
 // measured FP64 FMA throughput (TFLOP/s) over reps timed launches of a probe kernel (ops.cu)
 double fp64_fma_rate(int reps, cudaStream_t st);
 
+// ------------------------------------------------------------------ BDDC (bddc.cu)
+// sums over the slabs of other ranks: buf (count doubles, device memory when on_device) is
+// replaced by its sum over all ranks
+typedef void (*bddc_reduce_t)(double* buf, int64_t count, int on_device, void* ctx);
+struct Bddc;
+int slab_layer(int n, int p, int s);
+Bddc* bddc_create(System& S, int p, int s0, int s1, const amg_opts& ao, double inner_tol,
+                  bddc_reduce_t reduce, void* ctx, cudaStream_t st);
+void bddc_free(Bddc* B);
+double bddc_setup_ms(const Bddc& B);
+void bddc_run(Bddc& B, const double* f, double* u, const pcg_opts& o, bddc_reduce_t reduce,
+              void* ctx, cudaStream_t st, pcg_result& res);
+
 // ------------------------------------------------------------------ utilities
 void finalize_sums(const double* partials, int nblocks, int nv, double* out, cudaStream_t st,
                    const int* done = nullptr);

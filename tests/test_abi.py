@@ -11,7 +11,7 @@ def _declared_functions():
     text = open(os.path.join(ROOT, "include", "femamg.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)
-    keep = {n for n in names if n.startswith(("fem_", "amg_", "pcg_"))}
+    keep = {n for n in names if n.startswith(("fem_", "amg_", "pcg_", "bddc_"))}
     return sorted(keep)
 
 

@@ -25,6 +25,7 @@ PAIRS = {
     "fem_errors_result": "ErrorsResult",
     "fem_mesh_info": "MeshInfo",
     "fem_refine_stats": "RefineStats",
+    "bddc_opts": "BddcOpts",
 }
 
 
