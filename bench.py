@@ -437,20 +437,26 @@ TABLE4_N = (8, 16, 32, 64, 128, 256)
 
 def table4_sample(fa, torch, dev):
     """Table 4's whole grid: h = 1/8 ... 1/256 by rho = 1 ... 1e-12, for the paper's AMG
-    (red-black coarsening, averaging interpolation, symmetric Gauss-Seidel) and smoothed
-    aggregation with Chebyshev, each with FP64 and with FP32 V-cycles in FP64 CG (flexible
-    for FP32), stopped like the paper (preconditioned relative residual 1e-8).  Each entry:
+    (red-black coarsening, averaging interpolation, symmetric Gauss-Seidel; the split visiting
+    the unknowns by hashed priority, and in index order with FP64 V-cycles) and smoothed
+    aggregation with Chebyshev, with FP64 and with FP32 V-cycles in FP64 CG (flexible for
+    FP32), stopped like the paper (preconditioned relative residual 1e-8).  Each entry:
     iterations and assemble + set-up + solve time (the second of two runs: the first also
     tunes launch shapes)."""
     import fem_workloads as W
     variants = {"red_black_sgs": dict(coarsening=fa.AMG_COARSEN_RED_BLACK,
                                       smoother=fa.AMG_SMOOTHER_SGS),
+                "red_black_natural_sgs": dict(coarsening=fa.AMG_COARSEN_RED_BLACK,
+                                              smoother=fa.AMG_SMOOTHER_SGS,
+                                              order=fa.AMG_ORDER_NATURAL),
                 "sa_chebyshev": dict(coarsening=fa.AMG_COARSEN_SA,
                                      smoother=fa.AMG_SMOOTHER_CHEBYSHEV)}
     precs = {"fp64": fa.AMG_PREC_FP64, "fp32": fa.AMG_PREC_FP32}
     grid = {}
     for name, opts in variants.items():
         for pname, prec in precs.items():
+            if name == "red_black_natural_sgs" and pname == "fp32":
+                continue
             key = name + "_" + pname
             grid[key] = {}
             for rho in PAPER_TABLE4:
@@ -513,6 +519,44 @@ def config2_sample(fa, torch, dev, n: int = 128):
                              "solve_dof_iters_per_s": N * res["iterations"] / (res["solve_ms"] / 1e3)})
     return {"workload": "128^3 Kuhn mesh, 2,048,383 dofs, FP64 AMG-PCG (SA, Chebyshev 2) to 1e-8",
             "rows": rows}
+
+
+# Table 5 of the paper (Sec. 4.1): BDDC-PCG iterations (time) at h = 1/128 on RADON-1 with p
+# cores = subdomains (another partition: graph-partitioned subdomains; context)
+PAPER_TABLE5 = {1.0: [34, 34, 35, 36], 1e-4: [27, 27, 28, 30], 1e-12: [20, 20, 21, 21]}
+PAPER_TABLE5_P = [32, 64, 128, 256]
+
+
+def bddc_sample(fa, torch, dev, n: int = 128, slabs=(4, 8, 16)):
+    """BDDC-preconditioned interface CG (Sec. 3.2) on the 128^3 Kuhn mesh split into slabs of
+    cube layers, for rho = 1, 1e-4, 1e-12, stopped at 1e-8 on the interface residual
+    (subdomain AMG-PCG solves to 1e-12): iterations, set-up and solve time, and the global
+    relative residual, next to the paper's Table 5 (graph-partitioned subdomains, one core
+    each: context)."""
+    import fem_workloads as W
+    N = (n - 1) ** 3
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    rows = []
+    for rho in PAPER_TABLE5:
+        sys_ = fa.fem_assemble(n, rho, W.sine_target())
+        for p in slabs:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b = fa.bddc_setup(sys_, p, inner_tol=1e-12)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            res = fa.bddc_solve(b, None, u, tol=1e-8, max_iter=200)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            fa.bddc_destroy(b)
+            rows.append({"rho": rho, "slabs": p, "iterations": res["iterations"],
+                         "relres": res["relres"], "setup_s": t1 - t0, "solve_s": t2 - t1})
+        fa.fem_system_destroy(sys_)
+    return {"workload": "128^3 Kuhn mesh (2,048,383 dofs), slabs of cube layers along z, plane-"
+                        "average primal constraints, FP64 subdomain AMG-PCG to 1e-12, interface "
+                        "CG to 1e-8", "rows": rows,
+            "paper_table5_iterations": {"%g" % k: v for k, v in PAPER_TABLE5.items()},
+            "paper_table5_p": PAPER_TABLE5_P}
 
 
 def general_mesh_sample(fa, torch, dev, n: int = 32, refine: int = 2):
@@ -859,13 +903,14 @@ def run_ours(args, rank: int, world: int):
                    "kernel": "one FP32 V-cycle (all levels, replayed from a CUDA graph)",
                    "ms": vms, "algorithmic_bytes": vbytes, "peak_source": "measured copy rate"}
 
-    batched = serving = tables = table3 = table4 = general = adaptive = config2 = None
+    batched = serving = tables = table3 = table4 = general = adaptive = config2 = bddc = None
     if not args.no_extras:
         tables = paper_tables_sample(fa, torch, dev, n)
         table3 = table3_sample(fa, torch, dev, n)
         table4 = table4_sample(fa, torch, dev)
         config2 = config2_sample(fa, torch, dev)
         general = general_mesh_sample(fa, torch, dev)
+        bddc = bddc_sample(fa, torch, dev)
         adaptive = adaptive_sample(fa, torch, dev)
         batched = batched_sample(fa, torch, dev)
         serving = serving_sample(args.serve_requests)
@@ -934,6 +979,8 @@ def run_ours(args, rank: int, world: int):
         line["adaptive"] = adaptive
     if config2 is not None:
         line["config2"] = config2
+    if bddc is not None:
+        line["bddc"] = bddc
     if batched is not None:
         line["batched"] = batched
     if serving is not None:

@@ -325,10 +325,15 @@ typedef enum {
   AMG_SMOOTHER_SGS = 2
 } amg_smoother;
 /* Coarsening: smoothed aggregation (default), or the paper's red-black colouring with
- * averaging interpolation (Sec. 3.1 after KF1998: visit the unknowns by decreasing hash
- * priority; an unmarked one becomes coarse and its unmarked matrix-graph neighbours fine;
- * a fine unknown is interpolated by the average of its coarse neighbours). */
+ * averaging interpolation (Sec. 3.1 after KF1998: visit the unknowns in a fixed order; an
+ * unmarked one becomes coarse and its unmarked matrix-graph neighbours fine; a fine unknown
+ * is interpolated by the average of its coarse neighbours).  The visiting order of the
+ * red-black split: decreasing hash priority (default), or the unknowns' index order
+ * (AMG_ORDER_NATURAL: on the Kuhn grid the lexicographic order coarsens to every other grid
+ * point, and the iteration counts follow the paper's Table 4; the parallel rounds that find
+ * the greedy set then take about 3 (n - 1) rounds). */
 typedef enum { AMG_COARSEN_SA = 0, AMG_COARSEN_RED_BLACK = 1 } amg_coarsening;
+typedef enum { AMG_ORDER_HASH = 0, AMG_ORDER_NATURAL = 1 } amg_order;
 typedef enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_BF16 = 2 } amg_precision;
 
 /* Smoothed-aggregation set-up on the device; Sec. 3.1 coarsens by red-black colouring
@@ -357,6 +362,7 @@ typedef struct {
                             entries becomes the coarsest level (dense inverse if it
                             has <= coarse_max unknowns, else the smoother alone);
                             1..8192, default (and 0) 8192, the products' limit      */
+  int32_t order;         /* amg_order of the red-black split, default hash        */
 } amg_opts;
 
 typedef struct amg_hier_s* amg_hier;

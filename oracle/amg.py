@@ -42,7 +42,7 @@ import scipy.sparse as sp
 UNDECIDED, IN, OUT = 1, 2, 0
 DEFAULTS = dict(theta=0.05, smoother="chebyshev", degree=2, cheb_ratio=6.0,
                 coarse_max=256, max_levels=16, seed=0, min_ratio=0.9, coarsening="sa",
-                max_row=8192)
+                max_row=8192, order="hash")
 
 
 # ------------------------------------------------------------- utilities
@@ -283,14 +283,16 @@ def neighbours(A, i):
     return cols[(cols != i) & (vals != 0.0)]
 
 
-def red_black(A, seed: int) -> np.ndarray:
+def red_black(A, seed: int, order: str = "hash") -> np.ndarray:
     """Red-black colouring (Sec. 3.1, after KF1998 Algorithm 2): visit the unknowns by
-    decreasing priority; an unmarked one is marked black (coarse) and its unmarked
-    neighbours red (fine).  Returns the boolean coarse mask."""
+    decreasing priority (order "hash"), or by increasing index (order "natural"); an
+    unmarked one is marked black (coarse) and its unmarked neighbours red (fine).  Returns
+    the boolean coarse mask."""
     A = sp.csr_matrix(A)
     n = A.shape[0]
     mark = np.zeros(n, dtype=np.int8)  # 0 unmarked, 1 black, 2 red
-    for i in np.argsort(priority(n, seed))[::-1]:  # priorities are unique
+    visit = np.arange(n) if order == "natural" else np.argsort(priority(n, seed))[::-1]
+    for i in visit:  # priorities are unique
         if mark[i]:
             continue
         mark[i] = 1
@@ -394,7 +396,7 @@ def build_hierarchy(A, opts: dict | None = None, K=None, M=None):
         kf = o["coarsening"] == "kf"
         if not last:
             if kf:
-                coarse = red_black(Al, o["seed"] + lev)
+                coarse = red_black(Al, o["seed"] + lev, o["order"])
                 nagg = int(coarse.sum())
             else:
                 agg, nagg, smask = aggregate(Al, o["theta"], o["seed"] + lev)

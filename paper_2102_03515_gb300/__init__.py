@@ -21,7 +21,8 @@ A solve at h = 1/n with rho = h^2 and the smooth target of Sec. 4.1::
 from __future__ import annotations
 
 from ._binding import (  # noqa: F401
-    AMG_COARSEN_RED_BLACK, AMG_COARSEN_SA, AMG_PREC_BF16, AMG_PREC_FP32, AMG_PREC_FP64,
+    AMG_COARSEN_RED_BLACK, AMG_COARSEN_SA, AMG_ORDER_HASH, AMG_ORDER_NATURAL, AMG_PREC_BF16,
+    AMG_PREC_FP32, AMG_PREC_FP64,
     AMG_SMOOTHER_CHEBYSHEV, AMG_SMOOTHER_L1_JACOBI, AMG_SMOOTHER_SGS, FEM_FMT_AUTO, FEM_FMT_CSR,
     FEM_FMT_STENCIL, FemError, PCG_STOP_PRECONDITIONED, PCG_STOP_RESIDUAL, amg_default_opts,
     amg_hier_destroy, amg_hier_export, amg_hier_get_info, amg_setup, amg_vcycle,

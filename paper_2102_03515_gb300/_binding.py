@@ -25,6 +25,7 @@ FEM_TARGET = {"sine": 0, "box": 1, "bumps": 2, "sine_plus_one": 3, "quadvals": 4
 FEM_FMT_AUTO, FEM_FMT_STENCIL, FEM_FMT_CSR = 0, 1, 2
 AMG_SMOOTHER_CHEBYSHEV, AMG_SMOOTHER_L1_JACOBI, AMG_SMOOTHER_SGS = 0, 1, 2
 AMG_COARSEN_SA, AMG_COARSEN_RED_BLACK = 0, 1
+AMG_ORDER_HASH, AMG_ORDER_NATURAL = 0, 1
 AMG_PREC_FP64, AMG_PREC_FP32, AMG_PREC_BF16 = 0, 1, 2
 PCG_STOP_RESIDUAL, PCG_STOP_PRECONDITIONED = 0, 1
 
@@ -58,7 +59,8 @@ class AmgOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("smoother", C.c_int32), ("degree", C.c_int32),
                 ("cheb_ratio", C.c_double), ("coarse_max", C.c_int32),
                 ("max_levels", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint32),
-                ("rho_setup", C.c_double), ("coarsening", C.c_int32), ("max_row", C.c_int32)]
+                ("rho_setup", C.c_double), ("coarsening", C.c_int32), ("max_row", C.c_int32),
+                ("order", C.c_int32)]
 
 
 class HierInfo(C.Structure):

@@ -1674,8 +1674,14 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
 // coarse when it has the largest key among itself and its neighbours (IN > UNDECIDED >
 // OUT, then priority) and fine when a neighbour is already coarse -- the same set as the
 // sequential visit.  Neighbours: columns j != i of stored nonzero a_ij.
+// visiting priority of the red-black split: hashed, or decreasing with the index (the
+// index order)
+__device__ __forceinline__ uint64_t rb_prio(int64_t i, uint32_t s, int natural) {
+  return natural ? (((uint64_t)1 << 62) - 1 - (uint64_t)i) : prio_of(i, s);
+}
+
 __global__ void k_rb_round(int64_t N, const int32_t* rowptr, const int32_t* col, const double* val,
-                           uint32_t s, const uint8_t* state_in, uint8_t* state_out,
+                           uint32_t s, int natural, const uint8_t* state_in, uint8_t* state_out,
                            unsigned long long* undecided) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
@@ -1684,12 +1690,12 @@ __global__ void k_rb_round(int64_t N, const int32_t* rowptr, const int32_t* col,
     state_out[r] = st;
     return;
   }
-  const uint64_t key = ((uint64_t)ST_UND << 62) | prio_of(r, s);
+  const uint64_t key = ((uint64_t)ST_UND << 62) | rb_prio(r, s, natural);
   uint64_t best = key;
   for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
     const int j = col[e];
     if (j < 0 || j == r || val[e] == 0.0) continue;
-    const uint64_t kj = ((uint64_t)state_in[j] << 62) | prio_of(j, s);
+    const uint64_t kj = ((uint64_t)state_in[j] << 62) | rb_prio(j, s, natural);
     best = kj > best ? kj : best;
   }
   uint8_t ns = ST_UND;
@@ -2321,8 +2327,8 @@ void psmooth_stencil(int64_t N, const StencilRow& S, const int32_t* agg, double 
 
 // Red-black split of a level: state (IN = coarse), coarse ids cid (exclusive scan of the
 // coarse flags); returns the number of coarse nodes.
-int64_t red_black_split(const Csr4& A, uint32_t s, DevBuf<uint8_t>& state, DevBuf<int64_t>& cid,
-                        cudaStream_t st) {
+int64_t red_black_split(const Csr4& A, uint32_t s, int natural, DevBuf<uint8_t>& state,
+                        DevBuf<int64_t>& cid, cudaStream_t st) {
   const int64_t N = A.nrows;
   const unsigned g = grid_for(N, 256);
   DevBuf<uint8_t> s0(N, st), s1(N, st);
@@ -2331,11 +2337,14 @@ int64_t red_black_split(const Csr4& A, uint32_t s, DevBuf<uint8_t>& state, DevBu
   uint8_t* cur = s0;
   uint8_t* nxt = s1;
   bool finished = false;
+  // several rounds per check (extra rounds are no-ops): the index order decides a front of
+  // the grid per round, so it takes more rounds per check
+  const int per = natural ? 16 : 4;
   for (int round = 0; round < 100000; round++) {
     FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
-    for (int t = 0; t < 4; t++) {  // several rounds per check (extra rounds are no-ops)
-      if (t == 3) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
-      k_rb_round<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, s, cur, nxt, und);
+    for (int t = 0; t < per; t++) {
+      if (t == per - 1) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
+      k_rb_round<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, s, natural, cur, nxt, und);
       FEM_CHECK_LAUNCH();
       std::swap(cur, nxt);
     }
@@ -2505,7 +2514,8 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     DevBuf<int64_t> rbcid;
     if (!last) {
       if (rb)
-        ag.nagg = red_black_split(*Acur, seed_s, rbstate, rbcid, st);
+        ag.nagg = red_black_split(*Acur, seed_s, o.order == AMG_ORDER_NATURAL ? 1 : 0, rbstate,
+                                  rbcid, st);
       else
         ag = st0 ? aggregate_stencil(N, SR, seed_s, st) : aggregate(*Acur, d, o.theta, seed_s, st);
       tr.mark("level: aggregation");

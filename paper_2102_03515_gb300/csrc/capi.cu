@@ -432,6 +432,7 @@ void amg_default_opts(amg_opts* o) {
   o->rho_setup = 0.0;
   o->coarsening = AMG_COARSEN_SA;
   o->max_row = 8192;
+  o->order = AMG_ORDER_HASH;
 }
 
 fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hier* out) {
@@ -444,6 +445,8 @@ fem_status amg_setup(fem_system sys, const amg_opts* opts, void* stream, amg_hie
     if (opts) o = *opts;
     FEM_REQUIRE(o.theta >= 0.0 && o.theta < 1.0, FEM_EINVAL, "amg_setup: theta in [0, 1)");
     FEM_REQUIRE(o.max_row >= 0 && o.max_row <= 8192, FEM_EINVAL, "amg_setup: max_row in [0, 8192]");
+    FEM_REQUIRE(o.order == AMG_ORDER_HASH || o.order == AMG_ORDER_NATURAL, FEM_EINVAL,
+                "amg_setup: order is AMG_ORDER_HASH or AMG_ORDER_NATURAL");
     FEM_REQUIRE(o.degree >= 1 && o.degree <= 15, FEM_EINVAL, "amg_setup: degree in [1, 15]");
     FEM_REQUIRE(o.cheb_ratio > 1.0, FEM_EINVAL, "amg_setup: cheb_ratio > 1");
     FEM_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= 4096, FEM_EINVAL,

@@ -135,3 +135,33 @@ def test_batched_rejects_gauss_seidel(fa):
     finally:
         fa.amg_hier_destroy(h)
         fa.fem_system_destroy(sys_)
+
+
+@pytest.mark.parametrize("n,rho", [(16, 1.0), (17, 1.0 / 289), (12, 1e-4)])
+def test_natural_order_red_black_matches_oracle(fa, n, rho):
+    # visiting the unknowns in index order (the order the paper's Table 4 counts follow):
+    # C/F split and colours bit-exact, Galerkin operators, and the PCG iteration count
+    s = core.assemble(n, W.sine_target())
+    A = s.A(rho).tocsr()
+    o = dict(KF, order="natural")
+    Lo = amg.build_hierarchy(A, o)
+    _, it_o, _, _ = amg.pcg(A, s.f, lambda r: amg.vcycle(Lo, r, o), tol=1e-10)
+    sys_ = fa.fem_assemble(n, rho, W.sine_target())
+    h = fa.amg_setup(sys_, order=fa.AMG_ORDER_NATURAL, **_gpu_opts(fa))
+    try:
+        info = fa.amg_hier_get_info(h)
+        assert info["rows"] == [L.A.shape[0] for L in Lo]
+        for lev, L in enumerate(Lo):
+            N = L.A.shape[0]
+            Ag = G.export_level(fa, h, lev, 0, N, N)
+            assert G.sparse_rel(Ag, L.A) <= 1e-13, lev
+            if L.coarsest:
+                continue
+            cid = _export_int(fa, h, lev, 3, N)
+            assert np.array_equal(cid >= 0, L.coarse), lev
+        u = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        res = fa.pcg_solve(sys_, h, None, u, tol=1e-10)[0]
+        assert res["status"] == "FEM_OK" and res["iterations"] == it_o
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
