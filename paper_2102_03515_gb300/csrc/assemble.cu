@@ -352,10 +352,10 @@ __global__ void k_target_tables(TargetDev T, int n, int nterms, double* tab, dou
 // Per-cube load contributions: cube c gets cf[c*8 + local vertex] with local vertex
 // dx + 2 dy + 4 dz, summing w_q |tau| ubar(x_q) lambda_a(x_q) over its 6 tets and the
 // 4 points of each (Hammer-Stroud, barycentric (A,B,B,B) permutations, weight 1/4).
-// Loops over tets and points are unrolled so that every local index is static.
-template <bool UNIFORM>
-__global__ void k_cube_load(int n, const double* xyz, TargetDev T, const double* tab,
-                            const double* alpha, int nterms, double* cf) {
+// Loops over tets and points are unrolled so that every local index is static.  Used for
+// jittered meshes and for targets given at the quadrature points (xyz null: the uniform
+// grid).
+__global__ void k_cube_load(int n, const double* xyz, TargetDev T, double* cf) {
   constexpr int PP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   int64_t nc = (int64_t)n * n * n;
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -366,115 +366,103 @@ __global__ void k_cube_load(int n, const double* xyz, TargetDev T, const double*
 #pragma unroll
   for (int a = 0; a < 8; a++) acc[a] = 0.0;
   double Xc[8][3];
-  if (!UNIFORM) {
-    Coords C{xyz, n, 1.0 / n};
+  Coords C{xyz, n, 1.0 / n};
 #pragma unroll
-    for (int a = 0; a < 8; a++) C.get(ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1), Xc[a]);
-  }
-  const double h = 1.0 / n;
-  const int cc[3] = {ci, cj, ck};
+  for (int a = 0; a < 8; a++) C.get(ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1), Xc[a]);
 #pragma unroll
   for (int p = 0; p < 6; p++) {
     int lv[4];
     lv[0] = 0;
 #pragma unroll
     for (int s = 0; s < 3; s++) lv[s + 1] = lv[s] | (1 << PP[p][s]);
-    double vol = 0.0;
-    if (!UNIFORM) {
-      double X[4][3], g[4][3];
+    double X[4][3], g[4][3];
 #pragma unroll
-      for (int a = 0; a < 4; a++)
+    for (int a = 0; a < 4; a++)
 #pragma unroll
-        for (int d = 0; d < 3; d++) X[a][d] = Xc[lv[a]][d];
-      vol = fabs(tet_grads(X, g)) / 6.0;
-    }
+      for (int d = 0; d < 3; d++) X[a][d] = Xc[lv[a]][d];
+    const double vol = fabs(tet_grads(X, g)) / 6.0;
     double uq[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       double mu[4] = {B, B, B, B};
       mu[q] = A;
-      double u;
-      if (UNIFORM) {
-        // offset index along PP[p][0] (1 - mu0), PP[p][1] (mu2 + mu3), PP[p][2] (mu3)
-        int oax[3];
-        oax[PP[p][0]] = (q == 0) ? 4 : 5;
-        oax[PP[p][1]] = (q >= 2) ? 3 : 2;
-        oax[PP[p][2]] = (q == 3) ? 1 : 0;
-        u = 0.0;
-        for (int t = 0; t < nterms; t++) {
-          double g0 = __ldg(tab + ((t * 3 + 0) * n + cc[0]) * 6 + oax[0]);
-          double g1 = __ldg(tab + ((t * 3 + 1) * n + cc[1]) * 6 + oax[1]);
-          double g2 = __ldg(tab + ((t * 3 + 2) * n + cc[2]) * 6 + oax[2]);
-          u += alpha[t] * (g0 * g1 * g2);
-        }
-      } else {
-        double x[3] = {0, 0, 0};
+      double x[3] = {0, 0, 0};
 #pragma unroll
-        for (int a = 0; a < 4; a++)
+      for (int a = 0; a < 4; a++)
 #pragma unroll
-          for (int d = 0; d < 3; d++) x[d] += mu[a] * Xc[lv[a]][d];
-        u = T.kind == FEM_TARGET_QUADVALS ? T.qv[4 * (6 * c + p) + q]
-                                          : target_eval(T, x[0], x[1], x[2]);
-      }
-      uq[q] = u;
+        for (int d = 0; d < 3; d++) x[d] += mu[a] * Xc[lv[a]][d];
+      uq[q] = T.kind == FEM_TARGET_QUADVALS ? T.qv[4 * (6 * c + p) + q]
+                                            : target_eval(T, x[0], x[1], x[2]);
     }
     // sum_q (|tau|/4) u_q lambda_a(x_q) with lambda_a(x_q) = B + (A - B) [q == a]
     const double S = (uq[0] + uq[1]) + (uq[2] + uq[3]);
-    const double w = UNIFORM ? 1.0 : 0.25 * vol;
+    const double w = 0.25 * vol;
 #pragma unroll
     for (int a = 0; a < 4; a++) acc[lv[a]] += w * (B * S + (A - B) * uq[a]);
   }
-  const double scale = UNIFORM ? 0.25 * (h * h * h / 6.0) : 1.0;
 #pragma unroll
-  for (int a = 0; a < 8; a++) cf[8 * c + a] = scale * acc[a];
+  for (int a = 0; a < 8; a++) cf[8 * c + a] = acc[a];
 }
 
-// Uniform grid: one block per row of cubes (j, k); the products alpha_t g_t1(y) g_t2(z) of
-// the row's quadrature offsets are staged in shared memory, so each point costs one
-// product per separable term of the target.
-__global__ void __launch_bounds__(128) k_cube_load_rows(int n, const double* __restrict__ tab,
-                                                        const double* __restrict__ alpha,
-                                                        int nterms, double* cf) {
-  constexpr int PP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  extern __shared__ double t12[];  // [nterms][6 (y offset)][6 (z offset)]
-  const int cj = blockIdx.x, ck = blockIdx.y;
-  for (int q = threadIdx.x; q < nterms * 36; q += blockDim.x) {
-    const int t = q / 36, oy = (q / 6) % 6, oz = q % 6;
-    t12[q] = alpha[t] * (tab[((t * 3 + 1) * n + cj) * 6 + oy] * tab[((t * 3 + 2) * n + ck) * 6 + oz]);
+// Uniform grid, separable target: the load of node (I, J, K) collects, over the 6 tets of
+// each of its 8 cubes that contain it and the 4 points of each, 96 terms
+//   (|tau| / 4) lambda_a(x_q) ubar(x_q),   lambda_a(x_q) = B + (A - B) [q == a],
+// and every point sits, along axis d, at table row i_d - dd_d (dd the node's corner of the
+// cube) and one of the 6 offsets: its class along d is e_d = 6 dd_d + o_d, 12 classes per
+// axis.  With ubar = sum_t alpha_t g_t0 g_t1 g_t2 the load is
+//   f = scale sum_t sum_e0 g_t0(I, e0) T_t(e0),  T_t(e0) = alpha_t sum_{terms with e0} coef g_t1 g_t2,
+// and T depends on the row (J, K) only: one block per row of nodes computes it (in the
+// terms' fixed order: deterministic), then each node costs 12 products per target term.
+// Term k = 16 p + 4 a + q: tet p of the cube whose corner dd = lv_p(a) is the node, point q.
+__device__ __forceinline__ void load_term(int k, int e[3], bool& at_a) {
+  const int p = k >> 4, a = (k >> 2) & 3, q = k & 3;
+  // tet p walks from the cube's corner 0 to corner 7 along axes f0, f1, f2: the six
+  // orders (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0)
+  const int f0 = p >> 1, lo = f0 == 0 ? 1 : 0, hi = f0 == 2 ? 1 : 2;
+  const int f1 = (p & 1) ? hi : lo, f2 = (p & 1) ? lo : hi;
+  const int dd = (a >= 1 ? 1 << f0 : 0) | (a >= 2 ? 1 << f1 : 0) | (a >= 3 ? 1 << f2 : 0);
+  const int o0 = q == 0 ? 4 : 5, o1 = q >= 2 ? 3 : 2, o2 = q == 3 ? 1 : 0;
+#pragma unroll
+  for (int d = 0; d < 3; d++) e[d] = 6 * ((dd >> d) & 1) + (d == f0 ? o0 : d == f1 ? o1 : o2);
+  at_a = (q == a);
+}
+
+// table value of term t along axis d for node coordinate i (1..n-1) and class e
+__device__ __forceinline__ double tab_at(const double* tab, int n, int t, int d, int i, int e) {
+  return __ldg(tab + ((t * 3 + d) * n + (i - e / 6)) * 6 + e % 6);
+}
+
+__global__ void __launch_bounds__(128) k_load_sep(int n, const double* __restrict__ tab,
+                                                  const double* __restrict__ alpha, int nterms,
+                                                  double* __restrict__ f) {
+  extern __shared__ double Tt[];   // [nterms][12]
+  const int m = n - 1;
+  const int J = blockIdx.x + 1, K = blockIdx.y + 1;
+  const double A = (5.0 + 3.0 * sqrt(5.0)) / 20.0, B = (5.0 - sqrt(5.0)) / 20.0;
+  for (int te = threadIdx.x; te < nterms * 12; te += blockDim.x) {
+    const int t = te / 12, e0 = te % 12;
+    double s = 0.0;
+    for (int k = 0; k < 96; k++) {
+      int e[3];
+      bool at_a;
+      load_term(k, e, at_a);
+      if (e[0] != e0) continue;
+      s += (at_a ? A : B) * (tab_at(tab, n, t, 1, J, e[1]) * tab_at(tab, n, t, 2, K, e[2]));
+    }
+    Tt[te] = alpha[t] * s;
   }
   __syncthreads();
-  const double A = (5.0 + 3.0 * sqrt(5.0)) / 20.0, B = (5.0 - sqrt(5.0)) / 20.0;
   const double h = 1.0 / n;
   const double scale = 0.25 * (h * h * h / 6.0);
-  for (int ci = threadIdx.x; ci < n; ci += blockDim.x) {
-    double acc[8];
+  double* frow = f + (int64_t)m * ((J - 1) + (int64_t)m * (K - 1));
+  for (int I = threadIdx.x + 1; I <= m; I += blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < nterms; t++) {
+      const double* x = tab + ((t * 3) * n + (I - 1)) * 6;   // classes 6..11 (cube I-1), 0..5 (cube I)
 #pragma unroll
-    for (int a = 0; a < 8; a++) acc[a] = 0.0;
-#pragma unroll
-    for (int p = 0; p < 6; p++) {
-      int lv[4];
-      lv[0] = 0;
-#pragma unroll
-      for (int s = 0; s < 3; s++) lv[s + 1] = lv[s] | (1 << PP[p][s]);
-      double uq[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        int oax[3];
-        oax[PP[p][0]] = (q == 0) ? 4 : 5;
-        oax[PP[p][1]] = (q >= 2) ? 3 : 2;
-        oax[PP[p][2]] = (q == 3) ? 1 : 0;
-        double u = 0.0;
-        for (int t = 0; t < nterms; t++)
-          u += __ldg(tab + ((t * 3 + 0) * n + ci) * 6 + oax[0]) * t12[t * 36 + oax[1] * 6 + oax[2]];
-        uq[q] = u;
-      }
-      const double S = (uq[0] + uq[1]) + (uq[2] + uq[3]);
-#pragma unroll
-      for (int a = 0; a < 4; a++) acc[lv[a]] += B * S + (A - B) * uq[a];
+      for (int e0 = 0; e0 < 12; e0++) s = fma(__ldg(x + (e0 < 6 ? 6 + e0 : e0 - 6)), Tt[t * 12 + e0], s);
     }
-    const int64_t c = ci + (int64_t)n * (cj + (int64_t)n * ck);
-#pragma unroll
-    for (int a = 0; a < 8; a++) cf[8 * c + a] = scale * acc[a];
+    frow[I - 1] = scale * s;
   }
 }
 
@@ -514,24 +502,21 @@ __global__ void k_diag_inv(int64_t N, const int32_t* rowptr, const int32_t* col,
 void load_vector(System& S, const TargetDev& T, const fem_target& t, double* f, cudaStream_t st) {
   const int n = S.n;
   const int64_t N = S.N;
-  int64_t ncube = (int64_t)n * n * n;
-  DevBuf<double> cf(8 * ncube, st);
-  if (t.kind == FEM_TARGET_QUADVALS) {
-    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, S.uniform ? nullptr : S.xyz.p, T,
-                                                             nullptr, nullptr, 0, cf);
-    FEM_CHECK_LAUNCH();
-  } else if (S.uniform) {
+  if (N == 0) return;
+  if (S.uniform && t.kind != FEM_TARGET_QUADVALS) {
     int nterms = (t.kind == FEM_TARGET_BUMPS) ? t.nb : (t.kind == FEM_TARGET_SINE_PLUS_ONE ? 2 : 1);
     DevBuf<double> tab((size_t)nterms * 3 * n * 6, st), alpha(nterms, st);
     int total = nterms * 3 * n * 6;
     k_target_tables<<<grid_for(total, 256), 256, 0, st>>>(T, n, nterms, tab, alpha);
     FEM_CHECK_LAUNCH();
-    k_cube_load_rows<<<dim3(n, n), 128, (size_t)nterms * 36 * 8, st>>>(n, tab, alpha, nterms, cf);
+    k_load_sep<<<dim3(n - 1, n - 1), 128, (size_t)nterms * 12 * 8, st>>>(n, tab, alpha, nterms, f);
     FEM_CHECK_LAUNCH();
-  } else {
-    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, S.xyz, T, nullptr, nullptr, 0, cf);
-    FEM_CHECK_LAUNCH();
+    return;
   }
+  int64_t ncube = (int64_t)n * n * n;
+  DevBuf<double> cf(8 * ncube, st);
+  k_cube_load<<<grid_for(ncube, 128), 128, 0, st>>>(n, S.uniform ? nullptr : S.xyz.p, T, cf);
+  FEM_CHECK_LAUNCH();
   k_gather_load<<<grid_for(N, 256), 256, 0, st>>>(n, cf, f);
   FEM_CHECK_LAUNCH();
 }
@@ -1761,14 +1746,16 @@ void assemble_rhs_noalloc(System& S, const fem_target& t, double* f, cudaStream_
     const int total = nterms * 3 * n * 6;
     k_target_tables<<<grid_for(total, 256), 256, 0, st>>>(T, n, nterms, tab, alpha);
     FEM_CHECK_LAUNCH();
-    k_cube_load_rows<<<dim3(n, n), 128, (size_t)nterms * 36 * 8, st>>>(n, tab, alpha, nterms, cf);
-    FEM_CHECK_LAUNCH();
+    if (S.N > 0) {
+      k_load_sep<<<dim3(n - 1, n - 1), 128, (size_t)nterms * 12 * 8, st>>>(n, tab, alpha, nterms, f);
+      FEM_CHECK_LAUNCH();
+    }
   } else {
-    k_cube_load<false><<<grid_for(ncube, 128), 128, 0, st>>>(n, S.xyz, T, nullptr, nullptr, 0, cf);
+    k_cube_load<<<grid_for(ncube, 128), 128, 0, st>>>(n, S.xyz, T, cf);
+    FEM_CHECK_LAUNCH();
+    k_gather_load<<<grid_for(S.N, 256), 256, 0, st>>>(n, cf, f);
     FEM_CHECK_LAUNCH();
   }
-  k_gather_load<<<grid_for(S.N, 256), 256, 0, st>>>(n, cf, f);
-  FEM_CHECK_LAUNCH();
   // the host parameter arrays are read by the copies above: finish before returning
   FEM_CUDA(cudaStreamSynchronize(st));
 }
