@@ -943,6 +943,46 @@ __global__ void k_gj_step(int64_t N, int64_t k, const double* __restrict__ D, do
   }
 }
 
+// On the finest level of a uniform Kuhn grid every row of A holds the same values at the
+// same offsets (a subset of them at the boundary), so the strength graph, the Gershgorin
+// bounds and the smoothed prolongator follow from one interior row.  The kernels below
+// walk the stencil's offsets instead of A's columns; they take the same decisions and do
+// the same arithmetic, in the same order, as the CSR kernels above.
+struct StencilRow {
+  int m = 0;
+  uint32_t present = 0;      // bit d: the interior row has an entry at direction d
+  uint32_t strong = 0;       // bit d: that entry is a strong pair (never the diagonal)
+  double a[27];              // value at direction d
+};
+// direction d = (dx + 1) + 3 (dy + 1) + 9 (dz + 1): increasing d is increasing column
+// offset dx + m dy + m^2 dz (m >= 3), i.e. A's column order; d = 13 is the diagonal.
+constexpr int ST_DIAG = 13;
+
+__device__ __forceinline__ bool st_inb(int i, int j, int k, int d, int m) {
+  const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+  return (unsigned)(i + dx) < (unsigned)m && (unsigned)(j + dy) < (unsigned)m &&
+         (unsigned)(k + dz) < (unsigned)m;
+}
+
+__device__ __forceinline__ int64_t st_off(int d, int m) {
+  return (int64_t)(d % 3 - 1) + (int64_t)m * (d / 3 % 3 - 1) + (int64_t)m * m * (d / 9 - 1);
+}
+
+// strong-direction test: compile-time mask when MASK != 0, else the runtime one
+template <uint32_t MASK>
+__device__ __forceinline__ bool st_sel(uint32_t strong, int d) {
+  return MASK ? ((MASK >> d) & 1u) != 0 : ((strong >> d) & 1u) != 0;
+}
+
+__device__ __forceinline__ void st_ijk(int64_t r, int m, int& i, int& j, int& k) {
+  const uint32_t rr = (uint32_t)r, mm = (uint32_t)m;
+  const uint32_t q = rr / mm;
+  i = (int)(rr - q * mm);
+  k = (int)(q / mm);
+  j = (int)(q - (uint32_t)k * mm);
+}
+
+
 // ------------------------------------------------------------------ merge SpGEMM
 
 // C = A B when every row of B holds sorted, distinct columns: CSR4 rows, whose (-1, 0)
@@ -983,14 +1023,16 @@ __device__ __forceinline__ int group_min(int v, unsigned mask) {
 
 template <int G, int K>
 __global__ void __launch_bounds__(MG_BLOCK)
-    k_mg(int64_t nrows, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Acol,
-         const double* __restrict__ Aval, MgRows B, const int32_t* __restrict__ Bcol,
-         const double* __restrict__ Bval, int W, int lmax, int32_t* __restrict__ Ccol,
-         double* __restrict__ Cval, int64_t* __restrict__ Clen, unsigned int* overflow) {
+    k_mg(int64_t nrows, const int64_t* __restrict__ rlist, const int32_t* __restrict__ Arp,
+         const int32_t* __restrict__ Acol, const double* __restrict__ Aval, MgRows B,
+         const int32_t* __restrict__ Bcol, const double* __restrict__ Bval, int W, int lmax,
+         int32_t* __restrict__ Ccol, double* __restrict__ Cval, int64_t* __restrict__ Clen,
+         unsigned int* overflow) {
   extern __shared__ __align__(16) char smem[];
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
-  const int64_t r = (int64_t)blockIdx.x * (MG_BLOCK / G) + grp;
-  if (r >= nrows) return;
+  const int64_t rr = (int64_t)blockIdx.x * (MG_BLOCK / G) + grp;
+  if (rr >= nrows) return;
+  const int64_t r = rlist ? rlist[rr] : rr;   // the rows of C wanted (null: all)
   const unsigned mask = group_mask<G>();
   // per group: W + 1 sums, then the output position of every entry of every list (G K lists
   // of at most lmax entries) and 4 bytes (the odd strides start the groups in different
@@ -1078,6 +1120,298 @@ __global__ void k_mg_compact(int64_t nrows, int W, const int32_t* __restrict__ S
     Ccol[o0 + q] = q < c ? Scol[r * W + q] : -1;
     Cval[o0 + q] = q < c ? Sval[r * W + q] : 0.0;
   }
+}
+
+// A P on the uniform finest level.  A's rows are the stencil (directions in column order,
+// the same values in every row), so only P is read.  A block takes a brick of 8 x 4 x 4
+// rows, four lanes per row, and stages the P rows of the brick and its one-node halo
+// (every P row an A row of the brick names):
+//  1. the staged columns go into a hash set, and each distinct column gets as local id its
+//     rank among them, so local ids follow the column order; each staged row keeps its
+//     entries' local ids and values (in column order) and a 256-bit mask of its ids;
+//  2. a row's columns are the bits of the OR of its neighbours' masks (each lane ORs a
+//     quarter of the directions, shuffles join them), written out in increasing order;
+//  3. the directions are walked in column order, the four lanes splitting the neighbour's
+//     P row, and each product is added at its output position (the row mask's bits below
+//     its id): the merge kernel's products in the merge kernel's order, rounding for
+//     rounding (a P row's ids are distinct, so one direction adds once per position).
+// A row longer than the stride W writes its length only (flag bit 0); a brick beyond the
+// staging limits (256 distinct columns, AB_E staged entries, P rows of more than 8 stored
+// entries) gives up (bit 1: the caller takes the merge kernel).
+constexpr int AB_X = 8, AB_Y = 4, AB_Z = 4, AB_R = AB_X * AB_Y * AB_Z;   // 128 rows
+constexpr int AB_G = 4, AB_T = AB_G * AB_R;                              // 512 threads
+constexpr int AB_HX = AB_X + 2, AB_HY = AB_Y + 2, AB_HZ = AB_Z + 2;
+constexpr int AB_H = AB_HX * AB_HY * AB_HZ;   // 360 staged rows
+constexpr int AB_L = 8;                        // stored entries per staged P row
+constexpr int AB_E = 2048;                     // staged entries per brick
+constexpr int AB_IDS = 256;                    // local ids per brick
+constexpr int AB_W = AB_IDS / 32;              // mask words per row
+constexpr int AB_HASH = 512;                   // hash slots
+constexpr int AB_NIT = (AB_H * AB_L + AB_T - 1) / AB_T;   // staged entries per thread
+constexpr uint16_t AB_NONE = 0xFFFF;
+
+// shared-memory layout (bytes).  The first region holds the hash set and the staged
+// entries' slots while the brick is staged, then the rows' sums (row stride W | 1).
+struct AbSmem {
+  static constexpr size_t hkey = 0;                                   // int32 [AB_HASH]
+  static constexpr size_t slot = hkey + 4 * AB_HASH;                  // uint16 [AB_L][AB_H]
+  static constexpr size_t hlid = slot + 2 * AB_L * AB_H;              // uint8 [AB_HASH]
+  static constexpr size_t stage_end = (hlid + AB_HASH + 15) & ~size_t(15);
+  // after the first region
+  static constexpr size_t vals = 0;                                   // double [AB_E]
+  static constexpr size_t pa = vals + 8 * AB_E;                       // double [27]
+  static constexpr size_t nmask = pa + 8 * 28;                        // uint32 [AB_H][AB_W]
+  static constexpr size_t rmask = nmask + 4 * AB_H * AB_W;            // uint32 [AB_W][AB_R]
+  static constexpr size_t keys = rmask + 4 * AB_W * AB_R;             // int32 [AB_IDS]
+  static constexpr size_t lcol = keys + 4 * AB_IDS;                   // int32 [AB_IDS]
+  static constexpr size_t hrow = lcol + 4 * AB_IDS;                   // int32 [AB_H]
+  static constexpr size_t poff = hrow + 4 * AB_H;                     // int32 [28]
+  static constexpr size_t pdir = poff + 4 * 28;                       // int32 [28]
+  static constexpr size_t wsum = pdir + 4 * 28;                       // int32 [AB_T / 32]
+  static constexpr size_t ctl = wsum + 4 * (AB_T / 32);               // int32 [4]
+  static constexpr size_t kslot = ctl + 16;                           // uint16 [AB_IDS]
+  static constexpr size_t hoff = kslot + 2 * AB_IDS;                  // uint16 [AB_H]
+  static constexpr size_t elid = hoff + 2 * AB_H;                     // uint8 [AB_E]
+  static constexpr size_t rpre = elid + AB_E;                         // uint8 [AB_W][AB_R]
+  static constexpr size_t hlen = rpre + AB_W * AB_R;                  // uint8 [AB_H]
+  static constexpr size_t hcnt = hlen + AB_H;                         // uint8 [AB_H]
+  static constexpr size_t size = hcnt + AB_H;
+};
+static_assert(AbSmem::hcnt % 4 == 0 && AbSmem::nmask % 16 == 0, "shared-memory alignment");
+__host__ __device__ inline size_t ab_region(int W) {
+  const size_t acc = (((size_t)(W | 1) * AB_R * 8) + 15) & ~size_t(15);
+  return acc > AbSmem::stage_end ? acc : AbSmem::stage_end;
+}
+static size_t ab_smem(int W) { return ab_region(W) + AbSmem::size; }
+
+__global__ void __launch_bounds__(AB_T, 3) k_ap_brick(StencilRow S, const int32_t* __restrict__ Prp,
+                                                      const int32_t* __restrict__ Pcol,
+                                                      const double* __restrict__ Pval, int W,
+                                                      int32_t* __restrict__ Ccol,
+                                                      double* __restrict__ Cval,
+                                                      int64_t* __restrict__ Clen,
+                                                      unsigned int* flags) {
+  extern __shared__ __align__(16) char smem[];
+  int32_t* hkey = reinterpret_cast<int32_t*>(smem + AbSmem::hkey);
+  uint16_t* slot = reinterpret_cast<uint16_t*>(smem + AbSmem::slot);
+  uint8_t* hlid = reinterpret_cast<uint8_t*>(smem + AbSmem::hlid);
+  double* acc = reinterpret_cast<double*>(smem);
+  char* fx = smem + ab_region(W);
+  double* vals = reinterpret_cast<double*>(fx + AbSmem::vals);
+  double* pa = reinterpret_cast<double*>(fx + AbSmem::pa);
+  uint32_t* nmask = reinterpret_cast<uint32_t*>(fx + AbSmem::nmask);
+  uint32_t* rmask = reinterpret_cast<uint32_t*>(fx + AbSmem::rmask);
+  int32_t* keys = reinterpret_cast<int32_t*>(fx + AbSmem::keys);
+  int32_t* lcol = reinterpret_cast<int32_t*>(fx + AbSmem::lcol);
+  int32_t* hrow = reinterpret_cast<int32_t*>(fx + AbSmem::hrow);
+  int32_t* poff = reinterpret_cast<int32_t*>(fx + AbSmem::poff);
+  int32_t* pdir = reinterpret_cast<int32_t*>(fx + AbSmem::pdir);
+  int* wsum = reinterpret_cast<int*>(fx + AbSmem::wsum);
+  int* ctl = reinterpret_cast<int*>(fx + AbSmem::ctl);   // [0] distinct columns, [1] give up
+  uint16_t* kslot = reinterpret_cast<uint16_t*>(fx + AbSmem::kslot);
+  uint16_t* hoff = reinterpret_cast<uint16_t*>(fx + AbSmem::hoff);
+  uint8_t* elid = reinterpret_cast<uint8_t*>(fx + AbSmem::elid);
+  uint8_t* rpre = reinterpret_cast<uint8_t*>(fx + AbSmem::rpre);
+  uint8_t* hlen = reinterpret_cast<uint8_t*>(fx + AbSmem::hlen);
+  uint8_t* hcnt = reinterpret_cast<uint8_t*>(fx + AbSmem::hcnt);
+  const int m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int x0 = blockIdx.x * AB_X, y0 = blockIdx.y * AB_Y, z0 = blockIdx.z * AB_Z;
+  const int np = __popc(S.present);
+  if (tid < 27 && ((S.present >> tid) & 1u)) {   // the present directions in column order
+    const int j = __popc(S.present & ((1u << tid) - 1u));
+    pdir[j] = tid;
+    poff[j] = tid % 3 + AB_HX * (tid / 3 % 3 + AB_HY * (tid / 9));
+    pa[j] = S.a[tid];
+  }
+  for (int q = tid; q < AB_HASH; q += AB_T) hkey[q] = -1;
+  for (int q = tid; q < AB_H * AB_W; q += AB_T) nmask[q] = 0u;
+  if (tid == 0) {
+    ctl[0] = 0;
+    ctl[1] = 0;
+  }
+  // 1. the halo's P rows (staged entry t of halo row h at t AB_H + h)
+  for (int h = tid; h < AB_H; h += AB_T) {
+    const int gx = x0 + h % AB_HX - 1, gy = y0 + (h / AB_HX) % AB_HY - 1, gz = z0 + h / (AB_HX * AB_HY) - 1;
+    int b = 0, len = 0;
+    if ((unsigned)gx < (unsigned)m && (unsigned)gy < (unsigned)m && (unsigned)gz < (unsigned)m) {
+      const int64_t g = gx + (int64_t)m * (gy + (int64_t)m * gz);
+      b = Prp[g];
+      len = Prp[g + 1] - b;
+    }
+    hrow[h] = b;
+    hlen[h] = (uint8_t)min(len, AB_L);
+    hcnt[h] = 0;
+    if (len > AB_L) ctl[1] = 1;
+  }
+  __syncthreads();
+  // every staged entry's column and value loaded at once; columns into the hash set
+  int cst[AB_NIT];
+  double vst[AB_NIT];
+#pragma unroll
+  for (int u = 0; u < AB_NIT; u++) {
+    const int it = tid + AB_T * u;
+    const int h = it % AB_H, t = it / AB_H;
+    const bool ok = it < AB_H * AB_L && t < hlen[h];
+    cst[u] = ok ? Pcol[hrow[h] + t] : -1;
+    vst[u] = ok ? Pval[hrow[h] + t] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < AB_NIT; u++) {
+    const int it = tid + AB_T * u;
+    if (it < AB_H * AB_L) {
+      uint16_t sl = AB_NONE;
+      if (cst[u] >= 0) {
+        uint32_t hs = ((uint32_t)cst[u] * 0x9E3779B1u) >> 23;
+        for (int probe = 0; probe < AB_HASH; probe++) {
+          const int prev = atomicCAS(&hkey[hs], -1, cst[u]);
+          if (prev == -1 || prev == cst[u]) {
+            sl = (uint16_t)hs;
+            break;
+          }
+          hs = (hs + 1) & (AB_HASH - 1);
+        }
+        if (sl == AB_NONE) ctl[1] = 1;   // the set is full
+        else {
+          const int h = it % AB_H;
+          atomicAdd(reinterpret_cast<unsigned int*>(hcnt + (h & ~3)), 1u << (8 * (h & 3)));
+        }
+      }
+      slot[it] = sl;
+    }
+  }
+  __syncthreads();
+  // 2. local ids (the rank of each distinct column) and the staged rows' offsets
+  for (int q = tid; q < AB_HASH; q += AB_T) {
+    const int c = hkey[q];
+    if (c >= 0) {
+      const int u = atomicAdd(&ctl[0], 1);
+      if (u < AB_IDS) {
+        keys[u] = c;
+        kslot[u] = (uint16_t)q;
+      }
+    }
+  }
+  {  // exclusive scan of the true entry counts over the staged rows, one per thread
+    const int v = tid < AB_H ? hcnt[tid] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < wid; w++) base += wsum[w];
+    const int ex = base + incl - v;
+    if (tid < AB_H) hoff[tid] = (uint16_t)min(ex, 0xFFFF);
+    if (tid == AB_T - 1 && ex + v > AB_E) ctl[1] = 1;
+  }
+  __syncthreads();
+  const int nd = ctl[0];
+  if (nd > AB_IDS || ctl[1]) {
+    if (tid == 0) atomicOr(flags, 2u);
+    return;
+  }
+  if (tid < nd) {
+    const int c = keys[tid];
+    int rk = 0;
+    for (int u = 0; u < nd; u++) rk += keys[u] < c;
+    hlid[kslot[tid]] = (uint8_t)rk;
+    lcol[rk] = c;
+  }
+  __syncthreads();
+  // each staged row's ids, values and mask (true entries lead a CSR4 row, in column order)
+#pragma unroll
+  for (int u = 0; u < AB_NIT; u++) {
+    const int it = tid + AB_T * u;
+    if (it < AB_H * AB_L) {
+      const uint16_t sl = slot[it];
+      if (sl != AB_NONE) {
+        const int h = it % AB_H, t = it / AB_H;
+        const int L = hlid[sl];
+        atomicOr(&nmask[h * AB_W + (L >> 5)], 1u << (L & 31));
+        elid[hoff[h] + t] = (uint8_t)L;
+        vals[hoff[h] + t] = vst[u];
+      }
+    }
+  }
+  __syncthreads();   // the hash set and the slots are dead from here: the sums' space
+  // 3. row tid / 4, lane k of its group
+  const int row = tid >> 2, k = tid & 3;
+  const unsigned gm = 0xFu << (lane & ~3);
+  const int tx = row % AB_X, ty = (row / AB_X) % AB_Y, tz = row / (AB_X * AB_Y);
+  const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+  if (gx >= m || gy >= m || gz >= m) return;   // the whole group
+  const int64_t r = gx + (int64_t)m * (gy + (int64_t)m * gz);
+  const int h0 = tx + AB_HX * (ty + AB_HY * tz);   // halo index of direction d = 0
+  uint32_t inb = (1u << np) - 1u;                  // the row's present directions
+  if (!(gx >= 1 && gy >= 1 && gz >= 1 && gx <= m - 2 && gy <= m - 2 && gz <= m - 2)) {
+    inb = 0u;
+    for (int j = 0; j < np; j++)
+      if (st_inb(gx, gy, gz, pdir[j], m)) inb |= 1u << j;
+  }
+  uint32_t rm[AB_W];
+#pragma unroll
+  for (int w = 0; w < AB_W; w++) rm[w] = 0u;
+  for (int j = k; j < np; j += AB_G) {
+    if (!((inb >> j) & 1u)) continue;
+    const uint4* nm = reinterpret_cast<const uint4*>(nmask + (h0 + poff[j]) * AB_W);
+    const uint4 a = nm[0], b = nm[1];
+    rm[0] |= a.x; rm[1] |= a.y; rm[2] |= a.z; rm[3] |= a.w;
+    rm[4] |= b.x; rm[5] |= b.y; rm[6] |= b.z; rm[7] |= b.w;
+  }
+  int c = 0;
+#pragma unroll
+  for (int w = 0; w < AB_W; w++) {
+    rm[w] |= __shfl_xor_sync(gm, rm[w], 1, AB_G);
+    rm[w] |= __shfl_xor_sync(gm, rm[w], 2, AB_G);
+    if ((w & 3) == k) {
+      rmask[w * AB_R + row] = rm[w];
+      rpre[w * AB_R + row] = (uint8_t)c;
+    }
+    c += __popc(rm[w]);
+  }
+  if (c > W) {
+    if (k == 0) {
+      Clen[r] = c;
+      atomicOr(flags, 1u);
+    }
+    return;
+  }
+  double* ac = acc + (size_t)row * (W | 1);
+  for (int q = k; q < c; q += AB_G) ac[q] = 0.0;
+  __syncwarp(gm);
+  const uint32_t* rmk = rmask + row;
+  const uint8_t* rpr = rpre + row;
+  for (int j = 0; j < np; j++) {
+    if (!((inb >> j) & 1u)) continue;
+    const int h = h0 + poff[j];
+    const int n = hcnt[h], o = hoff[h];
+    const double a = pa[j];
+    for (int e = k; e < n; e += AB_G) {
+      const int L = elid[o + e];
+      const int w = L >> 5;
+      const int p = rpr[w * AB_R] + __popc(rmk[w * AB_R] & ((1u << (L & 31)) - 1u));
+      ac[p] = fma(a, vals[o + e], ac[p]);
+    }
+    __syncwarp(gm);
+  }
+  int32_t* crow = Ccol + r * W;
+  int q = 0;
+#pragma unroll
+  for (int w = 0; w < AB_W; w++) {
+    uint32_t word = rm[w];
+    while (word) {
+      const int bt = __ffs(word) - 1;
+      word &= word - 1;
+      if ((q & 3) == k) crow[q] = lcol[w * 32 + bt];
+      q++;
+    }
+  }
+  double* vrow = Cval + r * W;
+  for (int u = k; u < c; u += AB_G) vrow[u] = ac[u];
+  if (k == 0) Clen[r] = c;
 }
 
 }  // namespace
@@ -1320,9 +1654,9 @@ static size_t mg_smem(int G, int K, int W, int lmax) {
 }
 
 template <int G, int K>
-static void mg_launch(int64_t nr, const Csr4& A, const double* Aval, MgRows Brows,
-                      const int32_t* Bcol, const double* Bval, int lmax, Strided& C,
-                      unsigned int* ovf, cudaStream_t st) {
+static void mg_launch(int64_t nr, const int64_t* rlist, const Csr4& A, const double* Aval,
+                      MgRows Brows, const int32_t* Bcol, const double* Bval, int lmax,
+                      Strided& C, unsigned int* ovf, cudaStream_t st) {
   const unsigned g = (unsigned)((nr + MG_BLOCK / G - 1) / (MG_BLOCK / G));
   const size_t smem = mg_smem(G, K, C.W, lmax);
   static size_t attr = 48 * 1024;
@@ -1331,26 +1665,26 @@ static void mg_launch(int64_t nr, const Csr4& A, const double* Aval, MgRows Brow
                                   (int)smem));
     attr = smem;
   }
-  k_mg<G, K><<<g, MG_BLOCK, smem, st>>>(nr, A.rowptr, A.col, Aval, Brows, Bcol, Bval, C.W, lmax,
-                                        C.col, C.val, C.len, ovf);
+  k_mg<G, K><<<g, MG_BLOCK, smem, st>>>(nr, rlist, A.rowptr, A.col, Aval, Brows, Bcol, Bval, C.W,
+                                        lmax, C.col, C.val, C.len, ovf);
   FEM_CHECK_LAUNCH();
 }
 
 template <int G>
-static void mg_launch_k(int K, int64_t nr, const Csr4& A, const double* Aval, MgRows Brows,
-                        const int32_t* Bcol, const double* Bval, int lmax, Strided& C,
-                        unsigned int* ovf, cudaStream_t st) {
+static void mg_launch_k(int K, int64_t nr, const int64_t* rlist, const Csr4& A, const double* Aval,
+                        MgRows Brows, const int32_t* Bcol, const double* Bval, int lmax,
+                        Strided& C, unsigned int* ovf, cudaStream_t st) {
   switch (K) {
-    case 2: mg_launch<G, 2>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
-    case 4: mg_launch<G, 4>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
-    case 8: mg_launch<G, 8>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
-    default: mg_launch<G, 16>(nr, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    case 2: mg_launch<G, 2>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    case 4: mg_launch<G, 4>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    case 8: mg_launch<G, 8>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    default: mg_launch<G, 16>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
   }
 }
 
 // stride last used for a product of this shape (the next set-up of the same system starts
-// from it); 32 for a new shape
-static int mg_stride_guess(uint64_t key, int set) {
+// from it); dflt for a new shape
+static int mg_stride_guess(uint64_t key, int set, int dflt = 32) {
   static std::mutex mu;
   static std::unordered_map<uint64_t, int> seen;
   std::lock_guard<std::mutex> lk(mu);
@@ -1359,7 +1693,7 @@ static int mg_stride_guess(uint64_t key, int set) {
     return set;
   }
   auto it = seen.find(key);
-  return it == seen.end() ? 32 : it->second;
+  return it == seen.end() ? dflt : it->second;
 }
 
 // C = A B by the merge kernel, C at a fixed stride.  B's rows: CSR4 (Bs null) or the
@@ -1367,7 +1701,8 @@ static int mg_stride_guess(uint64_t key, int set) {
 // beyond 16 x 32 entries, B rows beyond 255 entries, or tables beyond the shared memory):
 // the caller takes the hash path.
 static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, const double* Bval,
-                         const Strided* Bs, Strided& C, cudaStream_t st) {
+                         const Strided* Bs, Strided& C, cudaStream_t st,
+                         const int64_t* rlist = nullptr, int64_t nlist = 0) {
   const int64_t nr = A.nrows;
   const int64_t nb = Bc ? Bc->nrows : Bs->nrows;
   if (nr == 0 || nb == 0) return false;
@@ -1415,12 +1750,17 @@ static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, cons
     C.val.alloc_async((size_t)nr * W, st);
     C.len.alloc_async(nr, st);
     FEM_CUDA(cudaMemsetAsync(ovf, 0, 4, st));
+    // only the listed rows (when a list is given): the others stay empty
+    if (rlist) FEM_CUDA(cudaMemsetAsync(C.len, 0, 8 * nr, st));
+    const int64_t nrun = rlist ? nlist : nr;
     const int32_t* bcol = Bc ? Bc->col.p : Bs->col.p;
-    switch (G) {
-      case 4: mg_launch_k<4>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
-      case 8: mg_launch_k<8>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
-      case 16: mg_launch_k<16>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
-      default: mg_launch_k<32>(K, nr, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+    if (nrun > 0) {
+      switch (G) {
+        case 4: mg_launch_k<4>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+        case 8: mg_launch_k<8>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+        case 16: mg_launch_k<16>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+        default: mg_launch_k<32>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+      }
     }
     C.maxlen = max_of(C.len, nr, st);
     unsigned int hov = 0;
@@ -1436,14 +1776,87 @@ static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, cons
   return false;
 }
 
+// A P on the uniform finest level by the brick kernel, at a fixed stride.  Returns false
+// when the kernel cannot take it (P rows beyond its staging, a brick beyond its limits):
+// the caller takes the merge kernel.
+static bool ap_brick(const StencilRow& S, const Csr4& P, Strided& C, cudaStream_t st) {
+  const int m = S.m;
+  const int64_t nr = P.nrows;
+  if (m < 3 || (int64_t)m * m * m != nr || nr == 0) return false;
+  {
+    DevBuf<int64_t> plen(nr, st);
+    k_row_len<<<grid_for(nr, 256), 256, 0, st>>>(nr, P.rowptr, plen);
+    FEM_CHECK_LAUNCH();
+    if (max_of(plen, nr, st) > AB_L) return false;
+  }
+  const uint64_t key = (uint64_t)nr * 0xD6E8FEB86659FD93ull ^ (uint64_t)P.nnz * 0x9E3779B97F4A7C15ull ^
+                       (uint64_t)P.ncols ^ 0xABull;
+  // rows of the uniform level's A P hold about 13 entries, 21 at most at 255^3
+  int W = mg_stride_guess(key, 0, 24);
+  static size_t attr = 48 * 1024;
+  DevBuf<unsigned int> flags(1, st);
+  const dim3 grid((unsigned)((m + AB_X - 1) / AB_X), (unsigned)((m + AB_Y - 1) / AB_Y),
+                  (unsigned)((m + AB_Z - 1) / AB_Z));
+  for (int attempt = 0; attempt < 2; attempt++) {
+    const size_t smem = ab_smem(W);
+    if (smem > 200 * 1024 || nr * (int64_t)W >= ((int64_t)1 << 31) || W > 255) return false;
+    if (smem > attr) {
+      FEM_CUDA(cudaFuncSetAttribute(k_ap_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = smem;
+    }
+    C.nrows = nr;
+    C.ncols = P.ncols;
+    C.W = W;
+    C.col.alloc_async((size_t)nr * W, st);
+    C.val.alloc_async((size_t)nr * W, st);
+    C.len.alloc_async(nr, st);
+    FEM_CUDA(cudaMemsetAsync(flags, 0, 4, st));
+    k_ap_brick<<<grid, AB_T, smem, st>>>(S, P.rowptr, P.col, P.val, W, C.col, C.val, C.len, flags);
+    FEM_CHECK_LAUNCH();
+    unsigned int hf = 0;
+    FEM_CUDA(cudaMemcpyAsync(&hf, flags, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    if (hf & 2u) return false;
+    C.maxlen = max_of(C.len, nr, st);
+    if (!hf) {
+      // the next product of this shape starts from the stride its rows need
+      mg_stride_guess(key, std::max(4, (int)((C.maxlen + 3) & ~3)));
+      return true;
+    }
+    W = (int)((C.maxlen + 3) & ~3);
+  }
+  return false;
+}
+
 // Galerkin product A_c = R (A P) by the merge kernel (A P at a fixed stride, A_c compacted
 // to CSR4).  Returns false when the kernel cannot take it (the hash path then runs); sets
 // *too_long when A P or A_c has a row longer than limit; *ap_entries (if given) receives the
 // entries of A P.
 bool galerkin_merge(const Csr4& A, const Csr4& P, const Csr4& R, Csr4& Ac, cudaStream_t st,
-                    bool* too_long, int64_t limit, int64_t* ap_entries) {
+                    bool* too_long, int64_t limit, int64_t* ap_entries, const StencilRow* sr) {
   Strided AP, RAP;
-  if (!spgemm_merge(A, A.val, &P, P.val, nullptr, AP, st)) return false;
+  // R (A P) reads the rows of A P that R's columns name, those of the nonempty rows of P:
+  // where many rows of P are empty (isolated nodes on the coarser levels), A P is formed on
+  // those rows only
+  DevBuf<int64_t> rlist;
+  int64_t nlist = 0;
+  if (!sr) {   // (the uniform finest level: every node has an aggregate)
+    const int64_t nr = P.nrows;
+    DevBuf<int64_t> plen(nr, st), flag(nr, st), scan(nr + 1, st);
+    k_row_len<<<grid_for(nr, 256), 256, 0, st>>>(nr, P.rowptr, plen);
+    FEM_CHECK_LAUNCH();
+    k_long_flag<<<grid_for(nr, 256), 256, 0, st>>>(nr, plen, 0, flag);
+    FEM_CHECK_LAUNCH();
+    nlist = exclusive_scan(flag, nr, scan, st);
+    if (4 * nlist < 3 * nr) {
+      rlist.alloc_async(std::max<int64_t>(nlist, 1), st);
+      k_flag_list<<<grid_for(nr, 256), 256, 0, st>>>(nr, flag, scan, rlist);
+      FEM_CHECK_LAUNCH();
+    }
+  }
+  if (!(sr && ap_brick(*sr, P, AP, st)) &&
+      !spgemm_merge(A, A.val, &P, P.val, nullptr, AP, st, rlist.p, nlist))
+    return false;
   if (ap_entries) *ap_entries = row_sum(AP.len, AP.nrows, st);
   if (AP.maxlen > limit) {
     *too_long = true;
@@ -1465,6 +1878,10 @@ bool galerkin_merge(const Csr4& A, const Csr4& P, const Csr4& R, Csr4& Ac, cudaS
   return true;
 }
 
+namespace {
+bool stencil_row(const Csr4& A, int m, double theta, StencilRow& R, cudaStream_t st);
+}  // namespace
+
 double galerkin_timed(const Hierarchy& H, int lev, int reps, cudaStream_t st,
                       int64_t* ap_entries) {
   FEM_REQUIRE(lev >= 0 && lev < (int)H.L.size() && !H.L[lev]->coarsest, FEM_EINVAL,
@@ -1472,6 +1889,9 @@ double galerkin_timed(const Hierarchy& H, int lev, int reps, cudaStream_t st,
   const Level& L = *H.L[lev];
   FEM_REQUIRE(L.A && L.A->val.p && L.A->nnz > 0, FEM_EINVAL,
               "amg_galerkin_timed: the level keeps no FP64 matrix");
+  // the uniform finest level's A P from the stencil, as the set-up takes it
+  StencilRow SR;
+  const bool sr = lev == 0 && L.stencil && stencil_row(*L.A, L.st.m, H.o.theta, SR, st);
   cudaEvent_t e0, e1;
   FEM_CUDA(cudaEventCreate(&e0));
   FEM_CUDA(cudaEventCreate(&e1));
@@ -1481,7 +1901,8 @@ double galerkin_timed(const Hierarchy& H, int lev, int reps, cudaStream_t st,
     bool too_long = false;
     FEM_CUDA(cudaEventRecord(e0, st));
     int64_t ape = 0;
-    const bool merged = galerkin_merge(*L.A, L.P, L.R, Ac, st, &too_long, kLongRowMax, &ape);
+    const bool merged = galerkin_merge(*L.A, L.P, L.R, Ac, st, &too_long, kLongRowMax, &ape,
+                                       sr ? &SR : nullptr);
     if (!merged && !too_long) {
       Csr4 AP;
       spgemm(*L.A, L.A->val, L.P, L.P.val, AP, st, true);
@@ -1832,45 +2253,6 @@ __global__ void k_colour_scatter(int64_t N, const int32_t* colour, unsigned long
 }
 
 // ------------------------------------------------------------------ uniform-grid level
-
-// On the finest level of a uniform Kuhn grid every row of A holds the same values at the
-// same offsets (a subset of them at the boundary), so the strength graph, the Gershgorin
-// bounds and the smoothed prolongator follow from one interior row.  The kernels below
-// walk the stencil's offsets instead of A's columns; they take the same decisions and do
-// the same arithmetic, in the same order, as the CSR kernels above.
-struct StencilRow {
-  int m = 0;
-  uint32_t present = 0;      // bit d: the interior row has an entry at direction d
-  uint32_t strong = 0;       // bit d: that entry is a strong pair (never the diagonal)
-  double a[27];              // value at direction d
-};
-// direction d = (dx + 1) + 3 (dy + 1) + 9 (dz + 1): increasing d is increasing column
-// offset dx + m dy + m^2 dz (m >= 3), i.e. A's column order; d = 13 is the diagonal.
-constexpr int ST_DIAG = 13;
-
-__device__ __forceinline__ bool st_inb(int i, int j, int k, int d, int m) {
-  const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-  return (unsigned)(i + dx) < (unsigned)m && (unsigned)(j + dy) < (unsigned)m &&
-         (unsigned)(k + dz) < (unsigned)m;
-}
-
-__device__ __forceinline__ int64_t st_off(int d, int m) {
-  return (int64_t)(d % 3 - 1) + (int64_t)m * (d / 3 % 3 - 1) + (int64_t)m * m * (d / 9 - 1);
-}
-
-// strong-direction test: compile-time mask when MASK != 0, else the runtime one
-template <uint32_t MASK>
-__device__ __forceinline__ bool st_sel(uint32_t strong, int d) {
-  return MASK ? ((MASK >> d) & 1u) != 0 : ((strong >> d) & 1u) != 0;
-}
-
-__device__ __forceinline__ void st_ijk(int64_t r, int m, int& i, int& j, int& k) {
-  const uint32_t rr = (uint32_t)r, mm = (uint32_t)m;
-  const uint32_t q = rr / mm;
-  i = (int)(rr - q * mm);
-  k = (int)(q / mm);
-  j = (int)(q - (uint32_t)k * mm);
-}
 
 template <uint32_t MASK>
 __global__ void k_st_mis_init(int64_t N, int m, uint32_t strong, uint8_t* state) {
@@ -2637,8 +3019,16 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     Csr4 AP;
     auto nxt = std::make_unique<Level>();
     bool merged = false;
+    // (the uniform finest level's A P from the stencil: A is not read)
+    StencilRow SRa;
+    const StencilRow* ap_sr = nullptr;
+    if (lev == 0 && Lv.stencil && !too_long && !S.pencil) {
+      if (st0) ap_sr = &SR;
+      else if (stencil_row(*Acur, Lv.st.m, o.theta, SRa, st)) ap_sr = &SRa;
+    }
     if (!too_long && !S.pencil)
-      merged = galerkin_merge(*Acur, Lv.P, Lv.R, nxt->Aown, st, &too_long, row_limit, nullptr);
+      merged = galerkin_merge(*Acur, Lv.P, Lv.R, nxt->Aown, st, &too_long, row_limit, nullptr,
+                              ap_sr);
     if (!merged && !too_long)
       spgemm(*Acur, Acur->val, Lv.P, Lv.P.val, AP, st, true, &too_long, row_limit);
     tr.mark("level: A P (spgemm)");
