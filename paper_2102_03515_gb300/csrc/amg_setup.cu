@@ -876,19 +876,23 @@ __global__ void k_scatter_t(int64_t nrows, const int32_t* rowptr, const int32_t*
     Tval[Trp[c] + p] = val[e];
   }
 }
-// sort each row by column (rank sort in a warp), pad
+// sort each row's first cnt entries by column (rank sort in a warp), pad the rest of the row:
+// rows of at most TM entries (rows of at most lo entries were sorted by an earlier pass;
+// longer rows are counted in err for the next one)
 constexpr int TMAX = 1024;
-__global__ void k_sort_rows(int64_t nrows, const int32_t* rp, const int64_t* cnt, int32_t* col,
-                            double* val, unsigned long long* err) {
-  __shared__ int sc[4][TMAX];
-  __shared__ double sv[4][TMAX];
+template <int TM>
+__global__ void k_sort_rows(int64_t nrows, const int32_t* rp, const int64_t* cnt, int lo,
+                            int32_t* col, double* val, unsigned long long* err) {
+  __shared__ int sc[4][TM];
+  __shared__ double sv[4][TM];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 4 + w;
   if (r >= nrows) return;
   const int c = (int)cnt[r];
+  if (c <= lo) return;
   const int o = rp[r];
-  if (c > TMAX) {
-    if (lane == 0) atomicAdd(err, 1ull);   // counted: k_sort_long sorts these rows
+  if (c > TM) {
+    if (lane == 0) atomicAdd(err, 1ull);   // counted: the next pass sorts these rows
     return;
   }
   for (int a = lane; a < c; a += 32) {
@@ -1027,7 +1031,7 @@ __global__ void __launch_bounds__(MG_BLOCK)
          const int32_t* __restrict__ Acol, const double* __restrict__ Aval, MgRows B,
          const int32_t* __restrict__ Bcol, const double* __restrict__ Bval, int W, int lmax,
          int32_t* __restrict__ Ccol, double* __restrict__ Cval, int64_t* __restrict__ Clen,
-         unsigned int* overflow) {
+         unsigned int* overflow, int upper) {
   extern __shared__ __align__(16) char smem[];
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
   const int64_t rr = (int64_t)blockIdx.x * (MG_BLOCK / G) + grp;
@@ -1041,7 +1045,13 @@ __global__ void __launch_bounds__(MG_BLOCK)
   double* acc = reinterpret_cast<double*>(smem) + (size_t)grp * (W + 1);
   uint8_t* pos = reinterpret_cast<uint8_t*>(reinterpret_cast<double*>(smem) + (size_t)NG * (W + 1)) +
                  (size_t)grp * (G * K * lmax + 4);
+  // upper part: each list's first entry at or above the row (B's rows are then unpadded)
+  int* skp = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(reinterpret_cast<double*>(smem) +
+                                                               (size_t)NG * (W + 1)) +
+                                    (size_t)NG * (G * K * lmax + 4)) +
+             grp * G * K;
   const int ea = Arp[r], e1 = Arp[r + 1];
+  const int lo = upper ? (int)r : 0;   // the smallest column wanted
   int cur[K], end[K], head[K], base[K];   // base + cursor: the entry's position slot
 #pragma unroll
   for (int s = 0; s < K; s++) {
@@ -1050,6 +1060,19 @@ __global__ void __launch_bounds__(MG_BLOCK)
     cur[s] = k >= 0 ? B.beg(k) : 0;
     end[s] = k >= 0 ? B.end(k) : 0;
     base[s] = (lane + G * s) * lmax - cur[s];
+    if (upper) {   // lower bound of the row in the sorted list
+      int n = end[s] - cur[s];
+      while (n > 0) {
+        const int half = n >> 1;
+        if (Bcol[cur[s] + half] < lo) {
+          cur[s] += half + 1;
+          n -= half + 1;
+        } else {
+          n = half;
+        }
+      }
+      skp[lane + G * s] = cur[s];
+    }
     const int h = cur[s] < end[s] ? Bcol[cur[s]] : MG_INF;
     head[s] = h < 0 ? MG_INF : h;
   }
@@ -1087,14 +1110,16 @@ __global__ void __launch_bounds__(MG_BLOCK)
     const int e = e0 + lane;
     const int k = e < e1 ? Acol[e] : -1;
     const int fb = k >= 0 ? B.beg(k) : 0, fe = k >= 0 ? B.end(k) : 0;
+    const int fs = (upper && k >= 0) ? skp[e - ea] : fb;   // first entry taken
     const double av = k >= 0 ? Aval[e] : 0.0;
     const int nt = min(G, e1 - e0);
     for (int t = 0; t < nt; t++) {
       const int b0 = __shfl_sync(mask, fb, t, G), b1 = __shfl_sync(mask, fe, t, G);
+      const int bs = __shfl_sync(mask, fs, t, G);
       const double a = __shfl_sync(mask, av, t, G);
       const uint8_t* pt = pos + (e0 - ea + t) * lmax - b0;
-      for (int f = b0 + lane; f < b1; f += G) {
-        if (Bcol[f] < 0) continue;
+      for (int f = bs + lane; f < b1; f += G) {
+        if (Bcol[f] < 0) continue;   // padding
         const int q = pt[f];
         acc[q] = fma(a, Bval[f], acc[q]);
       }
@@ -1106,19 +1131,59 @@ __global__ void __launch_bounds__(MG_BLOCK)
   if (lane == 0) Clen[r] = c;
 }
 
-// CSR4 from rows at a fixed stride (a warp per row; padding appended)
-__global__ void k_mg_compact(int64_t nrows, int W, const int32_t* __restrict__ Scol,
-                             const double* __restrict__ Sval, const int64_t* __restrict__ len,
-                             const int32_t* __restrict__ Crp, int32_t* __restrict__ Ccol,
-                             double* __restrict__ Cval) {
+// A symmetric product from its upper part U (columns >= row, at a fixed stride): row I of
+// the product is the lower part {(J, U[J][I]) : J < I} followed by U's row I.  A warp per row
+// of U: the count and the scatter of the lower entries (unordered until the rows are
+// sorted), then U's row after the sorted lower part.
+__global__ void k_u_count(int64_t nrows, int W, const int32_t* __restrict__ Ucol,
+                          const int64_t* __restrict__ Ulen, unsigned long long* cnt) {
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= nrows) return;
-  const int c = (int)len[r];
-  const int o0 = Crp[r], o1 = Crp[r + 1];
-  for (int q = lane; q < o1 - o0; q += 32) {
-    Ccol[o0 + q] = q < c ? Scol[r * W + q] : -1;
-    Cval[o0 + q] = q < c ? Sval[r * W + q] : 0.0;
+  const int c = (int)Ulen[r];
+  for (int q = lane; q < c; q += 32) {
+    const int j = Ucol[r * W + q];
+    if (j > r) atomicAdd(&cnt[j], 1ull);
+  }
+}
+
+__global__ void k_u_len(int64_t n, const unsigned long long* lcnt, const int64_t* Ulen,
+                        int64_t* lower, int64_t* total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  lower[i] = (int64_t)lcnt[i];
+  total[i] = (int64_t)lcnt[i] + Ulen[i];
+}
+
+__global__ void k_u_scatter(int64_t nrows, int W, const int32_t* __restrict__ Ucol,
+                            const double* __restrict__ Uval, const int64_t* __restrict__ Ulen,
+                            const int32_t* __restrict__ Crp, unsigned long long* fill,
+                            int32_t* __restrict__ Ccol, double* __restrict__ Cval) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  const int c = (int)Ulen[r];
+  for (int q = lane; q < c; q += 32) {
+    const int j = Ucol[r * W + q];
+    if (j <= r) continue;
+    const unsigned long long p = atomicAdd(&fill[j], 1ull);
+    Ccol[Crp[j] + p] = (int32_t)r;
+    Cval[Crp[j] + p] = Uval[r * W + q];
+  }
+}
+
+__global__ void k_u_upper(int64_t nrows, int W, const int32_t* __restrict__ Ucol,
+                          const double* __restrict__ Uval, const int64_t* __restrict__ Ulen,
+                          const int32_t* __restrict__ Crp, const int64_t* __restrict__ lower,
+                          int32_t* __restrict__ Ccol, double* __restrict__ Cval) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  const int c = (int)Ulen[r];
+  const int64_t o = Crp[r] + lower[r];
+  for (int q = lane; q < c; q += 32) {
+    Ccol[o + q] = Ucol[r * W + q];
+    Cval[o + q] = Uval[r * W + q];
   }
 }
 
@@ -1650,13 +1715,13 @@ struct Strided {
 };
 
 static size_t mg_smem(int G, int K, int W, int lmax) {
-  return (size_t)(MG_BLOCK / G) * ((size_t)(W + 1) * 8 + (size_t)G * K * lmax + 4);
+  return (size_t)(MG_BLOCK / G) * ((size_t)(W + 1) * 8 + (size_t)G * K * lmax + 4 + (size_t)G * K * 4);
 }
 
 template <int G, int K>
 static void mg_launch(int64_t nr, const int64_t* rlist, const Csr4& A, const double* Aval,
                       MgRows Brows, const int32_t* Bcol, const double* Bval, int lmax,
-                      Strided& C, unsigned int* ovf, cudaStream_t st) {
+                      Strided& C, unsigned int* ovf, int upper, cudaStream_t st) {
   const unsigned g = (unsigned)((nr + MG_BLOCK / G - 1) / (MG_BLOCK / G));
   const size_t smem = mg_smem(G, K, C.W, lmax);
   static size_t attr = 48 * 1024;
@@ -1666,19 +1731,19 @@ static void mg_launch(int64_t nr, const int64_t* rlist, const Csr4& A, const dou
     attr = smem;
   }
   k_mg<G, K><<<g, MG_BLOCK, smem, st>>>(nr, rlist, A.rowptr, A.col, Aval, Brows, Bcol, Bval, C.W,
-                                        lmax, C.col, C.val, C.len, ovf);
+                                        lmax, C.col, C.val, C.len, ovf, upper);
   FEM_CHECK_LAUNCH();
 }
 
 template <int G>
 static void mg_launch_k(int K, int64_t nr, const int64_t* rlist, const Csr4& A, const double* Aval,
                         MgRows Brows, const int32_t* Bcol, const double* Bval, int lmax,
-                        Strided& C, unsigned int* ovf, cudaStream_t st) {
+                        Strided& C, unsigned int* ovf, int upper, cudaStream_t st) {
   switch (K) {
-    case 2: mg_launch<G, 2>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
-    case 4: mg_launch<G, 4>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
-    case 8: mg_launch<G, 8>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
-    default: mg_launch<G, 16>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, st); break;
+    case 2: mg_launch<G, 2>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, upper, st); break;
+    case 4: mg_launch<G, 4>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, upper, st); break;
+    case 8: mg_launch<G, 8>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, upper, st); break;
+    default: mg_launch<G, 16>(nr, rlist, A, Aval, Brows, Bcol, Bval, lmax, C, ovf, upper, st); break;
   }
 }
 
@@ -1702,10 +1767,10 @@ static int mg_stride_guess(uint64_t key, int set, int dflt = 32) {
 // the caller takes the hash path.
 static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, const double* Bval,
                          const Strided* Bs, Strided& C, cudaStream_t st,
-                         const int64_t* rlist = nullptr, int64_t nlist = 0) {
+                         const int64_t* rlist = nullptr, int64_t nlist = 0, int upper = 0) {
   const int64_t nr = A.nrows;
   const int64_t nb = Bc ? Bc->nrows : Bs->nrows;
-  if (nr == 0 || nb == 0) return false;
+  if (nr == 0 || nb == 0 || (upper && Bc)) return false;   // (upper part: unpadded B rows)
   DevBuf<int64_t> len(nr, st);
   k_row_len<<<grid_for(nr, 256), 256, 0, st>>>(nr, A.rowptr, len);
   FEM_CHECK_LAUNCH();
@@ -1736,7 +1801,7 @@ static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, cons
   while ((int64_t)G * K < maxa) K <<= 1;
   const int64_t bcols = Bc ? Bc->ncols : Bs->ncols;
   const uint64_t key = (uint64_t)nr * 0x9E3779B97F4A7C15ull ^ (uint64_t)A.nnz * 0xC2B2AE3D27D4EB4Full ^
-                       (uint64_t)nb * 0x165667B19E3779F9ull ^ (uint64_t)bcols;
+                       (uint64_t)nb * 0x165667B19E3779F9ull ^ (uint64_t)bcols ^ (uint64_t)upper << 63;
   int W = mg_stride_guess(key, 0);
   DevBuf<unsigned int> ovf(1, st);
   for (int attempt = 0; attempt < 2; attempt++) {
@@ -1756,10 +1821,10 @@ static bool spgemm_merge(const Csr4& A, const double* Aval, const Csr4* Bc, cons
     const int32_t* bcol = Bc ? Bc->col.p : Bs->col.p;
     if (nrun > 0) {
       switch (G) {
-        case 4: mg_launch_k<4>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
-        case 8: mg_launch_k<8>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
-        case 16: mg_launch_k<16>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
-        default: mg_launch_k<32>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, st); break;
+        case 4: mg_launch_k<4>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, upper, st); break;
+        case 8: mg_launch_k<8>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, upper, st); break;
+        case 16: mg_launch_k<16>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, upper, st); break;
+        default: mg_launch_k<32>(K, nrun, rlist, A, Aval, R, bcol, Bval, (int)lmax, C, ovf, upper, st); break;
       }
     }
     C.maxlen = max_of(C.len, nr, st);
@@ -1828,10 +1893,14 @@ static bool ap_brick(const StencilRow& S, const Csr4& P, Strided& C, cudaStream_
   return false;
 }
 
-// Galerkin product A_c = R (A P) by the merge kernel (A P at a fixed stride, A_c compacted
-// to CSR4).  Returns false when the kernel cannot take it (the hash path then runs); sets
-// *too_long when A P or A_c has a row longer than limit; *ap_entries (if given) receives the
-// entries of A P.
+static bool sort_rows(int64_t nrows, const int32_t* rp, const int64_t* cnt, int32_t* col,
+                      double* val, cudaStream_t st);
+
+// Galerkin product A_c = R (A P) by the merge kernels (A P at a fixed stride: the brick kernel
+// on the uniform finest level; the upper part of A_c merged, its lower part mirrored, CSR4).
+// Returns false when the kernels cannot take it (the hash path then runs); sets *too_long
+// when A P or A_c has a row longer than limit; *ap_entries (if given) receives the entries of
+// A P.
 bool galerkin_merge(const Csr4& A, const Csr4& P, const Csr4& R, Csr4& Ac, cudaStream_t st,
                     bool* too_long, int64_t limit, int64_t* ap_entries, const StencilRow* sr) {
   Strided AP, RAP;
@@ -1862,18 +1931,35 @@ bool galerkin_merge(const Csr4& A, const Csr4& P, const Csr4& R, Csr4& Ac, cudaS
     *too_long = true;
     return true;
   }
-  if (!spgemm_merge(R, R.val, nullptr, AP.val, &AP, RAP, st)) return false;
-  if (RAP.maxlen > limit) {
+  // A_c is symmetric (A is, and R = P^T): the merge forms its upper part (columns >= row),
+  // the lower part is that part's transpose
+  if (!spgemm_merge(R, R.val, nullptr, AP.val, &AP, RAP, st, nullptr, 0, 1)) return false;
+  AP = Strided();
+  const int64_t nc = RAP.nrows;
+  DevBuf<unsigned long long> lcnt(nc, st), fill(nc, st);
+  FEM_CUDA(cudaMemsetAsync(lcnt, 0, 8 * nc, st));
+  FEM_CUDA(cudaMemsetAsync(fill, 0, 8 * nc, st));
+  const unsigned gw = grid_for(nc * 32, 256);
+  k_u_count<<<gw, 256, 0, st>>>(nc, RAP.W, RAP.col, RAP.len, lcnt);
+  FEM_CHECK_LAUNCH();
+  DevBuf<int64_t> lower(nc, st), total(nc, st);
+  k_u_len<<<grid_for(nc, 256), 256, 0, st>>>(nc, lcnt, RAP.len, lower, total);
+  FEM_CHECK_LAUNCH();
+  if (max_of(total, nc, st) > limit) {
     *too_long = true;
     return true;
   }
-  AP = Strided();
-  Ac.nrows = (int32_t)R.nrows;
+  Ac.nrows = (int32_t)nc;
   Ac.ncols = P.ncols;
-  rowptr_from_counts(RAP.len, RAP.nrows, Ac, st);
+  rowptr_from_counts(total, nc, Ac, st);
   Ac.val.alloc(Ac.nnz);
-  k_mg_compact<<<grid_for(RAP.nrows * 32, 256), 256, 0, st>>>(RAP.nrows, RAP.W, RAP.col, RAP.val,
-                                                              RAP.len, Ac.rowptr, Ac.col, Ac.val);
+  k_u_scatter<<<gw, 256, 0, st>>>(nc, RAP.W, RAP.col, RAP.val, RAP.len, Ac.rowptr, fill, Ac.col,
+                                  Ac.val);
+  FEM_CHECK_LAUNCH();
+  FEM_REQUIRE(sort_rows(nc, Ac.rowptr, lower, Ac.col, Ac.val, st), FEM_EUNSUPPORTED,
+              "Galerkin product: a coarse row has more than 8192 entries");
+  k_u_upper<<<gw, 256, 0, st>>>(nc, RAP.W, RAP.col, RAP.val, RAP.len, Ac.rowptr, lower, Ac.col,
+                                Ac.val);
   FEM_CHECK_LAUNCH();
   return true;
 }
@@ -1921,6 +2007,42 @@ double galerkin_timed(const Hierarchy& H, int lev, int reps, cudaStream_t st,
   return ms_sum / reps;
 }
 
+// Sort the first cnt[r] entries of every row r by column and pad the rest of the row: warp
+// rank sorts for rows of up to 128 and up to TMAX entries, a block bitonic sort beyond.
+// Returns false when a row holds more than kLongRowMax entries (left unsorted).
+static bool sort_rows(int64_t nrows, const int32_t* rp, const int64_t* cnt, int32_t* col,
+                      double* val, cudaStream_t st) {
+  if (nrows <= 0) return true;
+  DevBuf<unsigned long long> err(1, st);
+  FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+  const unsigned g = (unsigned)((nrows + 3) / 4);
+  k_sort_rows<128><<<g, 128, 0, st>>>(nrows, rp, cnt, -1, col, val, err);
+  FEM_CHECK_LAUNCH();
+  unsigned long long he = 0;
+  FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  if (!he) return true;
+  FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+  k_sort_rows<TMAX><<<g, 128, 0, st>>>(nrows, rp, cnt, 128, col, val, err);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  if (!he) return true;
+  FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
+  const size_t smem = 12 * (size_t)kLongRowMax;
+  static bool attr = false;
+  if (!attr) {
+    FEM_CUDA(cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    attr = true;
+  }
+  k_sort_long<<<(unsigned)nrows, kLongBlock, smem, st>>>(nrows, rp, cnt, TMAX, col, val, err);
+  FEM_CHECK_LAUNCH();
+  FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  return he == 0;
+}
+
 void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too_long,
                int64_t limit) {
   T.nrows = (int32_t)ncols;
@@ -1948,34 +2070,12 @@ void transpose(const Csr4& A, Csr4& T, int64_t ncols, cudaStream_t st, bool* too
                                                         fill, T.col, T.val);
     FEM_CHECK_LAUNCH();
   }
-  DevBuf<unsigned long long> err(1, st);
-  FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
-  if (ncols > 0) {
-    k_sort_rows<<<(unsigned)((ncols + 3) / 4), 128, 0, st>>>(ncols, T.rowptr, c64, T.col, T.val, err);
-    FEM_CHECK_LAUNCH();
-  }
-  unsigned long long he = 0;
-  FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
-  FEM_CUDA(cudaStreamSynchronize(st));
-  if (he) {
-    FEM_CUDA(cudaMemsetAsync(err, 0, 8, st));
-    const size_t smem = 12 * (size_t)kLongRowMax;
-    static bool attr = false;
-    if (!attr) {
-      FEM_CUDA(cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-      attr = true;
-    }
-    k_sort_long<<<(unsigned)ncols, kLongBlock, smem, st>>>(ncols, T.rowptr, c64, TMAX, T.col,
-                                                           T.val, err);
-    FEM_CHECK_LAUNCH();
-    FEM_CUDA(cudaMemcpyAsync(&he, err, 8, cudaMemcpyDeviceToHost, st));
-    FEM_CUDA(cudaStreamSynchronize(st));
-    if (he && too_long) {
+  if (!sort_rows(ncols, T.rowptr, c64, T.col, T.val, st)) {
+    if (too_long) {
       *too_long = true;
       return;
     }
-    FEM_REQUIRE(he == 0, FEM_EUNSUPPORTED, "transpose: a row has more than 8192 entries");
+    FEM_REQUIRE(false, FEM_EUNSUPPORTED, "transpose: a row has more than 8192 entries");
   }
 }
 
