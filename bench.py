@@ -33,7 +33,7 @@ ORACLE_N = 48          # reference-arm step: the same workload on a 48^3 mesh
 CPU_SAMPLE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from ncu captures of
 # the current kernels, by kernel: None until a capture of the current code exists
-TRAFFIC = {"galerkin_l0_n256": (5.30 + 3.19 + 5.96 + 0.86 + 1.02 + 0.80) * 1e9,
+TRAFFIC = {"galerkin_l0_n256": None,
            "cg_operator_n256": (265.38 + 104.65) * 1e6,
            "vcycle_fp32_n256": (4634.1 + 438.2) * 1e6}
 
@@ -846,25 +846,26 @@ def run_ours(args, rank: int, world: int):
 
     hbm = _measured_hbm_gbs()
     # ---- dominant kernels of a step (launch list): the set-up's Galerkin product on the
-    # finest level (two merge-SpGEMM launches and the compaction), recomputed from the
-    # hierarchy and timed with CUDA events on the stream it runs on
+    # finest level (A P by the brick kernel, the upper part of R (A P) by the merge kernel,
+    # its mirror), recomputed from the hierarchy and timed with CUDA events on the stream it
+    # runs on
     sys_ = fa.fem_assemble(n, rho, target)
     hg = fa.amg_setup(sys_, precision=fa.AMG_PREC_FP32)
     ginfo = fa.amg_hier_get_info(hg)
     gms, ap_entries = fa.amg_galerkin_timed(hg, 0, 5)
     fa.amg_hier_destroy(hg)
-    # compulsory bytes: A_0, P_0 and R_0 read once (12 bytes per stored entry, 4 per row
-    # pointer), A_0 P_0 written and read once (12 bytes per entry, 8 per row length, twice),
-    # A_1 written once and compacted (read and written: 12 bytes per entry, 3 times)
+    # compulsory bytes of the two-stage product: P_0 and R_0 read once (12 bytes per stored
+    # entry, 4 per row pointer; A_0 is the stencil, nothing to read), A_0 P_0 written and
+    # read once (12 bytes per entry, 8 per row length, twice), A_1 written once (12 bytes per
+    # entry, 4 per row pointer)
     rows0, rows1 = ginfo["rows"][0], ginfo["rows"][1]
-    gbytes = (12.0 * (ginfo["nnz"][0] + ginfo["pnnz"][0] + ginfo["rnnz"][0]) +
-              4.0 * (2 * rows0 + 1 + rows1 + 1) + 2 * (12.0 * ap_entries + 8.0 * rows0) +
-              3 * 12.0 * ginfo["nnz"][1] + 8.0 * rows1)
+    gbytes = (12.0 * (ginfo["pnnz"][0] + ginfo["rnnz"][0]) + 4.0 * (rows0 + 1 + 2 * (rows1 + 1)) +
+              2 * (12.0 * ap_entries + 8.0 * rows0) + 12.0 * ginfo["nnz"][1])
     galerkin_roof = {"bound": "hbm", "achieved": gbytes / (gms * 1e-3) / 1e9, "peak": hbm,
                      "unit": "GB/s", "frac": gbytes / (gms * 1e-3) / 1e9 / hbm,
                      "traffic": TRAFFIC["galerkin_l0_n256"],
-                     "kernel": "finest-level Galerkin product R (A P) (merge SpGEMM k_mg, "
-                               "2 launches + compaction)",
+                     "kernel": "finest-level Galerkin product R (A P) (k_ap_brick, upper "
+                               "part by k_mg, mirror k_u_*)",
                      "kernel_ms": gms, "algorithmic_bytes": gbytes, "ap_entries": ap_entries,
                      "peak_source": "measured copy rate"}
     # ---- CG's operator q = A p (double-float on the FP32 pipe), as CG launches it

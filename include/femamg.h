@@ -457,7 +457,11 @@ void pcg_default_opts(pcg_opts* opts);
  * nrhs = 1: u_dev is length N.  nrhs > 1: f_dev/u_dev are [N][nrhs] row-major and
  * rho_k_host gives one rho per column (the system must keep its pencil, the hierarchy
  * must come from amg_setup on it); each column is an independent solve.  res points to
- * nrhs results.  Returns FEM_OK when every column converged. */
+ * nrhs results.  Returns FEM_OK when every column converged.  On the uniform grid the
+ * columns' CG operator (nrhs > 1 and batch sessions) runs in double-float arithmetic --
+ * search directions rounded to 48 bits, each row within 2^-44 sum_j |a_ij p_j| as for
+ * fem_spmv_timed -- when tol >= 1e-12, and in FP64 for smaller tolerances; a column whose
+ * direction leaves the pairs' range takes FP64 for that iteration. */
 fem_status pcg_solve(fem_system sys, amg_hier hier, const double* f_dev, double* u_dev,
                      int32_t nrhs, const double* rho_k_host, const pcg_opts* opts,
                      void* stream, pcg_result* res);

@@ -25,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "solver.cuh"
 
 namespace fem {
@@ -37,7 +38,17 @@ constexpr int MAXB = 64;
 
 struct SlotState {
   double rho, bb, rr, rz, rz_old, pq, alpha, beta, zrp, tol2;
-  int iter, first, active, done, status, maxit, pad0, pad1;
+  int iter, first, active, done, status, maxit;
+  int dfop;   // q = A p in double-float (the uniform grid, tolerance >= 1e-12)
+  int pad1;
+};
+
+// per-slot coefficients of the double-float operator: c0, ca, cf, cb times 2^s, each as
+// three FP32 numbers (exact)
+struct MvDf {
+  float C[4][3];
+  int s;
+  int pad[3];
 };
 
 // per (level, slot) smoother coefficients: inv_theta, c1, c2 (degree 2) and, for the
@@ -393,6 +404,138 @@ __global__ void __launch_bounds__(256) k_mv_stencil64(const double* __restrict__
   if (slots) slot_partials<1>(acc, B, partials, nblocks, blockIdx.x + gridDim.x * blockIdx.y);
 }
 
+// q = A(rho_b) p for CG's FP64 search directions in double-float arithmetic (the FP32 pipe):
+// p arrives also as FP32 pairs (hi, lo) with p = hi + lo exactly (the update rounds p to 48
+// bits), and the class sums, products and their sum follow the single-vector operator
+// k_stencil_df term for term, in the same order; the result is hi + lo rounded to FP64 and
+// <p, q> is summed in FP64.  Thread (i, j, slot) marches its column in k like
+// k_mv_stencil_col (7 pair loads per point).  Slots without the double-float operator, and a
+// slot one of whose entries of p left the pairs' range (its rflag), take the FP64 operator.
+__global__ void __launch_bounds__(256) k_mv_stencil_df(const float2* __restrict__ v2,
+                                                       const double* __restrict__ v, int m,
+                                                       const MvDf* __restrict__ dfc,
+                                                       const double* coef /* [B][4] */, int B,
+                                                       double* y, const SlotState* slots,
+                                                       const int* rflag, double* partials,
+                                                       int nblocks) {
+  const int b = threadIdx.x & (B - 1);
+  const int ppb = blockDim.x / B;
+  const int i = blockIdx.x * ppb + threadIdx.x / B;
+  constexpr int KZV = 16;
+  const int k0 = blockIdx.z * KZV;
+  const int kend = min(k0 + KZV, m);
+  double acc[1] = {0.0};
+  const bool live = slots[b].active && !slots[b].done;
+  const bool df = slots[b].dfop && !rflag[b];
+  const int64_t sB = B, sj = (int64_t)m * B, sk = (int64_t)m * m * B;
+  if (i < m && live && df) {
+    float C[4][3];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int w = 0; w < 3; w++) C[u][w] = dfc[b].C[u][w];
+    const int sc = dfc[b].s;
+    for (int j = blockIdx.y; j < m; j += gridDim.y) {
+      const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1;
+      const int64_t row0 = ((int64_t)i + (int64_t)m * j) * B + b;
+      const float2* col = v2 + row0;
+      const float2 Z = make_float2(0.0f, 0.0f);
+      auto ld = [&](bool ok, int k, int64_t off) -> float2 {
+        return (ok && k >= 0 && k < m) ? __ldg(col + sk * k + off) : Z;
+      };
+      float2 cm = ld(true, k0 - 1, 0);
+      float2 m_im = ld(im, k0 - 1, -sB), m_jm = ld(jm, k0 - 1, -sj), m_ijm = ld(im && jm, k0 - 1, -sB - sj);
+      float2 c0v = ld(true, k0, 0);
+      float2 p_ip = ld(ip, k0, sB), p_jp = ld(jp, k0, sj), p_ijp = ld(ip && jp, k0, sB + sj);
+      float2 z_im = ld(im, k0, -sB), z_jm = ld(jm, k0, -sj), z_ijm = ld(im && jm, k0, -sB - sj);
+      float2 cp = ld(true, k0 + 1, 0);
+      float2 n_ip = ld(ip, k0 + 1, sB), n_jp = ld(jp, k0 + 1, sj), n_ijp = ld(ip && jp, k0 + 1, sB + sj);
+      for (int k = k0; k < kend; k++) {
+        const bool more = k + 1 < kend;
+        const float2 z2_im = ld(im && more, k + 1, -sB), z2_jm = ld(jm && more, k + 1, -sj),
+                     z2_ijm = ld(im && jm && more, k + 1, -sB - sj);
+        const float2 cp2 = ld(more, k + 2, 0);
+        const float2 n2_ip = ld(ip && more, k + 2, sB), n2_jp = ld(jp && more, k + 2, sj),
+                     n2_ijp = ld(ip && jp && more, k + 2, sB + sj);
+        const int64_t o = row0 + sk * k;
+        const double pc = v[o];
+        // class sums (the order of k_stencil_df)
+        float as = z_im.x, ac = z_im.y;
+        df_acc(as, ac, p_ip.x, p_ip.y);
+        df_acc(as, ac, z_jm.x, z_jm.y);
+        df_acc(as, ac, p_jp.x, p_jp.y);
+        df_acc(as, ac, cm.x, cm.y);
+        df_acc(as, ac, cp.x, cp.y);
+        float fs = p_ijp.x, fc = p_ijp.y;
+        df_acc(fs, fc, z_ijm.x, z_ijm.y);
+        df_acc(fs, fc, n_ip.x, n_ip.y);
+        df_acc(fs, fc, m_im.x, m_im.y);
+        df_acc(fs, fc, n_jp.x, n_jp.y);
+        df_acc(fs, fc, m_jm.x, m_jm.y);
+        float bs = n_ijp.x, bc = n_ijp.y;
+        df_acc(bs, bc, m_ijm.x, m_ijm.y);
+        float p0, l0, p1, l1, p2, l2, p3, l3;
+        df_mul(C[0][0], C[0][1], C[0][2], c0v.x, c0v.y, p0, l0);
+        df_mul(C[1][0], C[1][1], C[1][2], as, ac, p1, l1);
+        df_mul(C[2][0], C[2][1], C[2][2], fs, fc, p2, l2);
+        df_mul(C[3][0], C[3][1], C[3][2], bs, bc, p3, l3);
+        float ys = p0, yc = l0;
+        df_acc(ys, yc, p1, l1);
+        df_acc(ys, yc, p2, l2);
+        df_acc(ys, yc, p3, l3);
+        const float yh = ys + yc;   // FastTwoSum: |yc| small against ys
+        const float yl = yc - (yh - ys);
+        const double av = df_to_double(yh, sc) + df_to_double(yl, sc);
+        y[o] = av;
+        acc[0] += pc * av;
+        cm = c0v;
+        m_im = z_im;
+        m_jm = z_jm;
+        m_ijm = z_ijm;
+        c0v = cp;
+        p_ip = n_ip;
+        p_jp = n_jp;
+        p_ijp = n_ijp;
+        z_im = z2_im;
+        z_jm = z2_jm;
+        z_ijm = z2_ijm;
+        cp = cp2;
+        n_ip = n2_ip;
+        n_jp = n2_jp;
+        n_ijp = n2_ijp;
+      }
+    }
+  } else if (i < m && live) {   // FP64
+    const double c0 = coef[4 * b], ca = coef[4 * b + 1], cf = coef[4 * b + 2], cb = coef[4 * b + 3];
+    for (int j = blockIdx.y; j < m; j += gridDim.y) {
+      for (int k = k0; k < kend; k++) {
+        const int64_t o = ((int64_t)i + (int64_t)m * j + (int64_t)m * m * k) * B + b;
+        const bool im = i > 0, ip = i < m - 1, jm = j > 0, jp = j < m - 1, km = k > 0, kp = k < m - 1;
+        auto X = [&](bool ok, int64_t off) -> double { return ok ? v[o + off] : 0.0; };
+        double av = c0 * v[o];
+        av = fma(ca, X(im, -sB), av);
+        av = fma(ca, X(ip, sB), av);
+        av = fma(ca, X(jm, -sj), av);
+        av = fma(ca, X(jp, sj), av);
+        av = fma(ca, X(km, -sk), av);
+        av = fma(ca, X(kp, sk), av);
+        av = fma(cf, X(ip && jp, sB + sj), av);
+        av = fma(cf, X(im && jm, -sB - sj), av);
+        av = fma(cf, X(ip && kp, sB + sk), av);
+        av = fma(cf, X(im && km, -sB - sk), av);
+        av = fma(cf, X(jp && kp, sj + sk), av);
+        av = fma(cf, X(jm && km, -sj - sk), av);
+        av = fma(cb, X(ip && jp && kp, sB + sj + sk), av);
+        av = fma(cb, X(im && jm && km, -sB - sj - sk), av);
+        y[o] = av;
+        acc[0] += v[o] * av;
+      }
+    }
+  }
+  slot_partials<1>(acc, B, partials, nblocks,
+                   blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+}
+
 // ------------------------------------------------------------------ multivector CSR
 
 template <typename T, int VS>
@@ -701,7 +844,7 @@ __global__ void k_slot_sums2(const double* partials, int nb, int B, double* out)
 }
 
 __global__ void k_slot_admit(SlotState* S, const int32_t* slots, const double* sums, int nb,
-                             const double* rhos, double tol, int maxit) {
+                             const double* rhos, double tol, int maxit, int df_ok) {
   const int slot = slots[blockIdx.x];
   const double rho = rhos[blockIdx.x];
   double v[1] = {0.0};
@@ -717,6 +860,7 @@ __global__ void k_slot_admit(SlotState* S, const int32_t* slots, const double* s
     s.first = 1;
     s.active = 1;
     s.maxit = maxit;
+    s.dfop = df_ok && tol >= 1e-12;
     s.status = FEM_OK;
     s.done = (v[0] > 0.0) ? 0 : 1;
     if (!isfinite(v[0])) s.status = FEM_EBREAKDOWN;   // a non-finite right-hand side
@@ -724,8 +868,9 @@ __global__ void k_slot_admit(SlotState* S, const int32_t* slots, const double* s
 }
 
 // per-slot finalisations (one block per slot, fixed order over the block partials)
-__global__ void k_slot_fin_rz(SlotState* S, const double* partials, int nb, int B) {
+__global__ void k_slot_fin_rz(SlotState* S, const double* partials, int nb, int B, int* rflag) {
   const int b = blockIdx.x;
+  if (rflag && threadIdx.x == 0) rflag[b] = 0;   // raised again by this iteration's p
   double v[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     v[0] += partials[(int64_t)(0 * B + b) * nb + i];
@@ -789,15 +934,31 @@ __global__ void k_slot_fin_rr(SlotState* S, const double* partials, int nb, int 
   }
 }
 
-// p = z + beta p for live slots
-__global__ void k_mv_update_p(int64_t N, int B, const double* z, double* p, const SlotState* S) {
+// p = z + beta p for live slots; slots with the double-float operator round p to 48 bits and
+// write its FP32 pairs (p2), raising the slot's rflag for an entry outside the pairs' range.
+// (The grid stride is a multiple of B: a thread stays on one slot.)
+__global__ void k_mv_update_p(int64_t N, int B, const double* z, double* p, const SlotState* S,
+                              float2* p2, int* rflag) {
+  bool bad = false;
+  const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & (B - 1));
+  const SlotState& s = S[b];
+  if (!s.active || s.done) return;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N * B;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(idx & (B - 1));
-    const SlotState& s = S[b];
-    if (!s.active || s.done) continue;
-    p[idx] = z[idx] + s.beta * p[idx];
+    double pv = z[idx] + s.beta * p[idx];
+    if (p2 && s.dfop) {
+      float hi, lo;
+      double xs;
+      if (df_split(pv, hi, lo, xs)) {
+        p2[idx] = make_float2(hi, lo);
+        pv = xs;
+      } else {
+        bad = true;
+      }
+    }
+    p[idx] = pv;
   }
+  if (bad) atomicOr(&rflag[b], 1);
 }
 
 // x += alpha p; r_prev = r; r -= alpha q; per-slot <r, r>
@@ -900,6 +1061,9 @@ struct BatchSession {
   DevBuf<double> x, r, rprev, p, q, z, f;   // [N][B] FP64
   DevBuf<double> rho;                       // [B]
   DevBuf<double> coef64;                    // [B][4] FP64 stencil coefficients of A(rho_b)
+  DevBuf<MvDf> dfc;                         // [B] their double-float split (uniform grid)
+  DevBuf<float2> p2;                        // [N][B] p as FP32 pairs (uniform grid)
+  DevBuf<int> rflag;                        // [B] an entry of p outside the pairs' range
   DevBuf<LevCoef> lc;                       // [L][B]
   std::vector<LevCoef> hlc;
   DevBuf<SlotState> state;                  // [B]
@@ -1170,16 +1334,17 @@ void mv_vcycle(BatchSession& W, int lev, const double* b64, cudaStream_t st) {
   }
 }
 
-// q = A(rho_b) p in FP64 with per-slot <p, q>
+// q = A(rho_b) p with per-slot <p, q> (double-float on the uniform grid, else FP64)
 int mv_apply64(BatchSession& W, cudaStream_t st) {
   BatchLevel& L = *W.L[0];
   const int B = W.B;
   if (L.stencil) {
-    const dim3 sg = mv_sgrid(W.S->n - 1, B);
-    k_mv_stencil64<<<sg, 256, 0, st>>>(W.p, W.S->n - 1, W.coef64, B, W.q, W.state, W.partials,
-                                       sg.x * sg.y);
+    const dim3 sg = mv_colgrid(W.S->n - 1, B, 16);
+    const int nb = (int)(sg.x * sg.y * sg.z);
+    k_mv_stencil_df<<<sg, 256, 0, st>>>(W.p2, W.p, W.S->n - 1, W.dfc, W.coef64, B, W.q, W.state,
+                                        W.rflag, W.partials, nb);
     FEM_CHECK_LAUNCH();
-    return (int)(sg.x * sg.y);
+    return nb;
   } else {
     MvEpi<double> e;
     std::memset(&e, 0, sizeof(e));
@@ -1197,10 +1362,10 @@ void batch_iteration(BatchSession& W, cudaStream_t st) {
   const int B = W.B;
   const int64_t N = W.N;
   mv_vcycle(W, 0, W.r, st);
-  k_slot_fin_rz<<<B, 256, 0, st>>>(W.state, W.partials, W.nb_fine, B);
+  k_slot_fin_rz<<<B, 256, 0, st>>>(W.state, W.partials, W.nb_fine, B, W.rflag.p);
   FEM_CHECK_LAUNCH();
   const unsigned ge = persistent_grid(N * B, 256, 8);
-  k_mv_update_p<<<ge, 256, 0, st>>>(N, B, W.z, W.p, W.state);
+  k_mv_update_p<<<ge, 256, 0, st>>>(N, B, W.z, W.p, W.state, W.p2.p, W.rflag.p);
   FEM_CHECK_LAUNCH();
   int nb = mv_apply64(W, st);
   k_slot_fin_pq<<<B, 256, 0, st>>>(W.state, W.partials, nb, B);
@@ -1291,6 +1456,7 @@ int64_t batch_footprint(const System& S, const Hierarchy& H, int slots) {
   int B = 1;
   while (B < slots) B <<= 1;
   int64_t bytes = 7 * S.N * B * 8;  // x r rprev p q z f
+  if (S.stencil) bytes += S.N * B * 8;   // p as FP32 pairs
   for (auto& Lp : H.L) {
     bytes += 5 * Lp->N * B * 4;
     bytes += (Lp->A->nnz) * 8 + Lp->N * 8;
@@ -1365,6 +1531,14 @@ BatchSession* batch_create(System& S, Hierarchy& H, int slots, const pcg_opts& o
   }
   W->rho.alloc(B);
   W->coef64.alloc(4 * B);
+  W->rflag.alloc(B);
+  FEM_CUDA(cudaMemsetAsync(W->rflag, 0, 4 * B, st));
+  if (S.stencil) {
+    W->dfc.alloc(B);
+    FEM_CUDA(cudaMemsetAsync(W->dfc, 0, sizeof(MvDf) * B, st));
+    W->p2.alloc(N * B);
+    FEM_CUDA(cudaMemsetAsync(W->p2, 0, 8 * N * B, st));
+  }
   W->lc.alloc(H.L.size() * B);
   W->hlc.assign(H.L.size() * B, LevCoef{});
   W->state.alloc(B);
@@ -1461,6 +1635,18 @@ void batch_admit_many(BatchSession& W, const double* f, int64_t ld, int fcol0, c
         const double a[4] = {r * S.stK.c0 + S.stM.c0, r * S.stK.ca + S.stM.ca,
                              r * S.stK.cf + S.stM.cf, r * S.stK.cb + S.stM.cb};
         FEM_CUDA(cudaMemcpyAsync(W.coef64.p + 4 * slot[k], a, 32, cudaMemcpyHostToDevice, st));
+        if (l == 0 && W.dfc.p) {
+          Stencil sa;
+          sa.c0 = a[0];
+          sa.ca = a[1];
+          sa.cf = a[2];
+          sa.cb = a[3];
+          const DfOperator D = df_operator(sa);
+          MvDf md{};
+          std::memcpy(md.C, D.C, sizeof(md.C));
+          md.s = D.s;
+          FEM_CUDA(cudaMemcpyAsync(W.dfc.p + slot[k], &md, sizeof(MvDf), cudaMemcpyHostToDevice, st));
+        }
         lmax[k] = (std::fabs(a[0]) + 6 * std::fabs(a[1]) + 6 * std::fabs(a[2]) +
                    2 * std::fabs(a[3])) / a[0];
         LevCoef& c = W.hlc[l * B + slot[k]];
@@ -1523,7 +1709,8 @@ void batch_admit_many(BatchSession& W, const double* f, int64_t ld, int fcol0, c
   const unsigned gn = mv_grid(N, B);
   k_mv_norm2<<<gn, 256, 0, st>>>(N, B, W.f, W.partials, gn);
   FEM_CHECK_LAUNCH();
-  k_slot_admit<<<count, 256, 0, st>>>(W.state, dslot, W.partials, gn, drho, W.o.tol, W.o.max_iter);
+  k_slot_admit<<<count, 256, 0, st>>>(W.state, dslot, W.partials, gn, drho, W.o.tol, W.o.max_iter,
+                                      W.dfc.p != nullptr ? 1 : 0);
   FEM_CHECK_LAUNCH();
   FEM_CUDA(cudaStreamSynchronize(st));
   for (int k = 0; k < count; k++) {

@@ -2,8 +2,10 @@
 
 Each column is an independent solve of (rho_k K + M) u_k = f_k; the batched path uses an
 FP32 V-cycle inside FP64 flexible CG, so a column solved to ||r|| / ||f|| <= 1e-11 agrees
-with the oracle's exact solution to 1e-9 relative.  A slot's result must not depend on
-the other slots in the batch: compared bitwise.
+with the oracle's exact solution to 1e-9 relative.  On the uniform grid CG's operator runs
+in double-float arithmetic for tolerances down to 1e-12 and in FP64 below: a solve to 1e-13
+(FP64 operator) agrees with the oracle to 1e-11.  A slot's result must not depend on the
+other slots in the batch: compared bitwise.
 """
 import numpy as np
 import pytest
@@ -58,6 +60,33 @@ def test_batched_solve_matches_oracle(fa, n, jit, nrhs):
             assert res[k]["status"] == "FEM_OK", res[k]
             assert res[k]["relres"] <= 1e-10
             assert G.rel(Uh[:, k], refs[k]) <= 1e-9, k
+    finally:
+        fa.amg_hier_destroy(h)
+        fa.fem_system_destroy(sys_)
+
+
+@pytest.mark.parametrize("n,nrhs", [(12, 4), (16, 3)])
+def test_batched_solve_fp64_operator_matches_oracle(fa, n, nrhs):
+    sys_, h, xyz = _setup(fa, n)
+    try:
+        N = (n - 1) ** 3
+        rhos = W.log_uniform(nrhs, 1e-6, 1e-2, seed=7)
+        F = torch.empty((N, nrhs), dtype=torch.float64, device="cuda")
+        refs = []
+        for k in range(nrhs):
+            t = W.bump_target(2000 + k)
+            f = torch.empty(N, dtype=torch.float64, device="cuda")
+            fa.fem_assemble_rhs(sys_, t, f)
+            s = core.assemble(n, t)
+            F[:, k] = f
+            refs.append(core.cholesky_solve(s.A(rhos[k]).toarray(), s.f))
+        U = torch.zeros((N, nrhs), dtype=torch.float64, device="cuda")
+        res = fa.pcg_solve(sys_, h, F.contiguous(), U, nrhs=nrhs, rho_k=rhos, tol=1e-13)
+        Uh = U.cpu().numpy()
+        for k in range(nrhs):
+            assert res[k]["status"] == "FEM_OK", res[k]
+            assert res[k]["relres"] <= 1e-12
+            assert G.rel(Uh[:, k], refs[k]) <= 1e-11, k
     finally:
         fa.amg_hier_destroy(h)
         fa.fem_system_destroy(sys_)
