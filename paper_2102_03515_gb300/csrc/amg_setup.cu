@@ -2355,7 +2355,8 @@ __global__ void k_colour_scatter(int64_t N, const int32_t* colour, unsigned long
 // ------------------------------------------------------------------ uniform-grid level
 
 template <uint32_t MASK>
-__global__ void k_st_mis_init(int64_t N, int m, uint32_t strong, uint8_t* state) {
+__global__ void k_st_mis_init(int64_t N, int m, uint32_t strong, uint8_t* state, uint32_t s,
+                              uint64_t* key) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   int i, j, k;
@@ -2364,22 +2365,24 @@ __global__ void k_st_mis_init(int64_t N, int m, uint32_t strong, uint8_t* state)
 #pragma unroll
   for (int d = 0; d < 27; d++)
     if (st_sel<MASK>(strong, d)) any |= st_inb(i, j, k, d, m);
-  state[r] = any ? ST_UND : ST_OUT;
+  const uint8_t st = any ? ST_UND : ST_OUT;
+  state[r] = st;
+  key[r] = ((uint64_t)st << 62) | prio_of(r, s);
 }
 
 template <uint32_t MASK>
-__global__ void k_st_mis_m1(int64_t N, int m, uint32_t strong, const uint8_t* state, uint32_t s,
+// (key: each node's state above its priority, written by the previous round)
+__global__ void k_st_mis_m1(int64_t N, int m, uint32_t strong, const uint64_t* __restrict__ key,
                             uint64_t* m1) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   int i, j, k;
   st_ijk(r, m, i, j, k);
-  uint64_t best = ((uint64_t)state[r] << 62) | prio_of(r, s);
+  uint64_t best = key[r];
 #pragma unroll
   for (int d = 0; d < 27; d++) {
     if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
-    const int64_t q = r + st_off(d, m);
-    const uint64_t kq = ((uint64_t)state[q] << 62) | prio_of(q, s);
+    const uint64_t kq = key[r + st_off(d, m)];
     best = kq > best ? kq : best;
   }
   m1[r] = best;
@@ -2387,7 +2390,7 @@ __global__ void k_st_mis_m1(int64_t N, int m, uint32_t strong, const uint8_t* st
 
 template <uint32_t MASK>
 __global__ void k_st_mis_m2(int64_t N, int m, uint32_t strong, const uint64_t* m1, uint32_t s,
-                            const uint8_t* state_in, uint8_t* state_out,
+                            const uint8_t* state_in, uint8_t* state_out, uint64_t* key_out,
                             unsigned long long* undecided) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
@@ -2402,14 +2405,16 @@ __global__ void k_st_mis_m2(int64_t N, int m, uint32_t strong, const uint64_t* m
     best = kq > best ? kq : best;
   }
   uint8_t ns = st;
+  const uint64_t pr = prio_of(r, s);
   if (st == ST_UND) {
-    const uint64_t key = ((uint64_t)ST_UND << 62) | prio_of(r, s);
+    const uint64_t key = ((uint64_t)ST_UND << 62) | pr;
     if (best == key)
       ns = ST_IN;
     else if ((best >> 62) == ST_IN)
       ns = ST_OUT;
   }
   state_out[r] = ns;
+  key_out[r] = ((uint64_t)ns << 62) | pr;
   // count the nodes still undecided (one atomic per warp)
   const unsigned am = __activemask();
   const unsigned b = __ballot_sync(am, ns == ST_UND);
@@ -2565,11 +2570,15 @@ __global__ void k_st_agg_phase2(int64_t N, int m, uint32_t strong, const uint8_t
   agg[r] = best;
 }
 
-// k_psmooth on the stencil: the row's in-bounds diagonal and strong entries in column order
+// k_psmooth on the stencil: the row's in-bounds diagonal and strong entries in column order.
+// Three modes: the count of each row (Pcol and tcol null); the row into P's CSR4 (Pcol); the
+// row at a stride of 8 entries with its count (tcol: one pass, rows of more than 8 entries
+// raise *ovf)
 template <uint32_t MASK>
 __global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double dinv,
                              double omega, int64_t* cnt, const int32_t* Prp, int32_t* Pcol,
-                             double* Pval) {
+                             double* Pval, int32_t* tcol = nullptr, double* tval = nullptr,
+                             unsigned int* ovf = nullptr) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   int i, j, k;
@@ -2594,6 +2603,23 @@ __global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double
       keys[q] = a;
       vals[q] = v;
     }
+  }
+  if (tcol) {
+    int o = 0, q = 0;
+    while (q < m) {
+      const int key = keys[q];
+      double sum = vals[q++];
+      while (q < m && keys[q] == key) sum = __dadd_rn(sum, vals[q++]);
+      const double t = __dmul_rn(-omega, sum);
+      if (o < 8) {
+        tcol[r * 8 + o] = key;
+        tval[r * 8 + o] = key == ar ? __dadd_rn(1.0, t) : t;
+      }
+      o++;
+    }
+    cnt[r] = o;
+    if (o > 8) atomicOr(ovf, 1u);
+    return;
   }
   if (!Pcol) {
     int dd = 0;
@@ -2686,24 +2712,27 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
   Aggregation R;
   const unsigned g = grid_for(N, 256);
   DevBuf<uint8_t> s0(N, st), s1(N, st);
-  DevBuf<uint64_t> m1(N, st);
+  DevBuf<uint64_t> m1(N, st), k0(N, st), k1(N, st);
   DevBuf<unsigned long long> und(1, st);
-  k_st_mis_init<M><<<g, 256, 0, st>>>(N, S.m, S.strong, s0);
+  k_st_mis_init<M><<<g, 256, 0, st>>>(N, S.m, S.strong, s0, seed_s, k0);
   FEM_CHECK_LAUNCH();
   uint8_t* cur = s0;
   uint8_t* nxt = s1;
+  uint64_t* kcur = k0;
+  uint64_t* knxt = k1;
   bool finished = false;
   unsigned long long hu = (unsigned long long)N;
   int round = 0;
   for (; round < 10000; round += 2) {
     // two rounds per check of the undecided count (a round after the last is a no-op)
     for (int t = 0; t < 2; t++) {
-      k_st_mis_m1<M><<<g, 256, 0, st>>>(N, S.m, S.strong, cur, seed_s, m1);
+      k_st_mis_m1<M><<<g, 256, 0, st>>>(N, S.m, S.strong, kcur, m1);
       FEM_CHECK_LAUNCH();
       if (t == 1) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
-      k_st_mis_m2<M><<<g, 256, 0, st>>>(N, S.m, S.strong, m1, seed_s, cur, nxt, und);
+      k_st_mis_m2<M><<<g, 256, 0, st>>>(N, S.m, S.strong, m1, seed_s, cur, nxt, knxt, und);
       FEM_CHECK_LAUNCH();
       std::swap(cur, nxt);
+      std::swap(kcur, knxt);
     }
     FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
     FEM_CUDA(cudaStreamSynchronize(st));
@@ -2769,11 +2798,45 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
   return R;
 }
 
+// rows at a stride of 8 into CSR4 (padding appended)
+__global__ void k_p_compact8(int64_t N, const int32_t* tcol, const double* tval, const int64_t* cnt,
+                             const int32_t* Prp, int32_t* Pcol, double* Pval) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int c = (int)cnt[r];
+  const int o = Prp[r], o1 = Prp[r + 1];
+  for (int q = 0; q < o1 - o; q++) {
+    Pcol[o + q] = q < c ? tcol[r * 8 + q] : -1;
+    Pval[o + q] = q < c ? tval[r * 8 + q] : 0.0;
+  }
+}
+
 template <uint32_t M>
 void psmooth_stencil_t(int64_t N, const StencilRow& S, const int32_t* agg, double dinv,
                        double omega, Csr4& P, int64_t nagg, cudaStream_t st) {
   const unsigned g = grid_for(N, 256);
   DevBuf<int64_t> pc(N, st);
+  {  // one pass at a stride of 8 entries, then CSR4
+    DevBuf<int32_t> tcol(8 * N, st);
+    DevBuf<double> tval(8 * N, st);
+    DevBuf<unsigned int> ovf(1, st);
+    FEM_CUDA(cudaMemsetAsync(ovf, 0, 4, st));
+    k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, pc, nullptr, nullptr, nullptr, tcol,
+                                       tval, ovf);
+    FEM_CHECK_LAUNCH();
+    unsigned int ho = 0;
+    FEM_CUDA(cudaMemcpyAsync(&ho, ovf, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA(cudaStreamSynchronize(st));
+    if (!ho) {
+      P.nrows = (int32_t)N;
+      P.ncols = (int32_t)nagg;
+      rowptr_from_counts(pc, N, P, st);
+      P.val.alloc(P.nnz);
+      k_p_compact8<<<g, 256, 0, st>>>(N, tcol, tval, pc, P.rowptr, P.col, P.val);
+      FEM_CHECK_LAUNCH();
+      return;
+    }
+  }
   k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, pc, nullptr, nullptr, nullptr);
   FEM_CHECK_LAUNCH();
   P.nrows = (int32_t)N;
