@@ -133,14 +133,20 @@ namespace {
 
 // ------------------------------------------------------------------ small kernels
 
+// the diagonal of each row (0 if none), 8 lanes per row; a row holds its diagonal once
 __global__ void k_diag(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
                        double* d) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8;
+  const int lane = threadIdx.x % 8;
+  const int sh = threadIdx.x & 31 & ~7;
   if (r >= N) return;
-  double x = 0.0;
-  for (int e = rowptr[r]; e < rowptr[r + 1]; e++)
-    if (col[e] == r) x = v[e];
-  d[r] = x;
+  bool found = false;
+  for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += 8)
+    if (col[e] == r) {
+      d[r] = v[e];
+      found = true;
+    }
+  if (!((__ballot_sync(0xFFu << sh, found) >> sh) & 0xFFu) && lane == 0) d[r] = 0.0;
 }
 
 __global__ void k_recip(int64_t N, const double* d, double* o, float* o32) {
@@ -215,32 +221,47 @@ __global__ void k_sqrt(int64_t N, const double* d, double* sq) {
 }
 
 // strong pair: a_ij != 0 and |a_ij| >= (theta sqrt(a_ii)) sqrt(a_jj)
+// Strength of connection, 8 lanes per row (coalesced loads; rows in their stored order):
+// smask[e] for every entry, the row's strong count; then the strong columns in entry order
+constexpr int ST_G = 8;
 __global__ void k_strength(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
                            const double* sq, double theta, uint8_t* smask, int64_t* scount) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / ST_G;
+  const int lane = threadIdx.x % ST_G;
+  const unsigned gm = 0xFFu << (threadIdx.x & 31 & ~(ST_G - 1));
   if (r >= N) return;
-  int64_t c = 0;
+  int c = 0;
   const double tr = theta * sq[r];
-  for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
-    int j = col[e];
+  for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += ST_G) {
+    const int j = col[e];
     uint8_t s = 0;
     if (j >= 0 && j != r) {
-      double a = v[e];
+      const double a = v[e];
       s = (a != 0.0) && (fabs(a) >= tr * sq[j]);
     }
     smask[e] = s;
     c += s;
   }
-  scount[r] = c;
+#pragma unroll
+  for (int o = ST_G / 2; o > 0; o >>= 1) c += __shfl_xor_sync(gm, c, o, ST_G);
+  if (lane == 0) scount[r] = c;
 }
-
 __global__ void k_strength_fill(int64_t N, const int32_t* rowptr, const int32_t* col,
                                 const uint8_t* smask, const int64_t* sptr, int32_t* scol) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / ST_G;
+  const int lane = threadIdx.x % ST_G;
+  const int sh = threadIdx.x & 31 & ~(ST_G - 1);
+  const unsigned gm = 0xFFu << sh;
   if (r >= N) return;
   int64_t p = sptr[r];
-  for (int e = rowptr[r]; e < rowptr[r + 1]; e++)
-    if (smask[e]) scol[p++] = col[e];
+  const int e0 = rowptr[r], e1 = rowptr[r + 1];
+  for (int b = e0; b < e1; b += ST_G) {   // the group's rounds run together (same row)
+    const int e = b + lane;
+    const bool s = e < e1 && smask[e];
+    const unsigned bal = (__ballot_sync(gm, s) >> sh) & 0xFFu;
+    if (s) scol[p + __popc(bal & ((1u << lane) - 1u))] = col[e];
+    p += __popc(bal);
+  }
 }
 
 __global__ void k_mis_init(int64_t N, const int64_t* sptr, uint8_t* state) {
@@ -2096,7 +2117,7 @@ static double rowabs_max(const Csr4& A, const double* val, const uint8_t* mask, 
 
 double gershgorin(const Csr4& A, const double* val, cudaStream_t st) {
   DevBuf<double> d(A.nrows, st);
-  k_diag<<<grid_for(A.nrows, 256), 256, 0, st>>>(A.nrows, A.rowptr, A.col, val, d);
+  k_diag<<<grid_for(A.nrows * 8, 256), 256, 0, st>>>(A.nrows, A.rowptr, A.col, val, d);
   FEM_CHECK_LAUNCH();
   return rowabs_max(A, val, nullptr, d, nullptr, st);
 }
@@ -2138,11 +2159,12 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
   DevBuf<double> sq(N, st);
   k_sqrt<<<g, 256, 0, st>>>(N, d, sq);
   FEM_CHECK_LAUNCH();
-  k_strength<<<g, 256, 0, st>>>(N, A.rowptr, A.col, A.val, sq, theta, R.smask, scount);
+  const unsigned gs = grid_for(N * ST_G, 256);
+  k_strength<<<gs, 256, 0, st>>>(N, A.rowptr, A.col, A.val, sq, theta, R.smask, scount);
   FEM_CHECK_LAUNCH();
   int64_t snnz = exclusive_scan(scount, N, sptr, st);
   DevBuf<int32_t> scol(snnz > 0 ? snnz : 1, st);
-  k_strength_fill<<<g, 256, 0, st>>>(N, A.rowptr, A.col, R.smask, sptr, scol);
+  k_strength_fill<<<gs, 256, 0, st>>>(N, A.rowptr, A.col, R.smask, sptr, scol);
   FEM_CHECK_LAUNCH();
   DevBuf<uint8_t> s0(N, st), s1(N, st);
   DevBuf<uint64_t> m1(N, st);
@@ -2570,15 +2592,11 @@ __global__ void k_st_agg_phase2(int64_t N, int m, uint32_t strong, const uint8_t
   agg[r] = best;
 }
 
-// k_psmooth on the stencil: the row's in-bounds diagonal and strong entries in column order.
-// Three modes: the count of each row (Pcol and tcol null); the row into P's CSR4 (Pcol); the
-// row at a stride of 8 entries with its count (tcol: one pass, rows of more than 8 entries
-// raise *ovf)
+// k_psmooth on the stencil: the row's in-bounds diagonal and strong entries in column order
 template <uint32_t MASK>
 __global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double dinv,
                              double omega, int64_t* cnt, const int32_t* Prp, int32_t* Pcol,
-                             double* Pval, int32_t* tcol = nullptr, double* tval = nullptr,
-                             unsigned int* ovf = nullptr) {
+                             double* Pval) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   int i, j, k;
@@ -2603,23 +2621,6 @@ __global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double
       keys[q] = a;
       vals[q] = v;
     }
-  }
-  if (tcol) {
-    int o = 0, q = 0;
-    while (q < m) {
-      const int key = keys[q];
-      double sum = vals[q++];
-      while (q < m && keys[q] == key) sum = __dadd_rn(sum, vals[q++]);
-      const double t = __dmul_rn(-omega, sum);
-      if (o < 8) {
-        tcol[r * 8 + o] = key;
-        tval[r * 8 + o] = key == ar ? __dadd_rn(1.0, t) : t;
-      }
-      o++;
-    }
-    cnt[r] = o;
-    if (o > 8) atomicOr(ovf, 1u);
-    return;
   }
   if (!Pcol) {
     int dd = 0;
@@ -2798,45 +2799,11 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
   return R;
 }
 
-// rows at a stride of 8 into CSR4 (padding appended)
-__global__ void k_p_compact8(int64_t N, const int32_t* tcol, const double* tval, const int64_t* cnt,
-                             const int32_t* Prp, int32_t* Pcol, double* Pval) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N) return;
-  const int c = (int)cnt[r];
-  const int o = Prp[r], o1 = Prp[r + 1];
-  for (int q = 0; q < o1 - o; q++) {
-    Pcol[o + q] = q < c ? tcol[r * 8 + q] : -1;
-    Pval[o + q] = q < c ? tval[r * 8 + q] : 0.0;
-  }
-}
-
 template <uint32_t M>
 void psmooth_stencil_t(int64_t N, const StencilRow& S, const int32_t* agg, double dinv,
                        double omega, Csr4& P, int64_t nagg, cudaStream_t st) {
   const unsigned g = grid_for(N, 256);
   DevBuf<int64_t> pc(N, st);
-  {  // one pass at a stride of 8 entries, then CSR4
-    DevBuf<int32_t> tcol(8 * N, st);
-    DevBuf<double> tval(8 * N, st);
-    DevBuf<unsigned int> ovf(1, st);
-    FEM_CUDA(cudaMemsetAsync(ovf, 0, 4, st));
-    k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, pc, nullptr, nullptr, nullptr, tcol,
-                                       tval, ovf);
-    FEM_CHECK_LAUNCH();
-    unsigned int ho = 0;
-    FEM_CUDA(cudaMemcpyAsync(&ho, ovf, 4, cudaMemcpyDeviceToHost, st));
-    FEM_CUDA(cudaStreamSynchronize(st));
-    if (!ho) {
-      P.nrows = (int32_t)N;
-      P.ncols = (int32_t)nagg;
-      rowptr_from_counts(pc, N, P, st);
-      P.val.alloc(P.nnz);
-      k_p_compact8<<<g, 256, 0, st>>>(N, tcol, tval, pc, P.rowptr, P.col, P.val);
-      FEM_CHECK_LAUNCH();
-      return;
-    }
-  }
   k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, pc, nullptr, nullptr, nullptr);
   FEM_CHECK_LAUNCH();
   P.nrows = (int32_t)N;
@@ -3024,7 +2991,7 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     if (st0)
       k_fill<<<g, 256, 0, st>>>(N, SR.a[ST_DIAG], d);
     else
-      k_diag<<<g, 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, d);
+      k_diag<<<grid_for(N * 8, 256), 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, d);
     FEM_CHECK_LAUNCH();
     Lv.dinv.alloc(N);
     if (lowp) Lv.dinv32.alloc(N);
