@@ -35,7 +35,7 @@ CPU_SAMPLE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
 # the current kernels, by kernel: None until a capture of the current code exists
 TRAFFIC = {"galerkin_l0_n256": (11.852 + 5.813) * 1e9,   # the product's 22 launches
            "cg_operator_n256": (265.38 + 104.65) * 1e6,
-           "vcycle_fp32_n256": (4634.1 + 438.2) * 1e6}
+           "vcycle_fp32_n256": (4161.8 + 437.6) * 1e6}
 
 
 def reduce_over_ranks(x: float, op: str, world: int, device) -> float:
@@ -81,8 +81,10 @@ def vcycle_bytes(info: dict, flexible_r2: bool = False) -> float:
     d, b -> x) + 12 (residual) + 16 (post start: b, x -> r, d) + 28 (last step: d, r, x,
     FP64 z and <z, r>; + 8 with <z, r_prev>) bytes per row; a CSR level 64 bytes of vectors
     per row (8 + 12 + 12 + 16 + 16) and four passes over its matrix (8 bytes per stored
-    entry + 4 per row); R_l and P_l one pass each plus their vectors; the coarsest dense
-    inverse N^2 x 8 bytes."""
+    entry + 4 per row); R_l and P_l one pass each plus their vectors, except the matrix-free
+    finest level's prolongation: the stencil of the smoothed prolongator on the aggregates'
+    values (aggregate ids read twice, t written and read, x read and written: 24 bytes per
+    row, the coarse vector once); the coarsest dense inverse N^2 x 8 bytes."""
     L = info["levels"]
     rows, nnz, pnnz, rnnz = info["rows"], info["nnz"], info["pnnz"], info["rnnz"]
     total = 0.0
@@ -98,7 +100,10 @@ def vcycle_bytes(info: dict, flexible_r2: bool = False) -> float:
             total += 64.0 * N + 4 * (8.0 * nnz[lev] + 4.0 * N)
         Nc = rows[lev + 1]
         total += 8.0 * rnnz[lev] + 4.0 * Nc + 4.0 * N + 4.0 * Nc      # restriction
-        total += 8.0 * pnnz[lev] + 4.0 * N + 8.0 * N + 4.0 * Nc       # prolongation
+        if lev == 0 and info["finest_stencil"]:
+            total += 24.0 * N + 4.0 * Nc                              # stencil prolongation
+        else:
+            total += 8.0 * pnnz[lev] + 4.0 * N + 8.0 * N + 4.0 * Nc   # prolongation
     return total
 
 

@@ -3073,6 +3073,15 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     const double omega = rb ? 0.0 : 4.0 / (3.0 * lamF);
     if (st0) {
       psmooth_stencil(N, SR, Lv.agg, 1.0 / SR.a[ST_DIAG], omega, Lv.P, ag.nagg, st);
+      // the same prolongator as a stencil on the aggregates' values, for the V-cycle: centre
+      // 1 - w a_ii / a_ii (the identity and the diagonal term), strong direction d -w a_d / a_ii
+      const double dinv = 1.0 / SR.a[ST_DIAG];
+      Lv.pst = true;
+      Lv.pst_strong = SR.strong & ~(1u << ST_DIAG);
+      for (int d = 0; d < 27; d++) Lv.pst_c[d] = 0.0f;
+      Lv.pst_c[ST_DIAG] = (float)(1.0 - omega * (SR.a[ST_DIAG] * dinv));
+      for (int d = 0; d < 27; d++)
+        if ((Lv.pst_strong >> d) & 1u) Lv.pst_c[d] = (float)(-omega * (SR.a[d] * dinv));
       done_p = true;
     }
     DevBuf<double> dinvA;

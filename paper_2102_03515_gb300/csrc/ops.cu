@@ -1063,6 +1063,107 @@ void csr_spmv<float>(const Csr4& M, int prec, const float* x, float* y, bool acc
     launch_csr<float, float>(M, M.val32.p, x, e, nullptr, st, done);
 }
 
+// ------------------------------------------------------------------ stencil prolongation
+
+namespace {
+
+// t = P_t x_c on the uniform finest level in the ghost layout: each node takes its
+// aggregate's value (isolated nodes 0); the ghost faces of t stay zero.  Four nodes per
+// thread and round, their loads in flight together.
+constexpr int PST_U = 4;
+__global__ void k_inject_ghost(int m, const int32_t* __restrict__ agg, const float* __restrict__ xc,
+                               float* __restrict__ t, const int* done) {
+  if (done && *done) return;
+  const int64_t N = (int64_t)m * m * m;
+  const int64_t G = m + 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < N; r0 += PST_U * stride) {
+    int a[PST_U];
+#pragma unroll
+    for (int u = 0; u < PST_U; u++) {
+      const int64_t r = r0 + u * stride;
+      a[u] = r < N ? __ldg(agg + r) : -1;
+    }
+    float v[PST_U];
+#pragma unroll
+    for (int u = 0; u < PST_U; u++) v[u] = a[u] >= 0 ? __ldg(xc + a[u]) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < PST_U; u++) {
+      const int64_t r = r0 + u * stride;
+      if (r >= N) break;
+      const uint32_t r32 = (uint32_t)r, um = (uint32_t)m, q1 = r32 / um;
+      const int i = (int)(r32 - q1 * um), j = (int)(q1 % um), k = (int)(q1 / um);
+      t[(i + 1) + G * ((j + 1) + G * (k + 1))] = v[u];
+    }
+  }
+}
+
+struct PstCoef {
+  float c[27];
+};
+
+// x += [agg >= 0] (c[13] t + sum over the strong directions d of c[d] t(. + d)): the smoothed
+// prolongator's row of every node, from its own and its neighbours' aggregates (a direction
+// leaving the grid reads a zero ghost face).  Four nodes per thread and round.
+template <uint32_t MASK>   // the strong directions (0: the run-time mask `strong`)
+__global__ void k_prolong_st(int m, uint32_t strong, PstCoef pc, const int32_t* __restrict__ agg,
+                             const float* __restrict__ t, float* __restrict__ x, const int* done) {
+  if (done && *done) return;
+  const int64_t N = (int64_t)m * m * m;
+  const int64_t G = m + 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < N; r0 += PST_U * stride) {
+    int64_t g[PST_U];
+    bool live[PST_U];
+    float s[PST_U], xo[PST_U];
+#pragma unroll
+    for (int u = 0; u < PST_U; u++) {
+      const int64_t r = r0 + u * stride;
+      live[u] = r < N && __ldg(agg + r) >= 0;
+      const int64_t rr = r < N ? r : 0;
+      const uint32_t r32 = (uint32_t)rr, um = (uint32_t)m, q1 = r32 / um;
+      const int i = (int)(r32 - q1 * um), j = (int)(q1 % um), k = (int)(q1 / um);
+      g[u] = (i + 1) + G * ((j + 1) + G * (k + 1));
+    }
+#pragma unroll
+    for (int u = 0; u < PST_U; u++) {
+      s[u] = 0.0f;
+      xo[u] = 0.0f;
+      if (!live[u]) continue;
+      xo[u] = x[g[u]];
+      s[u] = pc.c[13] * __ldg(t + g[u]);
+#pragma unroll
+      for (int d = 0; d < 27; d++) {
+        if (d == 13 || !(((MASK ? MASK : strong) >> d) & 1u)) continue;
+        const int64_t off = (int64_t)(d % 3 - 1) + G * ((d / 3 % 3 - 1) + G * (d / 9 - 1));
+        s[u] += pc.c[d] * __ldg(t + g[u] + off);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PST_U; u++)
+      if (live[u]) x[g[u]] = xo[u] + s[u];
+  }
+}
+
+}  // namespace
+
+void prolong_stencil(const Level& L, const float* xc, float* x, cudaStream_t st) {
+  const int m = L.st.m;
+  const unsigned g = persistent_grid((int64_t)m * m * m, 256, 8);
+  const int bt = 256;
+  k_inject_ghost<<<g, bt, 0, st>>>(m, L.agg, xc, L.tf, L.done);
+  FEM_CHECK_LAUNCH();
+  PstCoef pc;
+  for (int d = 0; d < 27; d++) pc.c[d] = L.pst_c[d];
+  // the axis directions (strong on the Kuhn stencil's mass-dominated regime) compiled in
+  constexpr uint32_t kAxis = (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
+  if (L.pst_strong == kAxis)
+    k_prolong_st<kAxis><<<g, bt, 0, st>>>(m, L.pst_strong, pc, L.agg, L.tf, x, L.done);
+  else
+    k_prolong_st<0u><<<g, bt, 0, st>>>(m, L.pst_strong, pc, L.agg, L.tf, x, L.done);
+  FEM_CHECK_LAUNCH();
+}
+
 // Pre-smoothing from the zero initial guess.
 template <typename T>
 void smooth_pre_zero(const Level& Lv, int prec, const amg_opts& o, const ChebCoef& cc,

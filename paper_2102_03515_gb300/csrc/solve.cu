@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "dfloat.cuh"
 #include "solver.cuh"
@@ -178,7 +179,14 @@ void vc(Hierarchy& H, int lev, const T* b, T* x, const double* b64, const DotOut
   Level& C = *H.L[lev + 1];
   csr_spmv<T>(L.R, prec, rres, Bufs<T>::b(C), false, st, L.done);
   vc<T>(H, lev + 1, Bufs<T>::b(C), Bufs<T>::x(C), nullptr, nullptr, st);
-  csr_spmv<T>(L.P, prec, Bufs<T>::x(C), x, true, st, L.done, L.ghost ? L.st.m : 0);
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.ghost && L.pst && L.tf.p)   // the stencil prolongator (uniform finest level)
+      prolong_stencil(L, Bufs<T>::x(C), x, st);
+    else
+      csr_spmv<T>(L.P, prec, Bufs<T>::x(C), x, true, st, L.done, L.ghost ? L.st.m : 0);
+  } else {
+    csr_spmv<T>(L.P, prec, Bufs<T>::x(C), x, true, st, L.done, L.ghost ? L.st.m : 0);
+  }
   smooth_post<T>(L, prec, o, cc, b, x, r, d0, d1, st, dot);
 }
 
@@ -202,8 +210,9 @@ void alloc_level_vectors(Hierarchy& H) {
       L.d1f.alloc(NV);
       if (L.ghost) {
         L.rdf.alloc(N);
-        for (DevBuf<float>* v : {&L.xf, &L.bf, &L.rf, &L.d0f, &L.d1f})
-          FEM_CUDA(cudaMemset(v->p, 0, sizeof(float) * NV));
+        if (L.pst) L.tf.alloc(NV);
+        for (DevBuf<float>* v : {&L.xf, &L.bf, &L.rf, &L.d0f, &L.d1f, &L.tf})
+          if (v->p) FEM_CUDA(cudaMemset(v->p, 0, sizeof(float) * NV));
       }
     } else {
       L.x.alloc(N);

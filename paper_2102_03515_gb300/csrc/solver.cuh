@@ -81,6 +81,13 @@ struct Level {
   // layout with zero ghost faces ((m+2)^3 entries); rdf is its dense residual (restriction)
   bool ghost = false;
   DevBuf<float> rdf;
+  // uniform finest level with the stencil's smoothed prolongator: P = (I - w D^-1 A_F) P_t
+  // applied as x += [agg >= 0] (pc[13] t + sum over the strong directions d of pc[d] t(. + d)),
+  // t = P_t x_c (tf, ghost layout); pst set by the set-up, tf by the level vectors
+  bool pst = false;
+  uint32_t pst_strong = 0;
+  float pst_c[27];
+  DevBuf<float> tf;
 };
 
 struct Hierarchy {
@@ -173,6 +180,8 @@ void reset_ghost_vectors(Hierarchy& H, cudaStream_t st);
 template <typename T>
 void csr_spmv(const Csr4& M, int prec, const T* x, T* y, bool accumulate, cudaStream_t st,
               const int* done = nullptr, int ghost_m = 0);
+// x += P x_c on a level with the stencil prolongator (pst, ghost layout; FP32 vectors)
+void prolong_stencil(const Level& L, const float* xc, float* x, cudaStream_t st);
 
 // One Gauss-Seidel sweep over the colour classes (increasing order when forward):
 // x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii.
