@@ -36,8 +36,9 @@ def test_vcycle_byte_model_sums_its_terms():
     info = {"levels": 3, "rows": [1000, 100, 10], "nnz": [16000, 2000, 100],
             "pnnz": [4000, 400, 0], "rnnz": [3000, 300, 0], "finest_stencil": True}
     b = bench.vcycle_bytes(info)
-    fine = 84.0 * 1000 + (8 * 3000 + 4 * 100 + 4 * 1000 + 4 * 100) \
-        + (8 * 4000 + 4 * 1000 + 8 * 1000 + 4 * 100)
+    # the matrix-free finest level prolongs by the smoothed prolongator's stencil: 24 bytes
+    # per fine row and the coarse vector
+    fine = 84.0 * 1000 + (8 * 3000 + 4 * 100 + 4 * 1000 + 4 * 100) + (24 * 1000 + 4 * 100)
     mid = 64.0 * 100 + 4 * (8 * 2000 + 4 * 100) + (8 * 300 + 4 * 10 + 4 * 100 + 4 * 10) \
         + (8 * 400 + 4 * 100 + 8 * 100 + 4 * 10)
     coarsest = 8.0 * 10 * 10 + 12.0 * 10
