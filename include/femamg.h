@@ -445,7 +445,9 @@ typedef struct {
 typedef struct {
   int32_t iterations;
   int32_t status;           /* fem_status of the solve                                 */
-  double relres;            /* ||f - A u|| / ||f||, recomputed in FP64 at the end      */
+  double relres;            /* ||f - A u|| / ||f||, recomputed at the end: in FP64, or
+                               for tol >= 1e-10 on the uniform grid with the
+                               double-float operator (rows within 2^-44 sum|a_ij u_j|) */
   double prec_relres;       /* sqrt(<r,z>/<r0,z0>) at the last iteration               */
   double solve_ms;          /* device time of the iterations (CUDA events)             */
 } pcg_result;

@@ -639,8 +639,16 @@ void pcg_single(System& S, Hierarchy* H, const double* f, double* u, const pcg_o
     // that chunk stands
     if (status == FEM_ECANCELLED && hs.done) status = FEM_OK;
     iters += hs.iter;
-    // true residual
-    op_apply_d(L0, u, W.q, nullptr, nullptr, st);
+    // true residual: with the double-float operator when the tolerance leaves room for its
+    // 2^-44 bound (u split into pairs; an entry out of their range takes the FP64 rows), in
+    // FP64 otherwise
+    if (dfop && o.tol >= 1e-10) {
+      FEM_CUDA(cudaMemsetAsync(W.rflag, 0, sizeof(int), st));
+      df_split_vec(N, u, nullptr, W.p2, W.rflag, st);
+      op_apply_df(L0, dfo, W.p2, u, W.q, nullptr, st, nullptr, W.rflag);
+    } else {
+      op_apply_d(L0, u, W.q, nullptr, nullptr, st);
+    }
     k_sub<<<gv, 256, 0, st>>>(N, f, W.q);
     FEM_CHECK_LAUNCH();
     k_dot_self<<<gv, 256, 0, st>>>(N, W.q, f, W.partials);
