@@ -2411,14 +2411,14 @@ __global__ void k_st_mis_m1(int64_t N, int m, uint32_t strong, const uint64_t* _
 }
 
 template <uint32_t MASK>
+// (in place: a node reads and writes only its own state and key; a decided node keeps both)
 __global__ void k_st_mis_m2(int64_t N, int m, uint32_t strong, const uint64_t* m1, uint32_t s,
-                            const uint8_t* state_in, uint8_t* state_out, uint64_t* key_out,
-                            unsigned long long* undecided) {
+                            uint8_t* state, uint64_t* key, unsigned long long* undecided) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
+  if (state[r] != ST_UND) return;
   int i, j, k;
   st_ijk(r, m, i, j, k);
-  const uint8_t st = state_in[r];
   uint64_t best = m1[r];
 #pragma unroll
   for (int d = 0; d < 27; d++) {
@@ -2426,21 +2426,20 @@ __global__ void k_st_mis_m2(int64_t N, int m, uint32_t strong, const uint64_t* m
     const uint64_t kq = m1[r + st_off(d, m)];
     best = kq > best ? kq : best;
   }
-  uint8_t ns = st;
+  uint8_t ns = ST_UND;
   const uint64_t pr = prio_of(r, s);
-  if (st == ST_UND) {
-    const uint64_t key = ((uint64_t)ST_UND << 62) | pr;
-    if (best == key)
-      ns = ST_IN;
-    else if ((best >> 62) == ST_IN)
-      ns = ST_OUT;
+  if (best == (((uint64_t)ST_UND << 62) | pr))
+    ns = ST_IN;
+  else if ((best >> 62) == ST_IN)
+    ns = ST_OUT;
+  if (ns != ST_UND) {
+    state[r] = ns;
+    key[r] = ((uint64_t)ns << 62) | pr;
   }
-  state_out[r] = ns;
-  key_out[r] = ((uint64_t)ns << 62) | pr;
-  // count the nodes still undecided (one atomic per warp)
+  // count the nodes still undecided (one atomic per warp of the undecided threads)
   const unsigned am = __activemask();
-  const unsigned b = __ballot_sync(am, ns == ST_UND);
-  if ((threadIdx.x & 31) == __ffs(am) - 1 && b) atomicAdd(undecided, (unsigned long long)__popc(b));
+  const unsigned bl = __ballot_sync(am, ns == ST_UND);
+  if ((threadIdx.x & 31) == __ffs(am) - 1 && bl) atomicAdd(undecided, (unsigned long long)__popc(bl));
 }
 
 // List rounds (once few nodes are undecided): m1 over the nodes within distance 1 of an
@@ -2712,15 +2711,13 @@ template <uint32_t M>
 Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s, cudaStream_t st) {
   Aggregation R;
   const unsigned g = grid_for(N, 256);
-  DevBuf<uint8_t> s0(N, st), s1(N, st);
-  DevBuf<uint64_t> m1(N, st), k0(N, st), k1(N, st);
+  DevBuf<uint8_t> s0(N, st);
+  DevBuf<uint64_t> m1(N, st), k0(N, st);
   DevBuf<unsigned long long> und(1, st);
   k_st_mis_init<M><<<g, 256, 0, st>>>(N, S.m, S.strong, s0, seed_s, k0);
   FEM_CHECK_LAUNCH();
   uint8_t* cur = s0;
-  uint8_t* nxt = s1;
   uint64_t* kcur = k0;
-  uint64_t* knxt = k1;
   bool finished = false;
   unsigned long long hu = (unsigned long long)N;
   int round = 0;
@@ -2730,10 +2727,8 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
       k_st_mis_m1<M><<<g, 256, 0, st>>>(N, S.m, S.strong, kcur, m1);
       FEM_CHECK_LAUNCH();
       if (t == 1) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
-      k_st_mis_m2<M><<<g, 256, 0, st>>>(N, S.m, S.strong, m1, seed_s, cur, nxt, knxt, und);
+      k_st_mis_m2<M><<<g, 256, 0, st>>>(N, S.m, S.strong, m1, seed_s, cur, kcur, und);
       FEM_CHECK_LAUNCH();
-      std::swap(cur, nxt);
-      std::swap(kcur, knxt);
     }
     FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
     FEM_CUDA(cudaStreamSynchronize(st));
