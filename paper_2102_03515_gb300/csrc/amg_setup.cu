@@ -30,53 +30,127 @@ namespace {
 
 // ------------------------------------------------------------------ scan
 
-// Exclusive prefix sum of int64 counts (three passes: block sums, scan of block sums,
-// add block offsets).  out[n] receives the total.
-constexpr int SCAN_B = 1024;
+// Exclusive prefix sums over tiles of SCAN_TILE elements in three passes: the tiles' sums,
+// one block's scan of those sums, then every tile's scan from its offset.  Warp w of a
+// tile owns SCAN_V consecutive runs of 32 elements (coalesced loads, one value per lane
+// and run kept in registers between the tile's sum and its scan).  Integer sums: the
+// result does not depend on the order.  A loader maps an index to the summed value.
+constexpr int SCAN_T = 256, SCAN_V = 16, SCAN_TILE = SCAN_T * SCAN_V;
 
-__global__ void k_scan_blocks(const int64_t* in, int64_t n, int64_t* out, int64_t* bsum) {
-  __shared__ int64_t sh[SCAN_B];
-  int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
-  int64_t v = i < n ? in[i] : 0;
-  sh[threadIdx.x] = v;
+struct LoadI64 {
+  const int64_t* p;
+  __device__ int64_t operator()(int64_t i) const { return p[i]; }
+};
+struct LoadPad4 {  // counts rounded up to multiples of 4 (CSR4 rows)
+  const int64_t* p;
+  __device__ int64_t operator()(int64_t i) const { return (p[i] + 3) & ~(int64_t)3; }
+};
+struct LoadEqU8 {  // 1 where a byte equals v
+  const uint8_t* p;
+  uint8_t v;
+  __device__ int64_t operator()(int64_t i) const { return p[i] == v ? 1 : 0; }
+};
+
+__device__ __forceinline__ int64_t warp_sum_i64(int64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ int64_t warp_incl_scan_i64(int64_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+template <class L>
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(L ld, int64_t n, int64_t* tsum) {
+  __shared__ int64_t sh[SCAN_T / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)w * (32 * SCAN_V) + lane;
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_V; k++) {
+    const int64_t i = base + 32 * k;
+    if (i < n) s += ld(i);
+  }
+  s = warp_sum_i64(s);
+  if (lane == 0) sh[w] = s;
   __syncthreads();
-  for (int o = 1; o < SCAN_B; o <<= 1) {
-    int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-    __syncthreads();
-    sh[threadIdx.x] += t;
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_T / 32; q++) t += sh[q];
+    tsum[blockIdx.x] = t;
   }
-  if (i < n) out[i] = sh[threadIdx.x] - v;
-  if (threadIdx.x == SCAN_B - 1) bsum[blockIdx.x] = sh[SCAN_B - 1];
 }
 
-__global__ void k_scan_single(int64_t* bsum, int64_t nb) {
-  // one block; sequential chunks
-  __shared__ int64_t sh[SCAN_B];
+// One block of 1024 threads: exclusive scan of the nb tile sums in place, total in t[nb].
+__global__ void __launch_bounds__(1024) k_scan_tsums(int64_t* t, int64_t nb) {
+  __shared__ int64_t ws[32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t carry = 0;
-  for (int64_t base = 0; base < nb; base += SCAN_B) {
-    int64_t i = base + threadIdx.x;
-    int64_t v = i < nb ? bsum[i] : 0;
-    sh[threadIdx.x] = v;
+  for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
+    const int64_t i = b0 + threadIdx.x;
+    const int64_t v = i < nb ? t[i] : 0;
+    const int64_t x = warp_incl_scan_i64(v);
+    if (lane == 31) ws[w] = x;
     __syncthreads();
-    for (int o = 1; o < SCAN_B; o <<= 1) {
-      int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-      __syncthreads();
-      sh[threadIdx.x] += t;
-      __syncthreads();
-    }
-    if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+    if (w == 0) ws[lane] = warp_incl_scan_i64(ws[lane]);
     __syncthreads();
-    carry += sh[SCAN_B - 1];
+    if (i < nb) t[i] = carry + (w ? ws[w - 1] : 0) + x - v;
+    carry += ws[31];
     __syncthreads();
   }
-  if (threadIdx.x == 0) bsum[nb] = carry;
+  if (threadIdx.x == 0) t[nb] = carry;
 }
 
-__global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* bsum) {
-  int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
-  if (i < n) out[i] += bsum[blockIdx.x];
-  if (i == n - 1) out[n] = bsum[gridDim.x];
+template <class L, class O>
+__global__ void __launch_bounds__(SCAN_T) k_scan_out(L ld, int64_t n, const int64_t* tsum, O* out) {
+  __shared__ int64_t sh[SCAN_T / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)w * (32 * SCAN_V) + lane;
+  int64_t v[SCAN_V];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_V; k++) {
+    const int64_t i = base + 32 * k;
+    v[k] = i < n ? ld(i) : 0;
+    s += v[k];
+  }
+  s = warp_sum_i64(s);
+  if (lane == 0) sh[w] = s;
+  __syncthreads();
+  int64_t carry = tsum[blockIdx.x];
+  for (int q = 0; q < w; q++) carry += sh[q];
+#pragma unroll
+  for (int k = 0; k < SCAN_V; k++) {
+    const int64_t x = warp_incl_scan_i64(v[k]);
+    const int64_t i = base + 32 * k;
+    if (i < n) out[i] = (O)(carry + x - v[k]);
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = (O)tsum[gridDim.x];
+}
+
+// out[0..n]: exclusive scan of ld(0..n-1), the total in out[n]; returns the total (n > 0)
+template <class L, class O>
+int64_t scan_impl(L ld, int64_t n, O* out, cudaStream_t st) {
+  const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  DevBuf<int64_t> tsum(nb + 1, st);
+  k_scan_tiles<L><<<(unsigned)nb, SCAN_T, 0, st>>>(ld, n, tsum);
+  FEM_CHECK_LAUNCH();
+  k_scan_tsums<<<1, 1024, 0, st>>>(tsum, nb);
+  FEM_CHECK_LAUNCH();
+  k_scan_out<L, O><<<(unsigned)nb, SCAN_T, 0, st>>>(ld, n, tsum, out);
+  FEM_CHECK_LAUNCH();
+  int64_t total = 0;
+  FEM_CUDA(cudaMemcpyAsync(&total, tsum.p + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  FEM_CUDA(cudaStreamSynchronize(st));
+  return total;
 }
 
 }  // namespace
@@ -87,44 +161,27 @@ int64_t exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStream_t 
     FEM_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
     return 0;
   }
-  int64_t nb = (n + SCAN_B - 1) / SCAN_B;
-  DevBuf<int64_t> bsum(nb + 1, st);
-  k_scan_blocks<<<(unsigned)nb, SCAN_B, 0, st>>>(in, n, out, bsum);
-  FEM_CHECK_LAUNCH();
-  k_scan_single<<<1, SCAN_B, 0, st>>>(bsum, nb);
-  FEM_CHECK_LAUNCH();
-  k_scan_add<<<(unsigned)nb, SCAN_B, 0, st>>>(out, n, bsum);
-  FEM_CHECK_LAUNCH();
-  int64_t total = 0;
-  FEM_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  FEM_CUDA(cudaStreamSynchronize(st));
-  return total;
+  return scan_impl(LoadI64{in}, n, out, st);
 }
 
-namespace {
-
-__global__ void k_to_rowptr(const int64_t* in, int64_t n, int32_t* out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i <= n) out[i] = (int32_t)in[i];
+// out[0..n]: exclusive scan of [s[i] == v]; returns the number of such i.
+static int64_t count_scan_eq(const uint8_t* s, uint8_t v, int64_t n, int64_t* out, cudaStream_t st) {
+  if (n == 0) {
+    FEM_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+    return 0;
+  }
+  return scan_impl(LoadEqU8{s, v}, n, out, st);
 }
-
-// CSR4 row pointer from per-row real counts (each padded to a multiple of 4).
-__global__ void k_pad4(const int64_t* cnt, int64_t n, int64_t* padded) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) padded[i] = (cnt[i] + 3) & ~(int64_t)3;
-}
-
-}  // namespace
 
 void rowptr_from_counts(const int64_t* cnt, int64_t n, Csr4& C, cudaStream_t st) {
-  DevBuf<int64_t> padded(n, st), scan(n + 1, st);
-  k_pad4<<<grid_for(n, 256), 256, 0, st>>>(cnt, n, padded);
-  FEM_CHECK_LAUNCH();
-  int64_t total = exclusive_scan(padded, n, scan, st);
-  FEM_REQUIRE(total < ((int64_t)1 << 31), FEM_EUNSUPPORTED, "matrix with more than 2^31 entries");
   C.rowptr.alloc(n + 1);
-  k_to_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(scan, n, C.rowptr);
-  FEM_CHECK_LAUNCH();
+  int64_t total = 0;
+  if (n == 0)
+    FEM_CUDA(cudaMemsetAsync(C.rowptr, 0, sizeof(int32_t), st));
+  else
+    total = scan_impl(LoadPad4{cnt}, n, C.rowptr.p, st);
+  // (row pointers past 2^31 were truncated on the device; the matrix is refused here)
+  FEM_REQUIRE(total < ((int64_t)1 << 31), FEM_EUNSUPPORTED, "matrix with more than 2^31 entries");
   C.nnz = total;
   C.col.alloc(total);
 }
@@ -134,19 +191,27 @@ namespace {
 // ------------------------------------------------------------------ small kernels
 
 // the diagonal of each row (0 if none), 8 lanes per row; a row holds its diagonal once
+// a_ii (0 if the row has no diagonal entry): four lanes per row, one int4 of columns each
+// per step; at most one lane finds the column.
+constexpr int DG_G = 4;
 __global__ void k_diag(int64_t N, const int32_t* rowptr, const int32_t* col, const double* v,
                        double* d) {
-  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8;
-  const int lane = threadIdx.x % 8;
-  const int sh = threadIdx.x & 31 & ~7;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / DG_G;
+  const int sub = threadIdx.x % DG_G;
+  const int sh = threadIdx.x & 31 & ~(DG_G - 1);
   if (r >= N) return;
-  bool found = false;
-  for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += 8)
-    if (col[e] == r) {
-      d[r] = v[e];
-      found = true;
-    }
-  if (!((__ballot_sync(0xFFu << sh, found) >> sh) & 0xFFu) && lane == 0) d[r] = 0.0;
+  int pos = -1;
+  const int e1 = rowptr[r + 1];
+  for (int e = rowptr[r] + 4 * sub; e < e1; e += 4 * DG_G) {
+    const int4 c = *reinterpret_cast<const int4*>(col + e);
+    if (c.x == r) pos = e;
+    if (c.y == r) pos = e + 1;
+    if (c.z == r) pos = e + 2;
+    if (c.w == r) pos = e + 3;
+  }
+  const unsigned any = (__ballot_sync(0xFu << sh, pos >= 0) >> sh) & 0xFu;
+  if (pos >= 0) d[r] = v[pos];
+  if (!any && sub == 0) d[r] = 0.0;
 }
 
 __global__ void k_recip(int64_t N, const double* d, double* o, float* o32) {
@@ -195,6 +260,14 @@ template <>
 __global__ void k_convert<double, __nv_bfloat16>(int64_t n, const double* in, __nv_bfloat16* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = __float2bfloat16_rn((float)in[i]);
+}
+// four values per thread (CSR4 value arrays: n a multiple of 4, 32-byte aligned)
+__global__ void k_convert4_f32(int64_t n4, const double* in, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const double2 a = reinterpret_cast<const double2*>(in)[2 * i];
+  const double2 b = reinterpret_cast<const double2*>(in)[2 * i + 1];
+  reinterpret_cast<float4*>(out)[i] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
 
 // ------------------------------------------------------------------ strength + MIS-2
@@ -305,11 +378,6 @@ __global__ void k_mis_m2(int64_t N, const int64_t* sptr, const int32_t* scol, co
       *undecided = 1ull;  // any undecided node (a plain store: only "nonzero" is read)
   }
   state_out[r] = ns;
-}
-
-__global__ void k_root_flags(int64_t N, const uint8_t* state, int64_t* flag) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < N) flag[r] = state[r] == ST_IN;
 }
 
 __global__ void k_agg_phase1(int64_t N, const int64_t* sptr, const int32_t* scol,
@@ -2117,7 +2185,7 @@ static double rowabs_max(const Csr4& A, const double* val, const uint8_t* mask, 
 
 double gershgorin(const Csr4& A, const double* val, cudaStream_t st) {
   DevBuf<double> d(A.nrows, st);
-  k_diag<<<grid_for(A.nrows * 8, 256), 256, 0, st>>>(A.nrows, A.rowptr, A.col, val, d);
+  k_diag<<<grid_for((int64_t)A.nrows * DG_G, 256), 256, 0, st>>>(A.nrows, A.rowptr, A.col, val, d);
   FEM_CHECK_LAUNCH();
   return rowabs_max(A, val, nullptr, d, nullptr, st);
 }
@@ -2190,10 +2258,8 @@ Aggregation aggregate(const Csr4& A, const double* d, double theta, uint32_t see
     }
   }
   FEM_REQUIRE(finished, FEM_EDEVCHECK, "aggregation: MIS-2 did not terminate");
-  DevBuf<int64_t> flag(N, st), rootid(N + 1, st);
-  k_root_flags<<<g, 256, 0, st>>>(N, cur, flag);
-  FEM_CHECK_LAUNCH();
-  R.nagg = exclusive_scan(flag, N, rootid, st);
+  DevBuf<int64_t> rootid(N + 1, st);
+  R.nagg = count_scan_eq(cur, ST_IN, N, rootid, st);
   R.agg.alloc(N);
   DevBuf<uint8_t> p1(N, st);
   DevBuf<unsigned long long> err(1, st);
@@ -2412,34 +2478,37 @@ __global__ void k_st_mis_m1(int64_t N, int m, uint32_t strong, const uint64_t* _
 
 template <uint32_t MASK>
 // (in place: a node reads and writes only its own state and key; a decided node keeps both)
+// With a counter, the nodes still undecided are added to it, one atomic per block (one
+// address for the whole grid: per-warp atomics were most of the round's time).
 __global__ void k_st_mis_m2(int64_t N, int m, uint32_t strong, const uint64_t* m1, uint32_t s,
                             uint8_t* state, uint64_t* key, unsigned long long* undecided) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N) return;
-  if (state[r] != ST_UND) return;
-  int i, j, k;
-  st_ijk(r, m, i, j, k);
-  uint64_t best = m1[r];
+  bool und = false;
+  if (r < N && state[r] == ST_UND) {
+    int i, j, k;
+    st_ijk(r, m, i, j, k);
+    uint64_t best = m1[r];
 #pragma unroll
-  for (int d = 0; d < 27; d++) {
-    if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
-    const uint64_t kq = m1[r + st_off(d, m)];
-    best = kq > best ? kq : best;
+    for (int d = 0; d < 27; d++) {
+      if (!st_sel<MASK>(strong, d) || !st_inb(i, j, k, d, m)) continue;
+      const uint64_t kq = m1[r + st_off(d, m)];
+      best = kq > best ? kq : best;
+    }
+    uint8_t ns = ST_UND;
+    const uint64_t pr = prio_of(r, s);
+    if (best == (((uint64_t)ST_UND << 62) | pr))
+      ns = ST_IN;
+    else if ((best >> 62) == ST_IN)
+      ns = ST_OUT;
+    if (ns != ST_UND) {
+      state[r] = ns;
+      key[r] = ((uint64_t)ns << 62) | pr;
+    }
+    und = ns == ST_UND;
   }
-  uint8_t ns = ST_UND;
-  const uint64_t pr = prio_of(r, s);
-  if (best == (((uint64_t)ST_UND << 62) | pr))
-    ns = ST_IN;
-  else if ((best >> 62) == ST_IN)
-    ns = ST_OUT;
-  if (ns != ST_UND) {
-    state[r] = ns;
-    key[r] = ((uint64_t)ns << 62) | pr;
-  }
-  // count the nodes still undecided (one atomic per warp of the undecided threads)
-  const unsigned am = __activemask();
-  const unsigned bl = __ballot_sync(am, ns == ST_UND);
-  if ((threadIdx.x & 31) == __ffs(am) - 1 && bl) atomicAdd(undecided, (unsigned long long)__popc(bl));
+  if (!undecided) return;  // (the same for the whole grid)
+  const int c = __syncthreads_count(und);
+  if (threadIdx.x == 0 && c) atomicAdd(undecided, (unsigned long long)c);
 }
 
 // List rounds (once few nodes are undecided): m1 over the nodes within distance 1 of an
@@ -2498,21 +2567,16 @@ __global__ void k_st_list_apply(int64_t nu, const int64_t* __restrict__ ulist,
   if (t < nu) state[ulist[t]] = newst[t];
 }
 
-__global__ void k_st_und_flag(int64_t N, const uint8_t* state, int64_t* flag) {
+// the indices flagged in an exclusive scan of 0/1 flags, in order
+__global__ void k_list_from_scan(int64_t N, const int64_t* scan, int64_t* list) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < N) flag[r] = state[r] == ST_UND ? 1 : 0;
-}
-
-__global__ void k_list_from_flags(int64_t N, const int64_t* flag, const int64_t* scan,
-                                  int64_t* list) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < N && flag[r]) list[scan[r]] = r;
+  if (r < N && scan[r + 1] != scan[r]) list[scan[r]] = r;
 }
 
 // flag every node within distance 1 (strong directions) of a listed node
 template <uint32_t MASK>
 __global__ void k_st_mark_ring(int64_t nu, const int64_t* __restrict__ ulist, int m,
-                               uint32_t strong, int64_t* flag) {
+                               uint32_t strong, uint8_t* flag) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nu) return;
   const int64_t r = ulist[t];
@@ -2591,63 +2655,139 @@ __global__ void k_st_agg_phase2(int64_t N, int m, uint32_t strong, const uint8_t
   agg[r] = best;
 }
 
-// k_psmooth on the stencil: the row's in-bounds diagonal and strong entries in column order
+// k_psmooth on the stencil: the row's in-bounds diagonal and strong entries in column order.
+// With the strong set known at compile time the candidates (diagonal and strong directions,
+// in d order) stay in registers: a key's entry is its first candidate, its position the
+// number of smaller distinct keys, its sum taken over the candidates with that key in d
+// order -- the order of the insertion sort of the run-time path, so both give the same
+// bits.
+__host__ __device__ constexpr int sel_count(uint32_t s) {
+  int c = 0;
+  for (int d = 0; d < 27; d++) c += (int)((s >> d) & 1u);
+  return c;
+}
+// the direction of the q-th set bit of s
+__host__ __device__ constexpr int sel_nth(uint32_t s, int q) {
+  for (int d = 0; d < 27; d++)
+    if ((s >> d) & 1u) {
+      if (q == 0) return d;
+      q--;
+    }
+  return 0;
+}
 template <uint32_t MASK>
 __global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double dinv,
                              double omega, int64_t* cnt, const int32_t* Prp, int32_t* Pcol,
                              double* Pval) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N) return;
-  int i, j, k;
-  st_ijk(r, S.m, i, j, k);
-  const int32_t ar = agg[r];
-  int keys[27];
-  double vals[27];
-  int m = 0;
-  if (ar >= 0) {
+  if constexpr (MASK != 0u) {
+    constexpr uint32_t SEL = MASK | (1u << ST_DIAG);
+    constexpr int K = sel_count(SEL);
+    if (r >= N) return;
+    int i, j, k;
+    st_ijk(r, S.m, i, j, k);
+    const int32_t ar = agg[r];
+    int key[K];
+    double val[K];
 #pragma unroll
-    for (int d = 0; d < 27; d++) {
-      if ((d != ST_DIAG && !st_sel<MASK>(S.strong, d)) || !st_inb(i, j, k, d, S.m)) continue;
-      const int a = agg[r + st_off(d, S.m)];
-      if (a < 0) continue;
-      const double v = __dmul_rn(S.a[d], dinv);
-      int q = m++;
-      while (q > 0 && keys[q - 1] > a) {
-        keys[q] = keys[q - 1];
-        vals[q] = vals[q - 1];
-        q--;
+    for (int q = 0; q < K; q++) {
+      const int d = sel_nth(SEL, q);
+      key[q] = -1;
+      val[q] = 0.0;
+      if (ar >= 0 && st_inb(i, j, k, d, S.m)) {
+        key[q] = agg[r + st_off(d, S.m)];  // (-1: the neighbour is not aggregated)
+        val[q] = __dmul_rn(S.a[d], dinv);
       }
-      keys[q] = a;
-      vals[q] = v;
     }
-  }
-  if (!Pcol) {
-    int dd = 0;
-    for (int q = 0; q < m; q++) dd += (q == 0 || keys[q] != keys[q - 1]);
-    cnt[r] = dd;
-    return;
-  }
-  int64_t o = Prp[r];
-  const int64_t o1 = Prp[r + 1];
-  int q = 0;
-  while (q < m) {
-    const int key = keys[q];
-    double sum = vals[q++];
-    while (q < m && keys[q] == key) sum = __dadd_rn(sum, vals[q++]);
-    const double t = __dmul_rn(-omega, sum);
-    Pcol[o] = key;
-    Pval[o] = key == ar ? __dadd_rn(1.0, t) : t;
-    o++;
-  }
-  for (; o < o1; o++) {
-    Pcol[o] = -1;
-    Pval[o] = 0.0;
+    bool first[K];
+    int nd = 0;
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+      bool f = key[q] >= 0;
+#pragma unroll
+      for (int e = 0; e < q; e++)
+        if (key[e] == key[q]) f = false;
+      first[q] = f;
+      nd += f;
+    }
+    if (!Pcol) {
+      cnt[r] = nd;
+      return;
+    }
+    const int64_t o = Prp[r], o1 = Prp[r + 1];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+      if (!first[q]) continue;
+      int rank = 0;
+#pragma unroll
+      for (int e = 0; e < K; e++)
+        if (first[e] && key[e] < key[q]) rank++;
+      double sum = val[q];
+#pragma unroll
+      for (int e = q + 1; e < K; e++)
+        if (key[e] == key[q]) sum = __dadd_rn(sum, val[e]);
+      const double t = __dmul_rn(-omega, sum);
+      Pcol[o + rank] = key[q];
+      Pval[o + rank] = key[q] == ar ? __dadd_rn(1.0, t) : t;
+    }
+    for (int64_t p = o + nd; p < o1; p++) {
+      Pcol[p] = -1;
+      Pval[p] = 0.0;
+    }
+  } else {
+    if (r >= N) return;
+    int i, j, k;
+    st_ijk(r, S.m, i, j, k);
+    const int32_t ar = agg[r];
+    int keys[27];
+    double vals[27];
+    int m = 0;
+    if (ar >= 0) {
+      for (int d = 0; d < 27; d++) {
+        if ((d != ST_DIAG && !st_sel<MASK>(S.strong, d)) || !st_inb(i, j, k, d, S.m)) continue;
+        const int a = agg[r + st_off(d, S.m)];
+        if (a < 0) continue;
+        const double v = __dmul_rn(S.a[d], dinv);
+        int q = m++;
+        while (q > 0 && keys[q - 1] > a) {
+          keys[q] = keys[q - 1];
+          vals[q] = vals[q - 1];
+          q--;
+        }
+        keys[q] = a;
+        vals[q] = v;
+      }
+    }
+    if (!Pcol) {
+      int dd = 0;
+      for (int q = 0; q < m; q++) dd += (q == 0 || keys[q] != keys[q - 1]);
+      cnt[r] = dd;
+      return;
+    }
+    int64_t o = Prp[r];
+    const int64_t o1 = Prp[r + 1];
+    int q = 0;
+    while (q < m) {
+      const int key = keys[q];
+      double sum = vals[q++];
+      while (q < m && keys[q] == key) sum = __dadd_rn(sum, vals[q++]);
+      const double t = __dmul_rn(-omega, sum);
+      Pcol[o] = key;
+      Pval[o] = key == ar ? __dadd_rn(1.0, t) : t;
+      o++;
+    }
+    for (; o < o1; o++) {
+      Pcol[o] = -1;
+      Pval[o] = 0.0;
+    }
   }
 }
 
-__global__ void k_fill(int64_t n, double v, double* out) {
+__global__ void k_fill(int64_t n, double v, double* out, float* out32 = nullptr) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = v;
+  if (i >= n) return;
+  out[i] = v;
+  if (out32) out32[i] = (float)v;
 }
 
 // The interior row of A (centre of the grid) with its strong pairs, by the same test as
@@ -2710,7 +2850,7 @@ constexpr uint32_t kStBody = (1u << 0) | (1u << 26);
 template <uint32_t M>
 Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s, cudaStream_t st) {
   Aggregation R;
-  const unsigned g = grid_for(N, 256);
+  const unsigned g = grid_for(N, 256), g2 = grid_for(N, 512);
   DevBuf<uint8_t> s0(N, st);
   DevBuf<uint64_t> m1(N, st), k0(N, st);
   DevBuf<unsigned long long> und(1, st);
@@ -2727,7 +2867,8 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
       k_st_mis_m1<M><<<g, 256, 0, st>>>(N, S.m, S.strong, kcur, m1);
       FEM_CHECK_LAUNCH();
       if (t == 1) FEM_CUDA(cudaMemsetAsync(und, 0, 8, st));
-      k_st_mis_m2<M><<<g, 256, 0, st>>>(N, S.m, S.strong, m1, seed_s, cur, kcur, und);
+      k_st_mis_m2<M><<<g2, 512, 0, st>>>(N, S.m, S.strong, m1, seed_s, cur, kcur,
+                                          t == 1 ? und.p : nullptr);
       FEM_CHECK_LAUNCH();
     }
     FEM_CUDA(cudaMemcpyAsync(&hu, und, 8, cudaMemcpyDeviceToHost, st));
@@ -2740,19 +2881,18 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
   }
   if (!finished && round < 10000) {
     // the same rounds on the undecided nodes only (m1 on the nodes around them)
-    DevBuf<int64_t> flag(N, st), scan(N + 1, st);
-    k_st_und_flag<<<g, 256, 0, st>>>(N, cur, flag);
-    FEM_CHECK_LAUNCH();
-    const int64_t nu = exclusive_scan(flag, N, scan, st);
+    DevBuf<uint8_t> flag(N, st);
+    DevBuf<int64_t> scan(N + 1, st);
+    const int64_t nu = count_scan_eq(cur, ST_UND, N, scan, st);
     DevBuf<int64_t> ul(nu, st);
-    k_list_from_flags<<<g, 256, 0, st>>>(N, flag, scan, ul);
+    k_list_from_scan<<<g, 256, 0, st>>>(N, scan, ul);
     FEM_CHECK_LAUNCH();
-    FEM_CUDA(cudaMemsetAsync(flag, 0, 8 * N, st));
+    FEM_CUDA(cudaMemsetAsync(flag, 0, N, st));
     k_st_mark_ring<M><<<grid_for(nu, 256), 256, 0, st>>>(nu, ul, S.m, S.strong, flag);
     FEM_CHECK_LAUNCH();
-    const int64_t nvr = exclusive_scan(flag, N, scan, st);
+    const int64_t nvr = count_scan_eq(flag, 1, N, scan, st);
     DevBuf<int64_t> vl(nvr, st);
-    k_list_from_flags<<<g, 256, 0, st>>>(N, flag, scan, vl);
+    k_list_from_scan<<<g, 256, 0, st>>>(N, scan, vl);
     FEM_CHECK_LAUNCH();
     DevBuf<uint8_t> newst(nu, st);
     const unsigned gu = grid_for(nu, 256), gv = grid_for(nvr, 256);
@@ -2775,10 +2915,8 @@ Aggregation aggregate_stencil_t(int64_t N, const StencilRow& S, uint32_t seed_s,
     }
   }
   FEM_REQUIRE(finished, FEM_EDEVCHECK, "aggregation: MIS-2 did not terminate");
-  DevBuf<int64_t> flag(N, st), rootid(N + 1, st);
-  k_root_flags<<<g, 256, 0, st>>>(N, cur, flag);
-  FEM_CHECK_LAUNCH();
-  R.nagg = exclusive_scan(flag, N, rootid, st);
+  DevBuf<int64_t> rootid(N + 1, st);
+  R.nagg = count_scan_eq(cur, ST_IN, N, rootid, st);
   R.agg.alloc(N);
   DevBuf<uint8_t> p1(N, st);
   DevBuf<unsigned long long> err(1, st);
@@ -2866,11 +3004,8 @@ int64_t red_black_split(const Csr4& A, uint32_t s, int natural, DevBuf<uint8_t>&
   FEM_REQUIRE(finished, FEM_EDEVCHECK, "red-black coarsening did not terminate");
   state.alloc(N);
   FEM_CUDA(cudaMemcpyAsync(state, cur, N, cudaMemcpyDeviceToDevice, st));
-  DevBuf<int64_t> flag(N, st);
-  k_root_flags<<<g, 256, 0, st>>>(N, state, flag);
-  FEM_CHECK_LAUNCH();
   cid.alloc(N + 1);
-  return exclusive_scan(flag, N, cid, st);
+  return count_scan_eq(state, ST_IN, N, cid, st);
 }
 
 // Greedy colouring of a level's matrix graph and the node lists per colour.
@@ -2925,7 +3060,9 @@ void colour_level(Level& Lv, const Csr4& A, uint32_t s, cudaStream_t st) {
 void make_lowp(Csr4& A, int prec, cudaStream_t st) {
   if (prec == AMG_PREC_FP32 || prec == AMG_PREC_BF16) {
     A.val32.alloc(A.nnz);
-    if (A.nnz)
+    if (A.nnz % 4 == 0)
+      k_convert4_f32<<<grid_for(A.nnz / 4, 256), 256, 0, st>>>(A.nnz / 4, A.val, A.val32);
+    else
       k_convert<double, float><<<grid_for(A.nnz, 256), 256, 0, st>>>(A.nnz, A.val, A.val32);
     FEM_CHECK_LAUNCH();
   }
@@ -2982,12 +3119,14 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
     const uint32_t seed_s = (uint32_t)(0x9E3779B9u * (uint32_t)(o.seed + lev + 1));
     const bool st0 = lev == 0 && Lv.stencil && o.smoother == AMG_SMOOTHER_CHEBYSHEV && !rb &&
                      N > o.coarse_max && stencil_row(*Acur, Lv.st.m, o.theta, SR, st);
-    DevBuf<double> d(N, st);
-    if (st0)
-      k_fill<<<g, 256, 0, st>>>(N, SR.a[ST_DIAG], d);
-    else
-      k_diag<<<grid_for(N * 8, 256), 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, d);
-    FEM_CHECK_LAUNCH();
+    // (the stencil level's diagonal is one number: its reciprocal is formed on the host,
+    // correctly rounded like the device's division)
+    DevBuf<double> d;
+    if (!st0) {
+      d.alloc_async(N, st);
+      k_diag<<<grid_for(N * DG_G, 256), 256, 0, st>>>(N, Acur->rowptr, Acur->col, Acur->val, d);
+      FEM_CHECK_LAUNCH();
+    }
     Lv.dinv.alloc(N);
     if (lowp) Lv.dinv32.alloc(N);
     Lv.scalar_sinv = Lv.stencil && o.smoother == AMG_SMOOTHER_CHEBYSHEV;
@@ -2996,10 +3135,12 @@ void build_hierarchy(Hierarchy& H, System& S, const amg_opts& o, cudaStream_t st
       rowabs_max(*Acur, Acur->val, nullptr, d, l1, st);
       k_recip<<<g, 256, 0, st>>>(N, l1, Lv.dinv, lowp ? Lv.dinv32.p : nullptr);
       Lv.lmax = 1.0;
+    } else if (st0) {
+      k_fill<<<g, 256, 0, st>>>(N, 1.0 / SR.a[ST_DIAG], Lv.dinv, lowp ? Lv.dinv32.p : nullptr);
+      Lv.lmax = stencil_rowabs(SR, false);
     } else {
       k_recip<<<g, 256, 0, st>>>(N, d, Lv.dinv, lowp ? Lv.dinv32.p : nullptr);
-      Lv.lmax = st0 ? stencil_rowabs(SR, false)
-                    : rowabs_max(*Acur, Acur->val, nullptr, d, nullptr, st);
+      Lv.lmax = rowabs_max(*Acur, Acur->val, nullptr, d, nullptr, st);
     }
     FEM_CHECK_LAUNCH();
     if (lowp) {
