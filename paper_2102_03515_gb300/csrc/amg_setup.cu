@@ -2660,7 +2660,8 @@ __global__ void k_st_agg_phase2(int64_t N, int m, uint32_t strong, const uint8_t
 // in d order) stay in registers: a key's entry is its first candidate, its position the
 // number of smaller distinct keys, its sum taken over the candidates with that key in d
 // order -- the order of the insertion sort of the run-time path, so both give the same
-// bits.
+// bits.  V.a[d] = a_d / a_ii as the host rounds the product a_d * (1 / a_ii), the same
+// product the run-time path forms per row (GB300's FP64 pipe is the scarce one).
 __host__ __device__ constexpr int sel_count(uint32_t s) {
   int c = 0;
   for (int d = 0; d < 27; d++) c += (int)((s >> d) & 1u);
@@ -2676,9 +2677,9 @@ __host__ __device__ constexpr int sel_nth(uint32_t s, int q) {
   return 0;
 }
 template <uint32_t MASK>
-__global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double dinv,
-                             double omega, int64_t* cnt, const int32_t* Prp, int32_t* Pcol,
-                             double* Pval) {
+__global__ void k_st_psmooth(int64_t N, StencilRow S, StencilRow V, const int32_t* agg,
+                             double dinv, double omega, int64_t* cnt, const int32_t* Prp,
+                             int32_t* Pcol, double* Pval) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (MASK != 0u) {
     constexpr uint32_t SEL = MASK | (1u << ST_DIAG);
@@ -2696,7 +2697,7 @@ __global__ void k_st_psmooth(int64_t N, StencilRow S, const int32_t* agg, double
       val[q] = 0.0;
       if (ar >= 0 && st_inb(i, j, k, d, S.m)) {
         key[q] = agg[r + st_off(d, S.m)];  // (-1: the neighbour is not aggregated)
-        val[q] = __dmul_rn(S.a[d], dinv);
+        val[q] = V.a[d];
       }
     }
     bool first[K];
@@ -2936,14 +2937,17 @@ template <uint32_t M>
 void psmooth_stencil_t(int64_t N, const StencilRow& S, const int32_t* agg, double dinv,
                        double omega, Csr4& P, int64_t nagg, cudaStream_t st) {
   const unsigned g = grid_for(N, 256);
+  StencilRow V = S;
+  for (int d = 0; d < 27; d++) V.a[d] = S.a[d] * dinv;
   DevBuf<int64_t> pc(N, st);
-  k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, pc, nullptr, nullptr, nullptr);
+  k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, V, agg, dinv, omega, pc, nullptr, nullptr, nullptr);
   FEM_CHECK_LAUNCH();
   P.nrows = (int32_t)N;
   P.ncols = (int32_t)nagg;
   rowptr_from_counts(pc, N, P, st);
   P.val.alloc(P.nnz);
-  k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, agg, dinv, omega, nullptr, P.rowptr, P.col, P.val);
+  k_st_psmooth<M><<<g, 256, 0, st>>>(N, S, V, agg, dinv, omega, nullptr, P.rowptr, P.col,
+                                     P.val);
   FEM_CHECK_LAUNCH();
 }
 
