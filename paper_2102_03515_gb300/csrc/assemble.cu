@@ -142,40 +142,10 @@ __global__ void k_uniform_row(int n, double rho, double* out /* 45: K, M, A slot
   }
 }
 
-// CSR4 rows (16 slots) with values from per-type stencil coefficients; one thread per
-// stored entry (coalesced stores): slot p of row r holds the p-th existing neighbour.
-__global__ void k_csr_uniform(int m, Stencil sa, Stencil sk, Stencil sm, int32_t* rowptr,
-                              int32_t* col, double* aval, double* kval, double* mval) {
-  const int64_t N = (int64_t)m * m * m;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < N + 1) rowptr[e] = (int32_t)(16 * e);
-  if (e >= 16 * N) return;
-  // 32-bit index decode (16 N < 2^31 is checked at assembly)
-  const uint32_t r32 = (uint32_t)(e >> 4), um = (uint32_t)m;
-  const uint32_t q1 = r32 / um;
-  const int i = (int)(r32 - q1 * um), j = (int)(q1 % um), k = (int)(q1 / um);
-  const int p = (int)(e & 15);
-  int cnt = 0, cl = -1, t = 0;
-  for (int s = 0; s < 15; s++) {
-    const int ii = i + kSlotOff[s][0], jj = j + kSlotOff[s][1], kk = k + kSlotOff[s][2];
-    if (ii < 0 || jj < 0 || kk < 0 || ii >= m || jj >= m || kk >= m) continue;
-    if (cnt == p) {
-      cl = (int)(ii + (int64_t)m * (jj + (int64_t)m * kk));
-      t = kSlotType[s];
-    }
-    cnt++;
-  }
-  const double at[4] = {sa.c0, sa.ca, sa.cf, sa.cb}, kt[4] = {sk.c0, sk.ca, sk.cf, sk.cb},
-               mt[4] = {sm.c0, sm.ca, sm.cf, sm.cb};
-  col[e] = cl;
-  aval[e] = cl >= 0 ? at[t] : 0.0;
-  if (kval) kval[e] = cl >= 0 ? kt[t] : 0.0;
-  if (mval) mval[e] = cl >= 0 ? mt[t] : 0.0;
-}
-
-// The same rows, one thread per row with 16-byte stores: interior rows (all 15 neighbours on
-// the grid) take their columns from fixed offsets, rows next to the boundary list their
-// existing neighbours in slot order and pad.
+// CSR4 rows (16 slots) with values from per-type stencil coefficients, one thread per row
+// with 16-byte stores: slot p of row r holds the p-th existing neighbour.  Interior rows
+// (all 15 neighbours on the grid) take their columns from fixed offsets, rows next to the
+// boundary list their existing neighbours in slot order and pad.
 __global__ void k_csr_uniform_rows(int m, Stencil sa, Stencil sk, Stencil sm, int32_t* rowptr,
                                    int32_t* col, double* aval, double* kval, double* mval) {
   const int64_t N = (int64_t)m * m * m;
