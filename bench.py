@@ -33,7 +33,9 @@ ORACLE_N = 48          # reference-arm step: the same workload on a 48^3 mesh
 CPU_SAMPLE_N = 64        # cpu_baseline sample: the same workload on a 64^3 mesh
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from ncu captures of
 # the current kernels, by kernel: None until a capture of the current code exists
-TRAFFIC = {"galerkin_l0_n256": (11.852 + 5.813) * 1e9,   # the product's 22 launches
+# (the product's launches as captured; its small row-pointer scans changed since: 0.94 GB of
+# these bytes came from them and all sixteen small launches)
+TRAFFIC = {"galerkin_l0_n256": (11.852 + 5.813) * 1e9,
            "cg_operator_n256": (265.38 + 104.65) * 1e6,
            "vcycle_fp32_n256": (4161.8 + 437.6) * 1e6}
 
