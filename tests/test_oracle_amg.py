@@ -125,6 +125,64 @@ def test_prolongator_and_galerkin_operator_formulas():
     assert np.linalg.eigvalsh(Ac).min() > 0
 
 
+@pytest.mark.parametrize("n,rho", [(12, 1.0 / 144), (11, 1.0), (10, 1e-6)])
+def test_smoothed_prolongator_is_a_stencil_on_the_aggregates(n, rho):
+    """On the uniform Kuhn grid every row of A holds the interior row's values at the same
+    offsets and every diagonal is the same, so P x_c = [agg >= 0] ((1 - omega) t +
+    sum_strong (-omega a_d / a_ii) t(. + d)) with t = P_t x_c: the smoothed prolongator
+    written as a stencil on the aggregates' values (the form the uniform finest level
+    prolongs with).  Checked against the oracle's sparse P for three strong sets."""
+    s, A = _hier_problem(n, rho)
+    m = n - 1
+    agg, nagg, smask = amg.aggregate(A, 0.05, 0)
+    P, omega = amg.smoothed_prolongator(A, smask, agg, nagg)
+    # the interior row at the grid's centre: value and strength per offset
+    c = (m // 2) * (1 + m + m * m)
+    lo, hi = A.indptr[c], A.indptr[c + 1]
+    aii = A[c, c]
+    coef = {}
+    for e in range(lo, hi):
+        j = int(A.indices[e])
+        dz, rem = divmod(j - c + (1 + m + m * m), m * m)
+        dy, dx = divmod(rem, m)
+        off = (dx - 1, dy - 1, dz - 1)
+        assert j == c + off[0] + m * off[1] + m * m * off[2]
+        if smask[e]:
+            coef[off] = -omega * (A.data[e] / aii)
+    assert 0 < len(coef) <= 14
+    # what the stencil form needs: one diagonal value (the assembly sums each row's element
+    # contributions in its own order, so equal to rounding), and every row's strong entries
+    # are exactly the interior row's strong offsets that stay on the grid, with its values
+    np.testing.assert_allclose(A.diagonal(), aii, rtol=1e-14)
+    r = amg.rows_of(A)
+    on = {}
+    for e in range(A.nnz):
+        i, j = int(r[e]), int(A.indices[e])
+        if i == j:
+            continue
+        di, dj = np.unravel_index(i, (m, m, m)), np.unravel_index(j, (m, m, m))
+        off = (int(dj[2] - di[2]), int(dj[1] - di[1]), int(dj[0] - di[0]))
+        assert bool(smask[e]) == (off in coef), (i, j)
+        if smask[e]:
+            assert -omega * (A.data[e] / aii) == pytest.approx(coef[off], rel=1e-14)
+        on[(i, off)] = True
+    for i in range(m ** 3):   # every strong offset that stays on the grid is an entry
+        k, j, ii = np.unravel_index(i, (m, m, m))
+        for (dx, dy, dz) in coef:
+            if 0 <= ii + dx < m and 0 <= j + dy < m and 0 <= k + dz < m:
+                assert (i, (dx, dy, dz)) in on
+    rng = np.random.default_rng(n)
+    xc = rng.standard_normal(nagg)
+    t = np.where(agg >= 0, xc[np.maximum(agg, 0)], 0.0).reshape(m, m, m)   # [k][j][i]
+    tp = np.pad(t, 1)
+    y = (1.0 - omega) * t
+    for (dx, dy, dz), cd in coef.items():
+        y = y + cd * tp[1 + dz:1 + dz + m, 1 + dy:1 + dy + m, 1 + dx:1 + dx + m]
+    y = np.where(agg.reshape(m, m, m) >= 0, y, 0.0).ravel()
+    ref = P @ xc
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+
+
 def test_chebyshev_error_polynomial_closed_form():
     # D = I, A = diag(lam): after k steps from x0 = 0 for A x = A 1, the error is
     # -T_k((theta - lam)/delta) / T_k(theta/delta) (Chebyshev acceleration)
