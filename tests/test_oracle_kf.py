@@ -130,12 +130,12 @@ def test_natural_order_coarsens_to_every_other_grid_point(n):
 def test_natural_order_iterations_follow_table4():
     # with the index order and symmetric Gauss-Seidel, AMG-PCG (stopped like the paper, on the
     # preconditioned residual 1e-8) needs the iterations of the paper's Table 4 within one,
-    # for h = 1/8, 1/16 at rho = 1 and 1e-2 (the hashed order needs more at rho = 1)
+    # for h = 1/8, 1/16, 1/32 at rho = 1 and 1e-2 (the hashed order needs more at rho = 1)
     from tests.conftest import golden
     table = {row[0]: row[1:] for row in golden("table4_amg_iterations.txt")}
     o = dict(coarsening="kf", smoother="sgs", order="natural")
     for rho in (1.0, 1e-2):
-        for col, n in enumerate((8, 16)):
+        for col, n in enumerate((8, 16, 32)):
             s = core.assemble(n, W.sine_target())
             A = s.A(rho).tocsr()
             H = amg.build_hierarchy(A, o)
